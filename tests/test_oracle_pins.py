@@ -1,0 +1,357 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each test pins a part of ``oracle/lo_oracle.py`` to LAPACK, to 50-digit
+arithmetic, to a closed form, to an invariant the paper states, or to the
+values printed in the paper's stability table, so that a dropped term, a wrong
+sign or index, or a transposed operand anywhere in the oracle fails one of them.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lo_oracle as O
+from paper_2204_13393_gb300 import inputs as I
+
+ALGS = ["hh", "mgs2", "pip", "pip2"]
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _orthonormal(n, k, seed):
+    return I.haar(n, k, seed) if k else np.zeros((n, 0))
+
+
+def _lapack_qr(A):
+    q, r = np.linalg.qr(A)
+    d = np.where(np.diag(r) >= 0, 1.0, -1.0)
+    return q * d[None, :], r * d[:, None]
+
+
+# ---------------------------------------------------------------- primitives
+
+def test_cholesky_matches_lapack():
+    """cholesky_upper vs LAPACK potrf (numpy.linalg.cholesky gives L = N^T)."""
+    A = I.gaussian(50, 7, 1)
+    M = A.T @ A
+    N = O.cholesky_upper(M)
+    L = np.linalg.cholesky(M)
+    np.testing.assert_allclose(N, L.T, rtol=0, atol=1e-13 * np.abs(L).max())
+    assert np.all(np.tril(N, -1) == 0)
+
+
+def test_cholesky_breakdown():
+    M = np.array([[1.0, 2.0], [2.0, 1.0]])  # indefinite
+    with pytest.raises(O.Breakdown):
+        O.cholesky_upper(M)
+    with pytest.raises(O.Breakdown):
+        O.cholesky_upper(np.array([[np.nan]]))
+
+
+def test_solve_upper_right():
+    """X N^{-1} against a direct check X == Y @ N."""
+    Y = I.gaussian(40, 5, 2)
+    N = np.triu(I.gaussian(5, 5, 3)) + 4 * np.eye(5)
+    X = O.solve_upper_right(Y, N)
+    np.testing.assert_allclose(X @ N, Y, atol=1e-13)
+
+
+@pytest.mark.parametrize("shape", [(200, 7), (33, 33), (64, 1), (1000, 16)])
+def test_householder_matches_lapack(shape):
+    """Textbook HH QR vs LAPACK geqrf/orgqr after sign normalization."""
+    A = I.gaussian(*shape, seed=11 + shape[1])
+    Q, R = O.sign_normalize(*O.householder_qr(A))
+    Ql, Rl = _lapack_qr(A)
+    np.testing.assert_allclose(Q, Ql, atol=1e-13)
+    np.testing.assert_allclose(R, Rl, atol=1e-12 * np.abs(Rl).max())
+    assert np.all(np.diag(R) >= 0)
+    assert np.all(np.tril(R, -1) == 0)
+
+
+def test_householder_sign_choice_on_zero_pivot():
+    """sgn(0) = +1: a column whose pivot entry is exactly 0 still gives a
+    reflection with R_jj = -lambda before normalization (Alg. 6 sign rule)."""
+    A = np.array([[0.0, 1.0], [3.0, 0.0], [4.0, 2.0]])
+    Q, R = O.householder_qr(A)
+    assert R[0, 0] == pytest.approx(-5.0)
+    np.testing.assert_allclose(Q @ R, A, atol=1e-14)
+
+
+# ------------------------------------------------------- 50-digit brute force
+
+def _mp_pqr(Q, X, dps=50):
+    """PQR by classical Gram-Schmidt in 50-digit arithmetic (mpmath)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = dps
+    n, k = Q.shape
+    s = X.shape[1]
+    cols = [[mp.mpf(float(Q[r, c])) for r in range(n)] for c in range(k)]
+    # Q as given is orthonormal only to double precision: orthonormalize it
+    # exactly first (this changes it by ~1e-16, below the tolerances used).
+    basis = []
+    for v in cols:
+        w = list(v)
+        for b in basis:
+            c = mp.fsum(bi * wi for bi, wi in zip(b, w))
+            w = [wi - c * bi for wi, bi in zip(w, b)]
+        nr = mp.sqrt(mp.fsum(wi * wi for wi in w))
+        basis.append([wi / nr for wi in w])
+    P = np.zeros((k, s))
+    N = np.zeros((s, s))
+    U = np.zeros((n, s))
+    newb = []
+    for j in range(s):
+        w = [mp.mpf(float(X[r, j])) for r in range(n)]
+        for c, b in enumerate(basis):
+            co = mp.fsum(bi * wi for bi, wi in zip(b, w))
+            P[c, j] = float(co)
+            w = [wi - co * bi for wi, bi in zip(w, b)]
+        for c, b in enumerate(newb):
+            co = mp.fsum(bi * wi for bi, wi in zip(b, w))
+            N[c, j] = float(co)
+            w = [wi - co * bi for wi, bi in zip(w, b)]
+        nr = mp.sqrt(mp.fsum(wi * wi for wi in w))
+        N[j, j] = float(nr)
+        b = [wi / nr for wi in w]
+        newb.append(b)
+        U[:, j] = [float(x) for x in b]
+    return U, P, N
+
+
+@pytest.mark.parametrize("n,k,s", [(9, 3, 2), (12, 0, 3), (7, 4, 3), (10, 6, 1)])
+@pytest.mark.parametrize("alg", ALGS)
+def test_pqr_vs_50_digit_gram_schmidt(n, k, s, alg):
+    Q = _orthonormal(n, k, 100 + n)
+    X = I.gaussian(n, s, 200 + n + s)
+    Ue, Pe, Ne = _mp_pqr(Q, X)
+    U, P, N = O.pqr(Q, X, alg)
+    np.testing.assert_allclose(U, Ue, atol=1e-14)
+    np.testing.assert_allclose(P, Pe, atol=1e-14)
+    np.testing.assert_allclose(N, Ne, atol=1e-14)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_tree_vs_50_digit(alg):
+    """TreeTSPQR with 3 local blocks (10, 10, 13 rows) on a tiny two-step
+    problem equals the 50-digit PQR of the explicit basis."""
+    n, s = 33, 2
+    B = O.LocallyOrthogonalBasis(n, s, 10)
+    assert [e - b for b, e in B.bounds] == [10, 10, 13]
+    X0 = I.gaussian(n, s, 5)
+    X1 = I.gaussian(n, s, 6)
+    B.orthogonalize(X0, alg, alg)
+    Qexp = B.explicit()
+    Ue, Pe, Ne = _mp_pqr(Qexp, X1)
+    U, P, N = B.orthogonalize(X1, alg, alg)
+    np.testing.assert_allclose(U, Ue, atol=1e-14)
+    np.testing.assert_allclose(P, Pe, atol=1e-14)
+    np.testing.assert_allclose(N, Ne, atol=1e-14)
+
+
+# -------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_single_column_empty_basis(alg):
+    """s = 1, k = 0: U = w/||w||, N = ||w|| (sum of squares written out)."""
+    w = I.gaussian(300, 1, 7)
+    nrm = np.sqrt(sum(float(x) ** 2 for x in w[:, 0]))
+    U, P, N = O.pqr(np.zeros((300, 0)), w, alg)
+    assert P.shape == (0, 1)
+    assert N[0, 0] == pytest.approx(nrm, rel=1e-14)
+    np.testing.assert_allclose(U[:, 0], w[:, 0] / nrm, atol=1e-15)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_unit_vector_basis(alg):
+    """Q = I[:, :k]: P = X[:k], N = R-factor (LAPACK) of X[k:]."""
+    n, k, s = 80, 6, 4
+    Q = np.eye(n)[:, :k]
+    X = I.gaussian(n, s, 8)
+    U, P, N = O.pqr(Q, X, alg)
+    np.testing.assert_allclose(P, X[:k], atol=1e-14)
+    Ql, Rl = _lapack_qr(X[k:])
+    np.testing.assert_allclose(N, Rl, atol=1e-13)
+    np.testing.assert_allclose(U[:k], 0, atol=1e-14)
+    np.testing.assert_allclose(U[k:], Ql, atol=1e-13)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_known_decomposition(alg):
+    """X = Q M + Z S with Z orthonormal, Z ⟂ Q, S upper with positive
+    diagonal: the unique solution is P = M, N = S, U = Z.  A transposed P, a
+    wrong sign or a dropped term in any sub-algorithm breaks this."""
+    n, k, s = 200, 12, 5
+    QZ = I.haar(n, k + s, 9)
+    Q, Z = QZ[:, :k], QZ[:, k:]
+    M = I.gaussian(k, s, 10)
+    S = np.triu(I.gaussian(s, s, 11)) + np.diag(np.arange(1.0, s + 1) + 2.0)
+    S = S * np.where(np.diag(S) > 0, 1.0, -1.0)[:, None]
+    X = Q @ M + Z @ S
+    U, P, N = O.pqr(Q, X, alg)
+    np.testing.assert_allclose(P, M, atol=1e-12)
+    np.testing.assert_allclose(N, S, atol=1e-12)
+    np.testing.assert_allclose(U, Z, atol=1e-12)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_already_orthogonal_block(alg):
+    """X ⟂ span(Q), orthonormal: P = 0, N = I, U = X."""
+    QZ = I.haar(150, 10, 12)
+    Q, Z = QZ[:, :6], QZ[:, 6:]
+    U, P, N = O.pqr(Q, Z, alg)
+    np.testing.assert_allclose(P, 0, atol=1e-14)
+    np.testing.assert_allclose(N, np.eye(4), atol=1e-14)
+    np.testing.assert_allclose(U, Z, atol=1e-14)
+
+
+def test_cholqr_identity():
+    """k = 0: N^T N = X^T X and N = chol(X^T X)^T (LAPACK), the CholQR
+    identity of Sec. 3."""
+    X = I.gaussian(500, 6, 13)
+    for alg in ALGS:
+        _, _, N = O.pqr(np.zeros((500, 0)), X, alg)
+        L = np.linalg.cholesky(X.T @ X)
+        np.testing.assert_allclose(N, L.T, atol=1e-12 * np.abs(L).max())
+
+
+def test_pip2_combination_formula():
+    """The reiteration combine: X = Q P + U N must hold with
+    P = P1 + P2 N1 and N = N2 N1; the printed variant P1 N2 + P2, N2 + N1 N2
+    violates it (this pins the reading of Alg. 5 / Alg. 8)."""
+    n, k, s = 300, 8, 4
+    Q = I.haar(n, k, 14)
+    X = I.stewart(n, s, 1e3, 15) + Q @ I.gaussian(k, s, 16)
+    U1, P1, N1 = O.bcgs_pip(Q, X)
+    U, P2, N2 = O.bcgs_pip(Q, U1)
+    _, P, N = O.bcgs_pip2(Q, X)
+    np.testing.assert_allclose(Q @ P + U @ N, X, atol=1e-12)
+    printed_P, printed_N = P1 @ N2 + P2, N2 + N1 @ N2
+    assert np.linalg.norm(Q @ printed_P + U @ printed_N - X) > 1e-3
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("local,reduction", [("hh", "hh"), ("pip2", "pip2"), ("pip", "pip2"),
+                                             ("mgs2", "hh"), ("pip2", "hh")])
+@pytest.mark.parametrize("n,chunk", [(1000, 128), (777, 100), (300, 1000)])
+def test_tree_tspqr_equals_direct(local, reduction, n, chunk):
+    """Alg. 9 over several steps gives the same U, P, N as the direct PQR of
+    the explicit basis (the solution is unique), keeps every local Q_i
+    orthonormal, keeps sum T_i^T T_i = I, and its explicit basis is the
+    Q-factor of the direct QR of all blocks (Alg. 2 with LAPACK)."""
+    s, steps = 4, 5
+    B = O.LocallyOrthogonalBasis(n, s, chunk)
+    Xs = [I.gaussian(n, s, 300 + j) for j in range(steps)]
+    Rfull = np.zeros((s * steps, s * steps))
+    for j, X in enumerate(Xs):
+        Qexp = B.explicit()
+        Ud, Pd, Nd = O.pqr_householder(Qexp, X)
+        U, P, N = B.orthogonalize(X, local, reduction)
+        np.testing.assert_allclose(U, Ud, atol=1e-13)
+        np.testing.assert_allclose(P, Pd, atol=1e-13)
+        np.testing.assert_allclose(N, Nd, atol=1e-12)
+        Rfull[:j * s, j * s:(j + 1) * s] = P
+        Rfull[j * s:(j + 1) * s, j * s:(j + 1) * s] = N
+        for Qi in B.Qloc:
+            assert O.e_perp(Qi) < 1e-13
+        np.testing.assert_allclose(B.tree_gram(), np.eye(B.k), atol=1e-13)
+        for Ti in B.T:
+            np.testing.assert_allclose(np.tril(Ti, -1), 0, atol=1e-14)
+    A = np.hstack(Xs)
+    Ql, Rl = _lapack_qr(A)
+    np.testing.assert_allclose(B.explicit(), Ql, atol=1e-12)
+    np.testing.assert_allclose(Rfull, Rl, atol=1e-11 * np.abs(Rl).max())
+
+
+def test_single_chunk_tree_is_the_leaf():
+    """p = 1: the reduction acts on [[T_1, P_1], [0, N_1]] with T_1 = I-like,
+    so TreeTSPQR returns the leaf's own P and N."""
+    n, s = 256, 4
+    B = O.LocallyOrthogonalBasis(n, s, 1024)
+    assert len(B.bounds) == 1
+    X0, X1 = I.gaussian(n, s, 20), I.gaussian(n, s, 21)
+    B.orthogonalize(X0, "pip2", "pip2")
+    Q = B.Qloc[0] @ B.T[0]
+    Ul, Pl, Nl = O.bcgs_pip2(Q, X1)
+    U, P, N = B.orthogonalize(X1, "pip2", "pip2")
+    np.testing.assert_allclose(P, Pl, atol=1e-13)
+    np.testing.assert_allclose(N, Nl, atol=1e-13)
+    np.testing.assert_allclose(U, Ul, atol=1e-13)
+
+
+def test_apply_Q_matches_explicit():
+    n, s = 640, 3
+    B = O.LocallyOrthogonalBasis(n, s, 64)
+    for j in range(4):
+        B.orthogonalize(I.gaussian(n, s, 40 + j), "hh", "hh")
+    C = I.gaussian(B.k, 5, 50)
+    np.testing.assert_allclose(B.apply_Q(C), B.explicit() @ C, atol=1e-13)
+    A = np.hstack([I.gaussian(n, s, 40 + j) for j in range(4)])
+    Ql, _ = _lapack_qr(A)
+    np.testing.assert_allclose(B.apply_Q(np.eye(B.k)), Ql, atol=1e-12)
+
+
+def test_block_arnoldi_relation():
+    """Alg. 1: A V_m = V_{m+1} H (block Arnoldi relation) and V orthonormal,
+    with the operator a 1D Laplacian."""
+    n, s, m = 400, 2, 6
+
+    def lap(V):
+        out = 2 * V
+        out[1:] -= V[:-1]
+        out[:-1] -= V[1:]
+        return out
+
+    R0 = I.uniform(n, s, 60)
+    B = O.LocallyOrthogonalBasis(n, s, 64)
+    V, H, H0 = O.block_arnoldi(lap, R0, m, lambda Q, X: B.orthogonalize(X, "pip2", "pip2"))
+    assert O.e_perp(V) < 1e-13
+    np.testing.assert_allclose(lap(V[:, :m * s]), V @ H, atol=1e-12)
+    np.testing.assert_allclose(V[:, :s] @ H0, R0, atol=1e-13)
+
+
+# ---------------------------------------------- values printed in the paper
+
+def _golden():
+    rows = {}
+    with open(os.path.join(HERE, "golden", "tspqr_stability_kappa1e4.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            q, alg, lo, hi = line.split()
+            rows[(q, alg)] = (float(lo), float(hi))
+    return rows
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("alg", ["pip", "pip2", "hh"])
+def test_paper_stability_table(alg):
+    """Sec. 6.1 table, kappa = 1e4, n = 2^16, 32 columns, s = 4, 256-row local
+    problems: our Stewart matrix is another random draw, so the oracle must land
+    within a factor 10 of the printed range (e_perp) and below 10x its top
+    (residual).  The PIP case (~1e-9) pins the eps*kappa^2 loss of Alg. 7."""
+    g = _golden()
+    n, m, s = 2 ** 16, 32, 4
+    A = I.stewart(n, m, 1e4, 77)
+    B = O.LocallyOrthogonalBasis(n, s, 256)
+    Q, R = O.block_qr(A, s, lambda Qp, X: B.orthogonalize(X, alg, alg))
+    ep, res = O.e_perp(Q), O.residual(A, Q, R)
+    lo, hi = g[("e_perp", alg)]
+    assert lo / 10 <= ep <= hi * 10, (alg, ep)
+    assert res <= g[("residual", alg)][1] * 10, (alg, res)
+
+
+@pytest.mark.parametrize("alg,slope", [("pip", 2.0), ("pip2", 0.0), ("hh", 0.0)])
+def test_error_law_slopes(alg, slope):
+    """Sec. 3 / Sec. 6.1: e_perp = O(eps kappa^2) for PIP, O(eps) for PIP+
+    (while eps kappa^2 <= 1/2) and for HH.  Fit log e_perp over kappa = 1e2..1e6."""
+    n, m, s = 4096, 16, 4
+    ks = [1e2, 1e3, 1e4, 1e5, 1e6] if alg != "pip" else [1e2, 1e3, 1e4, 1e5]
+    errs = []
+    for kappa in ks:
+        A = I.stewart(n, m, kappa, 90)
+        B = O.LocallyOrthogonalBasis(n, s, 256)
+        Q, R = O.block_qr(A, s, lambda Qp, X: B.orthogonalize(X, alg, alg))
+        errs.append(O.e_perp(Q))
+    fit = np.polyfit(np.log10(ks), np.log10(errs), 1)[0]
+    assert abs(fit - slope) < 0.6, (alg, fit, errs)
