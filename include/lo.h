@@ -1,0 +1,187 @@
+/*
+ * lo.h — C ABI of the GB300 block-orthogonalization library (liblo).
+ *
+ * Implements the project-and-normalize (PQR) step of block Arnoldi / block
+ * GMRes as TreeTSPQR on a locally orthogonal basis, after Dreier & Engwer,
+ * "A Hardware-aware and Stable Orthogonalization Framework", arXiv 2204.13393:
+ *
+ *   PQR problem, eq. (pqr), Sec. 1: for orthonormal Q (n x k) and a new block
+ *   X (n x s) find orthonormal U (n x s) with Q^T U = 0, P (k x s) and upper
+ *   triangular N (s x s, positive diagonal) such that
+ *        [Q X] = [Q U] [[I, P], [0, N]].
+ *   In block Arnoldi (Alg. 1) P and N are the new column block of the block
+ *   Hessenberg matrix; this API returns them as H (= P) and R (= N).
+ *
+ *   Locally orthogonal representation, Sec. 4.1: the basis is never stored
+ *   explicitly; it is Q = diag(Q_1 .. Q_p) [T_1; ..; T_p] with local
+ *   orthonormal Q_i (one per row chunk) and upper-triangular tree factors T_i
+ *   whose stack is orthonormal.
+ *
+ *   TreeTSPQR, Alg. 9: a local PQR per chunk (BCGS-PIP, Alg. 7, reiterated as
+ *   BCGS-PIP+, Alg. 8, when the block is ill-conditioned), a reduction PQR of
+ *   the stacked small factors (BCGS-PIP+), and the assembly of U from the
+ *   block-wise products of Sec. 4.1.
+ *
+ * Conventions for every entry point:
+ *   - All matrices are float64, row-major.  "ld" is the row stride in
+ *     elements (ld >= number of columns).
+ *   - Device work is enqueued on the stream given at lo_basis_create.
+ *   - Pointers to n-row matrices (W, U, Y) may be device pointers or host
+ *     pointers (pageable or pinned); host data is staged through device
+ *     buffers owned by the basis, with the copies on the basis stream.
+ *   - The small outputs H and R are written to device or host memory as the
+ *     pointer's kind says.
+ *   - Functions return an lo_status; they never abort or throw across the ABI.
+ *   - The library allocates only in lo_basis_create (and lazily, once, the
+ *     host staging buffers).  Calls on one basis are not thread-safe.
+ */
+#ifndef LO_H_
+#define LO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lo_status {
+  LO_OK = 0,
+  LO_ERR_INVALID_ARG = 1,      /* bad pointer, size, stride or option           */
+  LO_ERR_CAPACITY = 2,         /* basis already holds max_blocks blocks         */
+  LO_ERR_CHUNK_TOO_SMALL = 3,  /* chunk_rows < max_blocks*s or n < max_blocks*s */
+  LO_ERR_BREAKDOWN = 4,        /* a Cholesky pivot <= tolerance: the new block  */
+                               /* is (numerically) rank deficient; deflation    */
+                               /* (Sec. 3, last paragraph) is not supported     */
+  LO_ERR_NONFINITE = 5,        /* NaN or Inf reached a small factor             */
+  LO_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                 */
+  LO_ERR_CUDA = 7,             /* a CUDA runtime call failed                    */
+  LO_ERR_OOM = 8,              /* device or pinned allocation failed            */
+  LO_ERR_UNSUPPORTED = 9       /* option combination not implemented            */
+} lo_status;
+
+/* Arithmetic of the O(n) passes. */
+typedef enum lo_precision {
+  LO_PREC_FP64 = 0,        /* every product in native float64                    */
+  LO_PREC_MIXED_FP32 = 1   /* first-pass Gram/projection in float32, then float64 */
+                           /* shifted Cholesky, one float64 CholeskyQR2-style    */
+                           /* refinement pass, float64 tree and update (Alg. 8   */
+                           /* pattern)                                            */
+} lo_precision;
+
+/* Local sub-algorithm (the "local subalgorithm" of Alg. 9). */
+typedef enum lo_leaf {
+  LO_LEAF_AUTO = 0,        /* BCGS-PIP, plus the PIP+ reiteration when the local */
+                           /* Cholesky factor's condition estimate says the      */
+                           /* single pass would lose orthogonality (decided on   */
+                           /* the device; no host synchronization)               */
+  LO_LEAF_PIP = 1,         /* BCGS-PIP, Alg. 7: one Gram pass                    */
+  LO_LEAF_PIP2 = 2         /* BCGS-PIP+, Alg. 8: always two Gram passes          */
+} lo_leaf;
+
+typedef struct lo_options {
+  int32_t precision;   /* lo_precision, default LO_PREC_FP64                     */
+  int32_t leaf;        /* lo_leaf, default LO_LEAF_AUTO                          */
+  int32_t reduction;   /* 0 = AUTO (PIP, plus reiteration when needed),          */
+                       /* 1 = PIP, 2 = PIP+ always.  Default 0                   */
+  int32_t sync;        /* 1 (default): lo_orthogonalize waits for its device     */
+                       /* work and returns the device status.  0: asynchronous;  */
+                       /* a device error is latched and returned by the next     */
+                       /* call or by lo_basis_sync.                              */
+  double refine_tol;   /* reiterate when eps * kappa_F(N)^2 exceeds this.        */
+                       /* <= 0 selects the default 1e-13.                        */
+} lo_options;
+
+typedef struct lo_basis lo_basis;
+
+/* Fill *opt with the defaults. */
+void lo_options_default(lo_options* opt);
+
+/*
+ * Create an empty basis for n-row blocks of width s, holding up to max_blocks
+ * blocks, with local row chunks of chunk_rows rows (p = max(1, n / chunk_rows)
+ * chunks; the remainder rows join the last chunk).  Every chunk must have at
+ * least max_blocks*s rows so that each local problem has full rank
+ * (LO_ERR_CHUNK_TOO_SMALL otherwise).  Requires 1 <= s <= 32 and
+ * max_blocks*s <= 1024.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream) of the current device.  opt may be NULL (defaults).
+ * Allocates all device memory of the basis (local panels n*max_blocks*s
+ * doubles, tree factors, scratch).  On failure *out is NULL.
+ */
+lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chunk_rows,
+                          const lo_options* opt, void* cuda_stream, lo_basis** out);
+
+/* Free everything owned by the basis.  NULL-safe. */
+void lo_basis_destroy(lo_basis* b);
+
+/* Drop all blocks (e.g. at a GMRes restart); keeps the allocations. */
+lo_status lo_basis_reset(lo_basis* b);
+
+/* Number of blocks currently in the basis (k = blocks * s columns). */
+int32_t lo_basis_num_blocks(const lo_basis* b);
+
+/* Number of local chunks p. */
+int32_t lo_basis_num_chunks(const lo_basis* b);
+
+/*
+ * One PQR step (Alg. 9): orthogonalize the n x s block W (row stride ldw)
+ * against the current basis (k = num_blocks*s columns).  Writes
+ *   U (n x s, row stride ldu)  the new orthonormal block, explicit (Sec. 1:
+ *                              U is needed explicitly to apply the operator),
+ *   H (k x s, row-major)       the projection P = Q^T W (may be NULL if k = 0),
+ *   R (s x s, row-major)       the normalizer N, upper triangular, diag > 0,
+ * and appends the block to the basis.  U may alias W (same pointer, same ld).
+ * H and R may be NULL if not wanted.  On any error the basis is unchanged
+ * (its block count is not advanced) and U, H, R are undefined.
+ */
+lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw,
+                           double* U, int64_t ldu, double* H, double* R);
+
+/*
+ * Y = Q C for the current basis (Sec. 5.1: the product QC of the second
+ * stage), computed chunk-wise as Y_i = Q_i (T_i C).  C is k x m row-major
+ * (k = num_blocks*s, row stride ldc >= m), host or device; Y is n x m
+ * (row stride ldy >= m), host or device.  With C = I_k this materializes the
+ * explicit basis.  1 <= m <= 64.
+ */
+lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc,
+                     double* Y, int64_t ldy);
+
+/*
+ * Orthogonalize count independent problems, one block each: for j < count,
+ * the same as lo_orthogonalize(bases[j], W[j], ldw[j], U[j], ldu[j], H[j],
+ * R[j]).  All bases must live on the same device and use the stream of
+ * bases[0]; W/U/H/R must be device pointers.  Returns the first error; bases
+ * without error advance.
+ */
+lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count,
+                                   const double* const* W, const int64_t* ldw,
+                                   double* const* U, const int64_t* ldu,
+                                   double* const* H, double* const* R);
+
+/* Wait for the basis stream and return (and clear) any latched device error. */
+lo_status lo_basis_sync(lo_basis* b);
+
+/*
+ * Copy the local factor of chunk i (its rows of the local panels, n_i x k,
+ * row-major with row stride k) and its tree factor T_i (k x k, row-major,
+ * zeros below the diagonal) to host memory.  For tests and inspection.
+ * Either destination may be NULL.  *rows receives n_i if rows != NULL.
+ */
+lo_status lo_basis_export_chunk(lo_basis* b, int32_t chunk, double* Qi_host,
+                                double* Ti_host, int64_t* rows);
+
+/* y = L x for the 2D 5-point Dirichlet Laplacian on an nx x ny grid
+ * (row-major grid points, n = nx*ny), applied to s columns at once: X and Y
+ * are n x s row-major device arrays with row strides ldx, ldy.  This is the
+ * operator of the block-GMRes test workload, not part of the PQR step. */
+lo_status lo_laplace5_apply(int32_t nx, int32_t ny, int32_t s, const double* X, int64_t ldx,
+                            double* Y, int64_t ldy, void* cuda_stream);
+
+/* Human-readable name of a status code (static string). */
+const char* lo_status_string(lo_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LO_H_ */
