@@ -87,7 +87,9 @@ typedef struct lo_options {
                        /* work and returns the device status.  0: asynchronous;  */
                        /* a device error is latched and returned by the next     */
                        /* call or by lo_basis_sync.                              */
-  double refine_tol;   /* reiterate when eps * kappa_F(N)^2 exceeds this.        */
+  double refine_tol;   /* reiterate when eps * kappa^2 exceeds this, where       */
+                       /* kappa = ||X||_F ||N^{-1}||_F for the block X and its  */
+                       /* normalizer N (the Gram cancellation factor).          */
                        /* <= 0 selects the default 1e-13.                        */
 } lo_options;
 
@@ -141,7 +143,7 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw,
  * stage), computed chunk-wise as Y_i = Q_i (T_i C).  C is k x m row-major
  * (k = num_blocks*s, row stride ldc >= m), host or device; Y is n x m
  * (row stride ldy >= m), host or device.  With C = I_k this materializes the
- * explicit basis.  1 <= m <= 64.
+ * explicit basis.  1 <= m <= 1024.
  */
 lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc,
                      double* Y, int64_t ldy);
@@ -176,6 +178,22 @@ lo_status lo_basis_export_chunk(lo_basis* b, int32_t chunk, double* Qi_host,
  * operator of the block-GMRes test workload, not part of the PQR step. */
 lo_status lo_laplace5_apply(int32_t nx, int32_t ny, int32_t s, const double* X, int64_t ldx,
                             double* Y, int64_t ldy, void* cuda_stream);
+
+/*
+ * Measurement hooks (used by the benchmark; not needed for normal use).
+ * lo_launch_count: number of kernels the library has launched in this process.
+ * lo_basis_set_profiling: when enabled, every group of kernels of this basis
+ *   (0 stage-1 Gram passes, 1 leaf factorizations, 2 reduction, 3 stage-2
+ *   update, 4 apply_Q) is bracketed by CUDA events on the basis stream.
+ * lo_basis_profile_read: waits for the recorded events and returns, per group,
+ *   the summed elapsed milliseconds and the number of bracketed intervals since
+ *   the last read (nkinds >= 5 entries in both arrays).
+ */
+long long lo_launch_count(void);
+/* Local Gram passes and reduction iterations the last step ran (waits for it). */
+lo_status lo_basis_last_step_info(lo_basis* b, int32_t* passes, int32_t* tree_iterations);
+lo_status lo_basis_set_profiling(lo_basis* b, int32_t enable);
+lo_status lo_basis_profile_read(lo_basis* b, double* ms, int64_t* intervals, int32_t nkinds);
 
 /* Human-readable name of a status code (static string). */
 const char* lo_status_string(lo_status st);

@@ -1,0 +1,554 @@
+// Host side of the C ABI (include/lo.h): basis object, argument validation,
+// staging of host buffers, kernel sequencing and status reporting.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lo_internal.h"
+
+using lo::GlobLayout;
+using lo::SlabInfo;
+using lo::SmallLayout;
+using lo::StepArgs;
+
+// Event-pair profiler for the kernel groups of one basis.
+struct Profiler : lo::ProfHook {
+  struct Pair {
+    int kind;
+    cudaEvent_t b, e;
+  };
+  bool enabled = false;
+  std::vector<Pair> done;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open[lo::kKindCount] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t ev = pool.back();
+      pool.pop_back();
+      return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    cudaEventCreate(&ev);
+    return ev;
+  }
+  void mark(int kind, bool begin, cudaStream_t st) override {
+    if (!enabled) return;
+    cudaEvent_t ev = get();
+    cudaEventRecord(ev, st);
+    if (begin) {
+      open[kind] = ev;
+    } else {
+      done.push_back(Pair{kind, open[kind], ev});
+      open[kind] = nullptr;
+    }
+  }
+  // Sum of elapsed times (ms) and number of intervals per kind; recycles the events.
+  cudaError_t collect(double* ms, long long* cnt) {
+    for (int k = 0; k < lo::kKindCount; ++k) {
+      ms[k] = 0.0;
+      cnt[k] = 0;
+    }
+    cudaError_t err = cudaSuccess;
+    for (auto& pr : done) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(pr.e);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pr.b, pr.e);
+      if (e != cudaSuccess) err = e;
+      ms[pr.kind] += t;
+      cnt[pr.kind] += 1;
+      pool.push_back(pr.b);
+      pool.push_back(pr.e);
+    }
+    done.clear();
+    return err;
+  }
+  ~Profiler() override {
+    for (auto& pr : done) {
+      cudaEventDestroy(pr.b);
+      cudaEventDestroy(pr.e);
+    }
+    for (auto ev : pool) cudaEventDestroy(ev);
+  }
+};
+
+struct lo_basis {
+  int64_t n = 0;
+  int s = 0, M = 0, cr = 0, p = 0, nb = 0, Kmax = 0;
+  lo_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double* V = nullptr;
+  double* T = nullptr;
+  double* part = nullptr;
+  double* small = nullptr;
+  double* glob = nullptr;
+  double* tsum = nullptr;
+  int* flags = nullptr;
+  int* h_flags = nullptr;  // pinned
+  SlabInfo* d_slabs = nullptr;
+  int32_t* d_chunk_slab0 = nullptr;
+  int64_t* d_chunk_row0 = nullptr;
+  int nslab = 0, slab_rows = 0, ngroups = 0;
+  int64_t tstride = 0;
+  std::vector<int64_t> chunk_row0;
+  // lazily allocated
+  double* stage_in = nullptr;
+  size_t stage_in_cap = 0;
+  double* stage_out = nullptr;
+  size_t stage_out_cap = 0;
+  double* zq = nullptr;
+  size_t zq_cap = 0;
+  double* cdev = nullptr;
+  size_t cdev_cap = 0;
+  Profiler prof;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+lo_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LO_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? LO_ERR_OOM : LO_ERR_CUDA;
+}
+
+lo_status status_from_bits(int bits) {
+  if (bits & (1 << LO_ERR_NONFINITE)) return LO_ERR_NONFINITE;
+  if (bits & (1 << LO_ERR_BREAKDOWN)) return LO_ERR_BREAKDOWN;
+  if (bits & (1 << LO_ERR_TIMEOUT)) return LO_ERR_TIMEOUT;
+  if (bits) return LO_ERR_CUDA;
+  return LO_OK;
+}
+
+lo_status ensure(double** buf, size_t* cap, size_t need) {
+  if (*cap >= need) return LO_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, need * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return LO_ERR_OOM;
+  }
+  *cap = need;
+  return LO_OK;
+}
+
+StepArgs make_args(const lo_basis* b) {
+  StepArgs a{};
+  a.n = b->n;
+  a.s = b->s;
+  a.M = b->M;
+  a.p = b->p;
+  a.nb = b->nb;
+  a.Kmax = b->Kmax;
+  a.V = b->V;
+  a.T = b->T;
+  a.tstride = b->tstride;
+  a.part = b->part;
+  a.small = b->small;
+  a.glob = b->glob;
+  a.tsum = b->tsum;
+  a.flags = b->flags;
+  a.slabs = b->d_slabs;
+  a.chunk_slab0 = b->d_chunk_slab0;
+  a.chunk_row0 = b->d_chunk_row0;
+  a.nslab = b->nslab;
+  a.slab_rows = b->slab_rows;
+  a.precision = b->opt.precision;
+  a.leaf = b->opt.leaf;
+  a.reduction = b->opt.reduction;
+  a.refine_tol = b->opt.refine_tol > 0 ? b->opt.refine_tol : 1e-13;
+  return a;
+}
+
+// Read and clear the latched device status (synchronizes the stream).
+lo_status read_status(lo_basis* b, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return from_cuda(e);
+  const int bits = b->h_flags[0];
+  if (bits) {
+    cudaMemsetAsync(b->flags, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
+  }
+  return status_from_bits(bits);
+}
+
+// Enqueue one PQR step on `st` for device-resident W/U.  Does not touch nb.
+lo_status enqueue_step(lo_basis* b, const double* W, int64_t ldw, double* U, int64_t ldu,
+                       cudaStream_t st) {
+  StepArgs a = make_args(b);
+  a.W = W;
+  a.ldw = ldw;
+  a.U = U;
+  a.ldu = ldu;
+  return from_cuda(lo::launch_step(a, st, &b->prof));
+}
+
+lo_status copy_small_outputs(lo_basis* b, double* H, double* R, cudaStream_t st) {
+  const GlobLayout GL = GlobLayout::make(b->Kmax, b->s);
+  const size_t ks = (size_t)b->nb * b->s * b->s, ss = (size_t)b->s * b->s;
+  cudaError_t e = cudaSuccess;
+  if (H && ks) e = cudaMemcpyAsync(H, b->glob + GL.P_acc, ks * sizeof(double), cudaMemcpyDefault, st);
+  if (e == cudaSuccess && R)
+    e = cudaMemcpyAsync(R, b->glob + GL.N_acc, ss * sizeof(double), cudaMemcpyDefault, st);
+  return from_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void lo_options_default(lo_options* opt) {
+  if (!opt) return;
+  opt->precision = LO_PREC_FP64;
+  opt->leaf = LO_LEAF_AUTO;
+  opt->reduction = 0;
+  opt->sync = 1;
+  opt->refine_tol = 1e-13;
+}
+
+const char* lo_status_string(lo_status st) {
+  switch (st) {
+    case LO_OK: return "ok";
+    case LO_ERR_INVALID_ARG: return "invalid argument";
+    case LO_ERR_CAPACITY: return "basis is full (max_blocks reached)";
+    case LO_ERR_CHUNK_TOO_SMALL: return "chunk has fewer rows than max_blocks*s";
+    case LO_ERR_BREAKDOWN: return "Cholesky breakdown: block is numerically rank deficient";
+    case LO_ERR_NONFINITE: return "non-finite value in a small factor";
+    case LO_ERR_TIMEOUT: return "bounded device wait timed out";
+    case LO_ERR_CUDA: return "CUDA runtime error";
+    case LO_ERR_OOM: return "out of memory";
+    case LO_ERR_UNSUPPORTED: return "unsupported option combination";
+  }
+  return "unknown status";
+}
+
+lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chunk_rows,
+                          const lo_options* opt, void* cuda_stream, lo_basis** out) {
+  if (!out) return LO_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || s < 1 || s > lo::kMaxS || max_blocks < 1 || chunk_rows < 1) return LO_ERR_INVALID_ARG;
+  const int64_t Kmax = (int64_t)max_blocks * s;
+  if (Kmax > lo::kMaxK || Kmax * s > lo::kMaxKS) return LO_ERR_INVALID_ARG;
+  lo_options o;
+  lo_options_default(&o);
+  if (opt) o = *opt;
+  if (o.precision < 0 || o.precision > 1 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
+      o.reduction > 2)
+    return LO_ERR_INVALID_ARG;
+  if (o.refine_tol <= 0) o.refine_tol = 1e-13;
+  const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
+  if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
+  const int p = (int)p64;
+  const int64_t min_rows = (p == 1) ? n : chunk_rows;
+  if (min_rows < Kmax) return LO_ERR_CHUNK_TOO_SMALL;
+
+  lo_basis* b = new (std::nothrow) lo_basis();
+  if (!b) return LO_ERR_OOM;
+  b->n = n;
+  b->s = s;
+  b->M = max_blocks;
+  b->cr = chunk_rows;
+  b->p = p;
+  b->Kmax = (int)Kmax;
+  b->opt = o;
+  b->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&b->device);
+  b->tstride = (int64_t)s * s * max_blocks * (max_blocks + 1) / 2;
+  b->slab_rows = 16 * s > 256 ? 16 * s : 256;
+
+  // chunks and slabs
+  std::vector<SlabInfo> slabs;
+  std::vector<int32_t> cs0;
+  b->chunk_row0.resize(p + 1);
+  for (int c = 0; c < p; ++c) {
+    const int64_t r0 = (int64_t)c * chunk_rows;
+    const int64_t r1 = (c == p - 1) ? n : r0 + chunk_rows;
+    b->chunk_row0[c] = r0;
+    cs0.push_back((int32_t)slabs.size());
+    for (int64_t r = r0; r < r1; r += b->slab_rows) {
+      SlabInfo si;
+      si.row0 = r;
+      si.rows = (int32_t)((r1 - r) < b->slab_rows ? (r1 - r) : b->slab_rows);
+      si.chunk = c;
+      slabs.push_back(si);
+    }
+  }
+  b->chunk_row0[p] = n;
+  cs0.push_back((int32_t)slabs.size());
+  b->nslab = (int)slabs.size();
+  b->ngroups = (p + lo::kTreeGroup - 1) / lo::kTreeGroup;
+
+  const SmallLayout SL = SmallLayout::make(b->Kmax, s);
+  const GlobLayout GL = GlobLayout::make(b->Kmax, s);
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+  };
+  alloc((void**)&b->V, sizeof(double) * (size_t)n * Kmax);
+  alloc((void**)&b->T, sizeof(double) * (size_t)p * b->tstride);
+  alloc((void**)&b->part, sizeof(double) * (size_t)b->nslab * Kmax * s);
+  alloc((void**)&b->small, sizeof(double) * (size_t)p * SL.stride);
+  alloc((void**)&b->glob, sizeof(double) * (size_t)GL.stride);
+  alloc((void**)&b->tsum, sizeof(double) * (size_t)b->ngroups * Kmax * s);
+  alloc((void**)&b->flags, sizeof(int) * lo::kFlagCount);
+  alloc((void**)&b->d_slabs, sizeof(SlabInfo) * slabs.size());
+  alloc((void**)&b->d_chunk_slab0, sizeof(int32_t) * cs0.size());
+  alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_flags, sizeof(int) * lo::kFlagCount);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_slabs, slabs.data(), sizeof(SlabInfo) * slabs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_chunk_slab0, cs0.data(), sizeof(int32_t) * cs0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_chunk_row0, b->chunk_row0.data(), sizeof(int64_t) * b->chunk_row0.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->T, 0, sizeof(double) * (size_t)p * b->tstride);
+  if (e == cudaSuccess) e = cudaMemset(b->flags, 0, sizeof(int) * lo::kFlagCount);
+  if (e == cudaSuccess) e = cudaMemset(b->glob, 0, sizeof(double) * (size_t)GL.stride);
+  if (e != cudaSuccess) {
+    lo_status st = from_cuda(e);
+    lo_basis_destroy(b);
+    return st;
+  }
+  *out = b;
+  return LO_OK;
+}
+
+void lo_basis_destroy(lo_basis* b) {
+  if (!b) return;
+  cudaFree(b->V);
+  cudaFree(b->T);
+  cudaFree(b->part);
+  cudaFree(b->small);
+  cudaFree(b->glob);
+  cudaFree(b->tsum);
+  cudaFree(b->flags);
+  cudaFree(b->d_slabs);
+  cudaFree(b->d_chunk_slab0);
+  cudaFree(b->d_chunk_row0);
+  cudaFree(b->stage_in);
+  cudaFree(b->stage_out);
+  cudaFree(b->zq);
+  cudaFree(b->cdev);
+  if (b->h_flags) cudaFreeHost(b->h_flags);
+  cudaGetLastError();
+  delete b;
+}
+
+lo_status lo_basis_reset(lo_basis* b) {
+  if (!b) return LO_ERR_INVALID_ARG;
+  b->nb = 0;
+  return LO_OK;
+}
+
+int32_t lo_basis_num_blocks(const lo_basis* b) { return b ? b->nb : -1; }
+
+int32_t lo_basis_num_chunks(const lo_basis* b) { return b ? b->p : -1; }
+
+lo_status lo_basis_sync(lo_basis* b) {
+  if (!b) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  return read_status(b, b->stream);
+}
+
+lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw, double* U, int64_t ldu,
+                           double* H, double* R) {
+  if (!b || !W || !U || ldw < b->s || ldu < b->s) return LO_ERR_INVALID_ARG;
+  if (b->nb >= b->M) return LO_ERR_CAPACITY;
+  cudaSetDevice(b->device);
+  cudaStream_t st = b->stream;
+  const int s = b->s;
+  const int64_t n = b->n;
+  const bool w_dev = is_device_ptr(W), u_dev = is_device_ptr(U);
+  const double* Wd = W;
+  int64_t ldwd = ldw;
+  double* Ud = U;
+  int64_t ldud = ldu;
+  lo_status rs;
+  if (!w_dev) {
+    if ((rs = ensure(&b->stage_in, &b->stage_in_cap, (size_t)n * s)) != LO_OK) return rs;
+    cudaError_t e = cudaMemcpy2DAsync(b->stage_in, s * sizeof(double), W, ldw * sizeof(double),
+                                      s * sizeof(double), n, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    Wd = b->stage_in;
+    ldwd = s;
+  }
+  if (!u_dev) {
+    if ((rs = ensure(&b->stage_out, &b->stage_out_cap, (size_t)n * s)) != LO_OK) return rs;
+    Ud = b->stage_out;
+    ldud = s;
+  }
+  if ((rs = enqueue_step(b, Wd, ldwd, Ud, ldud, st)) != LO_OK) return rs;
+  if ((rs = copy_small_outputs(b, H, R, st)) != LO_OK) return rs;
+  if (!u_dev) {
+    cudaError_t e = cudaMemcpy2DAsync(U, ldu * sizeof(double), Ud, s * sizeof(double), s * sizeof(double), n,
+                                      cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  if (b->opt.sync || !w_dev || !u_dev) {
+    lo_status d = read_status(b, st);
+    if (d != LO_OK) return d;
+  }
+  b->nb += 1;
+  return LO_OK;
+}
+
+lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const double* const* W,
+                                   const int64_t* ldw, double* const* U, const int64_t* ldu,
+                                   double* const* H, double* const* R) {
+  if (count < 0 || (count > 0 && (!bases || !W || !ldw || !U || !ldu))) return LO_ERR_INVALID_ARG;
+  if (count == 0) return LO_OK;
+  for (int j = 0; j < count; ++j) {
+    lo_basis* b = bases[j];
+    if (!b || !W[j] || !U[j] || ldw[j] < b->s || ldu[j] < b->s) return LO_ERR_INVALID_ARG;
+    if (b->nb >= b->M) return LO_ERR_CAPACITY;
+    if (b->device != bases[0]->device) return LO_ERR_INVALID_ARG;
+  }
+  cudaSetDevice(bases[0]->device);
+  cudaStream_t st = bases[0]->stream;
+  for (int j = 0; j < count; ++j) {
+    lo_basis* b = bases[j];
+    lo_status rs = enqueue_step(b, W[j], ldw[j], U[j], ldu[j], st);
+    if (rs == LO_OK) rs = copy_small_outputs(b, H ? H[j] : nullptr, R ? R[j] : nullptr, st);
+    if (rs != LO_OK) return rs;
+  }
+  lo_status first = LO_OK;
+  for (int j = 0; j < count; ++j) {
+    lo_basis* b = bases[j];
+    lo_status d = read_status(b, st);
+    if (d == LO_OK)
+      b->nb += 1;
+    else if (first == LO_OK)
+      first = d;
+  }
+  return first;
+}
+
+lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc, double* Y, int64_t ldy) {
+  if (!b || !Y || m < 1 || m > lo::kMaxK || ldy < m) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  cudaStream_t st = b->stream;
+  const int64_t n = b->n;
+  const int k = b->nb * b->s;
+  const bool y_dev = is_device_ptr(Y);
+  lo_status rs;
+  if (k == 0) {
+    cudaError_t e = y_dev ? cudaMemset2DAsync(Y, ldy * sizeof(double), 0, m * sizeof(double), n, st)
+                          : cudaSuccess;
+    if (!y_dev)
+      for (int64_t r = 0; r < n; ++r) memset(Y + r * ldy, 0, m * sizeof(double));
+    return from_cuda(e);
+  }
+  if (!C || ldc < m) return LO_ERR_INVALID_ARG;
+  const double* Cd = C;
+  int64_t ldcd = ldc;
+  if (!is_device_ptr(C)) {
+    if ((rs = ensure(&b->cdev, &b->cdev_cap, (size_t)k * m)) != LO_OK) return rs;
+    cudaError_t e = cudaMemcpy2DAsync(b->cdev, m * sizeof(double), C, ldc * sizeof(double), m * sizeof(double), k,
+                                      cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    Cd = b->cdev;
+    ldcd = m;
+  }
+  if ((rs = ensure(&b->zq, &b->zq_cap, (size_t)b->p * k * m)) != LO_OK) return rs;
+  double* Yd = Y;
+  int64_t ldyd = ldy;
+  if (!y_dev) {
+    if ((rs = ensure(&b->stage_out, &b->stage_out_cap, (size_t)n * m)) != LO_OK) return rs;
+    Yd = b->stage_out;
+    ldyd = m;
+  }
+  StepArgs a = make_args(b);
+  cudaError_t e = lo::launch_apply_q(a, Cd, m, ldcd, b->zq, Yd, ldyd, st, &b->prof);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (!y_dev) {
+    e = cudaMemcpy2DAsync(Y, ldy * sizeof(double), Yd, m * sizeof(double), m * sizeof(double), n, cudaMemcpyDefault,
+                          st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  if (b->opt.sync || !y_dev) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  return LO_OK;
+}
+
+lo_status lo_basis_export_chunk(lo_basis* b, int32_t chunk, double* Qi_host, double* Ti_host, int64_t* rows) {
+  if (!b || chunk < 0 || chunk >= b->p) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  const int s = b->s, k = b->nb * s;
+  const int64_t r0 = b->chunk_row0[chunk], r1 = b->chunk_row0[chunk + 1];
+  if (rows) *rows = r1 - r0;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (Qi_host && k > 0) {
+    for (int blk = 0; blk < b->nb && e == cudaSuccess; ++blk)
+      e = cudaMemcpy2D(Qi_host + blk * s, k * sizeof(double), b->V + (size_t)blk * b->n * s + r0 * s,
+                       s * sizeof(double), s * sizeof(double), r1 - r0, cudaMemcpyDeviceToHost);
+  }
+  if (Ti_host && k > 0 && e == cudaSuccess) {
+    std::vector<double> tb((size_t)b->tstride);
+    e = cudaMemcpy(tb.data(), b->T + (size_t)chunk * b->tstride, sizeof(double) * b->tstride, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+      memset(Ti_host, 0, sizeof(double) * (size_t)k * k);
+      for (int cb = 0; cb < b->nb; ++cb) {
+        const double* blk = tb.data() + lo::tblock_offset(cb, s);
+        for (int r = 0; r < (cb + 1) * s; ++r)
+          for (int j = 0; j < s; ++j) Ti_host[(size_t)r * k + cb * s + j] = blk[r * s + j];
+      }
+    }
+  }
+  return from_cuda(e);
+}
+
+long long lo_launch_count(void) { return lo::launches(); }
+
+lo_status lo_basis_last_step_info(lo_basis* b, int32_t* passes, int32_t* tree_iterations) {
+  if (!b) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  int f[lo::kFlagCount];
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(f, b->flags, sizeof(f), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  int L = 0, Tn = 0;
+  for (int t = 1; t <= lo::kMaxPass; ++t)
+    if (f[lo::kFlagPass + t - 1]) L = t;
+  for (int t = 1; t <= lo::kMaxTreeIter; ++t)
+    if (f[lo::kFlagTree + t - 1]) Tn = t;
+  if (passes) *passes = L;
+  if (tree_iterations) *tree_iterations = Tn;
+  return LO_OK;
+}
+
+lo_status lo_basis_set_profiling(lo_basis* b, int32_t enable) {
+  if (!b) return LO_ERR_INVALID_ARG;
+  b->prof.enabled = enable != 0;
+  return LO_OK;
+}
+
+lo_status lo_basis_profile_read(lo_basis* b, double* ms, int64_t* intervals, int32_t nkinds) {
+  if (!b || !ms || !intervals || nkinds < lo::kKindCount) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  long long cnt[lo::kKindCount];
+  cudaError_t e = b->prof.collect(ms, cnt);
+  for (int k = 0; k < lo::kKindCount; ++k) intervals[k] = cnt[k];
+  return from_cuda(e);
+}
+
+lo_status lo_laplace5_apply(int32_t nx, int32_t ny, int32_t s, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, void* cuda_stream) {
+  if (nx < 1 || ny < 1 || s < 1 || !X || !Y || ldx < s || ldy < s) return LO_ERR_INVALID_ARG;
+  return from_cuda(lo::launch_laplace5(nx, ny, s, X, ldx, Y, ldy, (cudaStream_t)cuda_stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Internal declarations shared by the host orchestration (lo_api.cu) and the
+// kernels (lo_kernels.cu).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lo.h"
+
+namespace lo {
+
+constexpr int kMaxS = 32;        // block width limit (one warp per column set)
+constexpr int kMaxK = 1024;      // max_blocks * s
+constexpr int kMaxKS = 8192;     // (k + s) * s entries of one Gram tile
+constexpr int kThreads = 256;    // threads of the streaming kernels
+constexpr int kMaxPass = 3;      // local Gram passes (PIP, PIP+, one more)
+constexpr int kMaxTreeIter = 3;  // reduction iterations
+constexpr int kTreeGroup = 64;   // chunks summed per CTA in the tree's first level
+
+// Flag words (int) in device memory.
+enum Flag : int {
+  kFlagStatus = 0,        // lo_status bits (OR of 1 << status) latched by kernels
+  kFlagPass = 1,          // [1 .. kMaxPass]: pass t requested (1) or not (0)
+  kFlagTree = 1 + kMaxPass + 1,  // [.. + kMaxTreeIter]: tree iteration requested
+  kFlagCount = 16
+};
+
+// One row slab of one chunk: the unit of work of the streaming kernels.
+struct SlabInfo {
+  int64_t row0;
+  int32_t rows;
+  int32_t chunk;
+};
+
+// Per-chunk small-matrix scratch, offsets in doubles (Kmax = M * s).
+struct SmallLayout {
+  int64_t P_last, P_comb, P_hat, Z;          // Kmax x s each
+  int64_t N_last, Ninv_last, N_comb, N_hat;  // s x s each
+  int64_t stride;
+  __host__ __device__ static SmallLayout make(int Kmax, int s) {
+    SmallLayout L;
+    int64_t ks = (int64_t)Kmax * s, ss = (int64_t)s * s;
+    L.P_last = 0;
+    L.P_comb = ks;
+    L.P_hat = 2 * ks;
+    L.Z = 3 * ks;
+    L.N_last = 4 * ks;
+    L.Ninv_last = L.N_last + ss;
+    L.N_comb = L.N_last + 2 * ss;
+    L.N_hat = L.N_last + 3 * ss;
+    L.stride = L.N_last + 4 * ss;
+    return L;
+  }
+};
+
+// Global small-matrix scratch, offsets in doubles.
+struct GlobLayout {
+  int64_t P_it, N_it, Ninv_it;   // this tree iteration: Kmax x s, s x s, s x s
+  int64_t P_acc, N_acc;          // combined over iterations (the outputs H, R)
+  int64_t Zsum;                  // Kmax x s, the summed contributions
+  int64_t stride;
+  __host__ __device__ static GlobLayout make(int Kmax, int s) {
+    GlobLayout L;
+    int64_t ks = (int64_t)Kmax * s, ss = (int64_t)s * s;
+    L.P_it = 0;
+    L.N_it = ks;
+    L.Ninv_it = ks + ss;
+    L.P_acc = ks + 2 * ss;
+    L.N_acc = 2 * ks + 2 * ss;
+    L.Zsum = 2 * ks + 3 * ss;
+    L.stride = 3 * ks + 3 * ss;
+    return L;
+  }
+};
+
+// Everything a kernel needs to know about a basis and the current step.
+struct StepArgs {
+  int64_t n;
+  int s, M, p, nb;          // nb = blocks already in the basis (k = nb * s)
+  int Kmax;
+  double* V;                // local panels: panel b at V + b * n * s, row-major n x s
+  double* T;                // tree factors, chunk stride tstride
+  int64_t tstride;
+  double* part;             // Gram partials: nslab x Kmax x s
+  double* small;            // per-chunk scratch, SmallLayout
+  double* glob;             // global scratch, GlobLayout
+  double* tsum;             // tree first-level sums: ngroups x Kmax x s
+  int* flags;
+  const SlabInfo* slabs;
+  const int32_t* chunk_slab0;   // first slab of chunk c (p + 1 entries)
+  const int64_t* chunk_row0;    // first row of chunk c (p + 1 entries)
+  int nslab;
+  int slab_rows;
+  int precision;
+  int leaf;
+  int reduction;
+  double refine_tol;
+  // the step's block and outputs
+  const double* W;
+  int64_t ldw;
+  double* U;
+  int64_t ldu;
+};
+
+// Offset (in doubles) of column block c inside one chunk's tree factor.
+__host__ __device__ inline int64_t tblock_offset(int c, int s) {
+  return (int64_t)s * s * c * (c + 1) / 2;
+}
+
+// Kernel groups timed by the optional profiling hook (lo_basis_set_profiling).
+enum KernelKind : int {
+  kKindGram = 0,     // stage-1 Gram passes
+  kKindLeaf = 1,     // per-chunk leaf factorizations
+  kKindTree = 2,     // reduction (tree combine)
+  kKindUpdate = 3,   // stage-2 assembly of U and of the new local block
+  kKindApply = 4,    // apply_Q
+  kKindCount = 5
+};
+
+// Records a CUDA event before/after each kernel group when profiling is on.
+struct ProfHook {
+  virtual void mark(int kind, bool begin, cudaStream_t st) = 0;
+  virtual ~ProfHook() {}
+};
+
+// Number of kernels this library has launched in this process.
+long long launches();
+void count_launches(int k);
+
+// Launchers (lo_kernels.cu).  All enqueue on `st` and return the launch error.
+cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook);
+cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ldc, double* Z,
+                           double* Y, int64_t ldy, cudaStream_t st, ProfHook* hook);
+cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, cudaStream_t st);
+
+}  // namespace lo

@@ -1,0 +1,707 @@
+// Float64 kernels of one TreeTSPQR step (Alg. 9) on the locally orthogonal
+// basis of Sec. 4.1, plus apply_Q and the 5-point Laplacian of the test
+// workload.
+//
+// Step = stage 1 (Gram passes + local leaf factorizations), reduction
+// (tree combine of the stacked small factors), stage 2 (assembly of U and of
+// the new local block).  Every reduction has a fixed order, so two runs give
+// bit-identical results.  No kernel waits on another CTA; breakdowns are
+// reported through the status flag word, never by trapping.
+#include <atomic>
+#include <cfloat>
+#include <cstdint>
+
+#include "lo_internal.h"
+
+namespace lo {
+namespace {
+
+__device__ __forceinline__ void set_status(int* flags, lo_status st) {
+  atomicOr(&flags[kFlagStatus], 1 << (int)st);
+}
+
+__device__ __forceinline__ double* chunk_small(const StepArgs& a, int c) {
+  return a.small + (int64_t)c * SmallLayout::make(a.Kmax, a.s).stride;
+}
+
+__device__ __forceinline__ int passes_run(const StepArgs& a) {
+  int L = 1;
+  for (int t = 2; t <= kMaxPass; ++t)
+    if (a.flags[kFlagPass + t - 1]) L = t;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Small dense helpers executed by a whole CTA on shared-memory matrices.
+
+// In-place upper Cholesky of the s x s symmetric matrix M (row-major, smem):
+// afterwards the upper triangle holds N with N^T N = M, the lower is zero.
+// A pivot <= tol (or non-finite) latches LO_ERR_BREAKDOWN / LO_ERR_NONFINITE
+// and is replaced by 1 so that no NaN propagates into later kernels' indexing.
+__device__ void cta_cholesky(double* M, int s, double tol, int* flags) {
+  for (int i = 0; i < s; ++i) {
+    if (threadIdx.x == 0) {
+      double d = M[i * s + i];
+      if (!isfinite(d)) {
+        set_status(flags, LO_ERR_NONFINITE);
+        d = 1.0;
+      } else if (!(d > tol)) {
+        set_status(flags, LO_ERR_BREAKDOWN);
+        d = 1.0;
+      }
+      M[i * s + i] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = M[i * s + i];
+    for (int j = i + 1 + threadIdx.x; j < s; j += blockDim.x) M[i * s + j] /= piv;
+    __syncthreads();
+    const int rem = s - i - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int j = i + 1 + e / rem, l = i + 1 + e % rem;
+      if (l >= j) M[j * s + l] -= M[i * s + j] * M[i * s + l];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x)
+    if (e / s > e % s) M[e] = 0.0;
+  __syncthreads();
+}
+
+// X = N^{-1} for upper-triangular N (smem), column by column.
+__device__ void cta_upper_inverse(const double* N, double* X, int s) {
+  for (int l = threadIdx.x; l < s; l += blockDim.x) {
+    for (int i = s - 1; i >= 0; --i) {
+      double v = (i == l) ? 1.0 : 0.0;
+      if (i <= l) {
+        for (int j = i + 1; j <= l; ++j) v -= N[i * s + j] * X[j * s + l];
+        v /= N[i * s + i];
+      } else {
+        v = 0.0;
+      }
+      X[i * s + l] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// C = A B for s x s matrices in smem (C must not alias A or B).
+__device__ void cta_matmul_ss(const double* A, const double* B, double* C, int s) {
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e / s, j = e % s;
+    double v = 0.0;
+    for (int q = 0; q < s; ++q) v += A[i * s + q] * B[q * s + j];
+    C[e] = v;
+  }
+  __syncthreads();
+}
+
+// Amplification estimate of a BCGS-PIP solve: kappa = ||X||_F ||N^{-1}||_F with
+// ||X||_F^2 = trace(G).  The Gram G - P^T P loses about eps * kappa^2 of its
+// relative accuracy to cancellation (the block's norm against its part
+// orthogonal to the basis), which is the orthogonality the single pass loses
+// (Sec. 3: O(eps kappa^2)); ||N||_F alone would miss the cancellation.
+__device__ double cta_pip_kappa(double trG, const double* Ninv, int s, double* red) {
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int e = 0; e < s * s; ++e) b += Ninv[e] * Ninv[e];
+    red[0] = sqrt(trG) * sqrt(b);
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Step bookkeeping: which passes / tree iterations are forced.
+
+__global__ void k_step_begin(int* flags, int force_pass2, int force_tree2) {
+  if (threadIdx.x == 0) {
+    for (int t = 1; t <= kMaxPass; ++t) flags[kFlagPass + t - 1] = (t == 1) || (t == 2 && force_pass2);
+    for (int t = 1; t <= kMaxTreeIter; ++t) flags[kFlagTree + t - 1] = (t == 1) || (t == 2 && force_tree2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1, Gram pass `pass` over one row slab of one chunk (Alg. 7 first line,
+// "at once"): the partial of C_i = [Q_i A_i]^T A_i where A_i is the block of
+// this pass: W_i for pass 1; for pass t >= 2 the previous iterate
+// Y = (A_prev - Q_i P_last) N_last^{-1} (Alg. 8, U_1), which is also written
+// into the new local panel so that the next stage reads it instead of
+// recomputing it.  TileT/Acc = float for the first pass of the mixed form.
+template <typename TileT, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int tile_rows) {
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s;
+  TileT* A = reinterpret_cast<TileT*>(smem_raw);  // tile_rows x Kt
+  const size_t tm_off = (sizeof(TileT) * (size_t)tile_rows * Kt + 15) & ~(size_t)15;
+  double* Tm = reinterpret_cast<double*>(smem_raw + tm_off);  // tile_rows x s
+  const int tid = threadIdx.x;
+  // thread -> (output entry, row group)
+  const int G = (E >= kThreads) ? 1 : kThreads / E;
+  const int J = (E + kThreads - 1) / kThreads;  // entries per thread when G == 1
+  const int g = (G == 1) ? 0 : tid / E;
+  const bool active = (G == 1) || (tid < G * E);
+  Acc acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = Acc(0);
+
+  const double* smallc = chunk_small(a, si.chunk);
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const double* Plast = smallc + SL.P_last;
+  const double* Ninv = smallc + SL.Ninv_last;
+  double* slot = a.V + (int64_t)a.nb * a.n * s;
+
+  for (int r0 = 0; r0 < si.rows; r0 += tile_rows) {
+    const int rows = min(tile_rows, si.rows - r0);
+    const int64_t grow0 = si.row0 + r0;
+    // Q_i rows: each panel's rows are contiguous (rows * s doubles)
+    for (int idx = tid; idx < rows * k; idx += kThreads) {
+      const int b = idx / (rows * s), rem = idx - b * rows * s, r = rem / s, j = rem - r * s;
+      A[r * Kt + b * s + j] = (TileT)a.V[(int64_t)b * a.n * s + (grow0 + r) * s + j];
+    }
+    if (pass == 1) {
+      for (int idx = tid; idx < rows * s; idx += kThreads) {
+        const int r = idx / s, l = idx - r * s;
+        A[r * Kt + k + l] = (TileT)a.W[(grow0 + r) * a.ldw + l];
+      }
+    } else {
+      __syncthreads();
+      const double* src = (pass == 2) ? a.W : slot;
+      const int64_t lds = (pass == 2) ? a.ldw : s;
+      for (int idx = tid; idx < rows * s; idx += kThreads) {
+        const int r = idx / s, l = idx - r * s;
+        double t = src[(grow0 + r) * lds + l];
+        for (int q = 0; q < k; ++q) t -= (double)A[r * Kt + q] * Plast[q * s + l];
+        Tm[r * s + l] = t;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < rows * s; idx += kThreads) {
+        const int r = idx / s, l = idx - r * s;
+        double y = 0.0;
+        for (int j = 0; j <= l; ++j) y += Tm[r * s + j] * Ninv[j * s + l];
+        A[r * Kt + k + l] = (TileT)y;
+        slot[(grow0 + r) * s + l] = y;
+      }
+    }
+    __syncthreads();
+    if (active) {
+      for (int r = g; r < rows; r += G) {
+        const TileT* Ar = A + r * Kt;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          if (j < J) {
+            const int e = (G == 1) ? tid + j * kThreads : tid - g * E;
+            if (e < E) {
+              const int q = e / s, l = e - q * s;
+              acc[j] += (Acc)Ar[q] * (Acc)Ar[k + l];
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  double* out = a.part + (int64_t)blockIdx.x * a.Kmax * s;
+  if (G == 1) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int e = tid + j * kThreads;
+      if (j < J && e < E) out[e] = (double)acc[j];
+    }
+  } else {
+    // fixed-order sum over the G row groups
+    double* red = reinterpret_cast<double*>(smem_raw);
+    if (active) red[tid] = (double)acc[0];
+    __syncthreads();
+    if (tid < E) {
+      double v = 0.0;
+      for (int gg = 0; gg < G; ++gg) v += red[gg * E + tid];
+      out[tid] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf factorization of pass `pass`, one CTA per chunk: sum the slab partials
+// in slab order, then N = chol(G - P^T P) (Alg. 7), N^{-1}, and the
+// reiteration bookkeeping of Alg. 8: P_comb <- P_comb + P N_comb,
+// N_comb <- N N_comb.  Decides on the next pass from kappa_F(N).
+__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel) {
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s, ss = s * s;
+  double* C = sm;             // Kt x s
+  double* M = C + E;          // s x s
+  double* Ni = M + ss;        // s x s
+  double* Nc = Ni + ss;       // s x s (old N_comb)
+  double* tmp = Nc + ss;      // s x s
+  double* red = tmp + ss;     // 4
+  const int sl0 = a.chunk_slab0[c], sl1 = a.chunk_slab0[c + 1];
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int sl = sl0; sl < sl1; ++sl) v += a.part[(int64_t)sl * a.Kmax * s + e];
+    C[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, j = e - i * s;
+    double m = C[(k + i) * s + j];
+    for (int q = 0; q < k; ++q) m -= C[q * s + i] * C[q * s + j];
+    M[e] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < s; ++i) tr += C[(k + i) * s + i];
+    red[1] = tr;
+  }
+  __syncthreads();
+  const double trG = red[1];
+  if (shift_rel > 0.0) {  // shifted Cholesky (first pass of the mixed form)
+    for (int i = threadIdx.x; i < s; i += blockDim.x) M[i * s + i] += shift_rel * trG;
+    __syncthreads();
+  }
+  const double tol = (double)s * DBL_EPSILON * trG;
+  cta_cholesky(M, s, tol, a.flags);
+  cta_upper_inverse(M, Ni, s);
+  const double kap = cta_pip_kappa(trG, Ni, s, red);
+
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  double* Plast = smallc + SL.P_last;
+  double* Pcomb = smallc + SL.P_comb;
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) Plast[e] = C[e];
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    smallc[SL.N_last + e] = M[e];
+    smallc[SL.Ninv_last + e] = Ni[e];
+    Nc[e] = (pass == 1) ? 0.0 : smallc[SL.N_comb + e];
+  }
+  __syncthreads();
+  if (pass == 1) {
+    for (int e = threadIdx.x; e < k * s; e += blockDim.x) Pcomb[e] = C[e];
+    for (int e = threadIdx.x; e < ss; e += blockDim.x) smallc[SL.N_comb + e] = M[e];
+  } else {
+    // P_comb += P Nc_old ; N_comb = N Nc_old
+    for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+      const int q = e / s, l = e - q * s;
+      double v = Pcomb[e];
+      for (int j = 0; j <= l; ++j) v += C[q * s + j] * Nc[j * s + l];
+      Pcomb[e] = v;
+    }
+    cta_matmul_ss(M, Nc, tmp, s);
+    for (int e = threadIdx.x; e < ss; e += blockDim.x) smallc[SL.N_comb + e] = tmp[e];
+  }
+  if (threadIdx.x == 0 && pass < kMaxPass) {
+    const bool auto_mode = (a.leaf == LO_LEAF_AUTO) || (a.precision == LO_PREC_MIXED_FP32);
+    if (auto_mode && !(DBL_EPSILON * kap * kap <= a.refine_tol))
+      atomicOr(&a.flags[kFlagPass + pass], 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reduction step (Sec. 4.1), solved with BCGS-PIP on the stacked factors
+// [[T_i, X_i], [0, Nx_i]], reiterated as in Alg. 8 when needed.
+// Iteration `it` input: (P_comb, N_comb) for it = 1, else (P_hat, N_hat).
+
+// z_i = [T_i^T X_i ; X_i^T X_i + Nx_i^T Nx_i]  ((k + s) x s)
+__global__ void __launch_bounds__(kThreads) k_tree_contrib(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, s = a.s, k = a.nb * s, ss = s * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  const double* Xg = smallc + (it == 1 ? SL.P_comb : SL.P_hat);
+  const double* Nxg = smallc + (it == 1 ? SL.N_comb : SL.N_hat);
+  double* X = sm;            // k x s
+  double* Nx = X + k * s;    // s x s
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) X[e] = Xg[e];
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) Nx[e] = Nxg[e];
+  __syncthreads();
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* Z = smallc + SL.Z;
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+    const int q = e / s, l = e - q * s, cb = q / s, qq = q - cb * s;
+    const double* Tb = Tc + tblock_offset(cb, s);   // ((cb+1) s) x s
+    double v = 0.0;
+    for (int r = 0; r < (cb + 1) * s; ++r) v += Tb[r * s + qq] * X[r * s + l];
+    Z[e] = v;
+  }
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, j = e - i * s;
+    double v = 0.0;
+    for (int r = 0; r < k; ++r) v += X[r * s + i] * X[r * s + j];
+    for (int r = 0; r < s; ++r) v += Nx[r * s + i] * Nx[r * s + j];
+    Z[k * s + e] = v;
+  }
+}
+
+// First level of the fixed-order sum over chunks: group g sums chunks
+// [g * kTreeGroup, (g + 1) * kTreeGroup) in index order.
+__global__ void __launch_bounds__(kThreads) k_tree_sum1(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  const int s = a.s, E = (a.nb * s + s) * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const int c0 = blockIdx.x * kTreeGroup, c1 = min(a.p, c0 + kTreeGroup);
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int c = c0; c < c1; ++c) v += a.small[(int64_t)c * SL.stride + SL.Z + e];
+    a.tsum[(int64_t)blockIdx.x * a.Kmax * s + e] = v;
+  }
+}
+
+// Second level + the small factorization of the reduction PQR:
+// P = sum T_i^T X_i, G = sum (X_i^T X_i + Nx_i^T Nx_i), N = chol(G - P^T P);
+// accumulates P_acc <- P_acc + P N_acc, N_acc <- N N_acc (Alg. 8 combine).
+__global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int ngroups) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  const int s = a.s, k = a.nb * s, E = (k + s) * s, ss = s * s;
+  const GlobLayout GL = GlobLayout::make(a.Kmax, s);
+  double* Z = a.glob + GL.Zsum;
+  double* M = sm;
+  double* Ni = M + ss;
+  double* Na = Ni + ss;
+  double* tmp = Na + ss;
+  double* red = tmp + ss;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < ngroups; ++g) v += a.tsum[(int64_t)g * a.Kmax * s + e];
+    Z[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, j = e - i * s;
+    double m = Z[(k + i) * s + j];
+    for (int q = 0; q < k; ++q) m -= Z[q * s + i] * Z[q * s + j];
+    M[e] = m;
+  }
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < s; ++i) tr += Z[(k + i) * s + i];
+    red[1] = tr;
+  }
+  __syncthreads();
+  const double trG = red[1];
+  cta_cholesky(M, s, (double)s * DBL_EPSILON * trG, a.flags);
+  cta_upper_inverse(M, Ni, s);
+  const double kap = cta_pip_kappa(trG, Ni, s, red);
+  double* P_it = a.glob + GL.P_it;
+  double* P_acc = a.glob + GL.P_acc;
+  double* N_acc = a.glob + GL.N_acc;
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) P_it[e] = Z[e];
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    a.glob[GL.N_it + e] = M[e];
+    a.glob[GL.Ninv_it + e] = Ni[e];
+    Na[e] = (it == 1) ? 0.0 : N_acc[e];
+  }
+  __syncthreads();
+  if (it == 1) {
+    for (int e = threadIdx.x; e < k * s; e += blockDim.x) P_acc[e] = Z[e];
+    for (int e = threadIdx.x; e < ss; e += blockDim.x) N_acc[e] = M[e];
+  } else {
+    for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+      const int q = e / s, l = e - q * s;
+      double v = P_acc[e];
+      for (int j = 0; j <= l; ++j) v += Z[q * s + j] * Na[j * s + l];
+      P_acc[e] = v;
+    }
+    cta_matmul_ss(M, Na, tmp, s);
+    for (int e = threadIdx.x; e < ss; e += blockDim.x) N_acc[e] = tmp[e];
+  }
+  if (threadIdx.x == 0 && it < kMaxTreeIter) {
+    if (a.reduction == 0 && !(DBL_EPSILON * kap * kap <= a.refine_tol))
+      atomicOr(&a.flags[kFlagTree + it], 1);
+  }
+}
+
+// Per chunk: X_hat = (X - T_i P) N^{-1}, Nx_hat = Nx N^{-1}; the result is
+// also written as column block nb of T_i: [Pt_i; Nt_i] (Alg. 9 output).
+__global__ void __launch_bounds__(kThreads) k_tree_update(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x, s = a.s, k = a.nb * s, ss = s * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const GlobLayout GL = GlobLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  const double* Xg = smallc + (it == 1 ? SL.P_comb : SL.P_hat);
+  const double* Nxg = smallc + (it == 1 ? SL.N_comb : SL.N_hat);
+  const double* Pg = a.glob + GL.P_it;
+  const double* Ninv = a.glob + GL.Ninv_it;
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* t = sm;           // k x s
+  double* Nx = t + k * s;   // s x s
+  double* Nin = Nx + ss;    // s x s
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    Nx[e] = Nxg[e];
+    Nin[e] = Ninv[e];
+  }
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+    const int r = e / s, l = e - r * s;
+    double v = Xg[e];
+    for (int cb = r / s; cb < a.nb; ++cb) {
+      const double* Tb = Tc + tblock_offset(cb, s);
+      for (int qq = 0; qq < s; ++qq) v -= Tb[r * s + qq] * Pg[(cb * s + qq) * s + l];
+    }
+    t[e] = v;
+  }
+  __syncthreads();
+  double* Ph = smallc + SL.P_hat;
+  double* Tnew = a.T + (int64_t)c * a.tstride + tblock_offset(a.nb, s);  // (k + s) x s
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+    const int r = e / s, l = e - r * s;
+    double v = 0.0;
+    for (int j = 0; j <= l; ++j) v += t[r * s + j] * Nin[j * s + l];
+    Ph[e] = v;
+    Tnew[e] = v;
+  }
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, l = e - i * s;
+    double v = 0.0;
+    if (i <= l)
+      for (int j = i; j <= l; ++j) v += Nx[i * s + j] * Nin[j * s + l];
+    smallc[SL.N_hat + e] = v;
+    Tnew[k * s + e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2 (assembly, Sec. 4.1): per row of chunk i,
+//   u = (A_last - q P_last) N_last^{-1}   -> new local panel (U_i)
+//   out = q Pt_i + u Nt_i                 -> caller's U
+// where A_last is W (one pass) or the stored previous iterate.
+__global__ void __launch_bounds__(kThreads) k_update(StepArgs a, int tile_rows) {
+  extern __shared__ __align__(16) double sm[];
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int s = a.s, k = a.nb * s;
+  const int L = passes_run(a);
+  double* slot = a.V + (int64_t)a.nb * a.n * s;
+  const double* src = (L == 1) ? a.W : slot;
+  const int64_t lds = (L == 1) ? a.ldw : s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const double* smallc = a.small + (int64_t)si.chunk * SL.stride;
+  const double* Plast = smallc + SL.P_last;
+  const double* Ninv = smallc + SL.Ninv_last;
+  const double* Tb = a.T + (int64_t)si.chunk * a.tstride + tblock_offset(a.nb, s);
+  const double* Pt = Tb;            // k x s
+  const double* Nt = Tb + k * s;    // s x s
+  double* Aq = sm;                          // tile_rows x k
+  double* Tm = Aq + tile_rows * k;          // tile_rows x s
+  double* Us = Tm + tile_rows * s;          // tile_rows x s
+  const int tid = threadIdx.x;
+  for (int r0 = 0; r0 < si.rows; r0 += tile_rows) {
+    const int rows = min(tile_rows, si.rows - r0);
+    const int64_t grow0 = si.row0 + r0;
+    for (int idx = tid; idx < rows * k; idx += kThreads) {
+      const int b = idx / (rows * s), rem = idx - b * rows * s, r = rem / s, j = rem - r * s;
+      Aq[r * k + b * s + j] = a.V[(int64_t)b * a.n * s + (grow0 + r) * s + j];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += kThreads) {
+      const int r = idx / s, l = idx - r * s;
+      double t = src[(grow0 + r) * lds + l];
+      for (int q = 0; q < k; ++q) t -= Aq[r * k + q] * Plast[q * s + l];
+      Tm[idx] = t;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += kThreads) {
+      const int r = idx / s, l = idx - r * s;
+      double u = 0.0;
+      for (int j = 0; j <= l; ++j) u += Tm[r * s + j] * Ninv[j * s + l];
+      Us[idx] = u;
+      slot[(grow0 + r) * s + l] = u;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rows * s; idx += kThreads) {
+      const int r = idx / s, l = idx - r * s;
+      double o = 0.0;
+      for (int q = 0; q < k; ++q) o += Aq[r * k + q] * Pt[q * s + l];
+      for (int j = 0; j <= l; ++j) o += Us[r * s + j] * Nt[j * s + l];
+      a.U[(grow0 + r) * a.ldu + l] = o;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// apply_Q: Z_i = T_i C (k x m) per chunk, then Y_i = Q_i Z_i.
+__global__ void __launch_bounds__(kThreads) k_apply_z(StepArgs a, const double* C, int m,
+                                                      int64_t ldc, double* Z) {
+  const int c = blockIdx.x, s = a.s, k = a.nb * s;
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* Zc = Z + (int64_t)c * k * m;
+  for (int e = threadIdx.x; e < k * m; e += blockDim.x) {
+    const int r = e / m, j = e - r * m;
+    double v = 0.0;
+    for (int cb = r / s; cb < a.nb; ++cb) {
+      const double* Tb = Tc + tblock_offset(cb, s);
+      for (int qq = 0; qq < s; ++qq) v += Tb[r * s + qq] * C[(int64_t)(cb * s + qq) * ldc + j];
+    }
+    Zc[e] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_apply_y(StepArgs a, int m, const double* Z, double* Y,
+                                                      int64_t ldy, int tile_rows) {
+  extern __shared__ __align__(16) double sm[];
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int s = a.s, k = a.nb * s;
+  const double* Zc = Z + (int64_t)si.chunk * k * m;
+  double* Aq = sm;
+  for (int r0 = 0; r0 < si.rows; r0 += tile_rows) {
+    const int rows = min(tile_rows, si.rows - r0);
+    const int64_t grow0 = si.row0 + r0;
+    for (int idx = threadIdx.x; idx < rows * k; idx += kThreads) {
+      const int b = idx / (rows * s), rem = idx - b * rows * s, r = rem / s, j = rem - r * s;
+      Aq[r * k + b * s + j] = a.V[(int64_t)b * a.n * s + (grow0 + r) * s + j];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rows * m; idx += kThreads) {
+      const int r = idx / m, j = idx - r * m;
+      double v = 0.0;
+      for (int q = 0; q < k; ++q) v += Aq[r * k + q] * Zc[q * m + j];
+      Y[(grow0 + r) * ldy + j] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// 2D 5-point Laplacian with homogeneous Dirichlet boundary, s columns.
+__global__ void k_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,
+                           int64_t ldy) {
+  const int64_t total = (int64_t)nx * ny * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pt = e / s;
+    const int l = (int)(e - pt * s);
+    const int ix = (int)(pt % nx), iy = (int)(pt / nx);
+    double v = 4.0 * X[pt * ldx + l];
+    if (ix > 0) v -= X[(pt - 1) * ldx + l];
+    if (ix < nx - 1) v -= X[(pt + 1) * ldx + l];
+    if (iy > 0) v -= X[(pt - nx) * ldx + l];
+    if (iy < ny - 1) v -= X[(pt + nx) * ldx + l];
+    Y[pt * ldy + l] = v;
+  }
+}
+
+// Shared-memory budget of the streaming kernels (bytes).
+constexpr int kTileSmem = 96 * 1024;
+
+int gram_tile_rows(int Kt, int s, int elem) {
+  int r = (kTileSmem - 8 * 32 * s) / (elem * Kt);
+  return r < 1 ? 1 : (r > 32 ? 32 : r);
+}
+
+int update_tile_rows(int k, int s) {
+  int per_row = 8 * (k + 2 * s);
+  int r = kTileSmem / per_row;
+  return r < 1 ? 1 : (r > 32 ? 32 : r);
+}
+
+bool g_attr_done = false;
+
+cudaError_t set_attrs() {
+  if (g_attr_done) return cudaSuccess;
+  const int big = 200 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_gram<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_gram<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_contrib, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_sum2, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_apply_y, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  g_attr_done = true;
+  return cudaSuccess;
+}
+
+std::atomic<long long> g_launches{0};
+
+inline void mark(ProfHook* h, int kind, bool begin, cudaStream_t st) {
+  if (h) h->mark(kind, begin, st);
+}
+
+}  // namespace
+
+long long launches() { return g_launches.load(); }
+void count_launches(int k) { g_launches += k; }
+
+cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
+  cudaError_t e = set_attrs();
+  if (e) return e;
+  const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
+  const bool mixed = (a.precision == LO_PREC_MIXED_FP32);
+  k_step_begin<<<1, 32, 0, st>>>(a.flags, (a.leaf == LO_LEAF_PIP2) || mixed, a.reduction == 2);
+  count_launches(1);
+  // stage 1
+  const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
+  for (int pass = 1; pass <= maxpass; ++pass) {
+    mark(hook, kKindGram, true, st);
+    if (pass == 1 && mixed) {
+      const int tr = gram_tile_rows(Kt, s, 4);
+      const size_t sm = (((size_t)4 * tr * Kt + 15) & ~(size_t)15) + 8 * (size_t)tr * s + 8 * kThreads;
+      k_gram<float, float><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
+    } else {
+      const int tr = gram_tile_rows(Kt, s, 8);
+      const size_t sm = (size_t)8 * tr * Kt + 8 * (size_t)tr * s + 8 * kThreads;
+      k_gram<double, double><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
+    }
+    mark(hook, kKindGram, false, st);
+    // shifted Cholesky for the float32 first pass: relative shift of the trace
+    const double shift = (pass == 1 && mixed) ? 1e-5 : 0.0;
+    const size_t smleaf = 8 * ((size_t)Kt * s + 4 * ss + 4);
+    mark(hook, kKindLeaf, true, st);
+    k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift);
+    mark(hook, kKindLeaf, false, st);
+    count_launches(2);
+  }
+  // reduction
+  const int ngroups = (a.p + kTreeGroup - 1) / kTreeGroup;
+  mark(hook, kKindTree, true, st);
+  for (int it = 1; it <= (a.reduction == 1 ? 1 : kMaxTreeIter); ++it) {
+    k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
+    k_tree_sum1<<<ngroups, kThreads, 0, st>>>(a, it);
+    k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
+    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
+    count_launches(4);
+  }
+  mark(hook, kKindTree, false, st);
+  // stage 2
+  const int tu = update_tile_rows(k, s);
+  mark(hook, kKindUpdate, true, st);
+  k_update<<<a.nslab, kThreads, (size_t)8 * tu * (k + 2 * s), st>>>(a, tu);
+  mark(hook, kKindUpdate, false, st);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ldc, double* Z,
+                           double* Y, int64_t ldy, cudaStream_t st, ProfHook* hook) {
+  cudaError_t e = set_attrs();
+  if (e) return e;
+  const int k = a.nb * a.s;
+  mark(hook, kKindApply, true, st);
+  k_apply_z<<<a.p, kThreads, 0, st>>>(a, C, m, ldc, Z);
+  int tr = kTileSmem / (8 * (k > 0 ? k : 1));
+  tr = tr < 1 ? 1 : (tr > 32 ? 32 : tr);
+  k_apply_y<<<a.nslab, kThreads, (size_t)8 * tr * k, st>>>(a, m, Z, Y, ldy, tr);
+  mark(hook, kKindApply, false, st);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, cudaStream_t st) {
+  const int64_t total = (int64_t)nx * ny * s;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  k_laplace5<<<(int)blocks, 256, 0, st>>>(nx, ny, s, X, ldx, Y, ldy);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace lo

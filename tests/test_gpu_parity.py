@@ -1,0 +1,332 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison uses the same seeded float64 inputs on both sides.  The PQR
+solution (U, P, N with diag(N) > 0) and the locally orthogonal representation
+(local Q_i and tree factors T_i) are unique, so they are compared element by
+element with the oracle's Householder-based TreeTSPQR.
+
+Tolerances (float64 path): relative Frobenius error of U, H, R, Q_i, T_i
+<= 1e-10; ||Q^T Q - I||_F <= 1e-12; ||A - QR||_F / ||A||_F <= 1e-13.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import lo_oracle as O
+from paper_2204_13393_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_REL = 1e-10
+TOL_PERP = 1e-12
+TOL_RES = 1e-13
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_13393_gb300 import lo
+
+    lo.library()
+    torch.cuda.set_device(0)
+
+
+def lo():
+    from paper_2204_13393_gb300 import lo as L
+
+    return L
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(x):
+    torch.cuda.synchronize()
+    return x.detach().cpu().numpy()
+
+
+def run_and_compare(n, s, M, cr, blocks, oracle_local="hh", oracle_reduction="hh", check_local=True,
+                    **opts):
+    """Orthogonalize `blocks` one after another on the GPU and in the oracle;
+    compare every output and the representation.  Returns the GPU basis."""
+    b = lo().Basis(n, s, M, cr, **opts)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    assert b.num_chunks == len(ora.bounds)
+    A = np.hstack(blocks)
+    Rfull = np.zeros((A.shape[1], A.shape[1]))
+    for j, Wh in enumerate(blocks):
+        U, H, R = b.orthogonalize(dev(Wh))
+        Uo, Po, No = ora.orthogonalize(Wh, oracle_local, oracle_reduction)
+        assert rel(host(U), Uo) <= TOL_REL, (j, rel(host(U), Uo))
+        assert rel(host(R), No) <= TOL_REL, (j, rel(host(R), No))
+        if j > 0:
+            assert rel(host(H), Po) <= TOL_REL, (j, rel(host(H), Po))
+            Rfull[:j * s, j * s:(j + 1) * s] = host(H)
+        Rfull[j * s:(j + 1) * s, j * s:(j + 1) * s] = host(R)
+        assert np.all(np.diag(host(R)) > 0)
+        assert np.all(np.tril(host(R), -1) == 0)
+    assert b.num_blocks == len(blocks)
+    Q = host(b.apply_Q(dev(np.eye(b.k))))
+    assert O.e_perp(Q) <= TOL_PERP
+    assert O.residual(A, Q, Rfull) <= TOL_RES
+    assert rel(Q, ora.explicit()) <= TOL_REL
+    if check_local:
+        Tg = 0
+        for c in range(b.num_chunks):
+            Qi, Ti = b.export_chunk(c)
+            assert rel(Qi, ora.Qloc[c]) <= TOL_REL, c
+            assert rel(Ti, np.triu(ora.T[c])) <= TOL_REL, c
+            assert O.e_perp(Qi) <= TOL_PERP
+            Tg = Tg + Ti.T @ Ti
+        assert np.abs(Tg - np.eye(b.k)).max() <= TOL_PERP
+    return b
+
+
+def gaussian_blocks(n, s, count, seed0):
+    return [I.gaussian(n, s, seed0 + j) for j in range(count)]
+
+
+def test_arnoldi_step_small_workload():
+    """n = 4096, s = 4, chunk_rows = 512: 8 prior blocks from seeded N(0,1)
+    blocks, then the new block; outputs H (32 x 4) and R (4 x 4)."""
+    n, s = 4096, 4
+    b = run_and_compare(n, s, 9, 512, gaussian_blocks(n, s, 9, I.seed_for(1)))
+    assert b.k == 36
+
+
+@pytest.mark.parametrize("n,s,cr,M", [
+    (5000, 4, 512, 6),      # ragged last chunk (904 rows), ragged slabs
+    (777, 2, 100, 5),       # small chunks, 7 chunks, last 177 rows
+    (300, 8, 1000, 4),      # one chunk (n < chunk_rows)
+    (2048, 1, 256, 8),      # s = 1
+    (4099, 16, 1024, 4),    # s = 16, ragged
+    (3000, 32, 1000, 3),    # s = 32 (maximum width)
+    (65573, 8, 4096, 6),    # many slabs per chunk, ragged
+])
+def test_shapes_and_ragged(n, s, cr, M):
+    run_and_compare(n, s, M, cr, gaussian_blocks(n, s, M, 1000 + n + s))
+
+
+@pytest.mark.parametrize("leaf", ["pip", "pip2", "auto"])
+@pytest.mark.parametrize("reduction", ["pip", "pip2", "auto"])
+def test_leaf_and_reduction_modes(leaf, reduction):
+    n, s = 6000, 4
+    run_and_compare(n, s, 5, 700, gaussian_blocks(n, s, 5, 2000), leaf=leaf, reduction=reduction,
+                    check_local=False)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+def test_stewart_block_qr(kappa):
+    """Alg. 2 on a Stewart matrix (32 columns, s = 4) with the automatic
+    reiteration: orthogonality and residual at float64 level; H and R are
+    compared with the oracle where their forward error kappa*eps allows."""
+    n, m, s = 16384, 32, 4
+    A = I.stewart(n, m, kappa, 500 + int(np.log10(kappa)))
+    blocks = [A[:, j * s:(j + 1) * s].copy() for j in range(m // s)]
+    b = lo().Basis(n, s, m // s, 1024)
+    ora = O.LocallyOrthogonalBasis(n, s, 1024)
+    Rg = np.zeros((m, m))
+    Ro = np.zeros((m, m))
+    for j, Wh in enumerate(blocks):
+        U, H, R = b.orthogonalize(dev(Wh))
+        Uo, Po, No = ora.orthogonalize(Wh, "hh", "hh")
+        if j:
+            Rg[:j * s, j * s:(j + 1) * s] = host(H)
+            Ro[:j * s, j * s:(j + 1) * s] = Po
+        Rg[j * s:(j + 1) * s, j * s:(j + 1) * s] = host(R)
+        Ro[j * s:(j + 1) * s, j * s:(j + 1) * s] = No
+    Q = host(b.apply_Q(dev(np.eye(m))))
+    assert O.e_perp(Q) <= TOL_PERP
+    assert O.residual(A, Q, Rg) <= TOL_RES
+    bound = 100 * kappa * np.finfo(float).eps
+    assert rel(Rg, Ro) <= max(TOL_REL, bound)
+
+
+def test_apply_Q_parity():
+    n, s = 9000, 4
+    b = lo().Basis(n, s, 6, 1000)
+    ora = O.LocallyOrthogonalBasis(n, s, 1000)
+    for j in range(6):
+        Wh = I.gaussian(n, s, 3000 + j)
+        b.orthogonalize(dev(Wh))
+        ora.orthogonalize(Wh, "hh", "hh")
+    for m in (1, 5, 64):
+        C = I.gaussian(b.k, m, 3100 + m)
+        Y = host(b.apply_Q(dev(C)))
+        assert rel(Y, ora.apply_Q(C)) <= TOL_REL
+        # host C and host Y through the same entry point
+        Yh = b.apply_Q(C)
+        assert np.array_equal(Yh, Y)
+
+
+def test_host_buffers_match_device_bitwise():
+    n, s = 5000, 8
+    W = [I.gaussian(n, s, 3200 + j) for j in range(3)]
+    bd = lo().Basis(n, s, 3, 512)
+    bh = lo().Basis(n, s, 3, 512)
+    for Wh in W:
+        Ud, Hd, Rd = bd.orthogonalize(dev(Wh))
+        Uh, Hh, Rh = bh.orthogonalize(Wh)        # numpy in, numpy out
+        assert isinstance(Uh, np.ndarray)
+        assert np.array_equal(host(Ud), Uh)
+        assert np.array_equal(host(Rd), Rh)
+        if Hd is not None:
+            assert np.array_equal(host(Hd), Hh)
+
+
+def test_strided_and_aliased_buffers():
+    """W with a row stride > s, and U written over W in place."""
+    n, s = 4000, 4
+    big = I.gaussian(n, 7, 3300)
+    Wh = big[:, 1:1 + s]
+    b1 = lo().Basis(n, s, 2, 500)
+    b2 = lo().Basis(n, s, 2, 500)
+    b1.orthogonalize(dev(I.gaussian(n, s, 3301)))
+    b2.orthogonalize(dev(I.gaussian(n, s, 3301)))
+    Wd = torch.from_numpy(big).cuda()[:, 1:1 + s]
+    assert Wd.stride(0) == 7
+    U1, _, R1 = b1.orthogonalize(Wd)
+    Wc = dev(Wh)
+    U2, _, R2 = b2.orthogonalize(Wc, U=Wc)
+    assert np.array_equal(host(U1), host(Wc))
+    assert np.array_equal(host(R1), host(R2))
+
+
+def test_bitwise_determinism():
+    n, s = 20000, 8
+    blocks = gaussian_blocks(n, s, 4, 3400)
+    outs = []
+    for _ in range(2):
+        b = lo().Basis(n, s, 4, 2048)
+        res = [tuple(host(x) for x in b.orthogonalize(dev(Wh)) if x is not None) for Wh in blocks]
+        outs.append(res)
+    for r1, r2 in zip(*outs):
+        for x, y in zip(r1, r2):
+            assert np.array_equal(x, y)
+
+
+def test_error_paths_leave_basis_unchanged():
+    L = lo()
+    n, s = 3000, 4
+    b = L.Basis(n, s, 3, 600)
+    b.orthogonalize(dev(I.gaussian(n, s, 3500)))
+    # a block inside the span of the basis: breakdown, block count unchanged
+    Q = host(b.apply_Q(dev(np.eye(s))))
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(dev(Q @ I.gaussian(s, s, 3501)))
+    assert e.value.name == "LO_ERR_BREAKDOWN"
+    assert b.num_blocks == 1
+    # NaN in the block
+    Wn = I.gaussian(n, s, 3502)
+    Wn[17, 2] = np.nan
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(dev(Wn))
+    assert e.value.name in ("LO_ERR_NONFINITE", "LO_ERR_BREAKDOWN")
+    assert b.num_blocks == 1
+    # the basis still works and agrees with the oracle
+    ora = O.LocallyOrthogonalBasis(n, s, 600)
+    ora.orthogonalize(I.gaussian(n, s, 3500), "hh", "hh")
+    Wg = I.gaussian(n, s, 3503)
+    U, H, R = b.orthogonalize(dev(Wg))
+    Uo, Po, No = ora.orthogonalize(Wg, "hh", "hh")
+    assert rel(host(U), Uo) <= TOL_REL
+    b.orthogonalize(dev(I.gaussian(n, s, 3504)))
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(dev(I.gaussian(n, s, 3505)))
+    assert e.value.name == "LO_ERR_CAPACITY"
+    assert b.num_blocks == 3
+
+
+def test_mixed_precision_form():
+    """First Gram pass in float32, shifted Cholesky, float64 refinement: the
+    results meet the float64 tolerances for Gaussian blocks."""
+    n, s = 32768, 16
+    blocks = gaussian_blocks(n, s, 4, 3600)
+    run_and_compare(n, s, 4, 2048, blocks, precision="mixed_fp32", check_local=False)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+def test_mixed_precision_stewart(kappa):
+    n, m, s = 32768, 32, 16
+    A = I.stewart(n, m, kappa, 600 + int(np.log10(kappa)))
+    b = lo().Basis(n, s, 2, 4096, precision="mixed_fp32")
+    U0, _, R0 = b.orthogonalize(dev(A[:, :s].copy()))
+    U1, H1, R1 = b.orthogonalize(dev(A[:, s:].copy()))
+    Q = host(b.apply_Q(dev(np.eye(m))))
+    R = np.zeros((m, m))
+    R[:s, :s] = host(R0)
+    R[:s, s:] = host(H1)
+    R[s:, s:] = host(R1)
+    assert O.e_perp(Q) <= TOL_PERP
+    assert O.residual(A, Q, R) <= TOL_RES
+
+
+def test_batched_uneven():
+    L = lo()
+    specs = [(5000, 4, 3), (12000, 8, 2), (3001, 16, 2), (9000, 4, 5)]
+    bases, oras, Ws, Us, Hs, Rs, want = [], [], [], [], [], [], []
+    for i, (n, s, kb) in enumerate(specs):
+        cr = max(512, (kb + 1) * s)
+        b = L.Basis(n, s, kb + 1, cr)
+        o = O.LocallyOrthogonalBasis(n, s, cr)
+        for j in range(kb):
+            Wh = I.gaussian(n, s, 3700 + 10 * i + j)
+            b.orthogonalize(dev(Wh))
+            o.orthogonalize(Wh, "hh", "hh")
+        Wh = I.gaussian(n, s, 3790 + i)
+        want.append(o.orthogonalize(Wh, "hh", "hh"))
+        bases.append(b)
+        Ws.append(dev(Wh))
+        Us.append(torch.empty(n, s, dtype=torch.float64, device="cuda"))
+        Hs.append(torch.empty(kb * s, s, dtype=torch.float64, device="cuda"))
+        Rs.append(torch.empty(s, s, dtype=torch.float64, device="cuda"))
+    L.orthogonalize_batched(bases, Ws, Us, Hs, Rs)
+    for b, (Uo, Po, No), U, H, R in zip(bases, want, Us, Hs, Rs):
+        assert rel(host(U), Uo) <= TOL_REL
+        assert rel(host(H), Po) <= TOL_REL
+        assert rel(host(R), No) <= TOL_REL
+        assert b.num_blocks == len(Po) // b.s + 1
+
+
+def test_laplace5_operator():
+    nx, ny, s = 37, 23, 3
+    X = I.uniform(nx * ny, s, 3800)
+    Y = host(lo().laplace5_apply(nx, ny, dev(X), torch.empty(nx * ny, s, dtype=torch.float64, device="cuda")))
+    G = X.reshape(ny, nx, s)
+    ref = 4 * G
+    ref[:, 1:] -= G[:, :-1]
+    ref[:, :-1] -= G[:, 1:]
+    ref[1:] -= G[:-1]
+    ref[:-1] -= G[1:]
+    assert np.abs(Y - ref.reshape(-1, s)).max() <= 1e-14
+
+
+def test_full_size_sampled_rows():
+    """The block-GMRes workload's sizes (n = 2^20, s = 8, 4096-row chunks):
+    three independent Gaussian blocks; every output compared with the oracle
+    (BCGS-PIP+ sub-algorithms) on 4096 sampled rows and in full for H, R."""
+    n, s, cr = 2 ** 20, 8, 4096
+    blocks = gaussian_blocks(n, s, 3, 3900)
+    b = lo().Basis(n, s, 31, cr)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    rows = np.sort(I.rng(3999).choice(n, 4096, replace=False))
+    for j, Wh in enumerate(blocks):
+        U, H, R = b.orthogonalize(dev(Wh))
+        Uo, Po, No = ora.orthogonalize(Wh, "pip2", "pip2")
+        assert rel(host(U)[rows], Uo[rows]) <= TOL_REL
+        assert rel(host(R), No) <= TOL_REL
+        if j:
+            assert rel(host(H), Po) <= TOL_REL
+    Q = b.apply_Q(dev(np.eye(b.k)))
+    G = (Q.T @ Q).cpu().numpy()
+    assert np.linalg.norm(G - np.eye(b.k)) <= TOL_PERP

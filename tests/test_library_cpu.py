@@ -1,0 +1,93 @@
+"""Host-side checks that need no GPU: the library builds, loads, exports every
+symbol include/lo.h declares, and rejects bad arguments before any device work."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_13393_gb300 import build, lo
+
+    if not os.path.exists(lo.LIB_PATH):
+        build.build()
+    return lo.library()
+
+
+def declared_symbols():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(lo_[a-zA-Z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ["lo_basis_create", "lo_orthogonalize", "lo_apply_Q", "lo_basis_destroy",
+                 "lo_orthogonalize_batched"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_exports(lib):
+    from paper_2204_13393_gb300 import lo
+
+    assert set(lo.EXPORTED) <= set(declared_symbols())
+
+
+def test_status_strings(lib):
+    for code in range(10):
+        assert lib.lo_status_string(code)
+    assert lib.lo_status_string(4).decode().startswith("Cholesky")
+
+
+def test_create_rejects_bad_arguments_without_device(lib):
+    """Validation happens before any CUDA call, so it runs on a CPU-only host."""
+    from paper_2204_13393_gb300 import lo
+
+    h = ctypes.c_void_p()
+    cases = [
+        ((0, 4, 8, 512), 1),           # n < 1
+        ((4096, 0, 8, 512), 1),        # s < 1
+        ((4096, 33, 8, 512), 1),       # s > 32
+        ((4096, 4, 0, 512), 1),        # max_blocks < 1
+        ((4096, 32, 64, 4096), 1),     # max_blocks*s > 1024 ... and k*s too large
+        ((4096, 4, 8, 16), 3),         # chunk_rows < max_blocks*s
+        ((20, 4, 8, 512), 3),          # single chunk with n < max_blocks*s
+    ]
+    for (n, s, M, cr), want in cases:
+        code = lib.lo_basis_create(n, s, M, cr, None, None, ctypes.byref(h))
+        assert code == want, ((n, s, M, cr), code)
+        assert h.value is None
+    bad = lo.Options()
+    lib.lo_options_default(ctypes.byref(bad))
+    bad.leaf = 7
+    assert lib.lo_basis_create(4096, 4, 8, 512, ctypes.byref(bad), None, ctypes.byref(h)) == 1
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.lo_orthogonalize(None, None, 4, None, 4, None, None) == 1
+    assert lib.lo_apply_Q(None, None, 1, 1, None, 1) == 1
+    assert lib.lo_basis_num_blocks(None) == -1
+    lib.lo_basis_destroy(None)
+
+
+def test_options_default(lib):
+    from paper_2204_13393_gb300 import lo
+
+    o = lo.Options()
+    lib.lo_options_default(ctypes.byref(o))
+    assert (o.precision, o.leaf, o.reduction, o.sync) == (0, 0, 0, 1)
+    assert o.refine_tol == pytest.approx(1e-13)
