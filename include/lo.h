@@ -195,6 +195,41 @@ lo_status lo_basis_last_step_info(lo_basis* b, int32_t* passes, int32_t* tree_it
 lo_status lo_basis_set_profiling(lo_basis* b, int32_t enable);
 lo_status lo_basis_profile_read(lo_basis* b, double* ms, int64_t* intervals, int32_t nkinds);
 
+/*
+ * Allocation-free tall-skinny QR: W = U R with the first step of the method
+ * (empty basis, k = 0: local Gram per chunk, leaf Cholesky with reiteration
+ * when needed, reduction of the stacked factors, assembly of U), for callers
+ * that cannot allocate device memory: code that runs where the memory budget
+ * is fixed up front (an application that owns every device allocation through
+ * its own pool, a process that must not grow its footprint after start-up) or
+ * a host thread for which cudaMalloc/cudaFree, with their implicit device
+ * synchronization, are not permitted.  The paper has no counterpart; it is an
+ * interface variant of the k = 0 step of lo_orthogonalize.
+ *
+ *   n, s, chunk_rows  as for lo_basis_create with max_blocks = 1 (1 <= s <= 32,
+ *                     every chunk at least s rows);
+ *   W                 device, n x s, row stride ldw >= s (read only);
+ *   U                 device, n x s, row stride s (written; it is also the
+ *                     working panel of the step).  U may equal W when
+ *                     ldw == s (in place); otherwise they must not overlap;
+ *   R                 device, s x s row-major, upper triangular, diag > 0;
+ *   cuda_stream       cudaStream_t of the current device (NULL = default).
+ *
+ * It allocates nothing: all scratch is one fixed 16 MiB array in device
+ * memory that every device loading the library holds until the process exits.
+ * A problem whose scratch does not fit (roughly p chunks * (8 s^2 + 1) doubles
+ * plus one s x s tile per 256-row slab) returns LO_ERR_CAPACITY before any
+ * device work.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) once for the device; make that first call
+ * before any stream capture.  Every call shares the array and leaves its
+ * contents behind, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialized by the caller.  The call waits for its
+ * stream and returns the step's status (LO_ERR_BREAKDOWN for a numerically
+ * rank-deficient W, LO_ERR_NONFINITE for NaN/Inf).
+ */
+lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, const double* W, int64_t ldw,
+                          double* U, double* R, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* lo_status_string(lo_status st);
 

@@ -705,3 +705,166 @@ cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx,
 }
 
 }  // namespace lo
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the first step (k = 0, a tall-skinny QR W = U R)
+// for callers that may not allocate device memory.  All scratch of the step
+// (flags, slab tables, Gram partials, per-chunk and global small matrices,
+// tree factors) lives in one fixed file-scope device array; the caller's U is
+// the working panel.  The kernels are the ones of the basis path, unchanged.
+namespace lo {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::atomic<void*> g_noalloc_ptr[kNoAllocMaxDevices];
+
+__global__ void k_noalloc_tables(int64_t n, int cr, int p, int slab_rows, int spc, int spl,
+                                 SlabInfo* slabs, int32_t* chunk_slab0, int64_t* chunk_row0) {
+  const int nslab = (p - 1) * spc + spl;
+  const int64_t rows_last = n - (int64_t)(p - 1) * cr;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nslab; i += gridDim.x * blockDim.x) {
+    int c, j;
+    int64_t crows;
+    if (i < (p - 1) * spc) {
+      c = i / spc;
+      j = i - c * spc;
+      crows = cr;
+    } else {
+      c = p - 1;
+      j = i - (p - 1) * spc;
+      crows = rows_last;
+    }
+    SlabInfo si;
+    si.row0 = (int64_t)c * cr + (int64_t)j * slab_rows;
+    const int64_t left = crows - (int64_t)j * slab_rows;
+    si.rows = (int32_t)(left < slab_rows ? left : slab_rows);
+    si.chunk = c;
+    slabs[i] = si;
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= p; c += gridDim.x * blockDim.x) {
+    chunk_slab0[c] = (c < p) ? c * spc : nslab;
+    chunk_row0[c] = (c < p) ? (int64_t)c * cr : n;
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace lo
+
+extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, const double* W,
+                                     int64_t ldw, double* U, double* R, void* cuda_stream) {
+  using namespace lo;
+  if (n < 1 || s < 1 || s > kMaxS || chunk_rows < 1 || !W || !U || !R || ldw < s) return LO_ERR_INVALID_ARG;
+  if (U == W) {
+    if (ldw != s) return LO_ERR_INVALID_ARG;  // in place only with a contiguous block
+  } else {
+    const double* wend = W + (n - 1) * ldw + s;  // distinct buffers must not overlap
+    const double* uend = U + n * s;
+    if (!(uend <= W || wend <= U)) return LO_ERR_INVALID_ARG;
+  }
+  const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
+  if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
+  const int p = (int)p64;
+  const int64_t min_rows = (p == 1) ? n : chunk_rows;
+  if (min_rows < s) return LO_ERR_CHUNK_TOO_SMALL;
+  const int slab_rows = 16 * s > 256 ? 16 * s : 256;
+  const int64_t rows_last = n - (int64_t)(p - 1) * chunk_rows;
+  const int spc = (int)((chunk_rows + slab_rows - 1) / slab_rows);
+  const int spl = (int)((rows_last + slab_rows - 1) / slab_rows);
+  const int64_t nslab64 = (int64_t)(p - 1) * spc + spl;
+  if (nslab64 > (1 << 30)) return LO_ERR_INVALID_ARG;
+  const int nslab = (int)nslab64;
+  const int ngroups = (p + kTreeGroup - 1) / kTreeGroup;
+  const SmallLayout SL = SmallLayout::make(s, s);
+  const GlobLayout GL = GlobLayout::make(s, s);
+  const size_t ss = (size_t)s * s;
+  // scratch layout
+  size_t off = 0;
+  const size_t o_flags = off;   off = align256(off + sizeof(int) * kFlagCount);
+  const size_t o_slabs = off;   off = align256(off + sizeof(SlabInfo) * (size_t)nslab);
+  const size_t o_cs0 = off;     off = align256(off + sizeof(int32_t) * (size_t)(p + 1));
+  const size_t o_cr0 = off;     off = align256(off + sizeof(int64_t) * (size_t)(p + 1));
+  const size_t o_part = off;    off = align256(off + sizeof(double) * (size_t)nslab * ss);
+  const size_t o_small = off;   off = align256(off + sizeof(double) * (size_t)p * SL.stride);
+  const size_t o_glob = off;    off = align256(off + sizeof(double) * (size_t)GL.stride);
+  const size_t o_tsum = off;    off = align256(off + sizeof(double) * (size_t)ngroups * ss);
+  const size_t o_T = off;       off = align256(off + sizeof(double) * (size_t)p * ss);
+  if (off > kNoAllocScratchBytes) return LO_ERR_CAPACITY;
+
+  // once per device: the device address of the scratch array
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return LO_ERR_CUDA;
+  }
+  void* base = g_noalloc_ptr[dev].load();
+  if (!base) {
+    if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) {
+      cudaGetLastError();
+      return LO_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev].store(base);
+  }
+  unsigned char* sc = static_cast<unsigned char*>(base);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+
+  StepArgs a{};
+  a.n = n;
+  a.s = s;
+  a.M = 1;
+  a.p = p;
+  a.nb = 0;
+  a.Kmax = s;
+  a.V = U;                    // the local panel of block 0 is the caller's U
+  a.T = reinterpret_cast<double*>(sc + o_T);
+  a.tstride = (int64_t)ss;
+  a.part = reinterpret_cast<double*>(sc + o_part);
+  a.small = reinterpret_cast<double*>(sc + o_small);
+  a.glob = reinterpret_cast<double*>(sc + o_glob);
+  a.tsum = reinterpret_cast<double*>(sc + o_tsum);
+  a.flags = reinterpret_cast<int*>(sc + o_flags);
+  a.slabs = reinterpret_cast<const SlabInfo*>(sc + o_slabs);
+  a.chunk_slab0 = reinterpret_cast<const int32_t*>(sc + o_cs0);
+  a.chunk_row0 = reinterpret_cast<const int64_t*>(sc + o_cr0);
+  a.nslab = nslab;
+  a.slab_rows = slab_rows;
+  a.precision = LO_PREC_FP64;
+  a.leaf = LO_LEAF_AUTO;
+  a.reduction = 0;
+  a.refine_tol = 1e-13;
+  a.W = W;
+  a.ldw = ldw;
+  a.U = U;
+  a.ldu = s;
+
+  // the status word must start at zero; everything else is written before it is read
+  cudaError_t e = cudaMemsetAsync(a.flags, 0, sizeof(int) * kFlagCount, st);
+  if (e == cudaSuccess) {
+    int blocks = (nslab + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    k_noalloc_tables<<<blocks, 256, 0, st>>>(n, chunk_rows, p, slab_rows, spc, spl,
+                                              reinterpret_cast<SlabInfo*>(sc + o_slabs),
+                                              reinterpret_cast<int32_t*>(sc + o_cs0),
+                                              reinterpret_cast<int64_t*>(sc + o_cr0));
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_step(a, st, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(R, a.glob + GL.N_acc, sizeof(double) * ss, cudaMemcpyDeviceToDevice, st);
+  int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, a.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LO_ERR_CUDA;
+  }
+  if (bits & (1 << LO_ERR_NONFINITE)) return LO_ERR_NONFINITE;
+  if (bits & (1 << LO_ERR_BREAKDOWN)) return LO_ERR_BREAKDOWN;
+  if (bits) return LO_ERR_CUDA;
+  return LO_OK;
+}

@@ -41,7 +41,7 @@ EXPORTED = [
     "lo_basis_reset", "lo_basis_num_blocks", "lo_basis_num_chunks", "lo_basis_sync",
     "lo_orthogonalize", "lo_orthogonalize_batched", "lo_apply_Q", "lo_basis_export_chunk",
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
-    "lo_basis_last_step_info",
+    "lo_basis_last_step_info", "lo_tsqr_noalloc",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q"]
 
@@ -106,6 +106,8 @@ def _lib():
     L.lo_basis_profile_read.restype = c_int32
     L.lo_basis_last_step_info.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32)]
     L.lo_basis_last_step_info.restype = c_int32
+    L.lo_tsqr_noalloc.argtypes = [c_int64, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
+    L.lo_tsqr_noalloc.restype = c_int32
     _L = L
     return L
 
@@ -286,6 +288,15 @@ def orthogonalize_batched(bases, Ws, Us, Hs=None, Rs=None):
     ph = arr([_ptr(h) for h in Hs], c_void_p) if Hs is not None else None
     pr = arr([_ptr(r) for r in Rs], c_void_p) if Rs is not None else None
     _check(_lib().lo_orthogonalize_batched(hb, cnt, pw, lw, pu, lu, ph, pr), "lo_orthogonalize_batched")
+
+
+def tsqr_noalloc(W, U, R, chunk_rows: int, stream=None):
+    """lo_tsqr_noalloc: W = U R without any device allocation (device tensors;
+    U contiguous n x s, R s x s)."""
+    n, s = int(W.shape[0]), int(W.shape[1])
+    _check(_lib().lo_tsqr_noalloc(n, s, int(chunk_rows), _ptr(W), _ld(W, s), _ptr(U), _ptr(R),
+                                  c_void_p(_stream_handle(stream))), "lo_tsqr_noalloc")
+    return U, R
 
 
 def launch_count() -> int:
