@@ -81,8 +81,10 @@ typedef enum lo_leaf {
 typedef struct lo_options {
   int32_t precision;   /* lo_precision, default LO_PREC_FP64                     */
   int32_t leaf;        /* lo_leaf, default LO_LEAF_AUTO                          */
-  int32_t reduction;   /* 0 = AUTO (PIP, plus reiteration when needed),          */
-                       /* 1 = PIP, 2 = PIP+ always.  Default 0                   */
+  int32_t reduction;   /* reduction sub-algorithm: 0 = AUTO (BCGS-PIP+, plus a   */
+                       /* third iteration when the estimate below asks for it), */
+                       /* 1 = BCGS-PIP (one iteration), 2 = BCGS-PIP+ exactly.  */
+                       /* Default 0                                              */
   int32_t sync;        /* 1 (default): lo_orthogonalize waits for its device     */
                        /* work and returns the device status.  0: asynchronous;  */
                        /* a device error is latched and returned by the next     */

@@ -224,6 +224,105 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
   }
 }
 
+// float64 -> float32 with integer operations only (round toward zero; |x| below
+// 2^-126 flushes to a signed zero, above the float32 range becomes a signed
+// infinity).  Used by the float32 first pass of the mixed form so that it never
+// issues work to GB300's narrow float64 pipe.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned r = sign | ((unsigned)(e - 896) << 23) | mant;
+  if (e < 897) r = sign;
+  if (e > 1150) r = sign | 0x7F800000u;
+  return __uint_as_float(r);
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc load_as(const double* p);
+template <>
+__device__ __forceinline__ double load_as<double>(const double* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_as<float>(const double* p) { return f32_trunc(__ldg(p)); }
+
+// Stage 1, first Gram pass, for block widths S in {1, 2, 4, 8, 16, 32}: the
+// partial of C_i = [Q_i W_i]^T W_i over one slab.  Each thread keeps a
+// TQ x S register tile of C (TQ = 32 / S columns of [Q_i W_i]); T threads
+// cover the k + S columns and G = 256 / T row groups split the slab's rows;
+// the groups are summed in a fixed order at the end.
+template <int S, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
+  constexpr int TQ = (32 / S) > 0 ? 32 / S : 1;
+  extern __shared__ __align__(16) double red[];
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int k = a.nb * S, Kt = k + S;
+  const int T = (Kt + TQ - 1) / TQ;
+  const int G = kThreads / T;
+  const int tid = threadIdx.x, g = tid / T, t = tid - g * T;
+  const bool active = g < G;
+  const int q0 = t * TQ;
+  Acc acc[TQ][S];
+#pragma unroll
+  for (int i = 0; i < TQ; ++i)
+#pragma unroll
+    for (int l = 0; l < S; ++l) acc[i][l] = Acc(0);
+  if (active) {
+    for (int r = g; r < si.rows; r += G) {
+      const int64_t row = si.row0 + r;
+      const double* wr = a.W + row * a.ldw;
+      Acc b[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) b[l] = load_as<Acc>(wr + l);
+      Acc av[TQ];
+#pragma unroll
+      for (int i = 0; i < TQ; ++i) {
+        const int q = q0 + i;
+        if (q < k)
+          av[i] = load_as<Acc>(a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S));
+        else if (q < Kt)
+          av[i] = load_as<Acc>(wr + (q - k));
+        else
+          av[i] = Acc(0);
+      }
+#pragma unroll
+      for (int i = 0; i < TQ; ++i)
+#pragma unroll
+        for (int l = 0; l < S; ++l) acc[i][l] += av[i] * b[l];
+    }
+#pragma unroll
+    for (int i = 0; i < TQ; ++i)
+#pragma unroll
+      for (int l = 0; l < S; ++l) red[(g * T + t) * (TQ * S) + i * S + l] = (double)acc[i][l];
+  }
+  __syncthreads();
+  double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S;
+  for (int e = tid; e < Kt * S; e += kThreads) {
+    const int q = e / S, l = e - q * S, tt = q / TQ, i = q - tt * TQ;
+    double v = 0.0;
+    for (int gg = 0; gg < G; ++gg) v += red[(gg * T + tt) * (TQ * S) + i * S + l];
+    out[e] = v;
+  }
+}
+
+template <typename Acc>
+cudaError_t launch_gram1(const StepArgs& a, cudaStream_t st) {
+  const size_t sm = sizeof(double) * kThreads * 32;
+  switch (a.s) {
+    case 1: k_gram1<1, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    case 2: k_gram1<2, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    case 4: k_gram1<4, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    case 8: k_gram1<8, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    case 16: k_gram1<16, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    case 32: k_gram1<32, Acc><<<a.nslab, kThreads, sm, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+bool gram1_supported(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32; }
+
 // ---------------------------------------------------------------------------
 // Leaf factorization of pass `pass`, one CTA per chunk: sum the slab partials
 // in slab order, then N = chol(G - P^T P) (Alg. 7), N^{-1}, and the
@@ -609,6 +708,14 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_gram<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_gram<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+#define LO_GRAM1_ATTR(S)                                                                            if ((e = cudaFuncSetAttribute(k_gram1<S, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))     return e;                                                                                       if ((e = cudaFuncSetAttribute(k_gram1<S, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  LO_GRAM1_ATTR(1)
+  LO_GRAM1_ATTR(2)
+  LO_GRAM1_ATTR(4)
+  LO_GRAM1_ATTR(8)
+  LO_GRAM1_ATTR(16)
+  LO_GRAM1_ATTR(32)
+#undef LO_GRAM1_ATTR
   if ((e = cudaFuncSetAttribute(k_tree_contrib, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_tree_sum2, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_tree_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
@@ -634,13 +741,18 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   if (e) return e;
   const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
   const bool mixed = (a.precision == LO_PREC_MIXED_FP32);
-  k_step_begin<<<1, 32, 0, st>>>(a.flags, (a.leaf == LO_LEAF_PIP2) || mixed, a.reduction == 2);
+  // The reduction always reiterates (BCGS-PIP+) unless plain PIP is asked for: its
+  // projection uses the stacked tree factors of all earlier steps, whose rounding
+  // errors a single pass amplifies step after step.
+  k_step_begin<<<1, 32, 0, st>>>(a.flags, (a.leaf == LO_LEAF_PIP2) || mixed, a.reduction != 1);
   count_launches(1);
   // stage 1
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
   for (int pass = 1; pass <= maxpass; ++pass) {
     mark(hook, kKindGram, true, st);
-    if (pass == 1 && mixed) {
+    if (pass == 1 && gram1_supported(s)) {
+      if ((e = mixed ? launch_gram1<float>(a, st) : launch_gram1<double>(a, st))) return e;
+    } else if (pass == 1 && mixed) {
       const int tr = gram_tile_rows(Kt, s, 4);
       const size_t sm = (((size_t)4 * tr * Kt + 15) & ~(size_t)15) + 8 * (size_t)tr * s + 8 * kThreads;
       k_gram<float, float><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
