@@ -206,7 +206,7 @@ def run_gpu(args):
     lo.library()
     n, s, m = NX * NY, S, M_RESTART
     stream = torch.cuda.current_stream()
-    basis = lo.Basis(n, s, m + 1, CHUNK, sync=False, stream=stream)
+    basis = lo.Basis(n, s, m + 1, CHUNK, sync=False, stream=stream, precision=args.precision)
     p = basis.num_chunks
     B = torch.from_numpy(I.uniform(n, s, I.seed_for(2, rank))).to(dev)
     Hbuf = [torch.empty(((j + 1) * s, s), dtype=torch.float64, device=dev) for j in range(m)]
@@ -290,7 +290,7 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
-        e2e = run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p)
+        e2e = run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, args.precision)
         cpu = cpu_baseline(args.cpu_budget) if world == 1 or rank == 0 else None
         clocks = clk.summary()
         out = {
@@ -301,7 +301,7 @@ def run_gpu(args):
                                    "s=8 RHS U(-1,1), m=30: 31 orthogonalizations (k=0..240) + apply_Q; "
                                    "stencil and host least-squares untimed",
                        "n": n, "s": s, "restart_blocks": m, "chunk_rows": CHUNK, "chunks": p,
-                       "precision": "fp64", "leaf": "auto", "reduction": "auto",
+                       "precision": args.precision, "leaf": "pip2", "reduction": "auto",
                        "l2": "inputs larger than L2 (basis 2.1 GB, 8 MB per block)",
                        "parallelism": f"replicas{world}"},
             "block_steps_per_s": round((m + 1) * args.steps * world / (t_local * 1e-3), 2),
@@ -321,7 +321,7 @@ def run_gpu(args):
     return out
 
 
-def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p):
+def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, basis_precision):
     """The same cycle's orthogonalizations through the public API with pinned
     host buffers: each call copies W in, U/H/R out and waits (wall clock)."""
     rec = []
@@ -333,7 +333,7 @@ def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p):
     Uh = torch.empty((n, s), dtype=torch.float64).pin_memory()
     Hh = torch.empty(((m + 1) * s, s), dtype=torch.float64).pin_memory()
     Rh = torch.empty((s, s), dtype=torch.float64).pin_memory()
-    hb = lo.Basis(n, s, m + 1, CHUNK, sync=True, stream=stream)
+    hb = lo.Basis(n, s, m + 1, CHUNK, sync=True, stream=stream, precision=basis_precision)
     torch.cuda.synchronize()
     t = 0.0
     h2d = d2h = 0
@@ -443,7 +443,7 @@ def run_profile_case(args):
     n, s, kb = 2 ** 20, 8, 15
     dev = torch.device("cuda", 0)
     lo.library()
-    b = lo.Basis(n, s, kb + 1, CHUNK, sync=True)
+    b = lo.Basis(n, s, kb + 1, CHUNK, sync=True, precision=args.precision)
     for j in range(kb):
         b.orthogonalize(torch.from_numpy(I.gaussian(n, s, I.seed_for(9, j))).to(dev))
     W = torch.from_numpy(I.gaussian(n, s, I.seed_for(9, kb))).to(dev)
@@ -451,9 +451,83 @@ def run_profile_case(args):
     b.set_profiling(True)
     b.orthogonalize(W)
     prof = b.profile_read()
-    print(json.dumps({"case": "profile", "n": n, "s": s, "k": kb * s, "chunks": b.num_chunks,
+    print(json.dumps({"case": "profile", "precision": args.precision, "n": n, "s": s, "k": kb * s,
+                      "chunks": b.num_chunks,
                       "kernel_ms": {g: round(v[0], 4) for g, v in prof.items()},
                       "passes_tree": b.last_step_info()}), flush=True)
+
+
+def run_batched_case(args):
+    """Batched uneven instances: 64 independent problems (n log-uniform in
+    [1e4, 2^20], s from {4, 8, 16}, 1..30 prior blocks built untimed, new block
+    N(0,1)); chunk rows from the autotuner; one lo_orthogonalize_batched call
+    (a cached CUDA graph) against 64 sequential lo_orthogonalize calls."""
+    import torch
+
+    from paper_2204_13393_gb300 import inputs as I
+    from paper_2204_13393_gb300 import lo
+
+    dev = torch.device("cuda", 0)
+    lo.library()
+    specs = I.batch_instances(64, I.seed_for(5))
+    bases, Ws, Us, Hs, Rs, kbs, nbytes, tuned = [], [], [], [], [], [], 0, {}
+    t_tune = time.perf_counter()
+    for i, (n, s, kb) in enumerate(specs):
+        M = kb + 1
+        key = (n, s, M)
+        if key not in tuned:
+            tuned[key] = lo.tune_chunk_rows(n, s, M, precision=args.precision)
+        cr = tuned[key]
+        b = lo.Basis(n, s, M, cr, precision=args.precision, sync=False)
+        g = torch.Generator(device=dev)
+        g.manual_seed(I.seed_for(5, i))
+        for j in range(kb):
+            b.orthogonalize(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+        b.sync()
+        bases.append(b)
+        Ws.append(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+        Us.append(torch.empty(n, s, dtype=torch.float64, device=dev))
+        Hs.append(torch.empty(kb * s, s, dtype=torch.float64, device=dev))
+        Rs.append(torch.empty(s, s, dtype=torch.float64, device=dev))
+        kbs.append(kb)
+        nbytes += orth_bytes(n, s, kb * s, b.num_chunks)
+    t_tune = time.perf_counter() - t_tune
+    stream = torch.cuda.current_stream()
+
+    def sequential():
+        for b, kb in zip(bases, kbs):
+            b.truncate(kb)
+        for b, W, U, H, R in zip(bases, Ws, Us, Hs, Rs):
+            b.orthogonalize(W, U=U, H=H, R=R)
+        for b in bases:
+            b.sync()
+
+    def batched():
+        for b, kb in zip(bases, kbs):
+            b.truncate(kb)
+        lo.orthogonalize_batched(bases, Ws, Us, Hs, Rs)
+
+    res = {}
+    for name, fn in (("sequential", sequential), ("batched", batched)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": "batched", "precision": args.precision, "instances": len(specs),
+                      "bytes_per_step": nbytes, "ms_batched": round(res["batched"], 3),
+                      "ms_sequential": round(res["sequential"], 3),
+                      "gbs_batched": round(nbytes / res["batched"] / 1e6, 1),
+                      "gbs_sequential": round(nbytes / res["sequential"] / 1e6, 1),
+                      "speedup": round(res["sequential"] / res["batched"], 3),
+                      "tuned_chunk_rows": sorted(set(tuned.values())), "setup_s": round(t_tune, 1)}),
+          flush=True)
 
 
 def main():
@@ -463,11 +537,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lo", choices=["lo", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
-    ap.add_argument("--case", default="cycle", choices=["cycle", "profile"],
-                    help="profile: one mid-cycle step for ncu captures")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc", "mixed_fp32"])
+    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched"],
+                    help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances")
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)
+        return
+    if args.case == "batched":
+        run_batched_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -62,25 +62,40 @@ typedef enum lo_status {
 /* Arithmetic of the O(n) passes. */
 typedef enum lo_precision {
   LO_PREC_FP64 = 0,        /* every product in native float64                    */
-  LO_PREC_MIXED_FP32 = 1   /* first-pass Gram/projection in float32, then float64 */
+  LO_PREC_MIXED_FP32 = 1,  /* first-pass Gram/projection in float32, then float64 */
                            /* shifted Cholesky, one float64 CholeskyQR2-style    */
                            /* refinement pass, float64 tree and update (Alg. 8   */
                            /* pattern)                                            */
+  LO_PREC_FP64_TC = 2      /* float64-accurate products of the O(n) passes on the */
+                           /* tensor cores: every float64 value is split into 7   */
+                           /* 8-bit digits against its column's largest exponent */
+                           /* (error-free splitting of Ozaki et al., Numer.      */
+                           /* Algorithms 59, 2012), the 28 significant digit      */
+                           /* products run as fp16 mma with exact float32        */
+                           /* accumulation, and are recombined in 64-bit         */
+                           /* integers.  Small factors stay float64.  Requires   */
+                           /* s in {1, 2, 4, 8, 16, 32}; values below 2^-1022    */
+                           /* (subnormals) count as zero.                        */
 } lo_precision;
 
 /* Local sub-algorithm (the "local subalgorithm" of Alg. 9). */
 typedef enum lo_leaf {
   LO_LEAF_AUTO = 0,        /* BCGS-PIP, plus the PIP+ reiteration when the local */
-                           /* Cholesky factor's condition estimate says the      */
-                           /* single pass would lose orthogonality (decided on   */
-                           /* the device; no host synchronization)               */
+                           /* condition estimate says the single pass would lose */
+                           /* orthogonality (decided on the device; no host      */
+                           /* synchronization).  Suited to well-conditioned,     */
+                           /* independent blocks; in a Krylov sequence the local */
+                           /* losses below the estimate accumulate.               */
   LO_LEAF_PIP = 1,         /* BCGS-PIP, Alg. 7: one Gram pass                    */
-  LO_LEAF_PIP2 = 2         /* BCGS-PIP+, Alg. 8: always two Gram passes          */
+  LO_LEAF_PIP2 = 2         /* BCGS-PIP+, Alg. 8: two Gram passes (the default),  */
+                           /* a third when the estimate still asks for it; a     */
+                           /* first-pass breakdown retries with the shift of     */
+                           /* shifted CholeskyQR3 and forces two more passes     */
 } lo_leaf;
 
 typedef struct lo_options {
   int32_t precision;   /* lo_precision, default LO_PREC_FP64                     */
-  int32_t leaf;        /* lo_leaf, default LO_LEAF_AUTO                          */
+  int32_t leaf;        /* lo_leaf, default LO_LEAF_PIP2                          */
   int32_t reduction;   /* reduction sub-algorithm: 0 = AUTO (BCGS-PIP+, plus a   */
                        /* third iteration when the estimate below asks for it), */
                        /* 1 = BCGS-PIP (one iteration), 2 = BCGS-PIP+ exactly.  */
@@ -151,16 +166,38 @@ lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc,
                      double* Y, int64_t ldy);
 
 /*
- * Orthogonalize count independent problems, one block each: for j < count,
- * the same as lo_orthogonalize(bases[j], W[j], ldw[j], U[j], ldu[j], H[j],
- * R[j]).  All bases must live on the same device and use the stream of
- * bases[0]; W/U/H/R must be device pointers.  Returns the first error; bases
- * without error advance.
+ * Orthogonalize count independent problems (uneven n, s, k), one block each:
+ * for j < count, the same as lo_orthogonalize(bases[j], W[j], ldw[j], U[j],
+ * ldu[j], H[j], R[j]).  The steps of all problems are captured once into one
+ * CUDA graph whose branches run concurrently (a fork over 8 internal streams,
+ * joined back into the stream of bases[0]); the graph is cached under the
+ * call's arguments (bases, their block counts, pointers, strides) and a repeat
+ * call with the same arguments is a single graph launch.  All bases must live
+ * on the same device and be distinct; W, U, H, R must be device pointers
+ * (H[j], R[j], or H, R themselves may be NULL).  Waits for the work.  Returns
+ * the first error; bases without error advance, the others are unchanged.
  */
 lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count,
                                    const double* const* W, const int64_t* ldw,
                                    double* const* U, const int64_t* ldu,
                                    double* const* H, double* const* R);
+
+/*
+ * Drop the trailing blocks so that num_blocks (<= the current count) remain.
+ * The representation of the first num_blocks blocks is not affected by later
+ * steps, so this is exact (a truncated restart, or re-running a step).
+ */
+lo_status lo_basis_truncate(lo_basis* b, int32_t num_blocks);
+
+/*
+ * Autotuner: time one step at half capacity for every candidate chunk size
+ * (powers of two from max(256, max_blocks*s) up to n) on a synthetic block of
+ * this shape and return the fastest in *chunk_rows.  Allocates temporary
+ * device memory; results are memoized per (log2 n in quarter steps, s,
+ * max_blocks, precision, leaf).  opt may be NULL.
+ */
+lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_options* opt,
+                             void* cuda_stream, int32_t* chunk_rows);
 
 /* Wait for the basis stream and return (and clear) any latched device error. */
 lo_status lo_basis_sync(lo_basis* b);
@@ -185,11 +222,12 @@ lo_status lo_laplace5_apply(int32_t nx, int32_t ny, int32_t s, const double* X, 
  * Measurement hooks (used by the benchmark; not needed for normal use).
  * lo_launch_count: number of kernels the library has launched in this process.
  * lo_basis_set_profiling: when enabled, every group of kernels of this basis
- *   (0 stage-1 Gram passes, 1 leaf factorizations, 2 reduction, 3 stage-2
- *   update, 4 apply_Q) is bracketed by CUDA events on the basis stream.
+ *   (0 stage-1 Gram pass 1, 1 leaf factorizations, 2 reduction, 3 stage-2
+ *   update, 4 apply_Q, 5 reiteration passes) is bracketed by CUDA events on the
+ *   basis stream.
  * lo_basis_profile_read: waits for the recorded events and returns, per group,
  *   the summed elapsed milliseconds and the number of bracketed intervals since
- *   the last read (nkinds >= 5 entries in both arrays).
+ *   the last read (nkinds >= 6 entries in both arrays).
  */
 long long lo_launch_count(void);
 /* Local Gram passes and reduction iterations the last step ran (waits for it). */

@@ -1,8 +1,13 @@
 // Host side of the C ABI (include/lo.h): basis object, argument validation,
 // staging of host buffers, kernel sequencing and status reporting.
+#include <chrono>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "lo_internal.h"
@@ -101,6 +106,13 @@ struct lo_basis {
   size_t zq_cap = 0;
   double* cdev = nullptr;
   size_t cdev_cap = 0;
+  // tensor-core form
+  int* colexp = nullptr;
+  int* srcexp_slab = nullptr;
+  int* srcexp = nullptr;
+  int* coefexp = nullptr;
+  uint32_t* coefdig = nullptr;
+  int64_t coefdig_stride = 0;
   Profiler prof;
 };
 
@@ -169,6 +181,12 @@ StepArgs make_args(const lo_basis* b) {
   a.leaf = b->opt.leaf;
   a.reduction = b->opt.reduction;
   a.refine_tol = b->opt.refine_tol > 0 ? b->opt.refine_tol : 1e-13;
+  a.colexp = b->colexp;
+  a.srcexp_slab = b->srcexp_slab;
+  a.srcexp = b->srcexp;
+  a.coefdig = b->coefdig;
+  a.coefexp = b->coefexp;
+  a.coefdig_stride = b->coefdig_stride;
   return a;
 }
 
@@ -206,6 +224,43 @@ lo_status copy_small_outputs(lo_basis* b, double* H, double* R, cudaStream_t st)
   return from_cuda(e);
 }
 
+// Stream pool and graph cache of lo_orthogonalize_batched (one per process).
+constexpr int kPool = 8;
+constexpr size_t kGraphCache = 8;
+struct GraphEntry {
+  std::vector<uintptr_t> key;
+  cudaGraphExec_t exec;
+  unsigned long long stamp;
+};
+struct BatchGraphs {
+  std::mutex mu;
+  int device = -1;
+  cudaStream_t st[kPool] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kPool] = {};
+  std::vector<GraphEntry> cache;
+  unsigned long long clock = 0;
+};
+BatchGraphs& batch_graphs() {
+  static BatchGraphs* g = new BatchGraphs();  // lives until process exit
+  return *g;
+}
+cudaError_t ensure_pool(BatchGraphs& bg, int device) {
+  if (bg.device == device) return cudaSuccess;
+  if (bg.device >= 0) {
+    for (auto& ent : bg.cache) cudaGraphExecDestroy(ent.exec);
+    bg.cache.clear();
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < kPool && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&bg.st[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.join[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) bg.device = device;
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -213,7 +268,7 @@ extern "C" {
 void lo_options_default(lo_options* opt) {
   if (!opt) return;
   opt->precision = LO_PREC_FP64;
-  opt->leaf = LO_LEAF_AUTO;
+  opt->leaf = LO_LEAF_PIP2;
   opt->reduction = 0;
   opt->sync = 1;
   opt->refine_tol = 1e-13;
@@ -245,9 +300,10 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options o;
   lo_options_default(&o);
   if (opt) o = *opt;
-  if (o.precision < 0 || o.precision > 1 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
+  if (o.precision < 0 || o.precision > 2 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
       o.reduction > 2)
     return LO_ERR_INVALID_ARG;
+  if (o.precision == LO_PREC_FP64_TC && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
   if (o.refine_tol <= 0) o.refine_tol = 1e-13;
   const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
   if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
@@ -307,6 +363,15 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   alloc((void**)&b->d_slabs, sizeof(SlabInfo) * slabs.size());
   alloc((void**)&b->d_chunk_slab0, sizeof(int32_t) * cs0.size());
   alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
+  if (o.precision == LO_PREC_FP64_TC) {
+    b->coefdig_stride = lo::oz_coef_words(b->Kmax, 2 * s);
+    alloc((void**)&b->colexp, sizeof(int) * (size_t)Kmax * p);
+    alloc((void**)&b->srcexp_slab, sizeof(int) * (size_t)b->nslab * 32);
+    alloc((void**)&b->srcexp, sizeof(int) * (size_t)p * 32);
+    alloc((void**)&b->coefexp, sizeof(int) * (size_t)p * 64);
+    alloc((void**)&b->coefdig, sizeof(uint32_t) * (size_t)p * b->coefdig_stride);
+    if (e == cudaSuccess) e = cudaMemset(b->colexp, 0, sizeof(int) * (size_t)Kmax * p);
+  }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_flags, sizeof(int) * lo::kFlagCount);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_slabs, slabs.data(), sizeof(SlabInfo) * slabs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_chunk_slab0, cs0.data(), sizeof(int32_t) * cs0.size(), cudaMemcpyHostToDevice);
@@ -340,6 +405,11 @@ void lo_basis_destroy(lo_basis* b) {
   cudaFree(b->stage_out);
   cudaFree(b->zq);
   cudaFree(b->cdev);
+  cudaFree(b->colexp);
+  cudaFree(b->srcexp_slab);
+  cudaFree(b->srcexp);
+  cudaFree(b->coefexp);
+  cudaFree(b->coefdig);
   if (b->h_flags) cudaFreeHost(b->h_flags);
   cudaGetLastError();
   delete b;
@@ -413,25 +483,179 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     if (!b || !W[j] || !U[j] || ldw[j] < b->s || ldu[j] < b->s) return LO_ERR_INVALID_ARG;
     if (b->nb >= b->M) return LO_ERR_CAPACITY;
     if (b->device != bases[0]->device) return LO_ERR_INVALID_ARG;
+    if (!is_device_ptr(W[j]) || !is_device_ptr(U[j])) return LO_ERR_INVALID_ARG;
+    if (H && H[j] && !is_device_ptr(H[j])) return LO_ERR_INVALID_ARG;
+    if (R && R[j] && !is_device_ptr(R[j])) return LO_ERR_INVALID_ARG;
+    for (int i = 0; i < j; ++i)
+      if (bases[i] == b) return LO_ERR_INVALID_ARG;  // one step per basis and call
   }
   cudaSetDevice(bases[0]->device);
-  cudaStream_t st = bases[0]->stream;
+  cudaStream_t cs = bases[0]->stream;
+  BatchGraphs& bg = batch_graphs();
+  std::lock_guard<std::mutex> lock(bg.mu);
+  cudaError_t e = ensure_pool(bg, bases[0]->device);
+  if (e != cudaSuccess) return from_cuda(e);
+  // key: everything the captured work depends on
+  std::vector<uintptr_t> key;
+  key.reserve(9 * (size_t)count + 2);
+  key.push_back((uintptr_t)count);
+  key.push_back((uintptr_t)cs);
   for (int j = 0; j < count; ++j) {
-    lo_basis* b = bases[j];
-    lo_status rs = enqueue_step(b, W[j], ldw[j], U[j], ldu[j], st);
-    if (rs == LO_OK) rs = copy_small_outputs(b, H ? H[j] : nullptr, R ? R[j] : nullptr, st);
-    if (rs != LO_OK) return rs;
+    key.push_back((uintptr_t)bases[j]);
+    key.push_back((uintptr_t)bases[j]->nb);
+    key.push_back((uintptr_t)W[j]);
+    key.push_back((uintptr_t)ldw[j]);
+    key.push_back((uintptr_t)U[j]);
+    key.push_back((uintptr_t)ldu[j]);
+    key.push_back((uintptr_t)(H ? H[j] : nullptr));
+    key.push_back((uintptr_t)(R ? R[j] : nullptr));
+    key.push_back((uintptr_t)bases[j]->h_flags);
   }
+  cudaGraphExec_t exec = nullptr;
+  for (auto& ent : bg.cache)
+    if (ent.key == key) {
+      exec = ent.exec;
+      ent.stamp = ++bg.clock;
+    }
+  if (!exec) {
+    // capture: fork onto the pool streams, one instance per stream round-robin, join
+    if ((e = lo::launch_prepare()) != cudaSuccess) return from_cuda(e);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return from_cuda(e);
+    lo_status rs = LO_OK;
+    cudaEventRecord(bg.fork, cs);
+    for (int i = 0; i < kPool; ++i) cudaStreamWaitEvent(bg.st[i], bg.fork, 0);
+    for (int j = 0; j < count && rs == LO_OK; ++j) {
+      lo_basis* b = bases[j];
+      cudaStream_t st = bg.st[j % kPool];
+      StepArgs a = make_args(b);
+      a.W = W[j];
+      a.ldw = ldw[j];
+      a.U = U[j];
+      a.ldu = ldu[j];
+      rs = from_cuda(lo::launch_step(a, st, nullptr));
+      if (rs == LO_OK) rs = copy_small_outputs(b, H ? H[j] : nullptr, R ? R[j] : nullptr, st);
+      if (rs == LO_OK)
+        rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+    for (int i = 0; i < kPool; ++i) {
+      cudaEventRecord(bg.join[i], bg.st[i]);
+      cudaStreamWaitEvent(cs, bg.join[i], 0);
+    }
+    e = cudaStreamEndCapture(cs, &graph);
+    if (rs != LO_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rs;
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (bg.cache.size() >= kGraphCache) {
+      size_t old = 0;
+      for (size_t i = 1; i < bg.cache.size(); ++i)
+        if (bg.cache[i].stamp < bg.cache[old].stamp) old = i;
+      cudaGraphExecDestroy(bg.cache[old].exec);
+      bg.cache.erase(bg.cache.begin() + old);
+    }
+    bg.cache.push_back(GraphEntry{key, exec, ++bg.clock});
+  }
+  for (int j = 0; j < count; ++j) bases[j]->h_flags[0] = 0;
+  e = cudaGraphLaunch(exec, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return from_cuda(e);
   lo_status first = LO_OK;
   for (int j = 0; j < count; ++j) {
     lo_basis* b = bases[j];
-    lo_status d = read_status(b, st);
-    if (d == LO_OK)
+    const int bits = b->h_flags[0];
+    if (bits == 0) {
       b->nb += 1;
-    else if (first == LO_OK)
-      first = d;
+    } else {
+      cudaMemset(b->flags, 0, sizeof(int));
+      if (first == LO_OK) first = status_from_bits(bits);
+    }
   }
   return first;
+}
+
+lo_status lo_basis_truncate(lo_basis* b, int32_t num_blocks) {
+  if (!b || num_blocks < 0 || num_blocks > b->nb) return LO_ERR_INVALID_ARG;
+  b->nb = num_blocks;
+  return LO_OK;
+}
+
+lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_options* opt,
+                             void* cuda_stream, int32_t* chunk_rows) {
+  if (!chunk_rows || n < 1 || s < 1 || s > lo::kMaxS || max_blocks < 1) return LO_ERR_INVALID_ARG;
+  *chunk_rows = 0;
+  const int64_t Kmax = (int64_t)max_blocks * s;
+  if (Kmax > lo::kMaxK || Kmax * s > lo::kMaxKS || n < Kmax) return LO_ERR_CHUNK_TOO_SMALL;
+  lo_options o;
+  lo_options_default(&o);
+  if (opt) o = *opt;
+  o.sync = 1;
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int, int>, int32_t> memo;
+  const int nbucket = (int)std::floor(std::log2((double)n) * 4.0);
+  const auto mkey = std::make_tuple(nbucket, (int)s, (int)max_blocks, (int)o.precision, (int)o.leaf);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find(mkey);
+    if (it != memo.end()) {
+      *chunk_rows = it->second;
+      return LO_OK;
+    }
+  }
+  // candidates: powers of two from max(Kmax, 256) up to n (and n itself for one chunk)
+  std::vector<int64_t> cand;
+  int64_t c0 = 256;
+  while (c0 < Kmax) c0 *= 2;
+  for (int64_t c = c0; c <= n && cand.size() < 9; c *= 2) cand.push_back(c);
+  if (cand.empty()) cand.push_back(n);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* Wd = nullptr;
+  double* Ud = nullptr;
+  if (cudaMalloc(&Wd, sizeof(double) * (size_t)n * s) != cudaSuccess ||
+      cudaMalloc(&Ud, sizeof(double) * (size_t)n * s) != cudaSuccess) {
+    cudaFree(Wd);
+    cudaGetLastError();
+    return LO_ERR_OOM;
+  }
+  cudaError_t e = lo::launch_fill_pattern(Wd, n * s, st);
+  const int kb = max_blocks > 1 ? max_blocks / 2 : 0;  // time the step at half capacity
+  double best_t = 1e300;
+  int64_t best = cand[0];
+  for (int64_t c : cand) {
+    if (e != cudaSuccess) break;
+    lo_basis* b = nullptr;
+    if (lo_basis_create(n, s, max_blocks, (int32_t)std::min<int64_t>(c, (int64_t)1 << 30), &o, cuda_stream, &b) != LO_OK)
+      continue;
+    bool ok = true;
+    for (int j = 0; j < kb && ok; ++j) ok = lo_orthogonalize(b, Wd, s, Ud, s, nullptr, nullptr) == LO_OK &&
+                                          lo::launch_fill_pattern(Wd, n * s, st) == cudaSuccess;
+    double t = 1e300;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      b->nb = kb;
+      cudaStreamSynchronize(st);
+      const auto t0 = std::chrono::steady_clock::now();
+      ok = lo_orthogonalize(b, Wd, s, Ud, s, nullptr, nullptr) == LO_OK;
+      const auto t1 = std::chrono::steady_clock::now();
+      t = std::min(t, std::chrono::duration<double>(t1 - t0).count());
+    }
+    lo_basis_destroy(b);
+    if (ok && t < best_t) {
+      best_t = t;
+      best = c;
+    }
+  }
+  cudaFree(Wd);
+  cudaFree(Ud);
+  if (e != cudaSuccess) return from_cuda(e);
+  *chunk_rows = (int32_t)best;
+  std::lock_guard<std::mutex> lock(mu);
+  memo[mkey] = *chunk_rows;
+  return LO_OK;
 }
 
 lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc, double* Y, int64_t ldy) {

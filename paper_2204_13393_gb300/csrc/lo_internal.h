@@ -58,6 +58,7 @@ struct GlobLayout {
   int64_t P_it, N_it, Ninv_it;   // this tree iteration: Kmax x s, s x s, s x s
   int64_t P_acc, N_acc;          // combined over iterations (the outputs H, R)
   int64_t Zsum;                  // Kmax x s, the summed contributions
+  int64_t scal;                  // 8 scalars: [0] = |W|_F^2 of the step
   int64_t stride;
   __host__ __device__ static GlobLayout make(int Kmax, int s) {
     GlobLayout L;
@@ -68,7 +69,8 @@ struct GlobLayout {
     L.P_acc = ks + 2 * ss;
     L.N_acc = 2 * ks + 2 * ss;
     L.Zsum = 2 * ks + 3 * ss;
-    L.stride = 3 * ks + 3 * ss;
+    L.scal = 3 * ks + 3 * ss;
+    L.stride = 3 * ks + 3 * ss + 8;
     return L;
   }
 };
@@ -100,7 +102,22 @@ struct StepArgs {
   int64_t ldw;
   double* U;
   int64_t ldu;
+  // float64-accurate tensor-core form (LO_PREC_FP64_TC); null otherwise
+  int* colexp;               // [Kmax][p]: largest biased exponent of each local column per chunk
+  int* srcexp_slab;          // [nslab][32]: the same for the block of the current pass, per slab
+  int* srcexp;               // [p][32]: ... per chunk
+  uint32_t* coefdig;         // [p][coefdig_stride]: digit planes of the scaled coefficients
+  int* coefexp;              // [p][64]: exponent of each coefficient column
+  int64_t coefdig_stride;    // uint32 words per chunk
 };
+
+// Digit planes of the tensor-core form: 7 planes of 8-bit digits per value.
+constexpr int kOzDigits = 7;
+// uint32 words of one chunk's coefficient planes for Kmax rows and `ncols` columns.
+__host__ __device__ inline int64_t oz_coef_words(int Kmax, int ncols) {
+  const int ksteps = (Kmax + 15) / 16, ntiles = (ncols + 7) / 8;
+  return (int64_t)ksteps * ntiles * kOzDigits * 64;
+}
 
 // Offset (in doubles) of column block c inside one chunk's tree factor.
 __host__ __device__ inline int64_t tblock_offset(int c, int s) {
@@ -109,12 +126,13 @@ __host__ __device__ inline int64_t tblock_offset(int c, int s) {
 
 // Kernel groups timed by the optional profiling hook (lo_basis_set_profiling).
 enum KernelKind : int {
-  kKindGram = 0,     // stage-1 Gram passes
+  kKindGram = 0,     // stage-1 Gram pass 1
   kKindLeaf = 1,     // per-chunk leaf factorizations
   kKindTree = 2,     // reduction (tree combine)
   kKindUpdate = 3,   // stage-2 assembly of U and of the new local block
   kKindApply = 4,    // apply_Q
-  kKindCount = 5
+  kKindRefine = 5,   // reiteration passes (new iterate + its Gram), passes >= 2
+  kKindCount = 6
 };
 
 // Records a CUDA event before/after each kernel group when profiling is on.
@@ -127,10 +145,22 @@ struct ProfHook {
 long long launches();
 void count_launches(int k);
 
+// One-time function attributes of every kernel (call before stream capture).
+cudaError_t launch_prepare();
+// Fill X[0:count) with a deterministic synthetic pattern (chunk-size tuner only).
+cudaError_t launch_fill_pattern(double* X, int64_t count, cudaStream_t st);
+
 // Launchers (lo_kernels.cu).  All enqueue on `st` and return the launch error.
 cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook);
 cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ldc, double* Z,
                            double* Y, int64_t ldy, cudaStream_t st, ProfHook* hook);
+// Tensor-core (Ozaki) launchers (lo_ozaki.cu).
+cudaError_t launch_oz_gram(const StepArgs& a, int pass, cudaStream_t st);
+cudaError_t launch_oz_ypass(const StepArgs& a, int pass, cudaStream_t st);
+cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st);
+bool oz_supported(int s);
+cudaError_t oz_set_attrs();
+
 cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,
                             int64_t ldy, cudaStream_t st);
 

@@ -36,17 +36,20 @@ __device__ __forceinline__ int passes_run(const StepArgs& a) {
 
 // In-place upper Cholesky of the s x s symmetric matrix M (row-major, smem):
 // afterwards the upper triangle holds N with N^T N = M, the lower is zero.
-// A pivot <= tol (or non-finite) latches LO_ERR_BREAKDOWN / LO_ERR_NONFINITE
-// and is replaced by 1 so that no NaN propagates into later kernels' indexing.
-__device__ void cta_cholesky(double* M, int s, double tol, int* flags) {
+// A pivot <= tol (or non-finite) sets *fail (shared memory, zeroed by the
+// caller) and, when flags is not null, latches LO_ERR_BREAKDOWN /
+// LO_ERR_NONFINITE; the pivot is replaced by 1 so that no NaN propagates.
+__device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail) {
   for (int i = 0; i < s; ++i) {
     if (threadIdx.x == 0) {
       double d = M[i * s + i];
       if (!isfinite(d)) {
-        set_status(flags, LO_ERR_NONFINITE);
+        if (flags) set_status(flags, LO_ERR_NONFINITE);
+        *fail = 1;
         d = 1.0;
       } else if (!(d > tol)) {
-        set_status(flags, LO_ERR_BREAKDOWN);
+        if (flags) set_status(flags, LO_ERR_BREAKDOWN);
+        *fail = 1;
         d = 1.0;
       }
       M[i * s + i] = sqrt(d);
@@ -65,6 +68,29 @@ __device__ void cta_cholesky(double* M, int s, double tol, int* flags) {
   for (int e = threadIdx.x; e < s * s; e += blockDim.x)
     if (e / s > e % s) M[e] = 0.0;
   __syncthreads();
+}
+
+// Cholesky of M with the shifted retry of shifted CholeskyQR3 (Fukaya,
+// Kannan, Nakatsukasa, Yamamoto, Yanagisawa, SIAM J. Sci. Comput. 42, 2020):
+// when allow_shift is set and the plain factorization breaks down (the block
+// is ill-conditioned beyond eps*kappa^2 < 1), factor M + sigma*I with
+// sigma = 11 (rows*s + s(s+1)) eps trace(G) instead and return true; the
+// caller then forces two further reiterations.  Without allow_shift a
+// breakdown latches the status.  save: s*s shared scratch.
+__device__ bool cta_cholesky_shifted(double* M, double* save, int s, double tol, double sigma, bool allow_shift,
+                                     int* flags, int* fail) {
+  if (threadIdx.x == 0) *fail = 0;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) save[e] = M[e];
+  __syncthreads();
+  cta_cholesky(M, s, tol, allow_shift ? nullptr : flags, fail);
+  const bool failed = *fail != 0;
+  __syncthreads();
+  if (!failed || !allow_shift) return false;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) M[e] = save[e] + ((e / s == e % s) ? sigma : 0.0);
+  if (threadIdx.x == 0) *fail = 0;
+  __syncthreads();
+  cta_cholesky(M, s, tol, flags, fail);
+  return true;
 }
 
 // X = N^{-1} for upper-triangular N (smem), column by column.
@@ -328,7 +354,7 @@ bool gram1_supported(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s =
 // in slab order, then N = chol(G - P^T P) (Alg. 7), N^{-1}, and the
 // reiteration bookkeeping of Alg. 8: P_comb <- P_comb + P N_comb,
 // N_comb <- N N_comb.  Decides on the next pass from kappa_F(N).
-__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel) {
+__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel, int allow_shift) {
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s, ss = s * s;
@@ -343,6 +369,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     double v = 0.0;
     for (int sl = sl0; sl < sl1; ++sl) v += a.part[(int64_t)sl * a.Kmax * s + e];
     C[e] = v;
+  }
+  if (a.srcexp) {  // tensor-core form: the pass block's column exponents per chunk
+    for (int l = threadIdx.x; l < s; l += blockDim.x) {
+      int m = 0;
+      for (int sl = sl0; sl < sl1; ++sl) m = max(m, a.srcexp_slab[(int64_t)sl * 32 + l]);
+      a.srcexp[(int64_t)c * 32 + l] = m;
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < ss; e += blockDim.x) {
@@ -364,7 +397,12 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     __syncthreads();
   }
   const double tol = (double)s * DBL_EPSILON * trG;
-  cta_cholesky(M, s, tol, a.flags);
+  const int64_t rows = a.chunk_row0[c + 1] - a.chunk_row0[c];
+  const double sigma = 11.0 * ((double)rows * s + (double)s * (s + 1)) * DBL_EPSILON * trG;
+  const bool shifted = cta_cholesky_shifted(M, tmp, s, tol, sigma, allow_shift != 0, a.flags,
+                                            reinterpret_cast<int*>(red + 2));
+  if (shifted && threadIdx.x == 0)
+    for (int t = pass + 1; t <= pass + 2 && t <= kMaxPass; ++t) atomicOr(&a.flags[kFlagPass + t - 1], 1);
   cta_upper_inverse(M, Ni, s);
   const double kap = cta_pip_kappa(trG, Ni, s, red);
 
@@ -394,7 +432,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     for (int e = threadIdx.x; e < ss; e += blockDim.x) smallc[SL.N_comb + e] = tmp[e];
   }
   if (threadIdx.x == 0 && pass < kMaxPass) {
-    const bool auto_mode = (a.leaf == LO_LEAF_AUTO) || (a.precision == LO_PREC_MIXED_FP32);
+    const bool auto_mode = (a.leaf != LO_LEAF_PIP) || (a.precision == LO_PREC_MIXED_FP32);
     if (auto_mode && !(DBL_EPSILON * kap * kap <= a.refine_tol))
       atomicOr(&a.flags[kFlagPass + pass], 1);
   }
@@ -484,7 +522,12 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
   }
   __syncthreads();
   const double trG = red[1];
-  cta_cholesky(M, s, (double)s * DBL_EPSILON * trG, a.flags);
+  const double sigma = 11.0 * ((double)a.p * (k + s) * s + (double)s * (s + 1)) * DBL_EPSILON * trG;
+  const bool shifted = cta_cholesky_shifted(M, tmp, s, (double)s * DBL_EPSILON * trG, sigma,
+                                            it == 1 && a.reduction != 1, a.flags, reinterpret_cast<int*>(red + 2));
+  if (shifted && threadIdx.x == 0)
+    for (int t = it + 1; t <= it + 2 && t <= kMaxTreeIter; ++t) atomicOr(&a.flags[kFlagTree + t - 1], 1);
+  if (it == 1 && threadIdx.x == 0) a.glob[GL.scal] = trG;  // |W|_F^2 of the step
   cta_upper_inverse(M, Ni, s);
   const double kap = cta_pip_kappa(trG, Ni, s, red);
   double* P_it = a.glob + GL.P_it;
@@ -509,6 +552,14 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
     }
     cta_matmul_ss(M, Na, tmp, s);
     for (int e = threadIdx.x; e < ss; e += blockDim.x) N_acc[e] = tmp[e];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // numerical rank: a normalizer diagonal at the rounding level of the block
+    // (the deflation case of Sec. 3, not supported) is a breakdown
+    const double floor_ = 64.0 * s * DBL_EPSILON * sqrt(a.glob[GL.scal]);
+    for (int i = 0; i < s; ++i)
+      if (!(fabs(N_acc[i * s + i]) > floor_)) set_status(a.flags, LO_ERR_BREAKDOWN);
   }
   if (threadIdx.x == 0 && it < kMaxTreeIter) {
     if (a.reduction == 0 && !(DBL_EPSILON * kap * kap <= a.refine_tol))
@@ -734,6 +785,33 @@ inline void mark(ProfHook* h, int kind, bool begin, cudaStream_t st) {
 }  // namespace
 
 long long launches() { return g_launches.load(); }
+
+cudaError_t launch_prepare() {
+  cudaError_t e = set_attrs();
+  if (e == cudaSuccess) e = oz_set_attrs();
+  return e;
+}
+
+namespace {
+// Deterministic, well-conditioned synthetic block for timing (a sum of sines of
+// incommensurate frequencies per column); used only by the chunk-size tuner.
+__global__ void k_fill_pattern(double* X, int64_t count, unsigned salt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (double)(i + 1) * 0.6180339887498949 + (double)salt * 0.7548776662466927;
+    X[i] = sin(x * 12.9898) + 0.5 * cos(x * 78.233);
+  }
+}
+unsigned g_fill_salt = 0;
+}  // namespace
+
+cudaError_t launch_fill_pattern(double* X, int64_t count, cudaStream_t st) {
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_fill_pattern<<<(int)blocks, 256, 0, st>>>(X, count, ++g_fill_salt);
+  count_launches(1);
+  return cudaGetLastError();
+}
 void count_launches(int k) { g_launches += k; }
 
 cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
@@ -748,9 +826,15 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   count_launches(1);
   // stage 1
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
+  const bool tc = (a.precision == LO_PREC_FP64_TC);
+  if (tc && (e = oz_set_attrs())) return e;
   for (int pass = 1; pass <= maxpass; ++pass) {
-    mark(hook, kKindGram, true, st);
-    if (pass == 1 && gram1_supported(s)) {
+    mark(hook, pass == 1 ? kKindGram : kKindRefine, true, st);
+    if (tc) {
+      if (pass >= 2 && (e = launch_oz_ypass(a, pass, st))) return e;
+      if ((e = launch_oz_gram(a, pass, st))) return e;
+      count_launches(pass >= 2 ? 3 : 1);
+    } else if (pass == 1 && gram1_supported(s)) {
       if ((e = mixed ? launch_gram1<float>(a, st) : launch_gram1<double>(a, st))) return e;
     } else if (pass == 1 && mixed) {
       const int tr = gram_tile_rows(Kt, s, 4);
@@ -761,12 +845,13 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       const size_t sm = (size_t)8 * tr * Kt + 8 * (size_t)tr * s + 8 * kThreads;
       k_gram<double, double><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
     }
-    mark(hook, kKindGram, false, st);
+    mark(hook, pass == 1 ? kKindGram : kKindRefine, false, st);
     // shifted Cholesky for the float32 first pass: relative shift of the trace
     const double shift = (pass == 1 && mixed) ? 1e-5 : 0.0;
     const size_t smleaf = 8 * ((size_t)Kt * s + 4 * ss + 4);
     mark(hook, kKindLeaf, true, st);
-    k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift);
+    const int allow_shift = (pass == 1 && !mixed && a.leaf != LO_LEAF_PIP) ? 1 : 0;
+    k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift, allow_shift);
     mark(hook, kKindLeaf, false, st);
     count_launches(2);
   }
@@ -782,11 +867,17 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   }
   mark(hook, kKindTree, false, st);
   // stage 2
-  const int tu = update_tile_rows(k, s);
   mark(hook, kKindUpdate, true, st);
-  k_update<<<a.nslab, kThreads, (size_t)8 * tu * (k + 2 * s), st>>>(a, tu);
+  if (tc) {
+    if ((e = cudaMemsetAsync(a.colexp + (int64_t)k * a.p, 0, sizeof(int) * (size_t)s * a.p, st))) return e;
+    if ((e = launch_oz_stage2(a, st))) return e;
+    count_launches(2);
+  } else {
+    const int tu = update_tile_rows(k, s);
+    k_update<<<a.nslab, kThreads, (size_t)8 * tu * (k + 2 * s), st>>>(a, tu);
+    count_launches(1);
+  }
   mark(hook, kKindUpdate, false, st);
-  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,720 @@
+// Float64-accurate products of the two O(n) passes on the tensor cores.
+//
+// GB300 runs float64 arithmetic at ~1.2 TFLOP/s, far below what the streaming
+// passes need; its fp16 tensor path is ~500x faster.  Each float64 value x of a
+// group g (a column of one chunk or slab) is written exactly as
+//     x = 2^(E_g - 1022) * sum_{t=1..7} d_t 2^(-8t) + r,   |r| < 2^(E_g - 1078)
+// with integer digits d_t in [-255, 255] (the bytes of x's significand aligned
+// to the group's largest biased exponent E_g; error-free splitting in the sense
+// of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012)).  Digits are
+// exact in fp16; a product of two digits has at most 16 bits, so a float32
+// accumulation of up to 256 of them (one 256-row slab, or 256 reduction columns)
+// is exact.  The 28 digit pairs with t + u <= 8 carry every term above 2^-56 of
+// the product's scale; they run as mma.sync m16n8k16 (fp16 in, float32
+// accumulate) and are recombined per output in a 64-bit integer before one
+// conversion to float64.
+//
+// Kernels:
+//   k_oz_gram    stage-1 Gram partial C = [Q_i A_i]^T A_i of one slab (Alg. 7,
+//                first line), the A_i^T side sliced per column exponent;
+//   k_oz_coef    per chunk, the float64 coefficient matrix of an assembly
+//                product (Sec. 4.1) scaled by the column exponents and sliced;
+//   k_oz_update  out = [Q_i A_i] Coef for one slab (stage 2, and the
+//                reiteration's new iterate), writing the new local panel.
+#include <cfloat>
+#include <cstdint>
+
+#include "lo_internal.h"
+
+namespace lo {
+namespace {
+
+constexpr int kPairs = 28;
+
+__device__ __forceinline__ void oz_status(int* flags, lo_status st) {
+  atomicOr(&flags[kFlagStatus], 1 << (int)st);
+}
+
+__device__ __forceinline__ int bexp(double x) {
+  return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7FF);
+}
+
+// Aligned significand of |x| against group exponent emax: Y < 2^56 as (yhi, ylo),
+// sign in bit 31 of sgn.  Zero, subnormals and values 2^56 below the group give 0.
+__device__ __forceinline__ void oz_split(double x, int emax, unsigned& yhi, unsigned& ylo, unsigned& sgn) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  sgn = hi & 0x80000000u;
+  unsigned mh = ((((hi & 0xFFFFFu) | 0x100000u) << 3) | (lo >> 29));
+  unsigned ml = lo << 3;
+  int sh = emax - e;
+  if (e == 0 || sh > 55 || sh < 0) {
+    mh = 0u;
+    ml = 0u;
+    sh = 0;
+  }
+  if (sh >= 32) {
+    ml = mh >> (sh - 32);
+    mh = 0u;
+  } else if (sh > 0) {
+    ml = __funnelshift_r(ml, mh, sh);
+    mh >>= sh;
+  }
+  yhi = mh;
+  ylo = ml;
+}
+
+// fp16x2 with the digits of plane t (1..7) of two values (low half = first).
+__device__ __forceinline__ unsigned oz_pack(int t, unsigned h0, unsigned l0, unsigned h1, unsigned l1,
+                                            unsigned sg2, unsigned bias2) {
+  const bool hiw = t <= 3;
+  const unsigned w0 = hiw ? h0 : l0, w1 = hiw ? h1 : l1;
+  const unsigned bi = hiw ? (unsigned)(3 - t) : (unsigned)(7 - t);
+  unsigned v = __byte_perm(w0, w1, bi | ((4u + bi) << 8));
+  v = (v & 0x00FF00FFu) | 0x64006400u;  // fp16 1024 + digit in each half
+  unsigned r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(sg2), "r"(bias2));
+  return r;
+}
+
+// Sign multiplier (+-1) and bias (-+1024) halves for a value pair.
+__device__ __forceinline__ void oz_signs(unsigned s0, unsigned s1, unsigned& sg2, unsigned& bias2) {
+  const unsigned sb = (s0 >> 16) | s1;
+  sg2 = 0x3C003C00u | sb;
+  bias2 = 0xE400E400u ^ sb;
+}
+
+// Write the 7 digit planes of a value pair into fragment storage.
+// base: plane 0 address; plane_stride in uint32 words; idx: word index in a plane.
+__device__ __forceinline__ void oz_store_pair(unsigned* base, int plane_stride, int idx, double x0, int e0,
+                                              double x1, int e1, int* flags) {
+  unsigned h0, l0, s0, h1, l1, s1;
+  oz_split(x0, e0, h0, l0, s0);
+  oz_split(x1, e1, h1, l1, s1);
+  if (bexp(x0) == 0x7FF || bexp(x1) == 0x7FF) oz_status(flags, LO_ERR_NONFINITE);
+  unsigned sg2, bias2;
+  oz_signs(s0, s1, sg2, bias2);
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t) base[(t - 1) * plane_stride + idx] = oz_pack(t, h0, l0, h1, l1, sg2, bias2);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The 28 digit pairs (t, u), t + u <= 8, as a compile-time walk.
+template <typename F>
+__device__ __forceinline__ void for_pairs(F&& f) {
+  int idx = 0;
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t)
+#pragma unroll
+    for (int u = 1; u <= kOzDigits; ++u)
+      if (t + u <= 8) f(idx++, t, u);
+}
+
+// Recombination of one output's 28 pair sums D_tu (exact integers, |D| < 2^24):
+//   sum_{t,u} D_tu 2^(-8(t+u)) = 2^-16 (S_2 + rest 2^-45),  S_v = sum_{t+u=v} D_tu,
+//   rest = S_3 2^37 + S_4 2^29 + S_5 2^21 + S_6 2^13 + S_7 2^5 + round(S_8 / 8)
+// (|rest| < 2^63).  S_2 and rest convert exactly to float64; one fused
+// multiply-add rounds the sum once, so the result carries float64 accuracy.
+__device__ __forceinline__ double oz_combine(const float (&acc)[kPairs][4], int j) {
+  int Sv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for_pairs([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j]); });
+  long long rest = (long long)Sv[3] * (1LL << 37);
+  rest += (long long)Sv[4] * (1LL << 29);
+  rest += (long long)Sv[5] * (1LL << 21);
+  rest += (long long)Sv[6] * (1LL << 13);
+  rest += (long long)Sv[7] * (1LL << 5);
+  rest += (long long)((Sv[8] + 4) >> 3);
+  return fma(__ll2double_rn(rest), 0x1p-45, (double)Sv[2]);
+}
+
+// The 28 pairs are split over two warp groups of 14 pairs each (digit t of
+// the streamed operand: group 0 takes t in {1, 4, 5}, group 1 takes
+// {2, 3, 6, 7}), so that a CTA runs 16 warps with half the accumulators each.
+constexpr int kGroupPairs = 14;
+__host__ __device__ constexpr bool pair_group_has(int g, int t) {
+  return g == 0 ? (t == 1 || t == 4 || t == 5) : (t == 2 || t == 3 || t == 6 || t == 7);
+}
+template <int G, typename F>
+__device__ __forceinline__ void for_group_pairs(F&& f) {
+  int idx = 0;
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t)
+#pragma unroll
+    for (int u = 1; u <= kOzDigits; ++u)
+      if (pair_group_has(G, t) && t + u <= 8) f(idx++, t, u);
+}
+
+// One group's share of the recombination of output j: S_2 and rest (see
+// oz_combine); the two groups' shares add as integers.
+template <int G>
+__device__ __forceinline__ void group_partial(const float (&acc)[kGroupPairs][4], int j, int& s2, long long& rest) {
+  int Sv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for_group_pairs<G>([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j]); });
+  s2 = Sv[2];
+  long long r = (long long)Sv[3] * (1LL << 37);
+  r += (long long)Sv[4] * (1LL << 29);
+  r += (long long)Sv[5] * (1LL << 21);
+  r += (long long)Sv[6] * (1LL << 13);
+  r += (long long)Sv[7] * (1LL << 5);
+  r += (long long)((Sv[8] + 4) >> 3);
+  rest = r;
+}
+
+__device__ __forceinline__ double partial_to_double(int s2, long long rest) {
+  return fma(__ll2double_rn(rest), 0x1p-45, (double)s2);
+}
+
+// 14 mma of one group: A fragments from shared-memory planes (uint4 per lane),
+// B fragments from planes at bsrc (uint2 per lane; shared or global memory).
+template <int G, bool BGLOBAL>
+__device__ __forceinline__ void group_mma(float (&acc)[kGroupPairs][4], const unsigned* apl, int a_stride,
+                                          const unsigned* bpl, int b_stride, int lane) {
+  unsigned af[kOzDigits][4], bf[kOzDigits][2];
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t) {
+    if (pair_group_has(G, t)) {
+      const uint4 v = *reinterpret_cast<const uint4*>(apl + (t - 1) * a_stride + lane * 4);
+      af[t - 1][0] = v.x; af[t - 1][1] = v.y; af[t - 1][2] = v.z; af[t - 1][3] = v.w;
+    }
+  }
+  constexpr int umax = (G == 0) ? 7 : 6;
+#pragma unroll
+  for (int u = 1; u <= umax; ++u) {
+    const uint2* bp = reinterpret_cast<const uint2*>(bpl + (u - 1) * b_stride + lane * 2);
+    const uint2 w = BGLOBAL ? __ldg(bp) : *bp;
+    bf[u - 1][0] = w.x; bf[u - 1][1] = w.y;
+  }
+  for_group_pairs<G>([&](int idx, int t, int u) { mma_f16(acc[idx], af[t - 1], bf[u - 1][0], bf[u - 1][1]); });
+}
+
+// v * 2^X for an integer X in a wide range (two exact power-of-two factors).
+__device__ __forceinline__ double scale2(double v, int X) {
+  if (X < -2044) return 0.0;
+  const int X1 = X / 2, X2 = X - X1;
+  const double f1 = __longlong_as_double((long long)(X1 + 1023) << 52);
+  const double f2 = __longlong_as_double((long long)(X2 + 1023) << 52);
+  return (v * f1) * f2;
+}
+
+// v * 2^X by adding X to the exponent field when the result stays normal
+// (integer work only); otherwise through scale2.
+__device__ __forceinline__ double scale_exp(double v, int X) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (v == 0.0) return 0.0;
+  if (e + X >= 1 && e + X <= 2046 && e != 0) return __longlong_as_double(b + ((long long)X << 52));
+  return scale2(v, X);
+}
+
+// cp.async helpers (Ampere-style asynchronous global->shared copies).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
+
+// ---------------------------------------------------------------------------
+// Stage-1 Gram partial of one slab and one group of MT*16 columns of [Q_i A].
+// mma: M = columns of [Q_i A] (16 per tile), N = columns of A (8 per tile),
+// K = rows (16 per step).  Warp w owns M-tile w % MT and N-tile w / MT.
+// The float64 tiles of the next 16 rows stream into shared memory with
+// cp.async while the current ones are sliced and multiplied.
+template <int S>
+struct GramSmem {
+  static constexpr int NT = (S + 7) / 8, MT = 8 / NT, CG = MT * 16, NC = NT * 8;
+  double raw[2][16][CG];
+  double rawB[2][16][S];
+  unsigned Apl[kOzDigits][MT][32][4];
+  unsigned Bpl[kOzDigits][NT][32][2];
+  long long xrest[8][32][4];
+  int xs2[8][32][4];
+  int Hs[32];
+  int Fs[CG];
+};
+
+template <int S>
+__device__ __forceinline__ void gram_prefetch(GramSmem<S>& sm, int buf, const StepArgs& a, const SlabInfo& si,
+                                              const double* src, int64_t lds, int r0, int col0, int k) {
+  constexpr int CG = GramSmem<S>::CG;
+  const int tid = threadIdx.x;
+  // columns of the local panels inside this group: whole panels (S divides 16, or CG == S)
+  const int qend = min(col0 + CG, k);
+  const int qn = qend > col0 ? qend - col0 : 0;  // multiple of S
+  if (S >= 2) {
+    const int per_row = qn / 2;  // 16-byte copies per row
+    for (int c = tid; c < 16 * per_row; c += 512) {
+      const int r = c / per_row, cc = c - r * per_row, q = col0 + 2 * cc;
+      const bool ok = r0 + r < si.rows;
+      const int64_t row = si.row0 + (ok ? r0 + r : 0);
+      cp_async16(&sm.raw[buf][r][2 * cc], a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S), ok);
+    }
+  } else {
+    for (int c = tid; c < 16 * qn; c += 512) {
+      const int r = c / qn, cc = c - r * qn, q = col0 + cc;
+      const bool ok = r0 + r < si.rows;
+      const int64_t row = si.row0 + (ok ? r0 + r : 0);
+      cp_async8(&sm.raw[buf][r][cc], a.V + (int64_t)q * a.n + row, ok);
+    }
+  }
+  // the block's own columns: in the A tile when inside this group, and as the B operand
+  const bool in_group = (k >= col0 && k < col0 + CG);
+  for (int c = tid; c < 16 * S; c += 512) {
+    const int r = c / S, l = c - r * S;
+    const bool ok = r0 + r < si.rows;
+    const int64_t row = si.row0 + (ok ? r0 + r : 0);
+    const double* g = src + row * lds + l;
+    cp_async8(&sm.rawB[buf][r][l], g, ok);
+    if (in_group) cp_async8(&sm.raw[buf][r][k - col0 + l], g, ok);
+  }
+}
+
+// Stage-1 Gram partial of one slab and one group of MT*16 columns of [Q_i A].
+// mma: M = columns of [Q_i A] (16 per tile), N = columns of A (8 per tile),
+// K = rows (16 per step).  Warp w owns tile w % 8 (M-tile (w % 8) % MT, N-tile
+// (w % 8) / MT) and pair group w / 8.  The float64 tiles of the next 16 rows
+// stream into shared memory with cp.async while the current ones are sliced
+// and multiplied.
+template <int S>
+__global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* src, int64_t lds, int pass) {
+  using SM = GramSmem<S>;
+  constexpr int NT = SM::NT, MT = SM::MT, CG = SM::CG, NC = SM::NC;
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int k = a.nb * S, Kt = k + S;
+  const int col0 = blockIdx.y * CG;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = warp >> 3, tile = warp & 7;
+  gram_prefetch<S>(sm, 0, a, si, src, lds, 0, col0, k);
+  cp_async_commit();
+  if (tid < 32) sm.Hs[tid] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < si.rows * S; idx += 512) {
+    const int r = idx / S, l = idx - r * S;
+    atomicMax(&sm.Hs[l], bexp(src[(si.row0 + r) * lds + l]));
+  }
+  __syncthreads();
+  if (blockIdx.y == 0 && tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = sm.Hs[tid];
+  for (int m = tid; m < CG; m += 512) {
+    const int col = col0 + m;
+    sm.Fs[m] = (col < k) ? a.colexp[(int64_t)col * a.p + si.chunk] : (col < Kt ? sm.Hs[col - k] : 0);
+  }
+  float acc[kGroupPairs][4];
+#pragma unroll
+  for (int i = 0; i < kGroupPairs; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  const int mt = tile % MT, nt = tile / MT;
+  const int nsteps = (si.rows + 15) / 16;
+  for (int st = 0; st < nsteps; ++st) {
+    const int buf = st & 1;
+    if (st + 1 < nsteps) gram_prefetch<S>(sm, buf ^ 1, a, si, src, lds, 16 * (st + 1), col0, k);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    // A: value pairs (rows 2j, 2j+1 of this step; column m)
+    for (int pi = tid; pi < 8 * CG; pi += 512) {
+      const int m = pi % CG, j = pi / CG;
+      const int col = col0 + m;
+      double x0 = 0.0, x1 = 0.0;
+      if (col < Kt) {
+        x0 = sm.raw[buf][2 * j][m];
+        x1 = sm.raw[buf][2 * j + 1][m];
+      }
+      const int mm = m & 15, kk = 2 * j;
+      const int ln = (mm & 7) * 4 + ((kk & 7) >> 1), rg = ((mm >> 3) & 1) + 2 * ((kk >> 3) & 1);
+      oz_store_pair(&sm.Apl[0][m >> 4][0][0], MT * 128, ln * 4 + rg, x0, sm.Fs[m], x1, sm.Fs[m], a.flags);
+    }
+    // B: value pairs of the block's columns
+    for (int pi = tid; pi < 8 * NC; pi += 512) {
+      const int n = pi % NC, j = pi / NC;
+      double x0 = 0.0, x1 = 0.0;
+      if (n < S) {
+        x0 = sm.rawB[buf][2 * j][n];
+        x1 = sm.rawB[buf][2 * j + 1][n];
+      }
+      const int e = (n < S) ? sm.Hs[n] : 0, kk = 2 * j;
+      const int ln = (n & 7) * 4 + ((kk & 7) >> 1), rg = (kk >> 3) & 1;
+      oz_store_pair(&sm.Bpl[0][n >> 3][0][0], NT * 64, ln * 2 + rg, x0, e, x1, e, a.flags);
+    }
+    __syncthreads();
+    if (grp == 0)
+      group_mma<0, false>(acc, &sm.Apl[0][mt][0][0], MT * 128, &sm.Bpl[0][nt][0][0], NT * 64, lane);
+    else
+      group_mma<1, false>(acc, &sm.Apl[0][mt][0][0], MT * 128, &sm.Bpl[0][nt][0][0], NT * 64, lane);
+  }
+  cp_async_wait0();
+  // flush: group 1 hands its integer partials to group 0, which writes
+  int s2[4];
+  long long rest[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (grp == 0)
+      group_partial<0>(acc, j, s2[j], rest[j]);
+    else
+      group_partial<1>(acc, j, s2[j], rest[j]);
+  }
+  if (grp == 1) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      sm.xs2[tile][lane][j] = s2[j];
+      sm.xrest[tile][lane][j] = rest[j];
+    }
+  }
+  __syncthreads();
+  if (grp == 0) {
+    const int g = lane >> 2, c = lane & 3;
+    double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int m = mt * 16 + g + ((j >> 1) << 3), n = nt * 8 + 2 * c + (j & 1);
+      const int col = col0 + m;
+      const double v = partial_to_double(s2[j] + sm.xs2[tile][lane][j], rest[j] + sm.xrest[tile][lane][j]);
+      if (col < Kt && n < S) out[(int64_t)col * S + n] = scale_exp(v, sm.Fs[m] + sm.Hs[n] - 2044 - 16);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coefficients of an assembly product for chunk c, scaled row by row by the
+// column exponents of [Q_i A] and sliced into B-fragment digit planes.
+//   mode 1 (new iterate of a reiteration, NOUT = 1): [-P N^{-1}; N^{-1}]
+//   mode 2 (stage 2, NOUT = 2): [-P N^{-1}, Pt - P N^{-1} Nt; N^{-1}, N^{-1} Nt]
+// with (P, N^{-1}) of the last local pass and [Pt; Nt] the new tree column block.
+template <int S, int NOUT>
+__global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
+  constexpr int NC = NOUT * S, NT = (NC + 7) / 8;
+  if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) double smc[];
+  const int c = blockIdx.x, k = a.nb * S, Kt = k + S;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, S);
+  const double* smallc = a.small + (int64_t)c * SL.stride;
+  const double* P = smallc + SL.P_last;
+  const double* Ninv = smallc + SL.Ninv_last;
+  const double* Tb = a.T + (int64_t)c * a.tstride + tblock_offset(a.nb, S);
+  double* Cf = smc;                               // Kt x NC (scaled)
+  double* PN = Cf + (size_t)Kt * NC;              // k x S: P N^{-1}
+  int* Gs = reinterpret_cast<int*>(PN + (size_t)k * S);  // NC
+  const int tid = threadIdx.x;
+  for (int e = tid; e < k * S; e += 256) {
+    const int q = e / S, l = e - q * S;
+    double v = 0.0;
+    for (int j = 0; j <= l; ++j) v += P[q * S + j] * Ninv[j * S + l];
+    PN[e] = v;
+  }
+  if (tid < NC) Gs[tid] = 0;
+  __syncthreads();
+  for (int e = tid; e < Kt * NC; e += 256) {
+    const int q = e / NC, n = e - q * NC;
+    double v;
+    if (n < S) {
+      v = (q < k) ? -PN[q * S + n] : Ninv[(q - k) * S + n];
+    } else {
+      const int l = n - S;
+      if (q < k) {
+        v = Tb[q * S + l];
+        for (int j = 0; j < S; ++j) v -= PN[q * S + j] * Tb[(k + j) * S + l];
+      } else {
+        v = 0.0;
+        for (int j = 0; j < S; ++j) v += Ninv[(q - k) * S + j] * Tb[(k + j) * S + l];
+      }
+    }
+    const int F = (q < k) ? a.colexp[(int64_t)q * a.p + c] : a.srcexp[(int64_t)c * 32 + (q - k)];
+    v = (F == 0 || v == 0.0) ? 0.0 : scale2(v, F - 1022);
+    Cf[e] = v;
+    atomicMax(&Gs[n], bexp(v));
+  }
+  __syncthreads();
+  unsigned* dig = a.coefdig + (int64_t)c * a.coefdig_stride;
+  const int ksteps = (Kt + 15) / 16;
+  // pairs (q even, q+1) for each column n
+  for (int pi = tid; pi < ksteps * 8 * NT * 8; pi += 256) {
+    const int n = pi % (NT * 8), qp = pi / (NT * 8), q = 2 * qp;
+    const double x0 = (n < NC && q < Kt) ? Cf[q * NC + n] : 0.0;
+    const double x1 = (n < NC && q + 1 < Kt) ? Cf[(q + 1) * NC + n] : 0.0;
+    const int e = (n < NC) ? Gs[n] : 0;
+    const int ks = q >> 4, kk = q & 15, nt = n >> 3;
+    const int ln = (n & 7) * 4 + ((kk & 7) >> 1), rg = (kk >> 3) & 1;
+    // layout: [kstep][ntile][plane][lane][2]
+    unsigned* base = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;
+    oz_store_pair(base, 64, ln * 2 + rg, x0, e, x1, e, a.flags);
+  }
+  for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
+}
+
+// ---------------------------------------------------------------------------
+// out = [Q_i A] Coef for one slab: NOUT = 1 writes the new iterate into the new
+// local panel; NOUT = 2 writes U_i into the panel and U to the caller, and
+// records the panel's column exponents.  mma: M = rows (16 per tile), N = output
+// columns, K = columns of [Q_i A] (16 per step).  Warp w: M-tile w % MT, N-tile
+// w / MT.  The next step's 16 columns of the row tile stream in with cp.async.
+template <int S, int NOUT>
+struct UpdSmem {
+  static constexpr int NC = NOUT * S, NT = (NC + 7) / 8, MT = (8 / NT) > 0 ? 8 / NT : 1, RT = MT * 16;
+  double raw[2][RT][16];
+  unsigned Apl[kOzDigits][MT][32][4];
+  long long xrest[8][32][4];
+  int xs2[8][32][4];
+  int Fs[1024];
+  int Cx[64];
+  int Ux[32];
+};
+
+template <int S, int NOUT>
+__device__ __forceinline__ void upd_prefetch(UpdSmem<S, NOUT>& sm, int buf, const StepArgs& a, const SlabInfo& si,
+                                             const double* src, int64_t lds, int rt, int ks, int k, int Kt) {
+  constexpr int RT = UpdSmem<S, NOUT>::RT;
+  for (int c = threadIdx.x; c < RT * 8; c += 512) {
+    const int r = c >> 3, j = c & 7, q0 = ks * 16 + 2 * j;
+    const bool rok = rt + r < si.rows;
+    const int64_t row = si.row0 + (rok ? rt + r : 0);
+    double* d = &sm.raw[buf][r][2 * j];
+    if (S >= 2 && q0 + 1 < k) {
+      cp_async16(d, a.V + (int64_t)(q0 / S) * a.n * S + row * S + (q0 % S), rok);
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = q0 + h;
+        const double* gp;
+        bool ok = rok && q < Kt;
+        if (q < k)
+          gp = a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S);
+        else if (q < Kt)
+          gp = src + row * lds + (q - k);
+        else
+          gp = src + row * lds;
+        cp_async8(d + h, gp, ok);
+      }
+    }
+  }
+}
+
+// out = [Q_i A] Coef for one slab: NOUT = 1 writes the new iterate into the new
+// local panel; NOUT = 2 writes U_i into the panel and U to the caller, and
+// records the panel's column exponents.  mma: M = rows (16 per tile), N = output
+// columns, K = columns of [Q_i A] (16 per step).  Warp w: tile w % 8 (M-tile
+// (w % 8) % MT, N-tile (w % 8) / MT), pair group w / 8.  The next step's 16
+// columns of the row tile stream in with cp.async.
+template <int S, int NOUT>
+__global__ void __launch_bounds__(512, 1) k_oz_update(StepArgs a, const double* src_fixed, int64_t lds_fixed,
+                                                      int pass) {
+  using SM = UpdSmem<S, NOUT>;
+  constexpr int NC = SM::NC, NT = SM::NT, MT = SM::MT, RT = SM::RT;
+  if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  SM& sm = *reinterpret_cast<SM*>(smraw);
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int c = si.chunk, k = a.nb * S, Kt = k + S;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = warp >> 3, tile = warp & 7;
+  const double* src = src_fixed;
+  int64_t lds = lds_fixed;
+  double* slot = a.V + (int64_t)a.nb * a.n * S;
+  if (NOUT == 2) {
+    int L = 1;
+    for (int t = 2; t <= kMaxPass; ++t)
+      if (a.flags[kFlagPass + t - 1]) L = t;
+    src = (L == 1) ? a.W : slot;
+    lds = (L == 1) ? a.ldw : S;
+  }
+  const int ksteps = (Kt + 15) / 16;
+  const int ntiles = (si.rows + RT - 1) / RT;
+  const int total = ntiles * ksteps;
+  upd_prefetch<S, NOUT>(sm, 0, a, si, src, lds, 0, 0, k, Kt);
+  cp_async_commit();
+  for (int q = tid; q < Kt; q += 512)
+    sm.Fs[q] = (q < k) ? a.colexp[(int64_t)q * a.p + c] : a.srcexp[(int64_t)c * 32 + (q - k)];
+  for (int n = tid; n < 64; n += 512) sm.Cx[n] = (n < NC) ? a.coefexp[(int64_t)c * 64 + n] : 0;
+  if (tid < 32) sm.Ux[tid] = 0;
+  const unsigned* dig = a.coefdig + (int64_t)c * a.coefdig_stride;
+  const int mt = tile % MT, nt = tile / MT;
+  const int g = lane >> 2, cl = lane & 3;
+  float acc[kGroupPairs][4];
+  double accd[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < kGroupPairs; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  for (int it = 0; it < total; ++it) {
+    const int rt = (it / ksteps) * RT, ks = it % ksteps, buf = it & 1;
+    if (it + 1 < total)
+      upd_prefetch<S, NOUT>(sm, buf ^ 1, a, si, src, lds, ((it + 1) / ksteps) * RT, (it + 1) % ksteps, k, Kt);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    // A: value pairs (row m, columns 2j, 2j+1 of this step)
+    for (int pi = tid; pi < RT * 8; pi += 512) {
+      const int j = pi & 7, m = pi >> 3;
+      const int q0 = ks * 16 + 2 * j;
+      const double x0 = sm.raw[buf][m][2 * j], x1 = sm.raw[buf][m][2 * j + 1];
+      const int e0 = q0 < Kt ? sm.Fs[q0] : 0, e1 = q0 + 1 < Kt ? sm.Fs[q0 + 1] : 0;
+      const int mm = m & 15, kk = 2 * j;
+      const int ln = (mm & 7) * 4 + ((kk & 7) >> 1), rg = ((mm >> 3) & 1) + 2 * ((kk >> 3) & 1);
+      oz_store_pair(&sm.Apl[0][m >> 4][0][0], MT * 128, ln * 4 + rg, x0, e0, x1, e1, a.flags);
+    }
+    __syncthreads();
+    const unsigned* bb = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;
+    if (grp == 0)
+      group_mma<0, true>(acc, &sm.Apl[0][mt][0][0], MT * 128, bb, 64, lane);
+    else
+      group_mma<1, true>(acc, &sm.Apl[0][mt][0][0], MT * 128, bb, 64, lane);
+    const bool last_k = (ks + 1 == ksteps);
+    if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
+      int s2[4];
+      long long rest[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (grp == 0)
+          group_partial<0>(acc, j, s2[j], rest[j]);
+        else
+          group_partial<1>(acc, j, s2[j], rest[j]);
+      }
+      if (grp == 1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          sm.xs2[tile][lane][j] = s2[j];
+          sm.xrest[tile][lane][j] = rest[j];
+        }
+      }
+      __syncthreads();
+      if (grp == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          accd[j] += partial_to_double(s2[j] + sm.xs2[tile][lane][j], rest[j] + sm.xrest[tile][lane][j]);
+      }
+#pragma unroll
+      for (int i = 0; i < kGroupPairs; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    }
+    if (last_k && grp == 0) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int m = mt * 16 + g + ((j >> 1) << 3), n = nt * 8 + 2 * cl + (j & 1);
+        const int r = rt + m;
+        if (r < si.rows && n < NC) {
+          const double d = scale_exp(accd[j], sm.Cx[n] - 1022 - 16);
+          const int64_t row = si.row0 + r;
+          if (n < S) {
+            slot[row * S + n] = d;
+            if (NOUT == 2) atomicMax(&sm.Ux[n], bexp(d));
+          } else {
+            a.U[row * a.ldu + (n - S)] = d;
+          }
+        }
+        accd[j] = 0.0;
+      }
+    }
+  }
+  cp_async_wait0();
+  if (NOUT == 2) {
+    __syncthreads();
+    if (tid < S) atomicMax(&a.colexp[(int64_t)(k + tid) * a.p + c], sm.Ux[tid]);
+  }
+}
+
+template <int S>
+cudaError_t gram_for(const StepArgs& a, int pass, cudaStream_t st) {
+  constexpr int NT = (S + 7) / 8, MT = 8 / NT, CG = MT * 16;
+  const int Kt = a.nb * S + S;
+  dim3 grid(a.nslab, (Kt + CG - 1) / CG);
+  const double* src = (pass == 1) ? a.W : a.V + (int64_t)a.nb * a.n * S;
+  const int64_t lds = (pass == 1) ? a.ldw : S;
+  k_oz_gram<S><<<grid, 512, sizeof(GramSmem<S>), st>>>(a, src, lds, pass);
+  return cudaGetLastError();
+}
+
+template <int S, int NOUT>
+size_t coef_smem(const StepArgs& a) {
+  const int k = a.nb * S, Kt = k + S;
+  return sizeof(double) * ((size_t)Kt * NOUT * S + (size_t)k * S) + sizeof(int) * 64;
+}
+
+template <int S>
+cudaError_t ypass_for(const StepArgs& a, int pass, cudaStream_t st) {
+  k_oz_coef<S, 1><<<a.p, 256, coef_smem<S, 1>(a), st>>>(a, pass);
+  const double* src = (pass == 2) ? a.W : a.V + (int64_t)a.nb * a.n * S;
+  const int64_t lds = (pass == 2) ? a.ldw : S;
+  k_oz_update<S, 1><<<a.nslab, 512, sizeof(UpdSmem<S, 1>), st>>>(a, src, lds, pass);
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t stage2_for(const StepArgs& a, cudaStream_t st) {
+  k_oz_coef<S, 2><<<a.p, 256, coef_smem<S, 2>(a), st>>>(a, 0);
+  k_oz_update<S, 2><<<a.nslab, 512, sizeof(UpdSmem<S, 2>), st>>>(a, nullptr, 0, 0);
+  return cudaGetLastError();
+}
+
+bool g_oz_attr = false;
+
+}  // namespace
+
+bool oz_supported(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32; }
+
+cudaError_t oz_set_attrs() {
+  if (g_oz_attr) return cudaSuccess;
+  const int big = 200 * 1024;
+  cudaError_t e;
+#define LO_OZ_ATTR(S)                                                                                  \
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))   \
+    return e;                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))   \
+    return e;                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_oz_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))      \
+    return e;                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_oz_update<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+    return e;                                                                                          \
+  if ((e = cudaFuncSetAttribute(k_oz_update<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  LO_OZ_ATTR(1)
+  LO_OZ_ATTR(2)
+  LO_OZ_ATTR(4)
+  LO_OZ_ATTR(8)
+  LO_OZ_ATTR(16)
+  LO_OZ_ATTR(32)
+#undef LO_OZ_ATTR
+  g_oz_attr = true;
+  return cudaSuccess;
+}
+
+#define LO_OZ_DISPATCH(CALL)       \
+  switch (a.s) {                   \
+    case 1: return CALL(1);        \
+    case 2: return CALL(2);        \
+    case 4: return CALL(4);        \
+    case 8: return CALL(8);        \
+    case 16: return CALL(16);      \
+    case 32: return CALL(32);      \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_oz_gram(const StepArgs& a, int pass, cudaStream_t st) {
+#define CALL(S) gram_for<S>(a, pass, st)
+  LO_OZ_DISPATCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_oz_ypass(const StepArgs& a, int pass, cudaStream_t st) {
+#define CALL(S) ypass_for<S>(a, pass, st)
+  LO_OZ_DISPATCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st) {
+#define CALL(S) stage2_for<S>(a, st)
+  LO_OZ_DISPATCH(CALL)
+#undef CALL
+}
+
+}  // namespace lo

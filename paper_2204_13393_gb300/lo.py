@@ -32,7 +32,7 @@ STATUS = {
     8: "LO_ERR_OOM",
     9: "LO_ERR_UNSUPPORTED",
 }
-PRECISION = {"fp64": 0, "mixed_fp32": 1}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "fp64_tc": 2}
 LEAF = {"auto": 0, "pip": 1, "pip2": 2}
 REDUCTION = {"auto": 0, "pip": 1, "pip2": 2}
 
@@ -41,9 +41,9 @@ EXPORTED = [
     "lo_basis_reset", "lo_basis_num_blocks", "lo_basis_num_chunks", "lo_basis_sync",
     "lo_orthogonalize", "lo_orthogonalize_batched", "lo_apply_Q", "lo_basis_export_chunk",
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
-    "lo_basis_last_step_info", "lo_tsqr_noalloc",
+    "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_basis_truncate", "lo_tune_chunk_rows",
 ]
-KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q"]
+KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
 
 class LoError(RuntimeError):
@@ -108,6 +108,10 @@ def _lib():
     L.lo_basis_last_step_info.restype = c_int32
     L.lo_tsqr_noalloc.argtypes = [c_int64, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
     L.lo_tsqr_noalloc.restype = c_int32
+    L.lo_basis_truncate.argtypes = [c_void_p, c_int32]
+    L.lo_basis_truncate.restype = c_int32
+    L.lo_tune_chunk_rows.argtypes = [c_int64, c_int32, c_int32, POINTER(Options), c_void_p, POINTER(c_int32)]
+    L.lo_tune_chunk_rows.restype = c_int32
     _L = L
     return L
 
@@ -173,7 +177,7 @@ class Basis:
     """A locally orthogonal basis (lo_basis) on the current CUDA device."""
 
     def __init__(self, n: int, s: int, max_blocks: int, chunk_rows: int, precision: str = "fp64",
-                 leaf: str = "auto", reduction: str = "auto", sync: bool = True,
+                 leaf: str = "pip2", reduction: str = "auto", sync: bool = True,
                  refine_tol: float = 0.0, stream=None):
         L = _lib()
         o = Options()
@@ -245,6 +249,9 @@ class Basis:
         _check(_lib().lo_apply_Q(self._h, _ptr(C), m, _ld(C, m), _ptr(Y), _ld(Y, m)), "lo_apply_Q")
         return Y
 
+    def truncate(self, num_blocks: int):
+        _check(_lib().lo_basis_truncate(self._h, int(num_blocks)), "lo_basis_truncate")
+
     def last_step_info(self):
         """(local Gram passes, reduction iterations) of the last step."""
         a, t = c_int32(), c_int32()
@@ -297,6 +304,20 @@ def tsqr_noalloc(W, U, R, chunk_rows: int, stream=None):
     _check(_lib().lo_tsqr_noalloc(n, s, int(chunk_rows), _ptr(W), _ld(W, s), _ptr(U), _ptr(R),
                                   c_void_p(_stream_handle(stream))), "lo_tsqr_noalloc")
     return U, R
+
+
+def tune_chunk_rows(n: int, s: int, max_blocks: int, precision: str = "fp64", leaf: str = "pip2",
+                    stream=None) -> int:
+    """lo_tune_chunk_rows: the fastest chunk size for this shape (measured)."""
+    L = _lib()
+    o = Options()
+    L.lo_options_default(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.leaf = LEAF[leaf]
+    out = c_int32()
+    _check(L.lo_tune_chunk_rows(int(n), int(s), int(max_blocks), ctypes.byref(o),
+                                c_void_p(_stream_handle(stream)), ctypes.byref(out)), "lo_tune_chunk_rows")
+    return out.value
 
 
 def launch_count() -> int:

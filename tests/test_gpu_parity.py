@@ -96,11 +96,15 @@ def gaussian_blocks(n, s, count, seed0):
     return [I.gaussian(n, s, seed0 + j) for j in range(count)]
 
 
-def test_arnoldi_step_small_workload():
+PRECISIONS = ["fp64", "fp64_tc"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_arnoldi_step_small_workload(precision):
     """n = 4096, s = 4, chunk_rows = 512: 8 prior blocks from seeded N(0,1)
     blocks, then the new block; outputs H (32 x 4) and R (4 x 4)."""
     n, s = 4096, 4
-    b = run_and_compare(n, s, 9, 512, gaussian_blocks(n, s, 9, I.seed_for(1)))
+    b = run_and_compare(n, s, 9, 512, gaussian_blocks(n, s, 9, I.seed_for(1)), precision=precision)
     assert b.k == 36
 
 
@@ -113,27 +117,30 @@ def test_arnoldi_step_small_workload():
     (3000, 32, 1000, 3),    # s = 32 (maximum width)
     (65573, 8, 4096, 6),    # many slabs per chunk, ragged
 ])
-def test_shapes_and_ragged(n, s, cr, M):
-    run_and_compare(n, s, M, cr, gaussian_blocks(n, s, M, 1000 + n + s))
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_shapes_and_ragged(n, s, cr, M, precision):
+    run_and_compare(n, s, M, cr, gaussian_blocks(n, s, M, 1000 + n + s), precision=precision)
 
 
 @pytest.mark.parametrize("leaf", ["pip", "pip2", "auto"])
 @pytest.mark.parametrize("reduction", ["pip", "pip2", "auto"])
-def test_leaf_and_reduction_modes(leaf, reduction):
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_leaf_and_reduction_modes(leaf, reduction, precision):
     n, s = 6000, 4
     run_and_compare(n, s, 5, 700, gaussian_blocks(n, s, 5, 2000), leaf=leaf, reduction=reduction,
-                    check_local=False)
+                    check_local=False, precision=precision)
 
 
-@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
-def test_stewart_block_qr(kappa):
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e8, 1e10])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_stewart_block_qr(kappa, precision):
     """Alg. 2 on a Stewart matrix (32 columns, s = 4) with the automatic
     reiteration: orthogonality and residual at float64 level; H and R are
     compared with the oracle where their forward error kappa*eps allows."""
     n, m, s = 16384, 32, 4
     A = I.stewart(n, m, kappa, 500 + int(np.log10(kappa)))
     blocks = [A[:, j * s:(j + 1) * s].copy() for j in range(m // s)]
-    b = lo().Basis(n, s, m // s, 1024)
+    b = lo().Basis(n, s, m // s, 1024, precision=precision)
     ora = O.LocallyOrthogonalBasis(n, s, 1024)
     Rg = np.zeros((m, m))
     Ro = np.zeros((m, m))
@@ -152,9 +159,30 @@ def test_stewart_block_qr(kappa):
     assert rel(Rg, Ro) <= max(TOL_REL, bound)
 
 
-def test_apply_Q_parity():
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_tall_skinny_qr_sweep(s, kappa, precision):
+    """The tall-skinny QR sweep's structure at reduced n (2^18 rows): k = 0,
+    A = U diag(sigma) V^T with log-spaced sigma; orthogonality and residual at
+    float64 level for every width and condition number; R compared with the
+    oracle (Householder TreeTSPQR) within its forward-error bound."""
+    n, cr = 2 ** 18, 4096
+    A = I.stewart(n, s, kappa, 700 + s + int(np.log10(kappa)))
+    b = lo().Basis(n, s, 1, cr, precision=precision)
+    U, _, R = b.orthogonalize(dev(A))
+    Uh, Rh = host(U), host(R)
+    assert O.e_perp(Uh) <= TOL_PERP
+    assert O.residual(A, Uh, Rh) <= TOL_RES
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    _, _, Ro = ora.orthogonalize(A, "hh", "hh")
+    assert rel(Rh, Ro) <= max(TOL_REL, 100 * kappa * np.finfo(float).eps)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_apply_Q_parity(precision):
     n, s = 9000, 4
-    b = lo().Basis(n, s, 6, 1000)
+    b = lo().Basis(n, s, 6, 1000, precision=precision)
     ora = O.LocallyOrthogonalBasis(n, s, 1000)
     for j in range(6):
         Wh = I.gaussian(n, s, 3000 + j)
@@ -202,12 +230,13 @@ def test_strided_and_aliased_buffers():
     assert np.array_equal(host(R1), host(R2))
 
 
-def test_bitwise_determinism():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_bitwise_determinism(precision):
     n, s = 20000, 8
     blocks = gaussian_blocks(n, s, 4, 3400)
     outs = []
     for _ in range(2):
-        b = lo().Basis(n, s, 4, 2048)
+        b = lo().Basis(n, s, 4, 2048, precision=precision)
         res = [tuple(host(x) for x in b.orthogonalize(dev(Wh)) if x is not None) for Wh in blocks]
         outs.append(res)
     for r1, r2 in zip(*outs):
@@ -215,10 +244,11 @@ def test_bitwise_determinism():
             assert np.array_equal(x, y)
 
 
-def test_error_paths_leave_basis_unchanged():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_error_paths_leave_basis_unchanged(precision):
     L = lo()
     n, s = 3000, 4
-    b = L.Basis(n, s, 3, 600)
+    b = L.Basis(n, s, 3, 600, precision=precision)
     b.orthogonalize(dev(I.gaussian(n, s, 3500)))
     # a block inside the span of the basis: breakdown, block count unchanged
     Q = host(b.apply_Q(dev(np.eye(s))))
@@ -298,6 +328,53 @@ def test_batched_uneven():
         assert b.num_blocks == len(Po) // b.s + 1
 
 
+def test_batched_graph_reuse_and_truncate():
+    """A repeat batched call with the same arguments replays the cached graph:
+    truncating the bases back and re-running gives bit-identical results, equal
+    to sequential calls; truncate drops blocks exactly."""
+    L = lo()
+    specs = [(6000, 8, 2), (20000, 4, 3), (3001, 16, 1)]
+    bases, Ws, Us, Hs, Rs, seq = [], [], [], [], [], []
+    for i, (n, s, kb) in enumerate(specs):
+        b = L.Basis(n, s, kb + 2, 1000)
+        b2 = L.Basis(n, s, kb + 2, 1000)
+        for j in range(kb):
+            Wj = dev(I.gaussian(n, s, 4000 + 10 * i + j))
+            b.orthogonalize(Wj)
+            b2.orthogonalize(Wj)
+        Wn = dev(I.gaussian(n, s, 4090 + i))
+        seq.append(tuple(host(x) for x in b2.orthogonalize(Wn)))
+        bases.append(b)
+        Ws.append(Wn)
+        Us.append(torch.empty(n, s, dtype=torch.float64, device="cuda"))
+        Hs.append(torch.empty(kb * s, s, dtype=torch.float64, device="cuda"))
+        Rs.append(torch.empty(s, s, dtype=torch.float64, device="cuda"))
+    outs = []
+    for rep in range(3):
+        for b, (n, s, kb) in zip(bases, specs):
+            b.truncate(kb)
+        L.orthogonalize_batched(bases, Ws, Us, Hs, Rs)
+        outs.append([(host(U), host(H), host(R)) for U, H, R in zip(Us, Hs, Rs)])
+    for rep in range(1, 3):
+        for a, c in zip(outs[0], outs[rep]):
+            for x, y in zip(a, c):
+                assert np.array_equal(x, y)
+    for (U, H, R), (Us_, Hs_, Rs_) in zip(outs[0], seq):
+        assert np.array_equal(U, Us_) and np.array_equal(H, Hs_) and np.array_equal(R, Rs_)
+    with pytest.raises(L.LoError):
+        bases[0].truncate(bases[0].num_blocks + 1)
+
+
+def test_chunk_rows_tuner():
+    L = lo()
+    cr = L.tune_chunk_rows(200000, 8, 6)
+    assert cr >= 256 and cr <= 200000 and (cr & (cr - 1)) == 0
+    assert L.tune_chunk_rows(200000, 8, 6) == cr    # memoized
+    b = L.Basis(200000, 8, 6, cr)
+    U, _, R = b.orthogonalize(dev(I.gaussian(200000, 8, 4100)))
+    assert O.e_perp(host(U)) <= TOL_PERP
+
+
 def test_laplace5_operator():
     nx, ny, s = 37, 23, 3
     X = I.uniform(nx * ny, s, 3800)
@@ -311,13 +388,14 @@ def test_laplace5_operator():
     assert np.abs(Y - ref.reshape(-1, s)).max() <= 1e-14
 
 
-def test_full_size_sampled_rows():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_full_size_sampled_rows(precision):
     """The block-GMRes workload's sizes (n = 2^20, s = 8, 4096-row chunks):
     three independent Gaussian blocks; every output compared with the oracle
     (BCGS-PIP+ sub-algorithms) on 4096 sampled rows and in full for H, R."""
     n, s, cr = 2 ** 20, 8, 4096
     blocks = gaussian_blocks(n, s, 3, 3900)
-    b = lo().Basis(n, s, 31, cr)
+    b = lo().Basis(n, s, 31, cr, precision=precision)
     ora = O.LocallyOrthogonalBasis(n, s, cr)
     rows = np.sort(I.rng(3999).choice(n, 4096, replace=False))
     for j, Wh in enumerate(blocks):

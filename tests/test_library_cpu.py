@@ -89,5 +89,5 @@ def test_options_default(lib):
 
     o = lo.Options()
     lib.lo_options_default(ctypes.byref(o))
-    assert (o.precision, o.leaf, o.reduction, o.sync) == (0, 0, 0, 1)
+    assert (o.precision, o.leaf, o.reduction, o.sync) == (0, 2, 0, 1)
     assert o.refine_tol == pytest.approx(1e-13)
