@@ -44,9 +44,12 @@ S = 8
 M_RESTART = 30
 CHUNK = 4096
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
-KERNEL_SRC = os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", "lo_kernels.cu")
-# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by
-# the sha256 (first 16 hex) of the kernel source it was taken on.
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", f) for f in ("lo_kernels.cu", "lo_ozaki.cu")]
+# DRAM bytes of one launch of the dominant kernel from one ncu capture (bench.py
+# --case profile: n = 2^20, s = 8, k = 120), with that launch's algorithmic bytes,
+# keyed by (kernel group, precision, sha256 prefix of the kernel sources).  The
+# reported traffic scales the measured ratio to the average launch of the cycle;
+# a source change invalidates the entry (traffic: null).
 TRAFFIC = {}
 
 
@@ -57,6 +60,14 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def peaks_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 def orth_bytes(n, s, k, p):
@@ -79,8 +90,11 @@ def gram_bytes_flops(n, s, k):
 
 
 def src_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 class Clocks:
@@ -251,42 +265,46 @@ def run_gpu(args):
     e_perp = float(torch.linalg.norm(G - torch.eye(G.shape[0], dtype=torch.float64, device=dev)))
     del Q, G
 
-    # dominant kernel group and its roofline
-    kinds = {g: v for g, v in prof.items() if v[1] > 0}
-    dom = max(kinds, key=lambda g: kinds[g][0])
+    # dominant kernel group (pass-1 Gram or stage-2 assembly) and its roofline
     hbm_peak, hbm_src = peaks()
-    if dom == "update":
-        bsum = fsum = 0
-        for j in range(m + 1):
-            b_, f_ = update_bytes_flops(n, s, j * s, p)
-            bsum += b_
-            fsum += f_
-        bsum *= args.steps
-        fsum *= args.steps
-    else:
-        bsum = fsum = 0
-        for j in range(m + 1):
-            b_, f_ = gram_bytes_flops(n, s, j * s)
-            bsum += b_
-            fsum += f_
-        bsum *= args.steps
-        fsum *= args.steps
+    tc = args.precision in ("fp64_tc", "mixed_tc")
+    kinds = {g: v for g, v in prof.items() if v[1] > 0}
+    dom = "update" if kinds.get("update", (0,))[0] >= kinds.get("gram", (0,))[0] else "gram"
+    bsum = fsum = 0
+    for j in range(m + 1):
+        b_, f_ = update_bytes_flops(n, s, j * s, p) if dom == "update" else gram_bytes_flops(n, s, j * s)
+        bsum += b_ * args.steps
+        fsum += f_ * args.steps
     t_dom = kinds[dom][0] * 1e-3
     ach_gbs = bsum / t_dom / 1e9
     ach_tf = fsum / t_dom / 1e12
-    alu_bound = (fsum / (FP64_PEAK_TFLOPS * 1e12)) > (bsum / (hbm_peak * 1e9))
-    kernel_name = {"update": "k_update", "gram": "k_gram"}.get(dom, dom)
-    traffic = TRAFFIC.get((kernel_name, src_hash()))
-    if alu_bound:
+    cap = TRAFFIC.get((dom, args.precision, src_hash()))
+    launches_dom = kinds[dom][1]
+    traffic = (round(cap["dram_bytes"] / cap["algorithmic_bytes"] * bsum / launches_dom)
+               if cap else None)
+    if tc:
+        kernel_name = {"update": "k_oz_update", "gram": "k_oz_gram"}[dom]
+        # tensor work: 28 fp16 digit-pair products per float64 product, 2 flops each
+        tens_tf = 28 * fsum / t_dom / 1e12
+        tens_peak = peaks_bf16()
+        bound = "hbm" if bsum / (hbm_peak * 1e9) >= 28 * fsum / (tens_peak * 1e12) else "tensor"
+        if bound == "hbm":
+            roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(ach_gbs / hbm_peak, 4), "traffic": traffic, "kernel": kernel_name,
+                    "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "tensor_tflops_fp16": round(tens_tf, 1), "launches": kinds[dom][1]}
+        else:
+            roof = {"bound": "tensor", "achieved": round(tens_tf, 1), "peak": tens_peak, "unit": "TFLOP/s",
+                    "frac": round(tens_tf / tens_peak, 4), "traffic": traffic, "kernel": kernel_name,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 mma at the same rate)",
+                    "hbm_achieved_gbs": round(ach_gbs, 1), "launches": kinds[dom][1]}
+    else:
+        kernel_name = {"update": "k_update", "gram": "k_gram1"}[dom]
         roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "kernel": kernel_name, "peak_source": "float64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz",
                 "hbm_achieved_gbs": round(ach_gbs, 1), "hbm_frac_of_measured": round(ach_gbs / hbm_peak, 4),
                 "launches": kinds[dom][1]}
-    else:
-        roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach_gbs / hbm_peak, 4), "traffic": traffic, "kernel": kernel_name,
-                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)", "launches": kinds[dom][1]}
 
     out = None
     if rank == 0:
@@ -530,6 +548,67 @@ def run_batched_case(args):
           flush=True)
 
 
+def run_mixed_case(args):
+    """Mixed-precision workload: n = 2^24 rows (--mixed-n), s = 16, 30 prior
+    blocks (480 columns, Gaussian, built untimed), new block a Stewart-type
+    matrix U diag(sigma) V^T with kappa in {1e2, 1e4, 1e6} (Haar factors from
+    torch.linalg.qr on the device).  Each step is timed with CUDA events for
+    the float64 tensor-core form and the mixed tensor-core form; the step's
+    orthogonality is sqrt(|U^T U - I|^2 + 2 |Q^T U|^2), with Q^T U measured by
+    one more projection of U (the H output of a PQR step of U)."""
+    import torch
+
+    from paper_2204_13393_gb300 import lo
+
+    dev = torch.device("cuda", 0)
+    lo.library()
+    n, s, kb = args.mixed_n, 16, 30
+    cr = 8192
+    out = {"case": "mixed", "n": n, "s": s, "k": kb * s, "chunk_rows": cr, "results": []}
+    g = torch.Generator(device=dev)
+    g.manual_seed(2204133930 + 4000)
+    prior = [torch.randn(n, s, dtype=torch.float64, device=dev, generator=g) for _ in range(kb)]
+    nbytes = orth_bytes(n, s, kb * s, max(1, n // cr))
+    for kappa in (1e2, 1e4, 1e6):
+        Uh, _ = torch.linalg.qr(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+        Vh, _ = torch.linalg.qr(torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+        sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device=dev)
+        W = (Uh * sig) @ Vh.T
+        # the block also has components along the basis, like a Krylov block
+        W = W + 0.5 * prior[kb - 1] / float(n) ** 0.5
+        row = {"kappa": kappa}
+        for prec in ("fp64_tc", "mixed_tc"):
+            b = lo.Basis(n, s, kb + 2, cr, precision=prec, sync=True)
+            for P in prior:
+                b.orthogonalize(P)
+            times = []
+            for rep in range(max(2, args.steps)):
+                b.truncate(kb)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                U, _, R = b.orthogonalize(W)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            passes = b.last_step_info()
+            UtU = U.T @ U
+            b.truncate(kb)
+            _, QtU, _ = b.orthogonalize(U.clone())   # H = Q^T U against the kb prior blocks
+            eye = torch.eye(s, dtype=torch.float64, device=dev)
+            qtu = QtU[:kb * s]
+            eperp = float(torch.sqrt(torch.linalg.norm(UtU - eye) ** 2 + 2 * torch.linalg.norm(qtu) ** 2))
+            ms = min(times[1:]) if len(times) > 1 else times[0]
+            row[prec] = {"ms": round(ms, 3), "gbs": round(nbytes / ms / 1e6, 1), "e_perp": eperp,
+                         "passes": passes[0], "tree_iterations": passes[1]}
+            b.close()
+            del U, R
+        row["speedup_mixed_vs_fp64"] = round(row["fp64_tc"]["ms"] / row["mixed_tc"]["ms"], 3)
+        out["results"].append(row)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,15 +616,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lo", choices=["lo", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc", "mixed_fp32"])
-    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched"],
-                    help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"])
+    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed"],
+                    help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances; "
+                         "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480")
+    ap.add_argument("--mixed-n", type=int, default=2 ** 24)
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)
         return
     if args.case == "batched":
         run_batched_case(args)
+        return
+    if args.case == "mixed":
+        run_mixed_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3

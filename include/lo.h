@@ -66,7 +66,7 @@ typedef enum lo_precision {
                            /* shifted Cholesky, one float64 CholeskyQR2-style    */
                            /* refinement pass, float64 tree and update (Alg. 8   */
                            /* pattern)                                            */
-  LO_PREC_FP64_TC = 2      /* float64-accurate products of the O(n) passes on the */
+  LO_PREC_FP64_TC = 2,     /* float64-accurate products of the O(n) passes on the */
                            /* tensor cores: every float64 value is split into 7   */
                            /* 8-bit digits against its column's largest exponent */
                            /* (error-free splitting of Ozaki et al., Numer.      */
@@ -76,6 +76,9 @@ typedef enum lo_precision {
                            /* integers.  Small factors stay float64.  Requires   */
                            /* s in {1, 2, 4, 8, 16, 32}; values below 2^-1022    */
                            /* (subnormals) count as zero.                        */
+  LO_PREC_MIXED_TC = 3     /* mixed form on the tensor-core path: the first Gram */
+                           /* pass in float32 (shifted float64 Cholesky), every  */
+                           /* further pass and the assembly as LO_PREC_FP64_TC   */
 } lo_precision;
 
 /* Local sub-algorithm (the "local subalgorithm" of Alg. 9). */

@@ -236,7 +236,9 @@ struct BatchGraphs {
   std::mutex mu;
   int device = -1;
   cudaStream_t st[kPool] = {};
+  cudaStream_t cap = nullptr;     // capture origin (the caller's stream may be the legacy one)
   cudaEvent_t fork = nullptr;
+  cudaEvent_t before = nullptr;
   cudaEvent_t join[kPool] = {};
   std::vector<GraphEntry> cache;
   unsigned long long clock = 0;
@@ -257,6 +259,8 @@ cudaError_t ensure_pool(BatchGraphs& bg, int device) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.join[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.before, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bg.cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) bg.device = device;
   return e;
 }
@@ -300,10 +304,11 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options o;
   lo_options_default(&o);
   if (opt) o = *opt;
-  if (o.precision < 0 || o.precision > 2 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
+  if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
       o.reduction > 2)
     return LO_ERR_INVALID_ARG;
-  if (o.precision == LO_PREC_FP64_TC && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
+  const bool tc = (o.precision == LO_PREC_FP64_TC || o.precision == LO_PREC_MIXED_TC);
+  if (tc && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
   if (o.refine_tol <= 0) o.refine_tol = 1e-13;
   const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
   if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
@@ -363,7 +368,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   alloc((void**)&b->d_slabs, sizeof(SlabInfo) * slabs.size());
   alloc((void**)&b->d_chunk_slab0, sizeof(int32_t) * cs0.size());
   alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
-  if (o.precision == LO_PREC_FP64_TC) {
+  if (tc) {
     b->coefdig_stride = lo::oz_coef_words(b->Kmax, 2 * s);
     alloc((void**)&b->colexp, sizeof(int) * (size_t)Kmax * p);
     alloc((void**)&b->srcexp_slab, sizeof(int) * (size_t)b->nslab * 32);
@@ -521,10 +526,10 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     // capture: fork onto the pool streams, one instance per stream round-robin, join
     if ((e = lo::launch_prepare()) != cudaSuccess) return from_cuda(e);
     cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(bg.cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return from_cuda(e);
     lo_status rs = LO_OK;
-    cudaEventRecord(bg.fork, cs);
+    cudaEventRecord(bg.fork, bg.cap);
     for (int i = 0; i < kPool; ++i) cudaStreamWaitEvent(bg.st[i], bg.fork, 0);
     for (int j = 0; j < count && rs == LO_OK; ++j) {
       lo_basis* b = bases[j];
@@ -541,9 +546,9 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     }
     for (int i = 0; i < kPool; ++i) {
       cudaEventRecord(bg.join[i], bg.st[i]);
-      cudaStreamWaitEvent(cs, bg.join[i], 0);
+      cudaStreamWaitEvent(bg.cap, bg.join[i], 0);
     }
-    e = cudaStreamEndCapture(cs, &graph);
+    e = cudaStreamEndCapture(bg.cap, &graph);
     if (rs != LO_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rs;

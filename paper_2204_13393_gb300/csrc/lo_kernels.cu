@@ -289,6 +289,18 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
   const int tid = threadIdx.x, g = tid / T, t = tid - g * T;
   const bool active = g < G;
   const int q0 = t * TQ;
+  if (a.srcexp_slab) {  // tensor-core assembly follows: the block's column exponents per slab
+    __shared__ int hs[32];
+    if (tid < 32) hs[tid] = 0;
+    __syncthreads();
+    for (int idx = tid; idx < si.rows * S; idx += kThreads) {
+      const int r = idx / S, l = idx - r * S;
+      const int ex = (int)((((unsigned long long)__double_as_longlong(a.W[(si.row0 + r) * a.ldw + l])) >> 52) & 0x7FF);
+      atomicMax(&hs[l], ex);
+    }
+    __syncthreads();
+    if (tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = hs[tid];
+  }
   Acc acc[TQ][S];
 #pragma unroll
   for (int i = 0; i < TQ; ++i)
@@ -432,7 +444,8 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     for (int e = threadIdx.x; e < ss; e += blockDim.x) smallc[SL.N_comb + e] = tmp[e];
   }
   if (threadIdx.x == 0 && pass < kMaxPass) {
-    const bool auto_mode = (a.leaf != LO_LEAF_PIP) || (a.precision == LO_PREC_MIXED_FP32);
+    const bool auto_mode = (a.leaf != LO_LEAF_PIP) || (a.precision == LO_PREC_MIXED_FP32) ||
+                           (a.precision == LO_PREC_MIXED_TC);
     if (auto_mode && !(DBL_EPSILON * kap * kap <= a.refine_tol))
       atomicOr(&a.flags[kFlagPass + pass], 1);
   }
@@ -818,7 +831,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   cudaError_t e = set_attrs();
   if (e) return e;
   const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
-  const bool mixed = (a.precision == LO_PREC_MIXED_FP32);
+  const bool mixed = (a.precision == LO_PREC_MIXED_FP32 || a.precision == LO_PREC_MIXED_TC);
   // The reduction always reiterates (BCGS-PIP+) unless plain PIP is asked for: its
   // projection uses the stacked tree factors of all earlier steps, whose rounding
   // errors a single pass amplifies step after step.
@@ -826,11 +839,11 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   count_launches(1);
   // stage 1
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
-  const bool tc = (a.precision == LO_PREC_FP64_TC);
+  const bool tc = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
   if (tc && (e = oz_set_attrs())) return e;
   for (int pass = 1; pass <= maxpass; ++pass) {
     mark(hook, pass == 1 ? kKindGram : kKindRefine, true, st);
-    if (tc) {
+    if (tc && !(pass == 1 && mixed)) {
       if (pass >= 2 && (e = launch_oz_ypass(a, pass, st))) return e;
       if ((e = launch_oz_gram(a, pass, st))) return e;
       count_launches(pass >= 2 ? 3 : 1);

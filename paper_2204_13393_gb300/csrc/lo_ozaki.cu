@@ -40,49 +40,32 @@ __device__ __forceinline__ int bexp(double x) {
 }
 
 // Aligned significand of |x| against group exponent emax: Y < 2^56 as (yhi, ylo),
-// sign in bit 31 of sgn.  Zero, subnormals and values 2^56 below the group give 0.
-__device__ __forceinline__ void oz_split(double x, int emax, unsigned& yhi, unsigned& ylo, unsigned& sgn) {
+// sign in bit 31 of sgn.  Zero, subnormals and values 2^56 below the group give 0;
+// returns true for Inf/NaN.
+__device__ __forceinline__ bool oz_split(double x, int emax, unsigned& yhi, unsigned& ylo, unsigned& sgn) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
   const int e = (int)((hi >> 20) & 0x7FFu);
   sgn = hi & 0x80000000u;
-  unsigned mh = ((((hi & 0xFFFFFu) | 0x100000u) << 3) | (lo >> 29));
-  unsigned ml = lo << 3;
-  int sh = emax - e;
-  if (e == 0 || sh > 55 || sh < 0) {
-    mh = 0u;
-    ml = 0u;
-    sh = 0;
-  }
-  if (sh >= 32) {
-    ml = mh >> (sh - 32);
-    mh = 0u;
-  } else if (sh > 0) {
-    ml = __funnelshift_r(ml, mh, sh);
-    mh >>= sh;
-  }
-  yhi = mh;
-  ylo = ml;
+  unsigned long long m = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 3;
+  const int sh = emax - e;
+  m = (e == 0 || sh > 55 || sh < 0) ? 0ull : (m >> sh);
+  yhi = (unsigned)(m >> 32);
+  ylo = (unsigned)m;
+  return e == 0x7FF;
 }
 
-// fp16x2 with the digits of plane t (1..7) of two values (low half = first).
-__device__ __forceinline__ unsigned oz_pack(int t, unsigned h0, unsigned l0, unsigned h1, unsigned l1,
-                                            unsigned sg2, unsigned bias2) {
+// fp16x2 with the digits of plane t (1..7) of two values (low half = first),
+// encoded as fp16 subnormals: the bits (sign << 15) | digit are the value
+// +-digit * 2^-24 exactly, so no arithmetic is needed; products of two digits
+// are integers times 2^-48, exact in float32.  sb: the two sign bits (bit 15
+// for the first value, bit 31 for the second).
+__device__ __forceinline__ unsigned oz_pack(int t, unsigned h0, unsigned l0, unsigned h1, unsigned l1, unsigned sb) {
   const bool hiw = t <= 3;
   const unsigned w0 = hiw ? h0 : l0, w1 = hiw ? h1 : l1;
   const unsigned bi = hiw ? (unsigned)(3 - t) : (unsigned)(7 - t);
-  unsigned v = __byte_perm(w0, w1, bi | ((4u + bi) << 8));
-  v = (v & 0x00FF00FFu) | 0x64006400u;  // fp16 1024 + digit in each half
-  unsigned r;
-  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(v), "r"(sg2), "r"(bias2));
-  return r;
-}
-
-// Sign multiplier (+-1) and bias (-+1024) halves for a value pair.
-__device__ __forceinline__ void oz_signs(unsigned s0, unsigned s1, unsigned& sg2, unsigned& bias2) {
-  const unsigned sb = (s0 >> 16) | s1;
-  sg2 = 0x3C003C00u | sb;
-  bias2 = 0xE400E400u ^ sb;
+  const unsigned v = __byte_perm(w0, w1, bi | ((4u + bi) << 8));
+  return (v & 0x00FF00FFu) | sb;
 }
 
 // Write the 7 digit planes of a value pair into fragment storage.
@@ -90,13 +73,11 @@ __device__ __forceinline__ void oz_signs(unsigned s0, unsigned s1, unsigned& sg2
 __device__ __forceinline__ void oz_store_pair(unsigned* base, int plane_stride, int idx, double x0, int e0,
                                               double x1, int e1, int* flags) {
   unsigned h0, l0, s0, h1, l1, s1;
-  oz_split(x0, e0, h0, l0, s0);
-  oz_split(x1, e1, h1, l1, s1);
-  if (bexp(x0) == 0x7FF || bexp(x1) == 0x7FF) oz_status(flags, LO_ERR_NONFINITE);
-  unsigned sg2, bias2;
-  oz_signs(s0, s1, sg2, bias2);
+  const bool bad = oz_split(x0, e0, h0, l0, s0) | oz_split(x1, e1, h1, l1, s1);
+  if (bad) oz_status(flags, LO_ERR_NONFINITE);
+  const unsigned sb = (s0 >> 16) | s1;
 #pragma unroll
-  for (int t = 1; t <= kOzDigits; ++t) base[(t - 1) * plane_stride + idx] = oz_pack(t, h0, l0, h1, l1, sg2, bias2);
+  for (int t = 1; t <= kOzDigits; ++t) base[(t - 1) * plane_stride + idx] = oz_pack(t, h0, l0, h1, l1, sb);
 }
 
 __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
@@ -125,7 +106,7 @@ __device__ __forceinline__ void for_pairs(F&& f) {
 // multiply-add rounds the sum once, so the result carries float64 accuracy.
 __device__ __forceinline__ double oz_combine(const float (&acc)[kPairs][4], int j) {
   int Sv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for_pairs([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j]); });
+  for_pairs([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j] * 0x1p48f); });
   long long rest = (long long)Sv[3] * (1LL << 37);
   rest += (long long)Sv[4] * (1LL << 29);
   rest += (long long)Sv[5] * (1LL << 21);
@@ -157,7 +138,7 @@ __device__ __forceinline__ void for_group_pairs(F&& f) {
 template <int G>
 __device__ __forceinline__ void group_partial(const float (&acc)[kGroupPairs][4], int j, int& s2, long long& rest) {
   int Sv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  for_group_pairs<G>([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j]); });
+  for_group_pairs<G>([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j] * 0x1p48f); });
   s2 = Sv[2];
   long long r = (long long)Sv[3] * (1LL << 37);
   r += (long long)Sv[4] * (1LL << 29);
@@ -238,7 +219,7 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 template <int S>
 struct GramSmem {
   static constexpr int NT = (S + 7) / 8, MT = 8 / NT, CG = MT * 16, NC = NT * 8;
-  double raw[2][16][CG];
+  double raw[2][16][CG + 1];  // one pad double per row: fragment-ordered reads hit 2 wavefronts
   double rawB[2][16][S];
   unsigned Apl[kOzDigits][MT][32][4];
   unsigned Bpl[kOzDigits][NT][32][2];
@@ -256,20 +237,13 @@ __device__ __forceinline__ void gram_prefetch(GramSmem<S>& sm, int buf, const St
   // columns of the local panels inside this group: whole panels (S divides 16, or CG == S)
   const int qend = min(col0 + CG, k);
   const int qn = qend > col0 ? qend - col0 : 0;  // multiple of S
-  if (S >= 2) {
-    const int per_row = qn / 2;  // 16-byte copies per row
-    for (int c = tid; c < 16 * per_row; c += 512) {
-      const int r = c / per_row, cc = c - r * per_row, q = col0 + 2 * cc;
-      const bool ok = r0 + r < si.rows;
-      const int64_t row = si.row0 + (ok ? r0 + r : 0);
-      cp_async16(&sm.raw[buf][r][2 * cc], a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S), ok);
-    }
-  } else {
-    for (int c = tid; c < 16 * qn; c += 512) {
-      const int r = c / qn, cc = c - r * qn, q = col0 + cc;
-      const bool ok = r0 + r < si.rows;
-      const int64_t row = si.row0 + (ok ? r0 + r : 0);
-      cp_async8(&sm.raw[buf][r][cc], a.V + (int64_t)q * a.n + row, ok);
+  {
+    const int r = tid >> 5, l0 = tid & 31;  // 16 rows x 32 lanes
+    const bool ok = r0 + r < si.rows;
+    const int64_t row = si.row0 + (ok ? r0 + r : 0);
+    for (int cc = l0; cc < qn; cc += 32) {
+      const int q = col0 + cc;
+      cp_async8(&sm.raw[buf][r][cc], a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S), ok);
     }
   }
   // the block's own columns: in the A tile when inside this group, and as the B operand
@@ -327,30 +301,31 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    // A: value pairs (rows 2j, 2j+1 of this step; column m)
+    // A: value pairs (rows 2j, 2j+1 of this step; column m), taken in fragment
+    // order so that each digit-plane store of a warp is 32 consecutive words
     for (int pi = tid; pi < 8 * CG; pi += 512) {
-      const int m = pi % CG, j = pi / CG;
+      const int mtile = pi >> 7, w = pi & 127, ln = w >> 2, rg = w & 3;
+      const int mm = (ln >> 2) + 8 * (rg & 1), j = (ln & 3) + 4 * (rg >> 1);
+      const int m = mtile * 16 + mm;
       const int col = col0 + m;
       double x0 = 0.0, x1 = 0.0;
       if (col < Kt) {
         x0 = sm.raw[buf][2 * j][m];
         x1 = sm.raw[buf][2 * j + 1][m];
       }
-      const int mm = m & 15, kk = 2 * j;
-      const int ln = (mm & 7) * 4 + ((kk & 7) >> 1), rg = ((mm >> 3) & 1) + 2 * ((kk >> 3) & 1);
-      oz_store_pair(&sm.Apl[0][m >> 4][0][0], MT * 128, ln * 4 + rg, x0, sm.Fs[m], x1, sm.Fs[m], a.flags);
+      oz_store_pair(&sm.Apl[0][mtile][0][0], MT * 128, w, x0, sm.Fs[m], x1, sm.Fs[m], a.flags);
     }
-    // B: value pairs of the block's columns
+    // B: value pairs of the block's columns, in fragment order
     for (int pi = tid; pi < 8 * NC; pi += 512) {
-      const int n = pi % NC, j = pi / NC;
+      const int ntile = pi >> 6, w = pi & 63, ln = w >> 1, rg = w & 1;
+      const int n = ntile * 8 + (ln >> 2), j = (ln & 3) + 4 * rg;
       double x0 = 0.0, x1 = 0.0;
       if (n < S) {
         x0 = sm.rawB[buf][2 * j][n];
         x1 = sm.rawB[buf][2 * j + 1][n];
       }
-      const int e = (n < S) ? sm.Hs[n] : 0, kk = 2 * j;
-      const int ln = (n & 7) * 4 + ((kk & 7) >> 1), rg = (kk >> 3) & 1;
-      oz_store_pair(&sm.Bpl[0][n >> 3][0][0], NT * 64, ln * 2 + rg, x0, e, x1, e, a.flags);
+      const int e = (n < S) ? sm.Hs[n] : 0;
+      oz_store_pair(&sm.Bpl[0][ntile][0][0], NT * 64, w, x0, e, x1, e, a.flags);
     }
     __syncthreads();
     if (grp == 0)
@@ -466,7 +441,7 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
 template <int S, int NOUT>
 struct UpdSmem {
   static constexpr int NC = NOUT * S, NT = (NC + 7) / 8, MT = (8 / NT) > 0 ? 8 / NT : 1, RT = MT * 16;
-  double raw[2][RT][16];
+  double raw[2][RT][17];  // one pad double per row (see GramSmem)
   unsigned Apl[kOzDigits][MT][32][4];
   long long xrest[8][32][4];
   int xs2[8][32][4];
@@ -484,22 +459,18 @@ __device__ __forceinline__ void upd_prefetch(UpdSmem<S, NOUT>& sm, int buf, cons
     const bool rok = rt + r < si.rows;
     const int64_t row = si.row0 + (rok ? rt + r : 0);
     double* d = &sm.raw[buf][r][2 * j];
-    if (S >= 2 && q0 + 1 < k) {
-      cp_async16(d, a.V + (int64_t)(q0 / S) * a.n * S + row * S + (q0 % S), rok);
-    } else {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int q = q0 + h;
-        const double* gp;
-        bool ok = rok && q < Kt;
-        if (q < k)
-          gp = a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S);
-        else if (q < Kt)
-          gp = src + row * lds + (q - k);
-        else
-          gp = src + row * lds;
-        cp_async8(d + h, gp, ok);
-      }
+    for (int h = 0; h < 2; ++h) {
+      const int q = q0 + h;
+      const double* gp;
+      bool ok = rok && q < Kt;
+      if (q < k)
+        gp = a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S);
+      else if (q < Kt)
+        gp = src + row * lds + (q - k);
+      else
+        gp = src + row * lds;
+      cp_async8(d + h, gp, ok);
     }
   }
 }
@@ -557,13 +528,13 @@ __global__ void __launch_bounds__(512, 1) k_oz_update(StepArgs a, const double* 
     __syncthreads();
     // A: value pairs (row m, columns 2j, 2j+1 of this step)
     for (int pi = tid; pi < RT * 8; pi += 512) {
-      const int j = pi & 7, m = pi >> 3;
+      const int mtile = pi >> 7, w = pi & 127, ln = w >> 2, rg = w & 3;
+      const int mm = (ln >> 2) + 8 * (rg & 1), j = (ln & 3) + 4 * (rg >> 1);
+      const int m = mtile * 16 + mm;
       const int q0 = ks * 16 + 2 * j;
       const double x0 = sm.raw[buf][m][2 * j], x1 = sm.raw[buf][m][2 * j + 1];
       const int e0 = q0 < Kt ? sm.Fs[q0] : 0, e1 = q0 + 1 < Kt ? sm.Fs[q0 + 1] : 0;
-      const int mm = m & 15, kk = 2 * j;
-      const int ln = (mm & 7) * 4 + ((kk & 7) >> 1), rg = ((mm >> 3) & 1) + 2 * ((kk >> 3) & 1);
-      oz_store_pair(&sm.Apl[0][m >> 4][0][0], MT * 128, ln * 4 + rg, x0, e0, x1, e1, a.flags);
+      oz_store_pair(&sm.Apl[0][mtile][0][0], MT * 128, w, x0, e0, x1, e1, a.flags);
     }
     __syncthreads();
     const unsigned* bb = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;

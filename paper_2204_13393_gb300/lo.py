@@ -32,7 +32,7 @@ STATUS = {
     8: "LO_ERR_OOM",
     9: "LO_ERR_UNSUPPORTED",
 }
-PRECISION = {"fp64": 0, "mixed_fp32": 1, "fp64_tc": 2}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "fp64_tc": 2, "mixed_tc": 3}
 LEAF = {"auto": 0, "pip": 1, "pip2": 2}
 REDUCTION = {"auto": 0, "pip": 1, "pip2": 2}
 

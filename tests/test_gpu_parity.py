@@ -277,19 +277,21 @@ def test_error_paths_leave_basis_unchanged(precision):
     assert b.num_blocks == 3
 
 
-def test_mixed_precision_form():
+@pytest.mark.parametrize("precision", ["mixed_fp32", "mixed_tc"])
+def test_mixed_precision_form(precision):
     """First Gram pass in float32, shifted Cholesky, float64 refinement: the
     results meet the float64 tolerances for Gaussian blocks."""
     n, s = 32768, 16
     blocks = gaussian_blocks(n, s, 4, 3600)
-    run_and_compare(n, s, 4, 2048, blocks, precision="mixed_fp32", check_local=False)
+    run_and_compare(n, s, 4, 2048, blocks, precision=precision, check_local=False)
 
 
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
-def test_mixed_precision_stewart(kappa):
+@pytest.mark.parametrize("precision", ["mixed_fp32", "mixed_tc"])
+def test_mixed_precision_stewart(kappa, precision):
     n, m, s = 32768, 32, 16
     A = I.stewart(n, m, kappa, 600 + int(np.log10(kappa)))
-    b = lo().Basis(n, s, 2, 4096, precision="mixed_fp32")
+    b = lo().Basis(n, s, 2, 4096, precision=precision)
     U0, _, R0 = b.orthogonalize(dev(A[:, :s].copy()))
     U1, H1, R1 = b.orthogonalize(dev(A[:, s:].copy()))
     Q = host(b.apply_Q(dev(np.eye(m))))
