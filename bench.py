@@ -152,6 +152,20 @@ class Clocks:
 
 # --------------------------------------------------------------------------- GPU arm
 
+def replica_reduce(ms_local, bytes_local, dist=None, device=None):
+    """Independent replicas (one problem per rank, no exchange in the method):
+    the job time is the slowest rank's, the work is the sum over ranks."""
+    if dist is None:
+        return float(ms_local), int(bytes_local)
+    import torch
+
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(bytes_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(b.item())
+
+
 def gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events, record=None):
     """One restart cycle on the device.  events: list receiving (start, end)
     CUDA event pairs around each hot-path call.  Returns the apply_Q result."""
@@ -250,13 +264,8 @@ def run_gpu(args):
     basis.set_profiling(False)
     prof = basis.profile_read()
     dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in events)
-    # max over ranks
-    t_local = dev_ms
-    if dist:
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_local = float(t.item())
-    total_bytes = bytes_cycle * args.steps * world
+    # replicas: max time over ranks, bytes of all ranks
+    t_local, total_bytes = replica_reduce(dev_ms, bytes_cycle * args.steps, dist, dev)
     gbs = total_bytes / (t_local * 1e-3) / 1e9
 
     # correctness of the last cycle (properties at full size)
@@ -320,6 +329,9 @@ def run_gpu(args):
                                    "stencil and host least-squares untimed",
                        "n": n, "s": s, "restart_blocks": m, "chunk_rows": CHUNK, "chunks": p,
                        "precision": args.precision, "leaf": "pip2", "reduction": "auto",
+                       "arithmetic": ("float64-accurate products on fp16 tensor cores (exact 8-bit digit "
+                                      "splitting, exact float32 sums, integer recombination); float64 "
+                                      "small factors") if args.precision == "fp64_tc" else args.precision,
                        "l2": "inputs larger than L2 (basis 2.1 GB, 8 MB per block)",
                        "parallelism": f"replicas{world}"},
             "block_steps_per_s": round((m + 1) * args.steps * world / (t_local * 1e-3), 2),
@@ -616,7 +628,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lo", choices=["lo", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"])
+    ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"],
+                    help="fp64_tc (default): float64-accurate products on the tensor cores; fp64: native float64")
     ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed"],
                     help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances; "
                          "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480")

@@ -494,8 +494,9 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum1(StepArgs a, int it) {
   if (!a.flags[kFlagTree + it - 1]) return;
   const int s = a.s, E = (a.nb * s + s) * s;
   const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  // blockIdx.y splits the entries so that many CTAs share the work
   const int c0 = blockIdx.x * kTreeGroup, c1 = min(a.p, c0 + kTreeGroup);
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < E; e += gridDim.y * blockDim.x) {
     double v = 0.0;
     for (int c = c0; c < c1; ++c) v += a.small[(int64_t)c * SL.stride + SL.Z + e];
     a.tsum[(int64_t)blockIdx.x * a.Kmax * s + e] = v;
@@ -873,7 +874,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   mark(hook, kKindTree, true, st);
   for (int it = 1; it <= (a.reduction == 1 ? 1 : kMaxTreeIter); ++it) {
     k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
-    k_tree_sum1<<<ngroups, kThreads, 0, st>>>(a, it);
+    k_tree_sum1<<<dim3(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, it);
     k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
     k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
     count_launches(4);

@@ -221,8 +221,8 @@ struct GramSmem {
   static constexpr int NT = (S + 7) / 8, MT = 8 / NT, CG = MT * 16, NC = NT * 8;
   double raw[2][16][CG + 1];  // one pad double per row: fragment-ordered reads hit 2 wavefronts
   double rawB[2][16][S];
-  unsigned Apl[kOzDigits][MT][32][4];
-  unsigned Bpl[kOzDigits][NT][32][2];
+  unsigned Apl[2][kOzDigits][MT][32][4];
+  unsigned Bpl[2][kOzDigits][NT][32][2];
   long long xrest[8][32][4];
   int xs2[8][32][4];
   int Hs[32];
@@ -295,13 +295,9 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
   for (int i = 0; i < kGroupPairs; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
   const int mt = tile % MT, nt = tile / MT;
   const int nsteps = (si.rows + 15) / 16;
-  for (int st = 0; st < nsteps; ++st) {
-    const int buf = st & 1;
-    if (st + 1 < nsteps) gram_prefetch<S>(sm, buf ^ 1, a, si, src, lds, 16 * (st + 1), col0, k);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    // A: value pairs (rows 2j, 2j+1 of this step; column m), taken in fragment
+  // slice the float64 tile of one 16-row step into digit-plane buffer pb
+  auto slice = [&](int rb, int pb) {
+    // A: value pairs (rows 2j, 2j+1 of the step; column m), taken in fragment
     // order so that each digit-plane store of a warp is 32 consecutive words
     for (int pi = tid; pi < 8 * CG; pi += 512) {
       const int mtile = pi >> 7, w = pi & 127, ln = w >> 2, rg = w & 3;
@@ -310,10 +306,10 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
       const int col = col0 + m;
       double x0 = 0.0, x1 = 0.0;
       if (col < Kt) {
-        x0 = sm.raw[buf][2 * j][m];
-        x1 = sm.raw[buf][2 * j + 1][m];
+        x0 = sm.raw[rb][2 * j][m];
+        x1 = sm.raw[rb][2 * j + 1][m];
       }
-      oz_store_pair(&sm.Apl[0][mtile][0][0], MT * 128, w, x0, sm.Fs[m], x1, sm.Fs[m], a.flags);
+      oz_store_pair(&sm.Apl[pb][0][mtile][0][0], MT * 128, w, x0, sm.Fs[m], x1, sm.Fs[m], a.flags);
     }
     // B: value pairs of the block's columns, in fragment order
     for (int pi = tid; pi < 8 * NC; pi += 512) {
@@ -321,17 +317,31 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
       const int n = ntile * 8 + (ln >> 2), j = (ln & 3) + 4 * rg;
       double x0 = 0.0, x1 = 0.0;
       if (n < S) {
-        x0 = sm.rawB[buf][2 * j][n];
-        x1 = sm.rawB[buf][2 * j + 1][n];
+        x0 = sm.rawB[rb][2 * j][n];
+        x1 = sm.rawB[rb][2 * j + 1][n];
       }
       const int e = (n < S) ? sm.Hs[n] : 0;
-      oz_store_pair(&sm.Bpl[0][ntile][0][0], NT * 64, w, x0, e, x1, e, a.flags);
+      oz_store_pair(&sm.Bpl[pb][0][ntile][0][0], NT * 64, w, x0, e, x1, e, a.flags);
     }
+  };
+  // pipeline: step st+2 streams into the raw buffer of step st, step st+1 is
+  // sliced while step st is multiplied; one barrier per step
+  if (nsteps > 1) gram_prefetch<S>(sm, 1, a, si, src, lds, 16, col0, k);
+  cp_async_commit();
+  cp_async_wait1();
+  __syncthreads();
+  slice(0, 0);
+  for (int st = 0; st < nsteps; ++st) {
+    cp_async_wait0();
     __syncthreads();
+    if (st + 2 < nsteps) gram_prefetch<S>(sm, st & 1, a, si, src, lds, 16 * (st + 2), col0, k);
+    cp_async_commit();
+    if (st + 1 < nsteps) slice((st + 1) & 1, (st + 1) & 1);
+    const int pb = st & 1;
     if (grp == 0)
-      group_mma<0, false>(acc, &sm.Apl[0][mt][0][0], MT * 128, &sm.Bpl[0][nt][0][0], NT * 64, lane);
+      group_mma<0, false>(acc, &sm.Apl[pb][0][mt][0][0], MT * 128, &sm.Bpl[pb][0][nt][0][0], NT * 64, lane);
     else
-      group_mma<1, false>(acc, &sm.Apl[0][mt][0][0], MT * 128, &sm.Bpl[0][nt][0][0], NT * 64, lane);
+      group_mma<1, false>(acc, &sm.Apl[pb][0][mt][0][0], MT * 128, &sm.Bpl[pb][0][nt][0][0], NT * 64, lane);
   }
   cp_async_wait0();
   // flush: group 1 hands its integer partials to group 0, which writes
@@ -442,7 +452,7 @@ template <int S, int NOUT>
 struct UpdSmem {
   static constexpr int NC = NOUT * S, NT = (NC + 7) / 8, MT = (8 / NT) > 0 ? 8 / NT : 1, RT = MT * 16;
   double raw[2][RT][17];  // one pad double per row (see GramSmem)
-  unsigned Apl[kOzDigits][MT][32][4];
+  unsigned Apl[2][kOzDigits][MT][32][4];
   long long xrest[8][32][4];
   int xs2[8][32][4];
   int Fs[1024];
@@ -519,29 +529,40 @@ __global__ void __launch_bounds__(512, 1) k_oz_update(StepArgs a, const double* 
   double accd[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int i = 0; i < kGroupPairs; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-  for (int it = 0; it < total; ++it) {
-    const int rt = (it / ksteps) * RT, ks = it % ksteps, buf = it & 1;
-    if (it + 1 < total)
-      upd_prefetch<S, NOUT>(sm, buf ^ 1, a, si, src, lds, ((it + 1) / ksteps) * RT, (it + 1) % ksteps, k, Kt);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    // A: value pairs (row m, columns 2j, 2j+1 of this step)
+  // slice the float64 tile of iteration it (row tile, 16 columns) into plane buffer pb
+  auto slice = [&](int itx, int rb, int pb) {
+    const int ks = itx % ksteps;
     for (int pi = tid; pi < RT * 8; pi += 512) {
       const int mtile = pi >> 7, w = pi & 127, ln = w >> 2, rg = w & 3;
       const int mm = (ln >> 2) + 8 * (rg & 1), j = (ln & 3) + 4 * (rg >> 1);
       const int m = mtile * 16 + mm;
       const int q0 = ks * 16 + 2 * j;
-      const double x0 = sm.raw[buf][m][2 * j], x1 = sm.raw[buf][m][2 * j + 1];
+      const double x0 = sm.raw[rb][m][2 * j], x1 = sm.raw[rb][m][2 * j + 1];
       const int e0 = q0 < Kt ? sm.Fs[q0] : 0, e1 = q0 + 1 < Kt ? sm.Fs[q0 + 1] : 0;
-      oz_store_pair(&sm.Apl[0][mtile][0][0], MT * 128, w, x0, e0, x1, e1, a.flags);
+      oz_store_pair(&sm.Apl[pb][0][mtile][0][0], MT * 128, w, x0, e0, x1, e1, a.flags);
     }
+  };
+  // pipeline as in k_oz_gram: iteration it+2 streams into the raw buffer of it,
+  // it+1 is sliced while it is multiplied; one barrier per iteration
+  if (total > 1) upd_prefetch<S, NOUT>(sm, 1, a, si, src, lds, (1 / ksteps) * RT, 1 % ksteps, k, Kt);
+  cp_async_commit();
+  cp_async_wait1();
+  __syncthreads();
+  slice(0, 0, 0);
+  for (int it = 0; it < total; ++it) {
+    const int rt = (it / ksteps) * RT, ks = it % ksteps;
+    cp_async_wait0();
     __syncthreads();
+    if (it + 2 < total)
+      upd_prefetch<S, NOUT>(sm, it & 1, a, si, src, lds, ((it + 2) / ksteps) * RT, (it + 2) % ksteps, k, Kt);
+    cp_async_commit();
+    if (it + 1 < total) slice(it + 1, (it + 1) & 1, (it + 1) & 1);
+    const int pb = it & 1;
     const unsigned* bb = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;
     if (grp == 0)
-      group_mma<0, true>(acc, &sm.Apl[0][mt][0][0], MT * 128, bb, 64, lane);
+      group_mma<0, true>(acc, &sm.Apl[pb][0][mt][0][0], MT * 128, bb, 64, lane);
     else
-      group_mma<1, true>(acc, &sm.Apl[0][mt][0][0], MT * 128, bb, 64, lane);
+      group_mma<1, true>(acc, &sm.Apl[pb][0][mt][0][0], MT * 128, bb, 64, lane);
     const bool last_k = (ks + 1 == ksteps);
     if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
       int s2[4];
