@@ -621,6 +621,71 @@ def run_mixed_case(args):
     print(json.dumps(out), flush=True)
 
 
+def run_tsqr_case(args):
+    """Tall-skinny QR (k = 0 step) at n = 2^24 rows (--tsqr-n): A = U diag(sigma)
+    V^T with Haar U, V (QR of Gaussians on the device) and sigma log-spaced from
+    1 to 1/kappa, kappa in {1e2, 1e6, 1e10}; s from --tsqr-s.  Each form (native
+    float64 and float64 on the tensor cores) gets the autotuned chunk size; one
+    step is timed with CUDA events (min over --steps repetitions after one
+    warm-up).  Algorithmic bytes 32ns: read A twice, write the local panel and
+    U.  Reported with e_perp = |U^T U - I|_F and |A - UR|_F / |A|_F."""
+    import torch
+
+    from paper_2204_13393_gb300 import lo
+
+    dev = torch.device("cuda", 0)
+    lo.library()
+    n = args.tsqr_n
+    hbm, _src = peaks()
+    out = {"case": "tsqr", "n": n, "results": []}
+    g = torch.Generator(device=dev)
+    g.manual_seed(2204133930 + 3000)
+    for s in [int(x) for x in args.tsqr_s.split(",")]:
+        nbytes = 32 * n * s
+        for kappa in (1e2, 1e6, 1e10):
+            Uh, _ = torch.linalg.qr(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+            Vh, _ = torch.linalg.qr(torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+            sig = torch.tensor([kappa ** (-j / max(s - 1.0, 1.0)) for j in range(s)], dtype=torch.float64,
+                               device=dev)
+            A = (Uh * sig) @ Vh.T
+            del Uh
+            row = {"s": s, "kappa": kappa}
+            for prec in ("fp64", "fp64_tc"):
+                cr = args.tsqr_cr or lo.tune_chunk_rows(n, s, 1, precision=prec)
+                b = lo.Basis(n, s, 1, cr, precision=prec, sync=True)
+                U = torch.empty_like(A)
+                times = []
+                for rep in range(1 + max(1, args.steps)):
+                    b.truncate(0)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, _, R = b.orthogonalize(A, U=U)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = min(times[1:])
+                b.truncate(0)
+                b.set_profiling(True)
+                b.orthogonalize(A, U=U)
+                prof = {g: round(v[0], 4) for g, v in b.profile_read().items() if v[0] > 0}
+                b.set_profiling(False)
+                eye = torch.eye(s, dtype=torch.float64, device=dev)
+                eperp = float(torch.linalg.norm(U.T @ U - eye))
+                res = float(torch.linalg.norm(A - U @ R) / torch.linalg.norm(A))
+                row[prec] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                             "frac_hbm": round(nbytes / ms / 1e6 / hbm, 3), "chunk_rows": cr,
+                             "e_perp": eperp, "residual": res, "passes": b.last_step_info()[0],
+                             "kernel_ms": prof}
+                b.close()
+                del U
+            out["results"].append(row)
+            print(json.dumps(row), flush=True)
+            del A
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -630,10 +695,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"],
                     help="fp64_tc (default): float64-accurate products on the tensor cores; fp64: native float64")
-    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed"],
+    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed", "tsqr"],
                     help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances; "
-                         "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480")
+                         "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480; "
+                         "tsqr: k = 0 steps at n = 2^24")
     ap.add_argument("--mixed-n", type=int, default=2 ** 24)
+    ap.add_argument("--tsqr-n", type=int, default=2 ** 24)
+    ap.add_argument("--tsqr-s", default="8", help="comma-separated block widths for --case tsqr")
+    ap.add_argument("--tsqr-cr", type=int, default=0, help="chunk rows for --case tsqr (0: autotuned)")
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)
@@ -643,6 +712,9 @@ def main():
         return
     if args.case == "mixed":
         run_mixed_case(args)
+        return
+    if args.case == "tsqr":
+        run_tsqr_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3

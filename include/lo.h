@@ -96,6 +96,21 @@ typedef enum lo_leaf {
                            /* shifted CholeskyQR3 and forces two more passes     */
 } lo_leaf;
 
+/*
+ * Storage of the local panels for the tensor-core forms (LO_PREC_FP64_TC,
+ * LO_PREC_MIXED_TC).  Both products of a step read every earlier local panel
+ * once per pass; the tensor cores take each float64 value as 7 exact 8-bit
+ * digits aligned to its column's largest exponent.  With digit planes the
+ * digits are made once, when the panel is created, and kept beside the
+ * float64 values as 8 byte planes (7 digits and a sign), 8 bytes per value:
+ * the basis takes twice the memory and the passes stream bytes instead of
+ * re-splitting float64 values.  Results are bitwise the same either way.
+ */
+typedef enum lo_digit_planes {
+  LO_PLANES_AUTO = 0, /* planes for the tensor-core forms when s is 8, 16 or 32  */
+  LO_PLANES_OFF = 1   /* split the float64 panels again in every pass           */
+} lo_digit_planes;
+
 typedef struct lo_options {
   int32_t precision;   /* lo_precision, default LO_PREC_FP64                     */
   int32_t leaf;        /* lo_leaf, default LO_LEAF_PIP2                          */
@@ -111,6 +126,8 @@ typedef struct lo_options {
                        /* kappa = ||X||_F ||N^{-1}||_F for the block X and its  */
                        /* normalizer N (the Gram cancellation factor).          */
                        /* <= 0 selects the default 1e-13.                        */
+  int32_t digit_planes;  /* lo_digit_planes, default LO_PLANES_AUTO              */
+  int32_t reserved_;     /* set to 0                                             */
 } lo_options;
 
 typedef struct lo_basis lo_basis;

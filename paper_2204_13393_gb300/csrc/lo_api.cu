@@ -113,6 +113,8 @@ struct lo_basis {
   int* coefexp = nullptr;
   uint32_t* coefdig = nullptr;
   int64_t coefdig_stride = 0;
+  uint8_t* dig = nullptr;  // digit planes of the panels (null when off)
+  int64_t dstride = 0;
   Profiler prof;
 };
 
@@ -187,6 +189,8 @@ StepArgs make_args(const lo_basis* b) {
   a.coefdig = b->coefdig;
   a.coefexp = b->coefexp;
   a.coefdig_stride = b->coefdig_stride;
+  a.dig = b->dig;
+  a.dstride = b->dstride;
   return a;
 }
 
@@ -276,6 +280,8 @@ void lo_options_default(lo_options* opt) {
   opt->reduction = 0;
   opt->sync = 1;
   opt->refine_tol = 1e-13;
+  opt->digit_planes = LO_PLANES_AUTO;
+  opt->reserved_ = 0;
 }
 
 const char* lo_status_string(lo_status st) {
@@ -305,7 +311,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options_default(&o);
   if (opt) o = *opt;
   if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
-      o.reduction > 2)
+      o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1)
     return LO_ERR_INVALID_ARG;
   const bool tc = (o.precision == LO_PREC_FP64_TC || o.precision == LO_PREC_MIXED_TC);
   if (tc && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
@@ -376,6 +382,10 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
     alloc((void**)&b->coefexp, sizeof(int) * (size_t)p * 64);
     alloc((void**)&b->coefdig, sizeof(uint32_t) * (size_t)p * b->coefdig_stride);
     if (e == cudaSuccess) e = cudaMemset(b->colexp, 0, sizeof(int) * (size_t)Kmax * p);
+    if (o.digit_planes == LO_PLANES_AUTO && lo::oz_planes_supported(s) && max_blocks > 1) {
+      b->dstride = (n + 15) / 16 * 16;
+      alloc((void**)&b->dig, (size_t)max_blocks * 8 * b->dstride * s);
+    }
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_flags, sizeof(int) * lo::kFlagCount);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_slabs, slabs.data(), sizeof(SlabInfo) * slabs.size(), cudaMemcpyHostToDevice);
@@ -415,6 +425,7 @@ void lo_basis_destroy(lo_basis* b) {
   cudaFree(b->srcexp);
   cudaFree(b->coefexp);
   cudaFree(b->coefdig);
+  cudaFree(b->dig);
   if (b->h_flags) cudaFreeHost(b->h_flags);
   cudaGetLastError();
   delete b;

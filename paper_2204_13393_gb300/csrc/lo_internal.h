@@ -109,6 +109,12 @@ struct StepArgs {
   uint32_t* coefdig;         // [p][coefdig_stride]: digit planes of the scaled coefficients
   int* coefexp;              // [p][64]: exponent of each coefficient column
   int64_t coefdig_stride;    // uint32 words per chunk
+  // digit planes of the local panels (tensor-core forms, s in {8, 16, 32}); null when off.
+  // Byte (panel b, plane t, row r, column j) at dig[((b * 8 + t) * dstride + r) * s + j]:
+  // planes 0..6 hold digits 1..7 of the value aligned to colexp of its chunk,
+  // plane 7 holds 0x80 for a negative value and 0 otherwise.
+  uint8_t* dig;
+  int64_t dstride;           // rows per plane: n rounded up to a multiple of 16
 };
 
 // Digit planes of the tensor-core form: 7 planes of 8-bit digits per value.
@@ -158,6 +164,9 @@ cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ld
 cudaError_t launch_oz_gram(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_oz_ypass(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st);
+// Digit planes of the panel written by stage 2 (a.dig set).
+cudaError_t launch_oz_digitize(const StepArgs& a, cudaStream_t st);
+bool oz_planes_supported(int s);
 bool oz_supported(int s);
 cudaError_t oz_set_attrs();
 

@@ -886,6 +886,10 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     if ((e = cudaMemsetAsync(a.colexp + (int64_t)k * a.p, 0, sizeof(int) * (size_t)s * a.p, st))) return e;
     if ((e = launch_oz_stage2(a, st))) return e;
     count_launches(2);
+    if (a.dig && a.nb + 1 < a.M) {  // the last panel is never read as a prior block
+      if ((e = launch_oz_digitize(a, st))) return e;
+      count_launches(1);
+    }
   } else {
     const int tu = update_tile_rows(k, s);
     k_update<<<a.nslab, kThreads, (size_t)8 * tu * (k + 2 * s), st>>>(a, tu);

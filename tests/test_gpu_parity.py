@@ -410,3 +410,53 @@ def test_full_size_sampled_rows(precision):
     Q = b.apply_Q(dev(np.eye(b.k)))
     G = (Q.T @ Q).cpu().numpy()
     assert np.linalg.norm(G - np.eye(b.k)) <= TOL_PERP
+
+
+# --- digit planes of the tensor-core forms -----------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64_tc", "mixed_tc"])
+@pytest.mark.parametrize("n,s,cr,M", [
+    (10001, 8, 1111, 40),   # odd chunk starts: 8-byte plane rows; 3 Gram column groups
+    (8191, 16, 700, 20),    # assembly over more than 256 columns (flush inside a row tile)
+    (6000, 32, 1500, 8),    # 512-row slabs; 8 Gram column groups
+])
+def test_digit_planes_bitwise(n, s, cr, M, precision):
+    """Panels kept as digit planes give bit-for-bit the products of re-splitting
+    the float64 panels in every pass: every output of every step, with the
+    reiteration passes included, and the final basis against the oracle."""
+    L = lo()
+    on = L.Basis(n, s, M, cr, precision=precision)
+    off = L.Basis(n, s, M, cr, precision=precision, digit_planes=False)
+    A = []
+    for j in range(M):
+        Wh = I.gaussian(n, s, 5000 + j)
+        if j % 3 == 2:  # a block close to the span of the first forces a third pass
+            Wh = Wh + 1e3 * A[0] @ I.gaussian(s, s, 5100 + j)
+        A.append(Wh)
+        W = dev(Wh)
+        r1 = [host(x) for x in on.orthogonalize(W) if x is not None]
+        r2 = [host(x) for x in off.orthogonalize(W) if x is not None]
+        for x, y in zip(r1, r2):
+            assert np.array_equal(x, y), j
+    Q = host(on.apply_Q(dev(np.eye(on.k))))
+    assert O.e_perp(Q) <= TOL_PERP
+    for c in (0, on.num_chunks - 1):
+        Qa, Ta = on.export_chunk(c)
+        Qb, Tb = off.export_chunk(c)
+        assert np.array_equal(Qa, Qb) and np.array_equal(Ta, Tb)
+
+
+@pytest.mark.parametrize("planes", [True, False])
+def test_saturated_digits_long_slab(planes):
+    """Columns of equal magnitude 1.99 make every leading digit 254; over a
+    512-row slab (s = 32) the leading digit products sum past 2^24 and must be
+    flushed before float32 rounds them.  One local pass (BCGS-PIP), so R is the
+    first Gram's Cholesky factor and shows any rounding there."""
+    n, s = 4096, 32
+    X = 1.99 * np.where(I.uniform(n, s, 5200) < 0.0, -1.0, 1.0)
+    b = lo().Basis(n, s, 1, n, precision="fp64_tc", leaf="pip", reduction="pip", digit_planes=planes)
+    U, _, R = b.orthogonalize(dev(X))
+    ora = O.LocallyOrthogonalBasis(n, s, n)
+    _, _, Ro = ora.orthogonalize(X, "hh", "hh")
+    assert rel(host(R), Ro) <= TOL_REL
+    assert O.e_perp(host(U)) <= TOL_PERP
