@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblo.so")
-SOURCES = ["lo_api.cu", "lo_kernels.cu", "lo_ozaki.cu"]
+SOURCES = ["lo_api.cu", "lo_kernels.cu", "lo_ozaki.cu", "lo_umma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -40,7 +40,7 @@ def _stale(obj: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "lo.h"))
     cc = nvcc()
     jobs = []

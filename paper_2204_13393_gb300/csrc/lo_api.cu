@@ -114,7 +114,8 @@ struct lo_basis {
   uint32_t* coefdig = nullptr;
   int64_t coefdig_stride = 0;
   uint8_t* dig = nullptr;  // digit planes of the panels (null when off)
-  int64_t dstride = 0;
+  int64_t dtiles = 0;
+  lo::UmmaMaps maps{};
   Profiler prof;
 };
 
@@ -190,7 +191,8 @@ StepArgs make_args(const lo_basis* b) {
   a.coefexp = b->coefexp;
   a.coefdig_stride = b->coefdig_stride;
   a.dig = b->dig;
-  a.dstride = b->dstride;
+  a.dtiles = b->dtiles;
+  a.maps = &b->maps;
   return a;
 }
 
@@ -339,6 +341,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   // chunks and slabs
   std::vector<SlabInfo> slabs;
   std::vector<int32_t> cs0;
+  int64_t tiles = 0;
   b->chunk_row0.resize(p + 1);
   for (int c = 0; c < p; ++c) {
     const int64_t r0 = (int64_t)c * chunk_rows;
@@ -350,6 +353,9 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
       si.row0 = r;
       si.rows = (int32_t)((r1 - r) < b->slab_rows ? (r1 - r) : b->slab_rows);
       si.chunk = c;
+      si.tile0 = (int32_t)tiles;
+      si.pad_ = 0;
+      tiles += (si.rows + 15) / 16;
       slabs.push_back(si);
     }
   }
@@ -376,6 +382,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
   if (tc) {
     b->coefdig_stride = lo::oz_coef_words(b->Kmax, 2 * s);
+    if (lo::umma_coef_words(b->Kmax, s) > b->coefdig_stride) b->coefdig_stride = lo::umma_coef_words(b->Kmax, s);
     alloc((void**)&b->colexp, sizeof(int) * (size_t)Kmax * p);
     alloc((void**)&b->srcexp_slab, sizeof(int) * (size_t)b->nslab * 32);
     alloc((void**)&b->srcexp, sizeof(int) * (size_t)p * 32);
@@ -383,8 +390,9 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
     alloc((void**)&b->coefdig, sizeof(uint32_t) * (size_t)p * b->coefdig_stride);
     if (e == cudaSuccess) e = cudaMemset(b->colexp, 0, sizeof(int) * (size_t)Kmax * p);
     if (o.digit_planes == LO_PLANES_AUTO && lo::oz_planes_supported(s) && max_blocks > 1) {
-      b->dstride = (n + 15) / 16 * 16;
-      alloc((void**)&b->dig, (size_t)max_blocks * 8 * b->dstride * s);
+      b->dtiles = tiles;
+      alloc((void**)&b->dig, (size_t)max_blocks * 8 * (size_t)tiles * 16 * s);
+      if (e == cudaSuccess) e = lo::umma_make_maps(b->dig, s, max_blocks, tiles, &b->maps);
     }
   }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_flags, sizeof(int) * lo::kFlagCount);

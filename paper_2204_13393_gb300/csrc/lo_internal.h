@@ -2,6 +2,7 @@
 // kernels (lo_kernels.cu).  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,6 +31,8 @@ struct SlabInfo {
   int64_t row0;
   int32_t rows;
   int32_t chunk;
+  int32_t tile0;   // first 16-row tile of the slab in the digit planes (slabs start new tiles)
+  int32_t pad_;
 };
 
 // Per-chunk small-matrix scratch, offsets in doubles (Kmax = M * s).
@@ -110,11 +113,20 @@ struct StepArgs {
   int* coefexp;              // [p][64]: exponent of each coefficient column
   int64_t coefdig_stride;    // uint32 words per chunk
   // digit planes of the local panels (tensor-core forms, s in {8, 16, 32}); null when off.
-  // Byte (panel b, plane t, row r, column j) at dig[((b * 8 + t) * dstride + r) * s + j]:
-  // planes 0..6 hold digits 1..7 of the value aligned to colexp of its chunk,
-  // plane 7 holds 0x80 for a negative value and 0 otherwise.
+  // Byte (panel b, plane t, tile tau, column j, row rho) at
+  //   dig[(((b * 8 + t) * dtiles + tau) * s + j) * 16 + rho]
+  // for row tau * 16 + rho of the slab tiling (SlabInfo::tile0); planes 0..6
+  // hold digits 1..7 of the value aligned to colexp of its chunk, plane 7 holds
+  // 0x80 for a negative value and 0 otherwise; rows past a slab's end are zero.
   uint8_t* dig;
-  int64_t dstride;           // rows per plane: n rounded up to a multiple of 16
+  int64_t dtiles;            // 16-row tiles of one plane
+  const struct UmmaMaps* maps;  // host-side TMA descriptors of dig (lo_umma.cu)
+};
+
+// TMA descriptors of a basis's digit planes: one box shape per kernel.
+struct UmmaMaps {
+  CUtensorMap gram;   // one tile of the 128-column group's panels, all planes
+  CUtensorMap upd;    // 8 tiles (128 rows) of the 16 columns of one step, all planes
 };
 
 // Digit planes of the tensor-core form: 7 planes of 8-bit digits per value.
@@ -164,9 +176,21 @@ cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ld
 cudaError_t launch_oz_gram(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_oz_ypass(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st);
-// Digit planes of the panel written by stage 2 (a.dig set).
-cudaError_t launch_oz_digitize(const StepArgs& a, cudaStream_t st);
 bool oz_planes_supported(int s);
+// Coefficients of an assembly product as tcgen05 B-operand images (lo_ozaki.cu).
+cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, cudaStream_t st);
+// tcgen05 forms over digit planes (lo_umma.cu): used when a.dig is set and the
+// step has prior blocks (nb >= 1).
+bool umma_enabled(const StepArgs& a);
+cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st);
+cudaError_t launch_umma_update(const StepArgs& a, int nout, int pass, cudaStream_t st);
+// Digit planes of the panel written by stage 2.
+cudaError_t launch_umma_digitize(const StepArgs& a, cudaStream_t st);
+cudaError_t umma_set_attrs();
+// Host: TMA descriptors over a digit-plane array of `panels` panels.
+cudaError_t umma_make_maps(uint8_t* dig, int s, int panels, int64_t dtiles, UmmaMaps* maps);
+// uint32 words of one chunk's coefficient images (both assembly products).
+int64_t umma_coef_words(int Kmax, int s);
 bool oz_supported(int s);
 cudaError_t oz_set_attrs();
 

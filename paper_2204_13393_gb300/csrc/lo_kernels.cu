@@ -803,6 +803,7 @@ long long launches() { return g_launches.load(); }
 cudaError_t launch_prepare() {
   cudaError_t e = set_attrs();
   if (e == cudaSuccess) e = oz_set_attrs();
+  if (e == cudaSuccess) e = umma_set_attrs();
   return e;
 }
 
@@ -842,6 +843,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
   const bool tc = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
   if (tc && (e = oz_set_attrs())) return e;
+  if (a.dig && (e = umma_set_attrs())) return e;
   for (int pass = 1; pass <= maxpass; ++pass) {
     mark(hook, pass == 1 ? kKindGram : kKindRefine, true, st);
     if (tc && !(pass == 1 && mixed)) {
@@ -887,7 +889,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     if ((e = launch_oz_stage2(a, st))) return e;
     count_launches(2);
     if (a.dig && a.nb + 1 < a.M) {  // the last panel is never read as a prior block
-      if ((e = launch_oz_digitize(a, st))) return e;
+      if ((e = launch_umma_digitize(a, st))) return e;
       count_launches(1);
     }
   } else {
@@ -963,6 +965,8 @@ __global__ void k_noalloc_tables(int64_t n, int cr, int p, int slab_rows, int sp
     const int64_t left = crows - (int64_t)j * slab_rows;
     si.rows = (int32_t)(left < slab_rows ? left : slab_rows);
     si.chunk = c;
+    si.tile0 = 0;
+    si.pad_ = 0;
     slabs[i] = si;
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= p; c += gridDim.x * blockDim.x) {

@@ -1,0 +1,184 @@
+// Digit arithmetic shared by the tensor-core kernels (lo_ozaki.cu: mma.sync
+// forms that split float64 values in every pass; lo_umma.cu: tcgen05 forms
+// over stored digit planes).  See lo_ozaki.cu for the scheme.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "lo_internal.h"
+
+namespace lo {
+namespace {
+
+constexpr int kPairs = 28;
+
+__device__ __forceinline__ void oz_status(int* flags, lo_status st) {
+  atomicOr(&flags[kFlagStatus], 1 << (int)st);
+}
+
+__device__ __forceinline__ int bexp(double x) {
+  return (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7FF);
+}
+
+// Aligned significand of |x| against group exponent emax: Y < 2^56 as (yhi, ylo),
+// sign in bit 31 of sgn.  Zero, subnormals and values 2^56 below the group give 0;
+// returns true for Inf/NaN.
+__device__ __forceinline__ bool oz_split(double x, int emax, unsigned& yhi, unsigned& ylo, unsigned& sgn) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  sgn = hi & 0x80000000u;
+  unsigned long long m = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 3;
+  const int sh = emax - e;
+  m = (e == 0 || sh > 55 || sh < 0) ? 0ull : (m >> sh);
+  yhi = (unsigned)(m >> 32);
+  ylo = (unsigned)m;
+  return e == 0x7FF;
+}
+
+// fp16x2 with the digits of plane t (1..7) of two values (low half = first),
+// encoded as fp16 subnormals: the bits (sign << 15) | digit are the value
+// +-digit * 2^-24 exactly, so no arithmetic is needed; products of two digits
+// are integers times 2^-48, exact in float32.  sb: the two sign bits (bit 15
+// for the first value, bit 31 for the second).
+__device__ __forceinline__ unsigned oz_pack(int t, unsigned h0, unsigned l0, unsigned h1, unsigned l1, unsigned sb) {
+  const bool hiw = t <= 3;
+  const unsigned w0 = hiw ? h0 : l0, w1 = hiw ? h1 : l1;
+  const unsigned bi = hiw ? (unsigned)(3 - t) : (unsigned)(7 - t);
+  const unsigned v = __byte_perm(w0, w1, bi | ((4u + bi) << 8));
+  return (v & 0x00FF00FFu) | sb;
+}
+
+// Write the 7 digit planes of a value pair into fragment storage.
+// base: plane 0 address; plane_stride in uint32 words; idx: word index in a plane.
+__device__ __forceinline__ void oz_store_pair(unsigned* base, int plane_stride, int idx, double x0, int e0,
+                                              double x1, int e1, int* flags) {
+  unsigned h0, l0, s0, h1, l1, s1;
+  const bool bad = oz_split(x0, e0, h0, l0, s0) | oz_split(x1, e1, h1, l1, s1);
+  if (bad) oz_status(flags, LO_ERR_NONFINITE);
+  const unsigned sb = (s0 >> 16) | s1;
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t) base[(t - 1) * plane_stride + idx] = oz_pack(t, h0, l0, h1, l1, sb);
+}
+
+__device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// The 28 digit pairs (t, u), t + u <= 8, as a compile-time walk.
+template <typename F>
+__device__ __forceinline__ void for_pairs(F&& f) {
+  int idx = 0;
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t)
+#pragma unroll
+    for (int u = 1; u <= kOzDigits; ++u)
+      if (t + u <= 8) f(idx++, t, u);
+}
+
+// Recombination of one output's 28 pair sums D_tu (exact integers, |D| < 2^24):
+//   sum_{t,u} D_tu 2^(-8(t+u)) = 2^-16 (S_2 + rest 2^-45),  S_v = sum_{t+u=v} D_tu,
+//   rest = S_3 2^37 + S_4 2^29 + S_5 2^21 + S_6 2^13 + S_7 2^5 + round(S_8 / 8)
+// (|rest| < 2^63).  S_2 and rest convert exactly to float64; one fused
+// multiply-add rounds the sum once, so the result carries float64 accuracy.
+// The 28 pairs are split over two warp groups of 14 pairs each (digit t of
+// the streamed operand: group 0 takes t in {1, 4, 5}, group 1 takes
+// {2, 3, 6, 7}), so that a CTA runs 16 warps with half the accumulators each.
+constexpr int kGroupPairs = 14;
+__host__ __device__ constexpr bool pair_group_has(int g, int t) {
+  return g == 0 ? (t == 1 || t == 4 || t == 5) : (t == 2 || t == 3 || t == 6 || t == 7);
+}
+template <int G, typename F>
+__device__ __forceinline__ void for_group_pairs(F&& f) {
+  int idx = 0;
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t)
+#pragma unroll
+    for (int u = 1; u <= kOzDigits; ++u)
+      if (pair_group_has(G, t) && t + u <= 8) f(idx++, t, u);
+}
+
+// One group's share of the recombination of output j: S_2 and rest (see
+// oz_combine); the two groups' shares add as integers.
+template <int G>
+__device__ __forceinline__ void group_partial(const float (&acc)[kGroupPairs][4], int j, int& s2, long long& rest) {
+  int Sv[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for_group_pairs<G>([&](int idx, int t, int u) { Sv[t + u] += __float2int_rn(acc[idx][j] * 0x1p48f); });
+  s2 = Sv[2];
+  long long r = (long long)Sv[3] * (1LL << 37);
+  r += (long long)Sv[4] * (1LL << 29);
+  r += (long long)Sv[5] * (1LL << 21);
+  r += (long long)Sv[6] * (1LL << 13);
+  r += (long long)Sv[7] * (1LL << 5);
+  r += (long long)((Sv[8] + 4) >> 3);
+  rest = r;
+}
+
+__device__ __forceinline__ double partial_to_double(int s2, long long rest) {
+  return fma(__ll2double_rn(rest), 0x1p-45, (double)s2);
+}
+
+// 14 mma of one group: A fragments from shared-memory planes (uint4 per lane),
+// B fragments from planes at bsrc (uint2 per lane; shared or global memory).
+template <int G, bool BGLOBAL>
+__device__ __forceinline__ void group_mma(float (&acc)[kGroupPairs][4], const unsigned* apl, int a_stride,
+                                          const unsigned* bpl, int b_stride, int lane) {
+  unsigned af[kOzDigits][4], bf[kOzDigits][2];
+#pragma unroll
+  for (int t = 1; t <= kOzDigits; ++t) {
+    if (pair_group_has(G, t)) {
+      const uint4 v = *reinterpret_cast<const uint4*>(apl + (t - 1) * a_stride + lane * 4);
+      af[t - 1][0] = v.x; af[t - 1][1] = v.y; af[t - 1][2] = v.z; af[t - 1][3] = v.w;
+    }
+  }
+  constexpr int umax = (G == 0) ? 7 : 6;
+#pragma unroll
+  for (int u = 1; u <= umax; ++u) {
+    const uint2* bp = reinterpret_cast<const uint2*>(bpl + (u - 1) * b_stride + lane * 2);
+    const uint2 w = BGLOBAL ? __ldg(bp) : *bp;
+    bf[u - 1][0] = w.x; bf[u - 1][1] = w.y;
+  }
+  for_group_pairs<G>([&](int idx, int t, int u) { mma_f16(acc[idx], af[t - 1], bf[u - 1][0], bf[u - 1][1]); });
+}
+
+// v * 2^X for an integer X in a wide range (two exact power-of-two factors).
+__device__ __forceinline__ double scale2(double v, int X) {
+  if (X < -2044) return 0.0;
+  const int X1 = X / 2, X2 = X - X1;
+  const double f1 = __longlong_as_double((long long)(X1 + 1023) << 52);
+  const double f2 = __longlong_as_double((long long)(X2 + 1023) << 52);
+  return (v * f1) * f2;
+}
+
+// v * 2^X by adding X to the exponent field when the result stays normal
+// (integer work only); otherwise through scale2.
+__device__ __forceinline__ double scale_exp(double v, int X) {
+  const long long b = __double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (v == 0.0) return 0.0;
+  if (e + X >= 1 && e + X <= 2046 && e != 0) return __longlong_as_double(b + ((long long)X << 52));
+  return scale2(v, X);
+}
+
+// cp.async helpers (Ampere-style asynchronous global->shared copies).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
+
+}  // namespace
+}  // namespace lo

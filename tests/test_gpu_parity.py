@@ -419,6 +419,8 @@ def test_full_size_sampled_rows(precision):
     (10001, 8, 1111, 40),   # odd chunk starts: 8-byte plane rows; 3 Gram column groups
     (8191, 16, 700, 20),    # assembly over more than 256 columns (flush inside a row tile)
     (6000, 32, 1500, 8),    # 512-row slabs; 8 Gram column groups
+    (65536, 16, 2048, 5),   # more CTAs than SMs: stage 2 reads the last iterate from the new panel
+    (65536, 32, 4096, 6),   # the same with four output groups per row tile
 ])
 def test_digit_planes_bitwise(n, s, cr, M, precision):
     """Panels kept as digit planes give bit-for-bit the products of re-splitting
