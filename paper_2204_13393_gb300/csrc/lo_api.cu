@@ -391,7 +391,10 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
     if (e == cudaSuccess) e = cudaMemset(b->colexp, 0, sizeof(int) * (size_t)Kmax * p);
     if (o.digit_planes == LO_PLANES_AUTO && lo::oz_planes_supported(s) && max_blocks > 1) {
       b->dtiles = tiles;
-      alloc((void**)&b->dig, (size_t)max_blocks * 8 * (size_t)tiles * 16 * s);
+      const size_t dbytes = (size_t)max_blocks * (s / 8) * lo::kOzDigits * (size_t)tiles * 256;
+      alloc((void**)&b->dig, dbytes);
+      // planes not yet written must hold finite digits (they meet zero coefficients)
+      if (e == cudaSuccess) e = cudaMemset(b->dig, 0, dbytes);
       if (e == cudaSuccess) e = lo::umma_make_maps(b->dig, s, max_blocks, tiles, &b->maps);
     }
   }

@@ -113,20 +113,20 @@ struct StepArgs {
   int* coefexp;              // [p][64]: exponent of each coefficient column
   int64_t coefdig_stride;    // uint32 words per chunk
   // digit planes of the local panels (tensor-core forms, s in {8, 16, 32}); null when off.
-  // Byte (panel b, plane t, tile tau, column j, row rho) at
-  //   dig[(((b * 8 + t) * dtiles + tau) * s + j) * 16 + rho]
-  // for row tau * 16 + rho of the slab tiling (SlabInfo::tile0); planes 0..6
-  // hold digits 1..7 of the value aligned to colexp of its chunk, plane 7 holds
-  // 0x80 for a negative value and 0 otherwise; rows past a slab's end are zero.
+  // fp16 digit t + 1 (t = 0..6, sign in bit 15) of the value in column j of
+  // panel b, row 8 eta + r of the slab tiling (a slab starts at eta = 2 tile0),
+  // aligned to colexp of its chunk, at byte
+  //   (((eta * Gtot + G) * 7 + t) * 128 + (j % 8) * 16 + r * 2),  G = b s / 8 + j / 8,
+  // Gtot = M s / 8 (8 x 8 core matrices of the tcgen05 operand layouts); rows
+  // past a slab's end are zero.
   uint8_t* dig;
-  int64_t dtiles;            // 16-row tiles of one plane
+  int64_t dtiles;            // 16-row tiles of the slab tiling
   const struct UmmaMaps* maps;  // host-side TMA descriptors of dig (lo_umma.cu)
 };
 
 // TMA descriptors of a basis's digit planes: one box shape per kernel.
 struct UmmaMaps {
-  CUtensorMap gram;   // one tile of the 128-column group's panels, all planes
-  CUtensorMap upd;    // 8 tiles (128 rows) of the 16 columns of one step, all planes
+  CUtensorMap upd;    // 16 8-row blocks (128 rows) of the 16 columns of one step, all planes
 };
 
 // Digit planes of the tensor-core form: 7 planes of 8-bit digits per value.

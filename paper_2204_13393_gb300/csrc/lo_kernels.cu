@@ -849,7 +849,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     if (tc && !(pass == 1 && mixed)) {
       if (pass >= 2 && (e = launch_oz_ypass(a, pass, st))) return e;
       if ((e = launch_oz_gram(a, pass, st))) return e;
-      count_launches(pass >= 2 ? 3 : 1);
+      count_launches(pass >= 2 ? 3 : (umma_enabled(a) ? 2 : 1));
     } else if (pass == 1 && gram1_supported(s)) {
       if ((e = mixed ? launch_gram1<float>(a, st) : launch_gram1<double>(a, st))) return e;
     } else if (pass == 1 && mixed) {

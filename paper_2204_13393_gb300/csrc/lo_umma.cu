@@ -13,20 +13,25 @@
 //     operands in shared memory and the accumulators in tensor memory (TMEM);
 //     the pairs of one digit t of [Q_i A] share one MMA whose B operand stacks
 //     the digit planes u = 1 .. 8 - t of the other factor along N;
-//   * the digit planes of prior panels arrive by TMA (cp.async.bulk.tensor)
-//     into a 4-stage ring tracked by mbarriers; the coefficient images of the
+//   * the digit planes of prior panels arrive by bulk copies (Gram) or TMA
+//     (cp.async.bulk.tensor, assembly) into a 5-stage ring tracked by
+//     mbarriers, three steps ahead; the coefficient images of the
 //     assembly arrive by cp.async.bulk on the same barriers;
-//   * digit bytes are expanded to fp16 with one byte permute per two values
-//     (a digit byte and a sign byte form the fp16 subnormal), straight into
-//     the canonical no-swizzle UMMA layouts: K-major for the Gram (the rows
-//     of a 16-row tile are contiguous per column in the planes), MN-major for
-//     the assembly;
-//   * the pass block itself (float64) is split on the fly.
+//   * the planes are stored in the canonical no-swizzle UMMA core-matrix
+//     order, so the loaded stages are the MMA operands as they are;
+//   * the pass block itself (float64) is split on the fly into the stage.
 //
-// Digit-plane layout (global): panel b, plane t (0..6: digit t + 1, 7: sign
-// byte 0x80 / 0), 16-row tile tau of the slab tiling, column j, row rho:
-//   dig[(((b * 8 + t) * dtiles + tau) * s + j) * 16 + rho]
-// Every slab starts a new tile, so each 16-row step of a kernel is one tile.
+// Digit-plane layout (global, fp16 digits with the sign in bit 15): 8-row
+// block eta of the slab tiling (rows 8 eta .. 8 eta + 7; a slab's rows start
+// at block 2 tile0), 8-column group G of the basis (G = b s / 8 + j / 8 for
+// column j of panel b; Gtot = max_blocks s / 8 groups), plane t (digit t + 1),
+// column c = j % 8, row r:
+//   byte (((eta * Gtot + G) * 7 + t) * 128 + c * 16 + r * 2)
+// i.e. 8 x 8 core matrices (one 16-byte row per column).  The Gram's step
+// (16 rows x 128 columns) is two contiguous 14 KB runs, loaded with
+// cp.async.bulk; the assembly's step (128 rows x 16 columns) is 16 runs of
+// 1792 bytes, one 2D TMA box.  In shared memory they are the K-major (Gram)
+// and MN-major (assembly) A operands as they are.
 //
 // Every wait on an mbarrier is bounded: on timeout the kernel records
 // LO_ERR_TIMEOUT, stops issuing tensor-core work and drains what it issued.
@@ -39,10 +44,11 @@
 namespace lo {
 namespace {
 
-constexpr int kUmmaThreads = 256;
-constexpr int kStages = 4;            // TMA ring depth
-constexpr int kStageBytes = 16384;    // digit bytes of one step (both kernels)
-constexpr int kAPlaneBytes = 4096;    // one 128 x 16 fp16 operand tile
+constexpr int kUmmaThreads = 288;     // 8 worker warps + 1 issuer warp
+constexpr int kIssuer = 256;          // lane 0 of warp 8 issues every load and MMA
+constexpr int kStages = 5;            // TMA ring depth
+constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
+constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
 constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
 
 __host__ __device__ constexpr int umma_round16(int x) { return (x + 15) / 16 * 16; }
@@ -74,6 +80,9 @@ __host__ __device__ constexpr uint32_t umma_idesc(int M, int N, int a_mn, int b_
 __device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count));
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
 }
@@ -93,12 +102,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return false;
   return true;
 }
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
-                                            uint32_t mb) {
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t mb) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(dst),
-      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mb)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(mb)
       : "memory");
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb) {
@@ -118,6 +126,11 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// CTA barrier entered by converged warps (bar.sync counts a diverged warp once).
+__device__ __forceinline__ void cta_sync() {
+  __syncwarp();
+  __syncthreads();
+}
 
 // TMEM loads, 32 lanes x N columns (32-bit): lane i of the warp gets row
 // (lane base + i), columns [col, col + N).
@@ -143,8 +156,10 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t (&r)[N]) {
 
 // Per-CTA control block at the end of dynamic shared memory.
 struct UmmaCtl {
-  uint64_t full[kStages];   // TMA ring
-  uint64_t mmad[2];         // MMAs of the operand buffer done
+  uint64_t full[kStages];   // loads of a stage landed (the issuer arms them)
+  uint64_t ready[kStages];  // the workers wrote their part of a step's operands (8 warp arrivals)
+  uint64_t mmad[2];         // MMAs of a step done (commit), alternating by step parity
+  uint64_t empty;           // the accumulators were drained (8 warp arrivals)
   uint32_t tslot;           // TMEM base written by tcgen05.alloc
   int abort;                // a bounded wait gave up: no further TMA or MMA is issued
   int issued;               // steps whose loads have been issued
@@ -224,9 +239,9 @@ __device__ __forceinline__ void expand16(const uint4& d, const uint4& g, uint4& 
 }
 
 // Split 8 float64 values x[0..7] (8 consecutive rows of one column) against
-// exponent e and store their fp16 digits as one 16-byte row of each of the 7
-// planes at dst + t * kAPlaneBytes.
-__device__ __forceinline__ void split8_store(const double* x, int e, unsigned char* dst, int* flags) {
+// exponent e and store their fp16 digits as one 16-byte core-matrix row of
+// each of the 7 planes at dst + t * plane.
+__device__ __forceinline__ void split8_store(const double* x, int e, unsigned char* dst, int plane, int* flags) {
   unsigned w[kOzDigits][4];
   bool bad = false;
 #pragma unroll
@@ -241,13 +256,13 @@ __device__ __forceinline__ void split8_store(const double* x, int e, unsigned ch
   if (bad) oz_status(flags, LO_ERR_NONFINITE);
 #pragma unroll
   for (int t = 0; t < kOzDigits; ++t)
-    *reinterpret_cast<uint4*>(dst + t * kAPlaneBytes) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    *reinterpret_cast<uint4*>(dst + t * plane) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
 // ---------------------------------------------------------------------------
 // Digit planes of the new panel (slot nb) once stage 2 has fixed its column
-// exponents.  One thread per (16-row tile, column): 16 values, 8 planes of 16
-// bytes each.
+// exponents.  One thread per (16-row tile, column): 16 values, 7 planes of
+// two 16-byte core-matrix rows each.
 template <int S>
 __global__ void __launch_bounds__(256) k_umma_digitize(StepArgs a) {
   __shared__ int ex[S];
@@ -256,71 +271,70 @@ __global__ void __launch_bounds__(256) k_umma_digitize(StepArgs a) {
   if (threadIdx.x < S) ex[threadIdx.x] = a.colexp[(int64_t)(k + threadIdx.x) * a.p + si.chunk];
   __syncthreads();
   const double* slot = a.V + (int64_t)a.nb * a.n * S;
-  const int64_t plane = a.dtiles * 16 * S;  // bytes per plane
-  uint8_t* base = a.dig + (int64_t)a.nb * 8 * plane;
   const int ntile = (si.rows + 15) / 16;
+  const int64_t gtot = (int64_t)a.M * (S / 8);
   for (int i = threadIdx.x; i < ntile * S; i += 256) {
     const int tt = i / S, j = i - tt * S;
-    double x[16];
+    const int64_t G = (int64_t)a.nb * (S / 8) + j / 8;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int row = tt * 16 + r;
-      x[r] = row < si.rows ? slot[(si.row0 + row) * S + j] : 0.0;
-    }
-    unsigned wd[kOzDigits][4], wg[4];
-    bool bad = false;
+    for (int h = 0; h < 2; ++h) {
+      const int64_t eta = 2 * (int64_t)(si.tile0 + tt) + h;
+      double x[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      unsigned h[4], l[4], g[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) bad |= oz_split(x[4 * q + r], ex[j], h[r], l[r], g[r]);
-#pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) {
-        const bool hw = t <= 3;
-        const unsigned bi = hw ? (unsigned)(3 - t) : (unsigned)(7 - t);
-        const unsigned sel = bi | ((4u + bi) << 4);
-        const unsigned w01 = __byte_perm(hw ? h[0] : l[0], hw ? h[1] : l[1], sel);
-        const unsigned w23 = __byte_perm(hw ? h[2] : l[2], hw ? h[3] : l[3], sel);
-        wd[t - 1][q] = __byte_perm(w01, w23, 0x5410);
+      for (int r = 0; r < 8; ++r) {
+        const int row = tt * 16 + h * 8 + r;
+        x[r] = row < si.rows ? slot[(si.row0 + row) * S + j] : 0.0;
       }
-      wg[q] = (g[0] >> 24) | (g[1] >> 16) | (g[2] >> 8) | g[3];
+      split8_store(x, ex[j], a.dig + (eta * gtot + G) * (kOzDigits * 128) + (j & 7) * 16, 128, a.flags);
     }
-    if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-    uint8_t* o = base + ((int64_t)(si.tile0 + tt) * S + j) * 16;
-#pragma unroll
-    for (int t = 0; t < kOzDigits; ++t)
-      *reinterpret_cast<uint4*>(o + t * plane) = make_uint4(wd[t][0], wd[t][1], wd[t][2], wd[t][3]);
-    *reinterpret_cast<uint4*>(o + 7 * plane) = make_uint4(wg[0], wg[1], wg[2], wg[3]);
   }
+}
+
+// Largest biased exponent of each column of a pass block over each slab
+// (the Gram's B-operand alignment); the reiteration's new iterate records its
+// own in k_umma_update.
+template <int S>
+__global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* src, int64_t lds) {
+  __shared__ int hs[S];
+  const SlabInfo si = a.slabs[blockIdx.x];
+  if (threadIdx.x < S) hs[threadIdx.x] = 0;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < si.rows * S; idx += 256) {
+    const int r = idx / S, l = idx - r * S;
+    atomicMax(&hs[l], bexp(src[(si.row0 + r) * lds + l]));
+  }
+  __syncthreads();
+  if (threadIdx.x < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + threadIdx.x] = hs[threadIdx.x];
 }
 
 // ---------------------------------------------------------------------------
 // Stage-1 Gram partial C = [Q_i A]^T A of one slab, for 128 columns of
 // [Q_i A] (grid.y) and NB columns of A (grid.z).  MMA: M = columns of [Q_i A],
-// N = (u, column of A), K = 16 rows per step.  A operand (K-major, one tile
-// per digit t): row m holds the 16 row digits of column m.  B operand
-// (K-major): row (u - 1) NB + n holds digit u of column n of A.
+// N = (u, column of A), K = 16 rows per step.  The A operand of digit t is
+// the loaded stage itself ([8-row block][group][t][128 B]: K-major,
+// SBO = 7 x 128, LBO = 16 x 7 x 128); the block's own columns are split into
+// it after the load.  B
+// operand (K-major): row (u - 1) NB + n holds digit u of column n of A.
 template <int S>
 struct GramLayout {
-  static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB, NP = 128 / S;
+  static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
   static constexpr int RB = umma_round16(7 * NB);
-  static constexpr int STG = 0;                                      // kStages x 16 KB
-  static constexpr int ABUF = STG + kStages * kStageBytes;           // 2 x 7 x 4 KB
-  static constexpr int BBUF = ABUF + 2 * kOzDigits * kAPlaneBytes;   // 2 x RB x 32 B
-  // private cp.async slots of the float64 values a thread splits (3 steps):
-  // the block's own columns in the A tile (S threads x 16 rows) and the B
-  // operand (4 NB threads x 4 rows)
+  static constexpr int STG = 0;                                 // kStages x [2][16][7][128 B]
+  static constexpr int BBUF = STG + kStages * kStageBytes;      // 2 x RB x 32 B
+  // private cp.async slots (3 steps) of the float64 values a thread splits:
+  // the block's own columns of the A tile (2 S units of 8 rows) and the B
+  // operand (4 NB units of 4 rows)
   static constexpr int SRCA = BBUF + 2 * RB * 32;
-  static constexpr int SRCB = SRCA + 3 * S * 16 * 8;
+  static constexpr int SRCB = SRCA + 3 * 2 * S * 8 * 8;
   static constexpr int CTL = SRCB + 3 * 4 * NB * 4 * 8;
-  static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;    // + alignment slack
+  static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
 };
 
 template <int S>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
-    k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass, const __grid_constant__ CUtensorMap tm) {
+    k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass) {
   using L = GramLayout<S>;
-  constexpr int NB = L::NB, NP = L::NP, RB = L::RB;
+  constexpr int NB = L::NB, RB = L::RB;
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
@@ -329,201 +343,207 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   const SlabInfo si = a.slabs[blockIdx.x];
   const int k = a.nb * S, Kt = k + S;
   const int col0 = blockIdx.y * 128, z = blockIdx.z;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int np_q = max(0, min(col0 + 128, k) - col0) / S;  // prior panels in the group
-  const int b0 = col0 / S;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gtot = a.M * (S / 8), g0 = col0 / 8;
+  const int ng = min(16, gtot - g0);            // column groups present in the digit planes
+  const bool has_q = k > col0 && ng > 0;        // prior panels in the group: loaded
   const int nsteps = (si.rows + 15) / 16;
-  const uint32_t full0 = su32(&ctl.full[0]), mmad0 = su32(&ctl.mmad[0]);
+  const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
+  const uint32_t empty = su32(&ctl.empty);
 
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(full0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(ready0 + 8 * i, 8);
+    }
     mbar_init(mmad0, 1);
     mbar_init(mmad0 + 8, 1);
+    mbar_init(empty, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
-    ctl.issued = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)),
                  "r"(umma_tcols(NB)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (tid < 32) ctl.Hs[tid] = 0;
-  // columns past Kt and B pad rows stay zero in both operand buffers
-  {
-    const int zc0 = max(0, Kt - col0);
-    for (int i = tid; i < 2 * kOzDigits * (128 - zc0) * 2; i += kUmmaThreads) {
-      const int h = i & 1, rest = i >> 1, m = zc0 + rest % (128 - zc0), bp = rest / (128 - zc0);
-      *reinterpret_cast<uint4*>(sm + L::ABUF + bp * kAPlaneBytes + (m & 7) * 16 + (m >> 3) * 256 + h * 128) =
+  if (tid < S) ctl.Hs[tid] = a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid];
+  for (int m = tid; m < 128; m += kUmmaThreads) {
+    const int col = col0 + m;
+    ctl.Fs[m] = (col < k) ? a.colexp[(int64_t)col * a.p + si.chunk] : 0;
+  }
+  if constexpr (RB > 7 * NB) {  // B pad rows stay zero
+    for (int i = tid; i < 2 * (RB - 7 * NB) * 2; i += kUmmaThreads) {
+      const int h = i & 1, rest = i >> 1, r = 7 * NB + rest % (RB - 7 * NB), bb = rest / (RB - 7 * NB);
+      *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
           make_uint4(0u, 0u, 0u, 0u);
-    }
-    if constexpr (RB > 7 * NB) {
-      for (int i = tid; i < 2 * (RB - 7 * NB) * 2; i += kUmmaThreads) {
-        const int h = i & 1, rest = i >> 1, r = 7 * NB + rest % (RB - 7 * NB), bb = rest / (RB - 7 * NB);
-        *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
-            make_uint4(0u, 0u, 0u, 0u);
-      }
     }
   }
   fence_async_smem();
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
-  // the ring: TMA loads of steps 0 .. kStages - 2
-  if (tid == 0 && np_q > 0) {
-    for (int j = 0; j < kStages - 1 && j < nsteps; ++j) {
-      mbar_expect_tx(full0 + 8 * j, 8 * NP * 16 * S);
-      tma_load_4d(su32(sm + L::STG + j * kStageBytes), &tm, 0, 0, si.tile0 + j, 8 * b0, full0 + 8 * j);
-      ctl.issued = j + 1;
-    }
-  }
-  // the pass block's column exponents over this slab
-  for (int idx = tid; idx < si.rows * S; idx += kUmmaThreads) {
-    const int r = idx / S, l = idx - r * S;
-    atomicMax(&ctl.Hs[l], bexp(src[(si.row0 + r) * lds + l]));
-  }
-  __syncthreads();
-  if (blockIdx.y == 0 && z == 0 && tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = ctl.Hs[tid];
-  for (int m = tid; m < 128; m += kUmmaThreads) {
-    const int col = col0 + m;
-    ctl.Fs[m] = (col < k) ? a.colexp[(int64_t)col * a.p + si.chunk] : (col < Kt ? ctl.Hs[col - k] : 0);
-  }
-  __syncthreads();
 
-  // roles: threads 0..127 expand column m = tid of the A tile; threads
-  // 128 .. 128 + 4 NB - 1 split the B operand: column n, rows 4 q .. 4 q + 3
-  const int m = tid, colm = col0 + tid;
-  const bool a_q = tid < 128 && colm < k, a_src = tid < 128 && colm >= k && colm < Kt;
-  const int bi = tid - 128;
-  const bool b_role = bi >= 0 && bi < 4 * NB;
-  const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
-  double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (a_src ? (colm - k) : 0) * 16;
-  double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + (b_role ? bi : 0) * 4;
-  // the float64 values this thread splits in step j, into its slot j % 3
-  auto load_src = [&](int j) {
-    const int r0 = j * 16;
-    if (a_src) {
-      double* d = xa_slot + (j % 3) * S * 16;
+  if (warp == 8) {
+    // ---- issuer: loads three steps ahead, one MMA group per step -----------
+    if (lane == 0) {
+      uint32_t idesc[kOzDigits];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const bool ok = r0 + r < si.rows;
-        cp_async8(d + r, src + (si.row0 + (ok ? r0 + r : 0)) * lds + (colm - k), ok);
-      }
-    }
-    if (b_role) {
-      double* d = xb_slot + (j % 3) * 4 * NB * 4;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int row = r0 + 4 * bq + r;
-        const bool ok = row < si.rows;
-        cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + z * NB + bn, ok);
-      }
-    }
-    cp_async_commit();
-  };
-  load_src(0);
-  if (nsteps > 1) load_src(1); else cp_async_commit();
-  double acc[NB];
-#pragma unroll
-  for (int j = 0; j < NB; ++j) acc[j] = 0.0;
-  uint32_t idesc[kOzDigits];
-#pragma unroll
-  for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 0, 0);
-
-  for (int st = 0; st < nsteps; ++st) {
-    const int s = st % kStages, bb = st & 1;
-    // refill the stage consumed in the previous step
-    if (tid == 0 && np_q > 0 && !ctl.abort && st + kStages - 1 < nsteps) {
-      const int j = st + kStages - 1, sj = j % kStages;
-      mbar_expect_tx(full0 + 8 * sj, 8 * NP * 16 * S);
-      tma_load_4d(su32(sm + L::STG + sj * kStageBytes), &tm, 0, 0, si.tile0 + j, 8 * b0, full0 + 8 * sj);
-      ctl.issued = j + 1;
-    }
-    if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
-    if (tid < 128 && np_q > 0 && st < ctl.issued) {
-      if (!mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1))) umma_timeout(ctl, a.flags);
-    }
-    if (st >= 2 && (tid < 128 || b_role) && !ctl.abort) {
-      if (!mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1))) umma_timeout(ctl, a.flags);
-    }
-    unsigned char* abuf = sm + L::ABUF + bb * kOzDigits * kAPlaneBytes;
-    const int aoff = (m & 7) * 16 + (m >> 3) * 256;
-    if (a_q) {
-      const int pi = m / S, j = m - pi * S;
-      const unsigned char* sp = sm + L::STG + s * kStageBytes + (pi * 8) * 16 * S + j * 16;
-      const uint4 g = *reinterpret_cast<const uint4*>(sp + 7 * 16 * S);
-#pragma unroll
-      for (int t = 0; t < kOzDigits; ++t) {
-        uint4 lo, hi;
-        expand16(*reinterpret_cast<const uint4*>(sp + t * 16 * S), g, lo, hi);
-        *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff) = lo;
-        *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff + 128) = hi;
-      }
-    } else if (a_src) {
-      const double* x = xa_slot + (st % 3) * S * 16;
-      split8_store(x, ctl.Fs[m], abuf + aoff, a.flags);
-      split8_store(x + 8, ctl.Fs[m], abuf + aoff + 128, a.flags);
-    }
-    if (b_role) {
-      unsigned h[4], l[4], g[4];
-      bool bad = false;
-      const int e = ctl.Hs[z * NB + bn];
-      const double* x = xb_slot + (st % 3) * 4 * NB * 4;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], g[r]);
-      if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-      unsigned char* bbuf = sm + L::BBUF + bb * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
-#pragma unroll
-      for (int u = 1; u <= kOzDigits; ++u) {
-        const int row = (u - 1) * NB + bn;
-        const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
-        const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
-        *reinterpret_cast<uint2*>(bbuf + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
-      }
-    }
-    if (tid == 0 && umma_timed_out(a.flags)) ctl.abort = 1;
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && !ctl.abort) {
-      tc_fence_after();
-      const uint32_t bdesc_addr = su32(sm + L::BBUF + bb * (RB * 32));
-      const uint64_t db = umma_sdesc(bdesc_addr, 128, 256);
-      const uint32_t accum = (st & 15) ? 1u : 0u;
-#pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) {
-        const uint64_t da = umma_sdesc(su32(abuf + (t - 1) * kAPlaneBytes), 128, 256);
-        umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
-      }
-      umma_commit(mmad0 + 8 * bb);
-    }
-    // exact float32 sums cover 16 steps (256 rows): drain the accumulators
-    if (((st + 1) & 15) == 0 || st + 1 == nsteps) {
-      if (tid < 128 && !ctl.abort) {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
-        if (!ok) {
+      for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 0, 0);
+      // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
+      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kStageBytes / 2, kOzDigits * 128);
+      const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
+      const uint32_t run = (uint32_t)max(ng, 0) * kOzDigits * 128;
+      auto issue = [&](int j) {
+        const int sj = j % kStages;
+        const int64_t eta = 2 * (int64_t)(si.tile0 + j);
+        const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
+        mbar_expect_tx(full0 + 8 * sj, 2 * run);
+        bulk_load(su32(sm + L::STG + sj * kStageBytes), gsrc, run, full0 + 8 * sj);
+        bulk_load(su32(sm + L::STG + sj * kStageBytes + kStageBytes / 2), gsrc + (int64_t)gtot * kOzDigits * 128,
+                  run, full0 + 8 * sj);
+      };
+      int issued = 0, landed = 0, drains = 0, committed = -1;
+      if (has_q)
+        for (; issued < kDist && issued < nsteps; ++issued) issue(issued);
+      for (int st = 0; st < nsteps; ++st) {
+        const int s = st % kStages, bb = st & 1;
+        bool ok = true;
+        // the stage of step st + kDist last served step st - 2
+        if (st >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1));
+        if (ok && has_q && issued < nsteps && issued == st + kDist) issue(issued++);
+        if (ok && has_q) {
+          ok = mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1));
+          if (ok) landed = st + 1;
+        }
+        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((st / kStages) & 1));
+        if (ok && (st & 15) == 0 && st > 0) ok = mbar_wait(empty, (uint32_t)(drains++ & 1));
+        if (!ok || umma_timed_out(a.flags)) {
           umma_timeout(ctl, a.flags);
-        } else {
-          tc_fence_after();
-          const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);
+          break;
+        }
+        tc_fence_after();
+        const uint64_t db = dB0 + (uint64_t)((bb * (RB * 32)) >> 4);
+        const uint32_t accum = (st & 15) ? 1u : 0u;
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4);
+        for (int t = 1; t <= kOzDigits; ++t) {
+          const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
+          umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
+        }
+        umma_commit(mmad0 + 8 * bb);
+        committed = st;
+      }
+      // drain what is still in flight before the CTA's memory is released
+      for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+      if (committed >= 0) mbar_wait(mmad0 + 8 * (committed & 1), (uint32_t)((committed >> 1) & 1));
+    }
+    __syncwarp();
+  } else {
+    // ---- workers (warps 0..7) ------------------------------------------------
+    // threads 0 .. 2S - 1 split the block's own columns into the A tile
+    // (column l = tid / 2, rows 8 (tid % 2) .. + 7; only in the group that
+    // holds them); threads 128 .. 128 + 4 NB - 1 split the B operand (column
+    // n, rows 4 q .. 4 q + 3)
+    const int al = tid >> 1, ah = tid & 1, am = k - col0 + al;
+    const bool a_src = tid < 2 * S && am >= 0 && am < 128;
+    const int bi = tid - 128;
+    const bool b_role = bi >= 0 && bi < 4 * NB;
+    const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
+    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (a_src ? tid : 0) * 8;
+    double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + (b_role ? bi : 0) * 4;
+    auto load_src = [&](int j) {
+      const int r0 = j * 16;
+      if (a_src) {
+        double* d = xa_slot + (j % 3) * 2 * S * 8;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int row = r0 + 8 * ah + r;
+          const bool ok = row < si.rows;
+          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + al, ok);
         }
       }
-      tc_fence_before();
-      __syncthreads();
+      if (b_role) {
+        double* d = xb_slot + (j % 3) * 4 * NB * 4;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = r0 + 4 * bq + r;
+          const bool ok = row < si.rows;
+          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + z * NB + bn, ok);
+        }
+      }
+      cp_async_commit();
+    };
+    load_src(0);
+    if (nsteps > 1) load_src(1); else cp_async_commit();
+    double acc[NB / 2];
+#pragma unroll
+    for (int j = 0; j < NB / 2; ++j) acc[j] = 0.0;
+    for (int st = 0; st < nsteps; ++st) {
+      const int s = st % kStages, bb = st & 1;
+      if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
+      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
+      // MMAs of step st - 2 done: B buffer bb is free (and no warp runs ahead)
+      if (st >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1)))
+        umma_timeout(ctl, a.flags);
+      unsigned char* stage = sm + L::STG + s * kStageBytes;
+      if (a_src && has_q && !ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1)))
+        umma_timeout(ctl, a.flags);
+      if (a_src)
+        split8_store(xa_slot + (st % 3) * 2 * S * 8, ctl.Hs[al],
+                     stage + ah * (kStageBytes / 2) + (am >> 3) * (kOzDigits * 128) + (am & 7) * 16, 128, a.flags);
+      if (b_role) {
+        unsigned h[4], l[4], g[4];
+        bool bad = false;
+        const int e = ctl.Hs[z * NB + bn];
+        const double* x = xb_slot + (st % 3) * 4 * NB * 4;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], g[r]);
+        if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
+        unsigned char* bbuf = sm + L::BBUF + bb * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
+#pragma unroll
+        for (int u = 1; u <= kOzDigits; ++u) {
+          const int row = (u - 1) * NB + bn;
+          const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
+          const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
+          *reinterpret_cast<uint2*>(bbuf + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ready0 + 8 * s);
+      // exact float32 sums cover 16 steps (256 rows): drain the accumulators;
+      // warps w and w + 4 take TMEM lanes 32 (w % 4) .. + 31, halves of the NB columns
+      if (((st + 1) & 15) == 0 || st + 1 == nsteps) {
+        if (!ctl.abort) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
+          if (!ok) {
+            umma_timeout(ctl, a.flags);
+          } else {
+            tc_fence_after();
+            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll
+            for (int c4 = 0; c4 < NB / 8; ++c4)
+              umma_drain<NB, 4>(tlane, (warp >> 2) * (NB / 2) + c4 * 4, acc + c4 * 4);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty);
+      }
+    }
+    // partial of this slab: column col0 + m, block columns z NB + (w / 4) NB / 2 ..
+    const int m = (warp & 3) * 32 + lane, colm = col0 + m;
+    if (colm < Kt && !ctl.abort) {
+      const int n0 = z * NB + (warp >> 2) * (NB / 2);
+      const int F = colm < k ? ctl.Fs[m] : ctl.Hs[colm - k];
+      double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S + (int64_t)colm * S + n0;
+#pragma unroll
+      for (int j = 0; j < NB / 2; ++j) out[j] = scale_exp(acc[j], F + ctl.Hs[n0 + j] - 2044 - 16);
     }
   }
-  // partial of this slab: column col0 + m, block columns z NB .. z NB + NB - 1
-  if (tid < 128 && colm < Kt && !ctl.abort) {
-    double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S + (int64_t)colm * S + z * NB;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) out[j] = scale_exp(acc[j], ctl.Fs[m] + ctl.Hs[z * NB + j] - 2044 - 16);
-  }
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(umma_tcols(NB)));
@@ -533,28 +553,27 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 // ---------------------------------------------------------------------------
 // out = [Q_i A] Coef for one slab.  MMA: M = 128 rows (one row tile),
 // N = (u, output column) for NB output columns at a time, K = 16 columns of
-// [Q_i A] per step.  With more than NB outputs the CTA runs the K loop of a
-// row tile once per group of NB outputs and writes the tile only after the
-// last group: the pass block may share storage with an output (the new panel
-// holds the last iterate; U may alias W), so no row is written before every
-// group has read it.  A operand MN-major (a column's 16 row digits are
-// contiguous in the planes); B operand: the coefficient image of the step
-// (k_oz_coef<UMMA>).  NOUT = 1: the reiteration's new iterate into the new
-// panel; NOUT = 2: U_i into the panel and U to the caller, plus the panel's
-// column exponents.
+// [Q_i A] per step.  The A operand of digit t is the TMA stage itself
+// ([8-row block][group][t][128 B]: MN-major, SBO = 2 x 7 x 128,
+// LBO = 7 x 128); the block's own columns are split into it.  B operand: the coefficient
+// image of the step (k_oz_coef<UMMA>).  With more than NB outputs the CTA
+// runs the K loop of a row tile once per group of NB outputs and writes the
+// tile only after the last group: the pass block may share storage with an
+// output (the new panel holds the last iterate; U may alias W), so no row is
+// written before every group has read it.  NOUT = 1: the reiteration's new
+// iterate into the new panel, and its column exponents per slab; NOUT = 2:
+// U_i into the panel and U to the caller, and the panel's column exponents.
 template <int S, int NOUT>
 struct UpdLayout {
   static constexpr int NC = NOUT * S, NB = NC < 16 ? NC : 16, NSPL = NC / NB;
-  static constexpr int SC = S < 16 ? S : 16;  // columns of one TMA inner box
   static constexpr int RB = umma_round16(7 * NB);
   static constexpr int BIMG = RB * 32;
-  static constexpr int STG = 0;
-  static constexpr int BST = STG + kStages * kStageBytes;
-  static constexpr int ABUF = BST + kStages * umma_round16(BIMG / 16) * 16;
+  static constexpr int STG = 0;                                        // kStages x [16][2][7][128 B]
+  static constexpr int BST = STG + kStages * kStageBytes;              // kStages coefficient images
   // private cp.async slots (3 steps) of the float64 values of the block's own
-  // columns that thread (column kk, tile tau) splits: 128 threads x 16 rows
-  static constexpr int SRCU = ABUF + 2 * kOzDigits * kAPlaneBytes;
-  static constexpr int CTL = SRCU + 3 * 128 * 16 * 8;
+  // columns that thread (column, tile, half) splits: 256 threads x 8 rows
+  static constexpr int SRCU = BST + kStages * umma_round16(BIMG / 16) * 16;
+  static constexpr int CTL = SRCU + 3 * 256 * 8 * 8;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
 };
 
@@ -563,14 +582,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_update(StepArgs a, const double* src_fixed, int64_t lds_fixed, int pass,
                   const __grid_constant__ CUtensorMap tm) {
   using L = UpdLayout<S, NOUT>;
-  constexpr int NC = L::NC, NB = L::NB, SC = L::SC, RB = L::RB, BIMG = L::BIMG;
+  constexpr int NC = L::NC, NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL;
   if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
   const SlabInfo si = a.slabs[blockIdx.x];
-  constexpr int NSPL = L::NSPL;
   const int c = si.chunk, k = a.nb * S, Kt = k + S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double* src = src_fixed;
@@ -587,12 +605,17 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   const int ntr = (si.rows + 127) / 128;
   const int nsteps = ntr * NSPL * KS;  // step = (row tile, output group, 16 columns)
   const unsigned char* img = reinterpret_cast<const unsigned char*>(a.coefdig + (int64_t)c * a.coefdig_stride);
-  const uint32_t full0 = su32(&ctl.full[0]), mmad0 = su32(&ctl.mmad[0]);
+  const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
+  const uint32_t empty = su32(&ctl.empty);
 
   if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(full0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full0 + 8 * i, 1);
+      mbar_init(ready0 + 8 * i, 8);
+    }
     mbar_init(mmad0, 1);
     mbar_init(mmad0 + 8, 1);
+    mbar_init(empty, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -605,160 +628,168 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     ctl.Fs[q] = (q < k) ? a.colexp[(int64_t)q * a.p + c] : a.srcexp[(int64_t)c * 32 + (q - k)];
   for (int n = tid; n < 64; n += kUmmaThreads) ctl.Cx[n] = (n < NC) ? a.coefexp[(int64_t)c * 64 + n] : 0;
   if (tid < 32) ctl.Ux[tid] = 0;
-  if (tid == 0) ctl.issued = 0;
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
 
-  // loads of step j: the digit bytes of its prior columns (TMA) and its
-  // coefficient image (bulk copy), both on full[j % kStages]
-  auto issue = [&](int j) {
-    const int sj = j % kStages, rt = (j / (NSPL * KS)) * 128, q0 = (j % KS) * 16, zj = (j / KS) % NSPL;
-    const bool has_q = q0 < k;
-    mbar_expect_tx(full0 + 8 * sj, (has_q ? kStageBytes : 0) + BIMG);
-    if (has_q) {
-      const int b = q0 / S, half = (q0 - b * S) / SC;
-      tma_load_4d(su32(sm + L::STG + sj * kStageBytes), &tm, 0, half, si.tile0 + rt / 16, 8 * b, full0 + 8 * sj);
-    }
-    bulk_load(su32(sm + L::BST + sj * umma_round16(BIMG / 16) * 16), img + (int64_t)(zj * KSMAX + j % KS) * BIMG,
-              BIMG, full0 + 8 * sj);
-    ctl.issued = j + 1;
-  };
-  // the MMAs read the coefficient image straight from its ring slot, so a slot
-  // is refilled only once the MMAs of its previous step are known complete:
-  // loads run two steps ahead
-  if (tid == 0)
-    for (int j = 0; j < 2 && j < nsteps; ++j) issue(j);
-
-  // A roles: thread (column kk = tid % 16 of the step, 16-row tile tau = tid / 16)
-  const int kk = tid & 15, tau = tid >> 4;
-  // the pass block's values this thread splits in step j, into its slot j % 3
-  double* xs_slot = reinterpret_cast<double*>(sm + L::SRCU) + (tid & 127) * 16;
-  auto load_src = [&](int j) {
-    const int rt = (j / (NSPL * KS)) * 128, q = (j % KS) * 16 + kk;
-    if (tid < 128 && q >= k && q < Kt) {
-      double* d = xs_slot + (j % 3) * 128 * 16;
+  if (warp == 8) {
+    // ---- issuer: loads three steps ahead, one MMA group per step -----------
+    if (lane == 0) {
+      uint32_t idesc[kOzDigits];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const int row = rt + 16 * tau + r;
-        const bool ok = row < si.rows;
-        cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+      for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 1, 0);
+      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kOzDigits * 128, 2 * kOzDigits * 128);
+      const uint64_t dB0 = umma_sdesc(su32(sm + L::BST), 128, 256);
+      // loads of step j: the digit planes of its prior columns (TMA) and its
+      // coefficient image (bulk copy), both on full[j % kStages]
+      auto issue = [&](int j) {
+        const int sj = j % kStages, rt = (j / (NSPL * KS)) * 128, q0 = (j % KS) * 16, zj = (j / KS) % NSPL;
+        const bool hq = q0 < k;
+        mbar_expect_tx(full0 + 8 * sj, (hq ? kStageBytes : 0) + BIMG);
+        if (hq)
+          tma_load_2d(su32(sm + L::STG + sj * kStageBytes), &tm, (q0 / 8) * (kOzDigits * 128 / 8),
+                      2 * (si.tile0 + rt / 16), full0 + 8 * sj);
+        bulk_load(su32(sm + L::BST + sj * umma_round16(BIMG / 16) * 16), img + (int64_t)(zj * KSMAX + j % KS) * BIMG,
+                  BIMG, full0 + 8 * sj);
+      };
+      int issued = 0, landed = 0, drains = 0, committed = -1;
+      for (; issued < kDist && issued < nsteps; ++issued) issue(issued);
+      for (int st = 0; st < nsteps; ++st) {
+        const int s = st % kStages, bb = st & 1, ks = st % KS;
+        bool ok = true;
+        // the stage of step st + kDist last served step st - 2
+        if (st >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1));
+        if (ok && issued < nsteps && issued == st + kDist) issue(issued++);
+        if (ok) {
+          ok = mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1));
+          if (ok) landed = st + 1;
+        }
+        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((st / kStages) & 1));
+        // a new accumulation interval starts once the previous one was drained
+        if (ok && (ks & 15) == 0 && st > 0) ok = mbar_wait(empty, (uint32_t)(drains++ & 1));
+        if (!ok || umma_timed_out(a.flags)) {
+          umma_timeout(ctl, a.flags);
+          break;
+        }
+        tc_fence_after();
+        const uint64_t db = dB0 + (uint64_t)((s * umma_round16(BIMG / 16) * 16) >> 4);
+        const uint32_t accum = (ks & 15) ? 1u : 0u;
+#pragma unroll
+        for (int t = 1; t <= kOzDigits; ++t) {
+          const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
+          umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
+        }
+        umma_commit(mmad0 + 8 * bb);
+        committed = st;
       }
+      for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+      if (committed >= 0) mbar_wait(mmad0 + 8 * (committed & 1), (uint32_t)((committed >> 1) & 1));
     }
-    cp_async_commit();
-  };
-  load_src(0);
-  if (nsteps > 1) load_src(1); else cp_async_commit();
-  // epilogue roles: warp w drains TMEM lanes 32 (w % 4) .. + 31 and output
-  // columns (w / 4) NB / 2 .. + NB / 2 - 1 of the split
-  constexpr int NH = NB / 2;
-  double acc[NH], res[NSPL][NH];
+    __syncwarp();
+  } else {
+    // ---- workers (warps 0..7): thread (column kk, 16-row tile tau, half h)
+    // of a step splits the block's own columns into the stage, and warp w
+    // drains TMEM lanes 32 (w % 4) .. + 31 and output columns
+    // (w / 4) NB / 2 .. + NB / 2 - 1 of the group
+    const int kk = tid & 15, tau = (tid >> 4) & 7, hh = (tid >> 7) & 1;
+    double* xs_slot = reinterpret_cast<double*>(sm + L::SRCU) + tid * 8;
+    auto load_src = [&](int j) {
+      const int rt = (j / (NSPL * KS)) * 128, q = (j % KS) * 16 + kk;
+      if (q >= k && q < Kt) {
+        double* d = xs_slot + (j % 3) * 256 * 8;
 #pragma unroll
-  for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-  uint32_t idesc[kOzDigits];
+        for (int r = 0; r < 8; ++r) {
+          const int row = rt + 16 * tau + 8 * hh + r;
+          const bool ok = row < si.rows;
+          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+        }
+      }
+      cp_async_commit();
+    };
+    load_src(0);
+    if (nsteps > 1) load_src(1); else cp_async_commit();
+    constexpr int NH = NB / 2;
+    double acc[NH], res[NSPL][NH];
 #pragma unroll
-  for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 1, 0);
-
-  for (int st = 0; st < nsteps; ++st) {
-    const int s = st % kStages, bb = st & 1;
-    const int rt = (st / (NSPL * KS)) * 128, ks = st % KS, q = ks * 16 + kk, zs = (st / KS) % NSPL;
-    if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
-    asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
-    if (tid < 128) {
-      if (st < ctl.issued && !mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1))) umma_timeout(ctl, a.flags);
+    for (int j = 0; j < NH; ++j) acc[j] = 0.0;
+    for (int st = 0; st < nsteps; ++st) {
+      const int s = st % kStages, bb = st & 1;
+      const int rt = (st / (NSPL * KS)) * 128, ks = st % KS, q = ks * 16 + kk, zs = (st / KS) % NSPL;
+      if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
+      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
+      // no warp runs more than two steps ahead of the MMAs
       if (st >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1)))
         umma_timeout(ctl, a.flags);
-      // the slot of step st + 2 last served step st - 2, whose MMAs are done
-      if (tid == 0 && !ctl.abort && st + 2 < nsteps) issue(st + 2);
-      unsigned char* abuf = sm + L::ABUF + bb * kOzDigits * kAPlaneBytes;
-      // MN-major: rows 16 tau .. +7 and +8 .. +15 of column kk
-      const int aoff = (2 * tau) * 128 + (kk & 7) * 16 + (kk >> 3) * 2048;
-      if (q < k) {
-        const int pp = (S == 8) ? (kk >> 3) * 8 : 0, j = (S == 8) ? (kk & 7) : kk;
-        const unsigned char* sp = sm + L::STG + s * kStageBytes + ((pp * 8 + tau) * 16 * SC) + j * 16;
-        const uint4 g = *reinterpret_cast<const uint4*>(sp + 7 * 8 * 16 * SC);
-#pragma unroll
-        for (int t = 0; t < kOzDigits; ++t) {
-          uint4 lo, hi;
-          expand16(*reinterpret_cast<const uint4*>(sp + t * 8 * 16 * SC), g, lo, hi);
-          *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff) = lo;
-          *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff + 128) = hi;
-        }
-      } else if (q < Kt) {
-        const double* x = xs_slot + (st % 3) * 128 * 16;
-        split8_store(x, ctl.Fs[q], abuf + aoff, a.flags);
-        split8_store(x + 8, ctl.Fs[q], abuf + aoff + 128, a.flags);
-      } else {
-#pragma unroll
-        for (int t = 0; t < kOzDigits; ++t) {
-          *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff) = make_uint4(0u, 0u, 0u, 0u);
-          *reinterpret_cast<uint4*>(abuf + t * kAPlaneBytes + aoff + 128) = make_uint4(0u, 0u, 0u, 0u);
-        }
-      }
-    }
-    if (tid == 0 && umma_timed_out(a.flags)) ctl.abort = 1;
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && !ctl.abort) {
-      tc_fence_after();
-      const unsigned char* abuf = sm + L::ABUF + bb * kOzDigits * kAPlaneBytes;
-      const uint64_t db = umma_sdesc(su32(sm + L::BST + s * umma_round16(BIMG / 16) * 16), 128, 256);
-      const uint32_t accum = (ks & 15) ? 1u : 0u;
-#pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) {
-        const uint64_t da = umma_sdesc(su32(abuf + (t - 1) * kAPlaneBytes), 2048, 128);
-        umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
-      }
-      umma_commit(mmad0 + 8 * bb);
-    }
-    const bool last_k = (ks + 1 == KS);
-    if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
-      if (!ctl.abort) {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
-        if (!ok) {
-          umma_timeout(ctl, a.flags);
+      unsigned char* stage = sm + L::STG + s * kStageBytes;
+      const bool writes = q >= k;  // the block's own columns, or zeros past Kt
+      // the stage's loads landed (its previous step's MMAs finished before they were issued)
+      if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1))) umma_timeout(ctl, a.flags);
+      if (writes) {
+        unsigned char* dst = stage + (2 * tau + hh) * (2 * kOzDigits * 128) + (kk >> 3) * (kOzDigits * 128) + (kk & 7) * 16;
+        if (q < Kt) {
+          split8_store(xs_slot + (st % 3) * 256 * 8, ctl.Fs[q], dst, 128, a.flags);
         } else {
-          tc_fence_after();
-          const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
-          for (int c4 = 0; c4 < NH / 4; ++c4) umma_drain<NB, 4>(tlane, (warp >> 2) * NH + c4 * 4, acc + c4 * 4);
+          for (int t = 0; t < kOzDigits; ++t) *reinterpret_cast<uint4*>(dst + t * 128) = make_uint4(0u, 0u, 0u, 0u);
         }
       }
-      if (last_k) {
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ready0 + 8 * s);
+      const bool last_k = (ks + 1 == KS);
+      if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
+        if (!ctl.abort) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
+          if (!ok) {
+            umma_timeout(ctl, a.flags);
+          } else {
+            tc_fence_after();
+            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
-        for (int zz = 0; zz < NSPL; ++zz)
-          if (zz == zs)
-#pragma unroll
-            for (int j = 0; j < NH; ++j) res[zz][j] = acc[j];
-#pragma unroll
-        for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-      }
-      const int r = rt + (warp & 3) * 32 + lane;
-      if (last_k && zs == NSPL - 1 && r < si.rows && !ctl.abort) {
-        const int64_t row = si.row0 + r;
-#pragma unroll
-        for (int zz = 0; zz < NSPL; ++zz)
-#pragma unroll
-          for (int j = 0; j < NH; ++j) {
-            const int n = zz * NB + (warp >> 2) * NH + j;
-            const double d = scale_exp(res[zz][j], ctl.Cx[n] - 1022 - 16);
-            if (n < S) {
-              slot[row * S + n] = d;
-              if (NOUT == 2) atomicMax(&ctl.Ux[n], bexp(d));
-            } else {
-              a.U[row * a.ldu + (n - S)] = d;
-            }
+            for (int c4 = 0; c4 < NH / 4; ++c4) umma_drain<NB, 4>(tlane, (warp >> 2) * NH + c4 * 4, acc + c4 * 4);
           }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty);
+        if (last_k) {
+#pragma unroll
+          for (int zz = 0; zz < NSPL; ++zz)
+            if (zz == zs)
+#pragma unroll
+              for (int j = 0; j < NH; ++j) res[zz][j] = acc[j];
+#pragma unroll
+          for (int j = 0; j < NH; ++j) acc[j] = 0.0;
+        }
+        const int r = rt + (warp & 3) * 32 + lane;
+        if (last_k && zs == NSPL - 1 && r < si.rows && !ctl.abort) {
+          const int64_t row = si.row0 + r;
+#pragma unroll
+          for (int zz = 0; zz < NSPL; ++zz)
+#pragma unroll
+            for (int j = 0; j < NH; ++j) {
+              const int n = zz * NB + (warp >> 2) * NH + j;
+              const double d = scale_exp(res[zz][j], ctl.Cx[n] - 1022 - 16);
+              if (n < S) {
+                slot[row * S + n] = d;
+                atomicMax(&ctl.Ux[n], bexp(d));
+              } else {
+                a.U[row * a.ldu + (n - S)] = d;
+              }
+            }
+        }
       }
-      tc_fence_before();
-      __syncthreads();
     }
   }
-  if (NOUT == 2 && tid < S && !ctl.abort) atomicMax(&a.colexp[(int64_t)(k + tid) * a.p + c], ctl.Ux[tid]);
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
+  if (tid < S && !ctl.abort) {
+    if (NOUT == 2)
+      atomicMax(&a.colexp[(int64_t)(k + tid) * a.p + c], ctl.Ux[tid]);
+    else
+      a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = ctl.Ux[tid];
+  }
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(umma_tcols(NB)));
@@ -774,7 +805,10 @@ cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   dim3 grid(a.nslab, (Kt + 127) / 128, L::NSPL);
   const double* src = (pass == 1) ? a.W : a.V + (int64_t)a.nb * a.n * S;
   const int64_t lds = (pass == 1) ? a.ldw : S;
-  k_umma_gram<S><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram);
+  // the pass block's exponents per slab: from a small pass over W for pass 1,
+  // from the reiteration's assembly (k_umma_update<S, 1>) afterwards
+  if (pass == 1) k_umma_srcexp<S><<<a.nslab, 256, 0, st>>>(a, src, lds);
+  k_umma_gram<S><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass);
   return cudaGetLastError();
 }
 
@@ -871,22 +905,16 @@ cudaError_t umma_make_maps(uint8_t* dig, int s, int panels, int64_t dtiles, Umma
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
   if (e != cudaSuccess || fn == nullptr || q != cudaDriverEntryPointSuccess) return e ? e : cudaErrorNotSupported;
   EncodeTiledFn encode = reinterpret_cast<EncodeTiledFn>(fn);
-  const int sc = s < 16 ? s : 16;
-  // dims (innermost first): the sc columns x 16 rows of one tile, column
-  // halves, tiles, planes of all panels
-  const cuuint64_t dims[4] = {(cuuint64_t)(16 * sc), (cuuint64_t)(s / sc), (cuuint64_t)dtiles,
-                              (cuuint64_t)(8 * panels)};
-  const cuuint64_t strides[3] = {(cuuint64_t)(16 * sc), (cuuint64_t)(16 * s), (cuuint64_t)(16 * s) * dtiles};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  const cuuint32_t box_gram[4] = {(cuuint32_t)(16 * sc), (cuuint32_t)(s / sc), 1, (cuuint32_t)(8 * (128 / s))};
-  const cuuint32_t box_upd[4] = {(cuuint32_t)(16 * sc), 1, 8, (cuuint32_t)(8 * (16 / sc))};
-  CUresult r = encode(&maps->gram, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, dig, dims, strides, box_gram, es,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  r = encode(&maps->upd, CU_TENSOR_MAP_DATA_TYPE_UINT8, 4, dig, dims, strides, box_upd, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  // 2D view in 8-byte elements: an 8-row block's row of all column groups
+  // (gtot x 7 x 128 bytes), 8-row blocks; box = 2 groups x 16 blocks
+  const cuuint64_t gtot = (cuuint64_t)panels * (s / 8);
+  const cuuint64_t dims[2] = {gtot * kOzDigits * 128 / 8, (cuuint64_t)(2 * dtiles)};
+  const cuuint64_t strides[1] = {gtot * kOzDigits * 128};
+  const cuuint32_t es[2] = {1, 1};
+  const cuuint32_t box[2] = {2 * kOzDigits * 128 / 8, 16};
+  const CUresult r = encode(&maps->upd, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, dig, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
