@@ -303,6 +303,10 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
       }
     }
     for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
+    // the new iterate's exponents per slab are maxima k_umma_update accumulates
+    if (NOUT == 1)
+      for (int i = tid; i < (a.chunk_slab0[c + 1] - a.chunk_slab0[c]) * 32; i += 256)
+        a.srcexp_slab[(int64_t)a.chunk_slab0[c] * 32 + i] = 0;
     return;
   }
   // pairs (q even, q+1) for each column n

@@ -60,7 +60,9 @@ __host__ __device__ constexpr int umma_col(int t, int nb) {
   for (int i = 1; i < t; ++i) c += umma_nt(i, nb);
   return c;
 }
-__host__ __device__ constexpr int umma_tcols(int nb) { return umma_col(8, nb) <= 256 ? 256 : 512; }
+// TMEM accumulator buffers (256 columns apart) that fit in the 512 columns.
+__host__ __device__ constexpr int umma_nacc(int nb) { return umma_col(8, nb) <= 256 ? 2 : 1; }
+constexpr int kTmemCols = 512;
 
 // --- PTX wrappers -------------------------------------------------------------
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -156,17 +158,12 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t (&r)[N]) {
 
 // Per-CTA control block at the end of dynamic shared memory.
 struct UmmaCtl {
-  uint64_t full[kStages];   // loads of a stage landed (the issuer arms them)
+  uint64_t full[kStages];   // loads of a stage landed (the issuer arms them every step)
   uint64_t ready[kStages];  // the workers wrote their part of a step's operands (8 warp arrivals)
   uint64_t mmad[2];         // MMAs of a step done (commit), alternating by step parity
-  uint64_t empty;           // the accumulators were drained (8 warp arrivals)
+  uint64_t empty[2];        // a TMEM accumulator buffer was drained (8 warp arrivals)
   uint32_t tslot;           // TMEM base written by tcgen05.alloc
   int abort;                // a bounded wait gave up: no further TMA or MMA is issued
-  int issued;               // steps whose loads have been issued
-  int Hs[32];               // column exponents of the pass block (this slab)
-  int Fs[1024];             // column exponents of [Q_i A]
-  int Cx[64];               // exponents of the coefficient columns
-  int Ux[32];               // new panel's column exponents (stage 2)
 };
 
 __device__ __forceinline__ void umma_timeout(UmmaCtl& c, int* flags) {
@@ -308,13 +305,14 @@ __global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* s
 }
 
 // ---------------------------------------------------------------------------
-// Stage-1 Gram partial C = [Q_i A]^T A of one slab, for 128 columns of
-// [Q_i A] (grid.y) and NB columns of A (grid.z).  MMA: M = columns of [Q_i A],
-// N = (u, column of A), K = 16 rows per step.  The A operand of digit t is
-// the loaded stage itself ([8-row block][group][t][128 B]: K-major,
-// SBO = 7 x 128, LBO = 16 x 7 x 128); the block's own columns are split into
-// it after the load.  B
-// operand (K-major): row (u - 1) NB + n holds digit u of column n of A.
+// Stage-1 Gram partials C = [Q_i A]^T A per slab.  Work item = (slab, group
+// of 128 columns of [Q_i A], group of NB columns of A); one persistent CTA
+// per SM walks its items, with loads running ahead across item boundaries.
+// MMA: M = columns of [Q_i A], N = (u, column of A), K = 16 rows per step.
+// The A operand of digit t is the loaded stage itself ([8-row block][group]
+// [t][128 B]: K-major, SBO = 7 x 128, LBO = 16 x 7 x 128); the block's own
+// columns are split into it after the load.  B operand (K-major): row
+// (u - 1) NB + n holds digit u of column n of A.
 template <int S>
 struct GramLayout {
   static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
@@ -330,26 +328,55 @@ struct GramLayout {
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
 };
 
+// One Gram work item and the walk over a CTA's items (w = blockIdx.x,
+// blockIdx.x + gridDim.x, ...), step by step.
+struct GramCursor {
+  int w, st, nsteps, slab, rows, tile0, chunk, col0, z;
+  int64_t row0;
+  bool valid;
+  __device__ __forceinline__ void load(const StepArgs& a, int nitems, int ngroups) {
+    valid = w < nitems;
+    if (!valid) return;
+    slab = w % a.nslab;
+    const int rest = w / a.nslab;
+    col0 = (rest % ngroups) * 128;
+    z = rest / ngroups;
+    const SlabInfo si = a.slabs[slab];
+    row0 = si.row0;
+    rows = si.rows;
+    tile0 = si.tile0;
+    chunk = si.chunk;
+    nsteps = (rows + 15) / 16;
+  }
+  __device__ __forceinline__ void start(const StepArgs& a, int nitems, int ngroups) {
+    w = blockIdx.x;
+    st = 0;
+    load(a, nitems, ngroups);
+  }
+  __device__ __forceinline__ void next(const StepArgs& a, int nitems, int ngroups) {
+    if (++st < nsteps) return;
+    w += gridDim.x;
+    st = 0;
+    load(a, nitems, ngroups);
+  }
+};
+
 template <int S>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass) {
   using L = GramLayout<S>;
-  constexpr int NB = L::NB, RB = L::RB;
+  constexpr int NB = L::NB, RB = L::RB, NSPL = L::NSPL, NACC = umma_nacc(NB);
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
-  const SlabInfo si = a.slabs[blockIdx.x];
   const int k = a.nb * S, Kt = k + S;
-  const int col0 = blockIdx.y * 128, z = blockIdx.z;
+  const int ngroups = (Kt + 127) / 128, nitems = a.nslab * ngroups * NSPL;
+  const int gtot = a.M * (S / 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int gtot = a.M * (S / 8), g0 = col0 / 8;
-  const int ng = min(16, gtot - g0);            // column groups present in the digit planes
-  const bool has_q = k > col0 && ng > 0;        // prior panels in the group: loaded
-  const int nsteps = (si.rows + 15) / 16;
   const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
-  const uint32_t empty = su32(&ctl.empty);
+  const uint32_t empty0 = su32(&ctl.empty[0]);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -358,19 +385,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     }
     mbar_init(mmad0, 1);
     mbar_init(mmad0 + 8, 1);
-    mbar_init(empty, 8);
+    mbar_init(empty0, 8);
+    mbar_init(empty0 + 8, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)),
-                 "r"(umma_tcols(NB)));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid < S) ctl.Hs[tid] = a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid];
-  for (int m = tid; m < 128; m += kUmmaThreads) {
-    const int col = col0 + m;
-    ctl.Fs[m] = (col < k) ? a.colexp[(int64_t)col * a.p + si.chunk] : 0;
   }
   if constexpr (RB > 7 * NB) {  // B pad rows stay zero
     for (int i = tid; i < 2 * (RB - 7 * NB) * 2; i += kUmmaThreads) {
@@ -386,7 +409,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   const uint32_t tbase = ctl.tslot;
 
   if (warp == 8) {
-    // ---- issuer: loads three steps ahead, one MMA group per step -----------
+    // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
     if (lane == 0) {
       uint32_t idesc[kOzDigits];
 #pragma unroll
@@ -394,49 +417,67 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
       const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kStageBytes / 2, kOzDigits * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
-      const uint32_t run = (uint32_t)max(ng, 0) * kOzDigits * 128;
-      auto issue = [&](int j) {
-        const int sj = j % kStages;
-        const int64_t eta = 2 * (int64_t)(si.tile0 + j);
-        const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
-        mbar_expect_tx(full0 + 8 * sj, 2 * run);
-        bulk_load(su32(sm + L::STG + sj * kStageBytes), gsrc, run, full0 + 8 * sj);
-        bulk_load(su32(sm + L::STG + sj * kStageBytes + kStageBytes / 2), gsrc + (int64_t)gtot * kOzDigits * 128,
-                  run, full0 + 8 * sj);
-      };
-      int issued = 0, landed = 0, drains = 0, committed = -1;
-      if (has_q)
-        for (; issued < kDist && issued < nsteps; ++issued) issue(issued);
-      for (int st = 0; st < nsteps; ++st) {
-        const int s = st % kStages, bb = st & 1;
-        bool ok = true;
-        // the stage of step st + kDist last served step st - 2
-        if (st >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1));
-        if (ok && has_q && issued < nsteps && issued == st + kDist) issue(issued++);
-        if (ok && has_q) {
-          ok = mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1));
-          if (ok) landed = st + 1;
+      // loads of global step j (cursor c): the digit planes of the group's prior
+      // panels, or a bare arrival when it has none
+      auto issue = [&](const GramCursor& c, int j) {
+        const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, gtot - g0);
+        if (k > c.col0 && ng > 0) {
+          const uint32_t run = (uint32_t)ng * kOzDigits * 128;
+          const int64_t eta = 2 * (int64_t)(c.tile0 + c.st);
+          const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
+          mbar_expect_tx(full0 + 8 * sj, 2 * run);
+          bulk_load(su32(sm + L::STG + sj * kStageBytes), gsrc, run, full0 + 8 * sj);
+          bulk_load(su32(sm + L::STG + sj * kStageBytes + kStageBytes / 2), gsrc + (int64_t)gtot * kOzDigits * 128,
+                    run, full0 + 8 * sj);
+        } else {
+          mbar_arrive(full0 + 8 * sj);
         }
-        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((st / kStages) & 1));
-        if (ok && (st & 15) == 0 && st > 0) ok = mbar_wait(empty, (uint32_t)(drains++ & 1));
+      };
+      GramCursor ld, cur;
+      ld.start(a, nitems, ngroups);
+      cur.start(a, nitems, ngroups);
+      int issued = 0, landed = 0, intervals = 0;
+      int64_t committed = -1;
+      for (; issued < kDist && ld.valid; ++issued, ld.next(a, nitems, ngroups)) issue(ld, issued);
+      for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
+        const int s = g % kStages, bb = g & 1;
+        bool ok = true;
+        // the stage of global step g + kDist last served step g - 2
+        if (g >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1));
+        if (ok && ld.valid) {
+          issue(ld, issued++);
+          ld.next(a, nitems, ngroups);
+        }
+        if (ok) {
+          ok = mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1));
+          if (ok) landed = g + 1;
+        }
+        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((g / kStages) & 1));
+        int buf = 0;
+        if ((cur.st & 15) == 0) {  // a new accumulation interval: its buffer must be drained
+          buf = intervals % NACC;
+          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * buf, (uint32_t)(((intervals / NACC) - 1) & 1));
+          ++intervals;
+        }
+        buf = (intervals - 1) % NACC;
         if (!ok || umma_timed_out(a.flags)) {
           umma_timeout(ctl, a.flags);
           break;
         }
         tc_fence_after();
         const uint64_t db = dB0 + (uint64_t)((bb * (RB * 32)) >> 4);
-        const uint32_t accum = (st & 15) ? 1u : 0u;
+        const uint32_t accum = (cur.st & 15) ? 1u : 0u;
 #pragma unroll
         for (int t = 1; t <= kOzDigits; ++t) {
           const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
-          umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
+          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
         umma_commit(mmad0 + 8 * bb);
-        committed = st;
+        committed = g;
       }
-      // drain what is still in flight before the CTA's memory is released
+      // what is still in flight completes before the CTA's memory is released
       for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
-      if (committed >= 0) mbar_wait(mmad0 + 8 * (committed & 1), (uint32_t)((committed >> 1) & 1));
+      if (committed >= 0) mbar_wait(mmad0 + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
     }
     __syncwarp();
   } else {
@@ -444,84 +485,103 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     // threads 0 .. 2S - 1 split the block's own columns into the A tile
     // (column l = tid / 2, rows 8 (tid % 2) .. + 7; only in the group that
     // holds them); threads 128 .. 128 + 4 NB - 1 split the B operand (column
-    // n, rows 4 q .. 4 q + 3)
-    const int al = tid >> 1, ah = tid & 1, am = k - col0 + al;
-    const bool a_src = tid < 2 * S && am >= 0 && am < 128;
+    // n, rows 4 q .. 4 q + 3); warp w drains TMEM lanes 32 (w % 4) .. + 31,
+    // columns (w / 4) NB / 2 .. + NB / 2 - 1
+    const int al = tid >> 1, ah = tid & 1;
     const int bi = tid - 128;
     const bool b_role = bi >= 0 && bi < 4 * NB;
     const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
-    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (a_src ? tid : 0) * 8;
+    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (tid < 2 * S ? tid : 0) * 8;
     double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + (b_role ? bi : 0) * 4;
-    auto load_src = [&](int j) {
-      const int r0 = j * 16;
-      if (a_src) {
-        double* d = xa_slot + (j % 3) * 2 * S * 8;
+    auto is_asrc = [&](const GramCursor& c) {
+      const int am = k - c.col0 + al;
+      return tid < 2 * S && am >= 0 && am < 128;
+    };
+    // the float64 values this thread splits in global step j (cursor c), into slot j % 3
+    auto load_src = [&](const GramCursor& c, int j) {
+      if (c.valid) {
+        const int r0 = c.st * 16;
+        if (is_asrc(c)) {
+          double* d = xa_slot + (j % 3) * 2 * S * 8;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int row = r0 + 8 * ah + r;
-          const bool ok = row < si.rows;
-          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + al, ok);
+          for (int r = 0; r < 8; ++r) {
+            const int row = r0 + 8 * ah + r;
+            const bool ok = row < c.rows;
+            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + al, ok);
+          }
         }
-      }
-      if (b_role) {
-        double* d = xb_slot + (j % 3) * 4 * NB * 4;
+        if (b_role) {
+          double* d = xb_slot + (j % 3) * 4 * NB * 4;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const int row = r0 + 4 * bq + r;
-          const bool ok = row < si.rows;
-          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + z * NB + bn, ok);
+          for (int r = 0; r < 4; ++r) {
+            const int row = r0 + 4 * bq + r;
+            const bool ok = row < c.rows;
+            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + bn, ok);
+          }
         }
       }
       cp_async_commit();
     };
-    load_src(0);
-    if (nsteps > 1) load_src(1); else cp_async_commit();
+    GramCursor ahead, cur;
+    ahead.start(a, nitems, ngroups);
+    cur.start(a, nitems, ngroups);
+    load_src(ahead, 0);
+    ahead.next(a, nitems, ngroups);
+    load_src(ahead, 1);
+    ahead.next(a, nitems, ngroups);
     double acc[NB / 2];
 #pragma unroll
     for (int j = 0; j < NB / 2; ++j) acc[j] = 0.0;
-    for (int st = 0; st < nsteps; ++st) {
-      const int s = st % kStages, bb = st & 1;
-      if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
-      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
-      // MMAs of step st - 2 done: B buffer bb is free (and no warp runs ahead)
-      if (st >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1)))
+    int intervals = 0;
+    for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
+      const int s = g % kStages, bb = g & 1;
+      load_src(ahead, g + 2);
+      ahead.next(a, nitems, ngroups);
+      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
+      // MMAs of step g - 2 done: B buffer bb is free (and no warp runs ahead)
+      if (g >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1)))
         umma_timeout(ctl, a.flags);
       unsigned char* stage = sm + L::STG + s * kStageBytes;
-      if (a_src && has_q && !ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1)))
-        umma_timeout(ctl, a.flags);
-      if (a_src)
-        split8_store(xa_slot + (st % 3) * 2 * S * 8, ctl.Hs[al],
+      if (is_asrc(cur)) {
+        const int am = k - cur.col0 + al;
+        if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
+        split8_store(xa_slot + (g % 3) * 2 * S * 8, a.srcexp_slab[(int64_t)cur.slab * 32 + al],
                      stage + ah * (kStageBytes / 2) + (am >> 3) * (kOzDigits * 128) + (am & 7) * 16, 128, a.flags);
+      }
       if (b_role) {
-        unsigned h[4], l[4], g[4];
+        unsigned h[4], l[4], gg[4];
         bool bad = false;
-        const int e = ctl.Hs[z * NB + bn];
-        const double* x = xb_slot + (st % 3) * 4 * NB * 4;
+        const int e = a.srcexp_slab[(int64_t)cur.slab * 32 + cur.z * NB + bn];
+        const double* x = xb_slot + (g % 3) * 4 * NB * 4;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], g[r]);
+        for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], gg[r]);
         if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
         unsigned char* bbuf = sm + L::BBUF + bb * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
 #pragma unroll
         for (int u = 1; u <= kOzDigits; ++u) {
           const int row = (u - 1) * NB + bn;
-          const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
-          const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
+          const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (gg[0] >> 16) | gg[1]);
+          const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (gg[2] >> 16) | gg[3]);
           *reinterpret_cast<uint2*>(bbuf + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
         }
       }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
-      // exact float32 sums cover 16 steps (256 rows): drain the accumulators;
-      // warps w and w + 4 take TMEM lanes 32 (w % 4) .. + 31, halves of the NB columns
-      if (((st + 1) & 15) == 0 || st + 1 == nsteps) {
-        if (!ctl.abort) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
-          if (!ok) {
+      // exact float32 sums cover 16 steps (256 rows): drain the accumulators
+      const bool item_end = cur.st + 1 == cur.nsteps;
+      if (((cur.st + 1) & 15) == 0 || item_end) {
+        const int buf = intervals % NACC;
+        ++intervals;
+        // warp-uniform decisions around the warp-collective TMEM loads
+        bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
+        if (alive) {
+          alive = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((g >> 1) & 1)));
+          if (!alive) {
             umma_timeout(ctl, a.flags);
           } else {
             tc_fence_after();
-            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
 #pragma unroll
             for (int c4 = 0; c4 < NB / 8; ++c4)
               umma_drain<NB, 4>(tlane, (warp >> 2) * (NB / 2) + c4 * 4, acc + c4 * 4);
@@ -529,40 +589,46 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty);
-      }
-    }
-    // partial of this slab: column col0 + m, block columns z NB + (w / 4) NB / 2 ..
-    const int m = (warp & 3) * 32 + lane, colm = col0 + m;
-    if (colm < Kt && !ctl.abort) {
-      const int n0 = z * NB + (warp >> 2) * (NB / 2);
-      const int F = colm < k ? ctl.Fs[m] : ctl.Hs[colm - k];
-      double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S + (int64_t)colm * S + n0;
+        if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+        if (item_end) {
+          // partial of this slab: column col0 + m, block columns z NB + (w / 4) NB / 2 ..
+          const int m = (warp & 3) * 32 + lane, colm = cur.col0 + m;
+          if (colm < Kt && alive) {
+            const int n0 = cur.z * NB + (warp >> 2) * (NB / 2);
+            const int* hs = a.srcexp_slab + (int64_t)cur.slab * 32;
+            const int F = colm < k ? a.colexp[(int64_t)colm * a.p + cur.chunk] : hs[colm - k];
+            double* out = a.part + (int64_t)cur.slab * a.Kmax * S + (int64_t)colm * S + n0;
 #pragma unroll
-      for (int j = 0; j < NB / 2; ++j) out[j] = scale_exp(acc[j], F + ctl.Hs[n0 + j] - 2044 - 16);
+            for (int j = 0; j < NB / 2; ++j) out[j] = scale_exp(acc[j], F + hs[n0 + j] - 2044 - 16);
+          }
+#pragma unroll
+          for (int j = 0; j < NB / 2; ++j) acc[j] = 0.0;
+        }
+      }
     }
   }
   tc_fence_before();
   cta_sync();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(umma_tcols(NB)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
   }
 }
 
 // ---------------------------------------------------------------------------
-// out = [Q_i A] Coef for one slab.  MMA: M = 128 rows (one row tile),
-// N = (u, output column) for NB output columns at a time, K = 16 columns of
-// [Q_i A] per step.  The A operand of digit t is the TMA stage itself
-// ([8-row block][group][t][128 B]: MN-major, SBO = 2 x 7 x 128,
-// LBO = 7 x 128); the block's own columns are split into it.  B operand: the coefficient
-// image of the step (k_oz_coef<UMMA>).  With more than NB outputs the CTA
-// runs the K loop of a row tile once per group of NB outputs and writes the
-// tile only after the last group: the pass block may share storage with an
-// output (the new panel holds the last iterate; U may alias W), so no row is
-// written before every group has read it.  NOUT = 1: the reiteration's new
-// iterate into the new panel, and its column exponents per slab; NOUT = 2:
-// U_i into the panel and U to the caller, and the panel's column exponents.
+// out = [Q_i A] Coef per slab; one persistent CTA per SM walks its slabs.
+// MMA: M = 128 rows (one row tile), N = (u, output column) for NB output
+// columns at a time, K = 16 columns of [Q_i A] per step.  The A operand of
+// digit t is the TMA stage itself ([8-row block][group][t][128 B]: MN-major,
+// SBO = 2 x 7 x 128, LBO = 7 x 128); the block's own columns are split into
+// it.  B operand: the coefficient image of the step (k_oz_coef<UMMA>).  With
+// more than NB outputs the K loop of a row tile runs once per group of NB
+// outputs and the tile is written only after the last group: the pass block
+// may share storage with an output (the new panel holds the last iterate;
+// U may alias W), so no row is written before every group has read it.
+// NOUT = 1: the reiteration's new iterate into the new panel, and its column
+// exponents per slab; NOUT = 2: U_i into the panel and U to the caller, and
+// the panel's column exponents.
 template <int S, int NOUT>
 struct UpdLayout {
   static constexpr int NC = NOUT * S, NB = NC < 16 ? NC : 16, NSPL = NC / NB;
@@ -577,19 +643,47 @@ struct UpdLayout {
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
 };
 
+// The walk over a CTA's slabs, step by step: step = (row tile, output
+// group, 16 columns).
+struct UpdCursor {
+  int w, st, nsteps, rows, tile0, chunk;
+  int64_t row0;
+  bool valid;
+  __device__ __forceinline__ void load(const StepArgs& a, int per_tile) {
+    valid = w < a.nslab;
+    if (!valid) return;
+    const SlabInfo si = a.slabs[w];
+    row0 = si.row0;
+    rows = si.rows;
+    tile0 = si.tile0;
+    chunk = si.chunk;
+    nsteps = ((rows + 127) / 128) * per_tile;
+  }
+  __device__ __forceinline__ void start(const StepArgs& a, int per_tile) {
+    w = blockIdx.x;
+    st = 0;
+    load(a, per_tile);
+  }
+  __device__ __forceinline__ void next(const StepArgs& a, int per_tile) {
+    if (++st < nsteps) return;
+    w += gridDim.x;
+    st = 0;
+    load(a, per_tile);
+  }
+};
+
 template <int S, int NOUT>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_update(StepArgs a, const double* src_fixed, int64_t lds_fixed, int pass,
                   const __grid_constant__ CUtensorMap tm) {
   using L = UpdLayout<S, NOUT>;
-  constexpr int NC = L::NC, NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL;
+  constexpr int NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL, NACC = umma_nacc(NB);
   if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
-  const SlabInfo si = a.slabs[blockIdx.x];
-  const int c = si.chunk, k = a.nb * S, Kt = k + S;
+  const int k = a.nb * S, Kt = k + S;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double* src = src_fixed;
   int64_t lds = lds_fixed;
@@ -601,12 +695,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     src = (Lp == 1) ? a.W : slot;
     lds = (Lp == 1) ? a.ldw : S;
   }
-  const int KS = (Kt + 15) / 16, KSMAX = (a.Kmax + 15) / 16;
-  const int ntr = (si.rows + 127) / 128;
-  const int nsteps = ntr * NSPL * KS;  // step = (row tile, output group, 16 columns)
-  const unsigned char* img = reinterpret_cast<const unsigned char*>(a.coefdig + (int64_t)c * a.coefdig_stride);
+  const int KS = (Kt + 15) / 16, KSMAX = (a.Kmax + 15) / 16, per_tile = NSPL * KS;
   const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
-  const uint32_t empty = su32(&ctl.empty);
+  const uint32_t empty0 = su32(&ctl.empty[0]);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -615,59 +706,70 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     }
     mbar_init(mmad0, 1);
     mbar_init(mmad0 + 8, 1);
-    mbar_init(empty, 8);
+    mbar_init(empty0, 8);
+    mbar_init(empty0 + 8, 8);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)),
-                 "r"(umma_tcols(NB)));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int q = tid; q < Kt; q += kUmmaThreads)
-    ctl.Fs[q] = (q < k) ? a.colexp[(int64_t)q * a.p + c] : a.srcexp[(int64_t)c * 32 + (q - k)];
-  for (int n = tid; n < 64; n += kUmmaThreads) ctl.Cx[n] = (n < NC) ? a.coefexp[(int64_t)c * 64 + n] : 0;
-  if (tid < 32) ctl.Ux[tid] = 0;
   tc_fence_before();
   cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
 
   if (warp == 8) {
-    // ---- issuer: loads three steps ahead, one MMA group per step -----------
+    // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
     if (lane == 0) {
       uint32_t idesc[kOzDigits];
 #pragma unroll
       for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 1, 0);
       const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kOzDigits * 128, 2 * kOzDigits * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BST), 128, 256);
-      // loads of step j: the digit planes of its prior columns (TMA) and its
-      // coefficient image (bulk copy), both on full[j % kStages]
-      auto issue = [&](int j) {
-        const int sj = j % kStages, rt = (j / (NSPL * KS)) * 128, q0 = (j % KS) * 16, zj = (j / KS) % NSPL;
+      // loads of global step j (cursor c): the digit planes of its prior
+      // columns (TMA) and its coefficient image (bulk copy), on full[j % kStages]
+      auto issue = [&](const UpdCursor& c, int j) {
+        const int sj = j % kStages, rt = (c.st / per_tile) * 128, ks = c.st % KS, zj = (c.st / KS) % NSPL;
+        const int q0 = ks * 16;
         const bool hq = q0 < k;
         mbar_expect_tx(full0 + 8 * sj, (hq ? kStageBytes : 0) + BIMG);
         if (hq)
           tma_load_2d(su32(sm + L::STG + sj * kStageBytes), &tm, (q0 / 8) * (kOzDigits * 128 / 8),
-                      2 * (si.tile0 + rt / 16), full0 + 8 * sj);
-        bulk_load(su32(sm + L::BST + sj * umma_round16(BIMG / 16) * 16), img + (int64_t)(zj * KSMAX + j % KS) * BIMG,
+                      2 * (c.tile0 + rt / 16), full0 + 8 * sj);
+        const unsigned char* img =
+            reinterpret_cast<const unsigned char*>(a.coefdig + (int64_t)c.chunk * a.coefdig_stride);
+        bulk_load(su32(sm + L::BST + sj * umma_round16(BIMG / 16) * 16), img + (int64_t)(zj * KSMAX + ks) * BIMG,
                   BIMG, full0 + 8 * sj);
       };
-      int issued = 0, landed = 0, drains = 0, committed = -1;
-      for (; issued < kDist && issued < nsteps; ++issued) issue(issued);
-      for (int st = 0; st < nsteps; ++st) {
-        const int s = st % kStages, bb = st & 1, ks = st % KS;
+      UpdCursor ld, cur;
+      ld.start(a, per_tile);
+      cur.start(a, per_tile);
+      int issued = 0, landed = 0, intervals = 0;
+      int64_t committed = -1;
+      for (; issued < kDist && ld.valid; ++issued, ld.next(a, per_tile)) issue(ld, issued);
+      for (int g = 0; cur.valid; ++g, cur.next(a, per_tile)) {
+        const int s = g % kStages, bb = g & 1, ks = cur.st % KS;
         bool ok = true;
-        // the stage of step st + kDist last served step st - 2
-        if (st >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1));
-        if (ok && issued < nsteps && issued == st + kDist) issue(issued++);
-        if (ok) {
-          ok = mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1));
-          if (ok) landed = st + 1;
+        // the stage of global step g + kDist last served step g - 2
+        if (g >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1));
+        if (ok && ld.valid) {
+          issue(ld, issued++);
+          ld.next(a, per_tile);
         }
-        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((st / kStages) & 1));
-        // a new accumulation interval starts once the previous one was drained
-        if (ok && (ks & 15) == 0 && st > 0) ok = mbar_wait(empty, (uint32_t)(drains++ & 1));
+        if (ok) {
+          ok = mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1));
+          if (ok) landed = g + 1;
+        }
+        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((g / kStages) & 1));
+        if ((ks & 15) == 0) {  // a new accumulation interval: its buffer must be drained
+          const int b = intervals % NACC;
+          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1));
+          ++intervals;
+        }
+        const int buf = (intervals - 1) % NACC;
         if (!ok || umma_timed_out(a.flags)) {
           umma_timeout(ctl, a.flags);
           break;
@@ -678,13 +780,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 #pragma unroll
         for (int t = 1; t <= kOzDigits; ++t) {
           const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
-          umma_f16(tbase + (uint32_t)umma_col(t, NB), da, db, idesc[t - 1], accum);
+          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
         umma_commit(mmad0 + 8 * bb);
-        committed = st;
+        committed = g;
       }
       for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
-      if (committed >= 0) mbar_wait(mmad0 + 8 * (committed & 1), (uint32_t)((committed >> 1) & 1));
+      if (committed >= 0) mbar_wait(mmad0 + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
     }
     __syncwarp();
   } else {
@@ -694,41 +796,50 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     // (w / 4) NB / 2 .. + NB / 2 - 1 of the group
     const int kk = tid & 15, tau = (tid >> 4) & 7, hh = (tid >> 7) & 1;
     double* xs_slot = reinterpret_cast<double*>(sm + L::SRCU) + tid * 8;
-    auto load_src = [&](int j) {
-      const int rt = (j / (NSPL * KS)) * 128, q = (j % KS) * 16 + kk;
-      if (q >= k && q < Kt) {
-        double* d = xs_slot + (j % 3) * 256 * 8;
+    auto load_src = [&](const UpdCursor& c, int j) {
+      if (c.valid) {
+        const int rt = (c.st / per_tile) * 128, q = (c.st % KS) * 16 + kk;
+        if (q >= k && q < Kt) {
+          double* d = xs_slot + (j % 3) * 256 * 8;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int row = rt + 16 * tau + 8 * hh + r;
-          const bool ok = row < si.rows;
-          cp_async8(d + r, src + (si.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+          for (int r = 0; r < 8; ++r) {
+            const int row = rt + 16 * tau + 8 * hh + r;
+            const bool ok = row < c.rows;
+            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+          }
         }
       }
       cp_async_commit();
     };
-    load_src(0);
-    if (nsteps > 1) load_src(1); else cp_async_commit();
+    UpdCursor ahead, cur;
+    ahead.start(a, per_tile);
+    cur.start(a, per_tile);
+    load_src(ahead, 0);
+    ahead.next(a, per_tile);
+    load_src(ahead, 1);
+    ahead.next(a, per_tile);
     constexpr int NH = NB / 2;
     double acc[NH], res[NSPL][NH];
 #pragma unroll
     for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-    for (int st = 0; st < nsteps; ++st) {
-      const int s = st % kStages, bb = st & 1;
-      const int rt = (st / (NSPL * KS)) * 128, ks = st % KS, q = ks * 16 + kk, zs = (st / KS) % NSPL;
-      if (st + 2 < nsteps) load_src(st + 2); else cp_async_commit();
-      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step st
+    int intervals = 0;
+    for (int g = 0; cur.valid; ++g, cur.next(a, per_tile)) {
+      const int s = g % kStages, bb = g & 1;
+      const int rt = (cur.st / per_tile) * 128, ks = cur.st % KS, q = ks * 16 + kk, zs = (cur.st / KS) % NSPL;
+      load_src(ahead, g + 2);
+      ahead.next(a, per_tile);
+      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
       // no warp runs more than two steps ahead of the MMAs
-      if (st >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((st - 2) >> 1) & 1)))
+      if (g >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1)))
         umma_timeout(ctl, a.flags);
       unsigned char* stage = sm + L::STG + s * kStageBytes;
-      const bool writes = q >= k;  // the block's own columns, or zeros past Kt
       // the stage's loads landed (its previous step's MMAs finished before they were issued)
-      if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((st / kStages) & 1))) umma_timeout(ctl, a.flags);
-      if (writes) {
-        unsigned char* dst = stage + (2 * tau + hh) * (2 * kOzDigits * 128) + (kk >> 3) * (kOzDigits * 128) + (kk & 7) * 16;
+      if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
+      if (q >= k) {  // the block's own columns, or zeros past Kt
+        unsigned char* dst =
+            stage + (2 * tau + hh) * (2 * kOzDigits * 128) + (kk >> 3) * (kOzDigits * 128) + (kk & 7) * 16;
         if (q < Kt) {
-          split8_store(xs_slot + (st % 3) * 256 * 8, ctl.Fs[q], dst, 128, a.flags);
+          split8_store(xs_slot + (g % 3) * 256 * 8, a.srcexp[(int64_t)cur.chunk * 32 + (q - k)], dst, 128, a.flags);
         } else {
 #pragma unroll
           for (int t = 0; t < kOzDigits; ++t) *reinterpret_cast<uint4*>(dst + t * 128) = make_uint4(0u, 0u, 0u, 0u);
@@ -739,20 +850,24 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
       const bool last_k = (ks + 1 == KS);
       if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
-        if (!ctl.abort) {
-          const bool ok = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((st >> 1) & 1)));
-          if (!ok) {
+        const int buf = intervals % NACC;
+        ++intervals;
+        // warp-uniform decisions around the warp-collective operations
+        bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
+        if (alive) {
+          alive = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((g >> 1) & 1)));
+          if (!alive) {
             umma_timeout(ctl, a.flags);
           } else {
             tc_fence_after();
-            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
 #pragma unroll
             for (int c4 = 0; c4 < NH / 4; ++c4) umma_drain<NB, 4>(tlane, (warp >> 2) * NH + c4 * 4, acc + c4 * 4);
           }
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(empty);
+        if (lane == 0) mbar_arrive(empty0 + 8 * buf);
         if (last_k) {
 #pragma unroll
           for (int zz = 0; zz < NSPL; ++zz)
@@ -762,19 +877,27 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 #pragma unroll
           for (int j = 0; j < NH; ++j) acc[j] = 0.0;
         }
-        const int r = rt + (warp & 3) * 32 + lane;
-        if (last_k && zs == NSPL - 1 && r < si.rows && !ctl.abort) {
-          const int64_t row = si.row0 + r;
+        if (last_k && zs == NSPL - 1 && alive) {
+          const int r = rt + (warp & 3) * 32 + lane;
+          const bool in = r < cur.rows;
+          const int64_t row = cur.row0 + (in ? r : 0);
 #pragma unroll
           for (int zz = 0; zz < NSPL; ++zz)
 #pragma unroll
             for (int j = 0; j < NH; ++j) {
               const int n = zz * NB + (warp >> 2) * NH + j;
-              const double d = scale_exp(res[zz][j], ctl.Cx[n] - 1022 - 16);
+              const double d = scale_exp(res[zz][j], a.coefexp[(int64_t)cur.chunk * 64 + n] - 1022 - 16);
               if (n < S) {
-                slot[row * S + n] = d;
-                atomicMax(&ctl.Ux[n], bexp(d));
-              } else {
+                if (in) slot[row * S + n] = d;
+                // the column's largest exponent over the slab (NOUT = 1) or chunk (NOUT = 2)
+                const int ex = __reduce_max_sync(0xffffffffu, in ? bexp(d) : 0);
+                if (lane == 0) {
+                  if (NOUT == 2)
+                    atomicMax(&a.colexp[(int64_t)(k + n) * a.p + cur.chunk], ex);
+                  else
+                    atomicMax(&a.srcexp_slab[(int64_t)cur.w * 32 + n], ex);
+                }
+              } else if (in) {
                 a.U[row * a.ldu + (n - S)] = d;
               }
             }
@@ -784,25 +907,30 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   }
   tc_fence_before();
   cta_sync();
-  if (tid < S && !ctl.abort) {
-    if (NOUT == 2)
-      atomicMax(&a.colexp[(int64_t)(k + tid) * a.p + c], ctl.Ux[tid]);
-    else
-      a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = ctl.Ux[tid];
-  }
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(umma_tcols(NB)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols));
   }
 }
 
 bool g_umma_attr = false;
 
+int umma_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  return sms;
+}
+
 template <int S>
 cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   using L = GramLayout<S>;
   const int Kt = a.nb * S + S;
-  dim3 grid(a.nslab, (Kt + 127) / 128, L::NSPL);
+  const int nitems = a.nslab * ((Kt + 127) / 128) * L::NSPL;
+  dim3 grid(nitems < umma_sms() ? nitems : umma_sms());
   const double* src = (pass == 1) ? a.W : a.V + (int64_t)a.nb * a.n * S;
   const int64_t lds = (pass == 1) ? a.ldw : S;
   // the pass block's exponents per slab: from a small pass over W for pass 1,
@@ -815,7 +943,7 @@ cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
 template <int S, int NOUT>
 cudaError_t umma_update_for(const StepArgs& a, int pass, cudaStream_t st) {
   using L = UpdLayout<S, NOUT>;
-  dim3 grid(a.nslab);
+  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
   const double* src = nullptr;
   int64_t lds = 0;
   if (NOUT == 1) {
