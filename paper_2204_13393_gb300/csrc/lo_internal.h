@@ -178,12 +178,17 @@ cudaError_t launch_oz_ypass(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st);
 bool oz_planes_supported(int s);
 // Coefficients of an assembly product as tcgen05 B-operand images (lo_ozaki.cu).
-cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, cudaStream_t st);
+// mode 1: images of k_umma_update; mode 2: the image of k_umma_update0.
+cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, int mode, cudaStream_t st);
 // tcgen05 forms over digit planes (lo_umma.cu): used when a.dig is set and the
 // step has prior blocks (nb >= 1).
 bool umma_enabled(const StepArgs& a);
 cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st);
 cudaError_t launch_umma_update(const StepArgs& a, int nout, int pass, cudaStream_t st);
+// tcgen05 forms of a step without prior blocks (k = 0, s in {8, 16}); no digit planes needed.
+bool umma0_enabled(const StepArgs& a);
+cudaError_t launch_umma_gram0(const StepArgs& a, int pass, cudaStream_t st);
+cudaError_t launch_umma_update0(const StepArgs& a, int nout, int pass, cudaStream_t st);
 // Digit planes of the panel written by stage 2.
 cudaError_t launch_umma_digitize(const StepArgs& a, cudaStream_t st);
 cudaError_t umma_set_attrs();

@@ -843,7 +843,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
   const bool tc = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
   if (tc && (e = oz_set_attrs())) return e;
-  if (a.dig && (e = umma_set_attrs())) return e;
+  if (tc && (e = umma_set_attrs())) return e;
   for (int pass = 1; pass <= maxpass; ++pass) {
     mark(hook, pass == 1 ? kKindGram : kKindRefine, true, st);
     if (tc && !(pass == 1 && mixed)) {

@@ -214,13 +214,21 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
 //   mode 2 (stage 2, NOUT = 2): [-P N^{-1}, Pt - P N^{-1} Nt; N^{-1}, N^{-1} Nt]
 // with (P, N^{-1}) of the last local pass and [Pt; Nt] the new tree column block.
 //
-// UMMA = true writes the coefficients instead as tcgen05 B-operand images for
+// MODE 1 writes the coefficients instead as tcgen05 B-operand images for
 // k_umma_update: per output split z (NB = min(NOUT*S, 16) columns) and 16-row
 // step ks, a K-major no-swizzle tile of R = round16(7 NB) rows x 16 K, row
 // (u - 1) NB + n holding digit u of column z NB + n (rows past 7 NB zero):
 // byte ((row % 8) * 16 + (row / 8) * 256 + (kk % 8) * 2 + (kk / 8) * 128) of
 // image (z * ceil(Kmax / 16) + ks), images R * 32 bytes apart.
-template <int S, int NOUT, bool UMMA>
+//
+// MODE 2 (no prior blocks, Kt = S) writes one image for k_umma_update0 whose
+// K index is (digit t of the block, block column) and whose N index is
+// (digit-sum class j, output column): row j NC + n, column kk = (t - 1) S + q
+// holds digit v_j - t of coefficient (q, n) when that digit exists, where
+// v_j = j + 2 for j < 6 and v = 8 for j = 6 (t in pair group 0) and j = 7 (t
+// in pair group 1); K-major no-swizzle, KK = round16(7 S) columns, byte
+// ((row % 8) * 16 + (row / 8) * (KK / 8) * 128 + (kk % 8) * 2 + (kk / 8) * 128).
+template <int S, int NOUT, int MODE>
 __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
   constexpr int NC = NOUT * S, NT = (NC + 7) / 8;
   if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
@@ -266,7 +274,42 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
   __syncthreads();
   unsigned* dig = a.coefdig + (int64_t)c * a.coefdig_stride;
   const int ksteps = (Kt + 15) / 16;
-  if constexpr (UMMA) {
+  if constexpr (MODE == 2) {
+    constexpr int KK = (7 * S + 15) / 16 * 16, SBO = (KK / 8) * 128, BYTES = NC * SBO;  // 8 NC rows
+    unsigned char* img = reinterpret_cast<unsigned char*>(dig);
+    for (int i = tid; i < BYTES / 16; i += 256) reinterpret_cast<uint4*>(img)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // one item = (block column q, output column n): its 7 digits, placed
+    // wherever digit u = v_j - t of a class j meets digit t of the block
+    for (int it = tid; it < S * NC; it += 256) {
+      const int q = it / NC, n = it - q * NC;
+      unsigned h, l, g;
+      if (oz_split(Cf[q * NC + n], Gs[n], h, l, g)) oz_status(a.flags, LO_ERR_NONFINITE);
+      const unsigned sign = (g >> 16) & 0x8000u;
+#pragma unroll
+      for (int t = 1; t <= kOzDigits; ++t) {
+        const int kk = (t - 1) * S + q;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int v = j < 6 ? j + 2 : 8;
+          const int u = v - t;
+          if (u < 1 || u > kOzDigits) continue;
+          if (j == 6 && !pair_group_has(0, t)) continue;
+          if (j == 7 && !pair_group_has(1, t)) continue;
+          const unsigned byte = (u <= 3) ? ((h >> (8 * (3 - u))) & 0xFFu) : ((l >> (8 * (7 - u))) & 0xFFu);
+          const int row = j * NC + n;
+          *reinterpret_cast<unsigned short*>(img + (row & 7) * 16 + (row >> 3) * SBO + (kk & 7) * 2 + (kk >> 3) * 128) =
+              (unsigned short)(sign | byte);
+        }
+      }
+    }
+    for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
+    if (NOUT == 1)
+      for (int i = tid; i < (a.chunk_slab0[c + 1] - a.chunk_slab0[c]) * 32; i += 256)
+        a.srcexp_slab[(int64_t)a.chunk_slab0[c] * 32 + i] = 0;
+    return;
+  }
+  if constexpr (MODE == 1) {
     constexpr int NB = NC < 16 ? NC : 16, NSPL = NC / NB, R = (7 * NB + 15) / 16 * 16;
     const int KS = (a.Kmax + 15) / 16;
     unsigned char* img = reinterpret_cast<unsigned char*>(dig);
@@ -293,7 +336,7 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
         *reinterpret_cast<uint2*>(base + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
       }
     }
-    if (R > 7 * NB) {  // pad rows
+    if constexpr (R > 7 * NB) {  // pad rows
       for (int it = tid; it < NSPL * ksteps * (R - 7 * NB) * 4; it += 256) {
         const int kq = it & 3, rest = it >> 2;
         const int pr = rest % (R - 7 * NB), zks = rest / (R - 7 * NB), ks = zks % ksteps, z = zks / ksteps;
@@ -501,6 +544,7 @@ __global__ void __launch_bounds__(512, 1) k_oz_update(StepArgs a, const double* 
 template <int S>
 cudaError_t gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   if (umma_enabled(a)) return launch_umma_gram(a, pass, st);
+  if (umma0_enabled(a)) return launch_umma_gram0(a, pass, st);
   constexpr int NT = (S + 7) / 8, MT = 8 / NT, CG = MT * 16;
   const int Kt = a.nb * S + S;
   dim3 grid(a.nslab, (Kt + CG - 1) / CG);
@@ -519,10 +563,14 @@ size_t coef_smem(const StepArgs& a) {
 template <int S>
 cudaError_t ypass_for(const StepArgs& a, int pass, cudaStream_t st) {
   if (umma_enabled(a)) {
-    cudaError_t e = launch_oz_coef_umma(a, 1, pass, st);
+    cudaError_t e = launch_oz_coef_umma(a, 1, pass, 1, st);
     return e ? e : launch_umma_update(a, 1, pass, st);
   }
-  k_oz_coef<S, 1, false><<<a.p, 256, coef_smem<S, 1>(a), st>>>(a, pass);
+  if (umma0_enabled(a)) {
+    cudaError_t e = launch_oz_coef_umma(a, 1, pass, 2, st);
+    return e ? e : launch_umma_update0(a, 1, pass, st);
+  }
+  k_oz_coef<S, 1, 0><<<a.p, 256, coef_smem<S, 1>(a), st>>>(a, pass);
   const double* src = (pass == 2) ? a.W : a.V + (int64_t)a.nb * a.n * S;
   const int64_t lds = (pass == 2) ? a.ldw : S;
   k_oz_update<S, 1><<<a.nslab, 512, sizeof(UpdSmem<S, 1>), st>>>(a, src, lds, pass);
@@ -532,10 +580,14 @@ cudaError_t ypass_for(const StepArgs& a, int pass, cudaStream_t st) {
 template <int S>
 cudaError_t stage2_for(const StepArgs& a, cudaStream_t st) {
   if (umma_enabled(a)) {
-    cudaError_t e = launch_oz_coef_umma(a, 2, 0, st);
+    cudaError_t e = launch_oz_coef_umma(a, 2, 0, 1, st);
     return e ? e : launch_umma_update(a, 2, 0, st);
   }
-  k_oz_coef<S, 2, false><<<a.p, 256, coef_smem<S, 2>(a), st>>>(a, 0);
+  if (umma0_enabled(a)) {
+    cudaError_t e = launch_oz_coef_umma(a, 2, 0, 2, st);
+    return e ? e : launch_umma_update0(a, 2, 0, st);
+  }
+  k_oz_coef<S, 2, 0><<<a.p, 256, coef_smem<S, 2>(a), st>>>(a, 0);
   k_oz_update<S, 2><<<a.nslab, 512, sizeof(UpdSmem<S, 2>), st>>>(a, nullptr, 0, 0);
   return cudaGetLastError();
 }
@@ -552,9 +604,9 @@ cudaError_t oz_set_attrs() {
   const int big = 200 * 1024;
   cudaError_t e;
 #define LO_OZ_ATTR(S)                                                                                  \
-  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
     return e;                                                                                          \
-  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
     return e;                                                                                          \
   if ((e = cudaFuncSetAttribute(k_oz_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, big)))      \
     return e;                                                                                          \
@@ -569,13 +621,17 @@ cudaError_t oz_set_attrs() {
   LO_OZ_ATTR(32)
 #undef LO_OZ_ATTR
 #define LO_OZ_ATTR_UMMA(S)                                                                                 \
-  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) \
     return e;                                                                                              \
-  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_oz_coef<S, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   LO_OZ_ATTR_UMMA(8)
   LO_OZ_ATTR_UMMA(16)
   LO_OZ_ATTR_UMMA(32)
 #undef LO_OZ_ATTR_UMMA
+  if ((e = cudaFuncSetAttribute(k_oz_coef<8, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_oz_coef<8, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_oz_coef<16, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_oz_coef<16, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
 
   g_oz_attr = true;
   return cudaSuccess;
@@ -610,11 +666,26 @@ cudaError_t launch_oz_stage2(const StepArgs& a, cudaStream_t st) {
 #undef CALL
 }
 
-cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, cudaStream_t st) {
+cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, int mode, cudaStream_t st) {
+  if (mode == 2) {
+    switch (a.s * 4 + nout) {
+#define LO_COEF_UMMA0(S, NOUT)                                                    \
+  case S * 4 + NOUT:                                                              \
+    k_oz_coef<S, NOUT, 2><<<a.p, 256, coef_smem<S, NOUT>(a), st>>>(a, pass);     \
+    return cudaGetLastError();
+      LO_COEF_UMMA0(8, 1)
+      LO_COEF_UMMA0(8, 2)
+      LO_COEF_UMMA0(16, 1)
+      LO_COEF_UMMA0(16, 2)
+#undef LO_COEF_UMMA0
+      default:
+        return cudaErrorInvalidValue;
+    }
+  }
   switch (a.s * 4 + nout) {
 #define LO_COEF_UMMA(S, NOUT)                                                                \
   case S * 4 + NOUT:                                                                         \
-    k_oz_coef<S, NOUT, true><<<a.p, 256, coef_smem<S, NOUT>(a), st>>>(a, pass);             \
+    k_oz_coef<S, NOUT, 1><<<a.p, 256, coef_smem<S, NOUT>(a), st>>>(a, pass);                \
     return cudaGetLastError();
     LO_COEF_UMMA(8, 1)
     LO_COEF_UMMA(8, 2)

@@ -45,6 +45,7 @@ namespace lo {
 namespace {
 
 constexpr int kUmmaThreads = 288;     // 8 worker warps + 1 issuer warp
+constexpr int kUmma0Threads = 256;    // the k = 0 kernels
 constexpr int kIssuer = 256;          // lane 0 of warp 8 issues every load and MMA
 constexpr int kStages = 5;            // TMA ring depth
 constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
@@ -913,6 +914,401 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Steps without prior blocks (k = 0, Kt = S), s in {8, 16}: the per-digit
+// forms above would spend a whole 128-row M tile and seven MMAs on S
+// columns.  Here the digit index moves into the MMA dimensions instead, and
+// each slab is staged whole in shared memory (its exponents come from there).
+
+// Gram of the block A over one slab: the stacked tile T (row (t - 1) S + q
+// = digit t of column q, K = 16 rows per step, K-major) is both operands of
+// one MMA per 16 rows: D[(t, q)][(u, n)] = sum_rows d_t(A_q) d_u(A_n), M = 7 S
+// rows padded to 64 / 128, N = 7 S.  The pairs t + u <= 8 are summed per
+// (q, n) into the integer pair sums of the recombination.
+template <int S>
+struct Gram0Layout {
+  static constexpr int M = S == 8 ? 64 : 128, N = 7 * S, TILE = (M / 8) * 256, STEPS = 16;
+  static constexpr int X = 0;                               // 2 slabs x 256 rows x S float64
+  static constexpr int TL = X + 2 * 256 * S * 8;            // 2 slabs x STEPS tiles
+  static constexpr int SV = TL + 2 * STEPS * TILE;          // pair sums: S x 8 x S ints
+  static constexpr int HS = SV + S * 8 * S * 4;             // column exponents: 2 x 32 ints
+  static constexpr int CTL = HS + 2 * 32 * 4;
+  static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
+};
+
+// Slab w's rows of src, float64, into X (rows past the slab zero).
+template <int S>
+__device__ __forceinline__ void stage_slab(double* X, const StepArgs& a, int w, const double* src, int64_t lds) {
+  const SlabInfo si = a.slabs[w];
+  for (int i = threadIdx.x; i < 256 * S; i += kUmma0Threads) {
+    const int r = i / S, c = i - r * S;
+    const bool ok = r < si.rows;
+    cp_async8(X + i, src + (si.row0 + (ok ? r : 0)) * lds + c, ok);
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_gram0(StepArgs a, const double* src, int64_t lds,
+                                                                  int pass) {
+  using L = Gram0Layout<S>;
+  constexpr int M = L::M, N = L::N, TILE = L::TILE;
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  if (umma_timed_out(a.flags)) return;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
+  int* Sv = reinterpret_cast<int*>(sm + L::SV);
+  int* Hs = reinterpret_cast<int*>(sm + L::HS);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t mmad0 = su32(&ctl.mmad[0]);
+  if (tid == 0) {
+    mbar_init(mmad0, 1);
+    mbar_init(mmad0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ctl.abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // pad rows of every tile stay zero; pair sums start at zero
+  for (int i = tid; i < 2 * L::STEPS * (M - N) * 2; i += kUmma0Threads) {
+    const int h = i & 1, rest = i >> 1, r = N + rest % (M - N), tl = rest / (M - N);
+    *reinterpret_cast<uint4*>(sm + L::TL + tl * TILE + (r & 7) * 16 + (r >> 3) * 256 + h * 128) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int i = tid; i < S * 8 * S; i += kUmma0Threads) Sv[i] = 0;
+  int w = blockIdx.x;
+  if (w < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X), a, w, src, lds);
+  cp_async_commit();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = ctl.tslot;
+  const uint32_t idesc = umma_idesc(M, N, 0, 0);
+
+  // recombine and write the partial of slab wp (TMEM buffer b)
+  auto drain = [&](int wp, int j) {
+    const int b = j & 1;
+    const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * b, (uint32_t)((j >> 1) & 1)));
+    if (!ok) umma_timeout(ctl, a.flags);
+    tc_fence_after();
+    const bool alive = __all_sync(0xffffffffu, ctl.abort == 0);  // warp-uniform around the TMEM loads
+    if (warp < 4 && alive) {
+      const int R = (M == 64) ? (lane < 16 ? 16 * warp + lane : -1) : 32 * warp + lane;
+      const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 128);
+      const int t = R >= 0 ? R / S + 1 : 0, q = R >= 0 ? R % S : 0;
+#pragma unroll
+      for (int c8 = 0; c8 < N / 8; ++c8) {
+        uint32_t r8[8];
+        tmem_ld8(tl + (uint32_t)(c8 * 8), r8);
+        tmem_wait_ld();
+        if (R >= 0 && R < N) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int col = c8 * 8 + e, u = col / S + 1, n = col % S, v = t + u;
+            if (v > 8) continue;
+            const int d = __float2int_rn(__uint_as_float(r8[e]) * 0x1p48f);
+            const int slotv = v < 8 ? v - 2 : (pair_group_has(0, t) ? 6 : 7);
+            atomicAdd(&Sv[(q * 8 + slotv) * S + n], d);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    const int* hs = Hs + 32 * (j & 1);
+    for (int i = tid; i < S * S && !ctl.abort; i += kUmma0Threads) {
+      const int q = i / S, n = i - q * S;
+      const int* sv = Sv + q * 8 * S + n;
+      long long rest = (long long)sv[1 * S] * (1LL << 37);
+      rest += (long long)sv[2 * S] * (1LL << 29);
+      rest += (long long)sv[3 * S] * (1LL << 21);
+      rest += (long long)sv[4 * S] * (1LL << 13);
+      rest += (long long)sv[5 * S] * (1LL << 5);
+      rest += (long long)((sv[6 * S] + 4) >> 3) + (long long)((sv[7 * S] + 4) >> 3);
+      const double v = partial_to_double(sv[0], rest);
+      a.part[(int64_t)wp * a.Kmax * S + q * S + n] = scale_exp(v, hs[q] + hs[n] - 2044 - 16);
+    }
+    if (tid < S && !ctl.abort) a.srcexp_slab[(int64_t)wp * 32 + tid] = hs[tid];
+    __syncthreads();
+    for (int i = tid; i < S * 8 * S; i += kUmma0Threads) Sv[i] = 0;
+  };
+
+  int prev = -1;
+  for (int j = 0; w < a.nslab; ++j, w += gridDim.x) {
+    const int b = j & 1;
+    double* X = reinterpret_cast<double*>(sm + L::X) + b * 256 * S;
+    const int wn = w + gridDim.x;
+    if (wn < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X) + (b ^ 1) * 256 * S, a, wn, src, lds);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    if (tid < 32) Hs[32 * b + tid] = 0;
+    __syncthreads();
+    const int rows = a.slabs[w].rows, nsteps = (rows + 15) / 16;
+    // items (step, column, quad of 4 rows): exponents first, then the digits
+    constexpr int ITEMS = L::STEPS * S * 4;
+    int mx = 0;
+    for (int it = tid; it < ITEMS; it += kUmma0Threads) {
+      const int q = it % S, r0 = (it / S) * 4;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) mx = max(mx, bexp(X[(r0 + r) * S + q]));
+      if (it + kUmma0Threads >= ITEMS || (it + kUmma0Threads) % S != q) {
+        atomicMax(&Hs[32 * b + q], mx);
+        mx = 0;
+      }
+    }
+    __syncthreads();
+    unsigned char* tiles = sm + L::TL + b * L::STEPS * TILE;
+    for (int it = tid; it < ITEMS; it += kUmma0Threads) {
+      const int q = it % S, qd = (it / S) & 3, st = it / (4 * S);
+      if (st >= nsteps) continue;
+      const double* x = X + (st * 16 + qd * 4) * S + q;
+      unsigned h[4], l[4], g[4];
+      bool bad = false;
+      const int e = Hs[32 * b + q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) bad |= oz_split(x[r * S], e, h[r], l[r], g[r]);
+      if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
+      unsigned char* tb = tiles + st * TILE + (qd & 1) * 8 + (qd >> 1) * 128;
+#pragma unroll
+      for (int t = 1; t <= kOzDigits; ++t) {
+        const int row = (t - 1) * S + q;
+        const unsigned w0 = oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
+        const unsigned w1 = oz_pack(t, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
+        *reinterpret_cast<uint2*>(tb + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && !ctl.abort && !umma_timed_out(a.flags)) {
+      tc_fence_after();
+      const uint64_t d0 = umma_sdesc(su32(tiles), 128, 256);
+      for (int st = 0; st < nsteps; ++st) {
+        const uint64_t d = d0 + (uint64_t)((st * TILE) >> 4);
+        umma_f16(tbase + (uint32_t)(b * 128), d, d, idesc, st > 0 ? 1u : 0u);
+      }
+      umma_commit(mmad0 + 8 * b);
+    } else if (tid == 0) {
+      umma_timeout(ctl, a.flags);
+    }
+    // the previous slab's accumulators drain while these MMAs run
+    if (prev >= 0) drain(prev, j - 1);
+    prev = w;
+    // the next slab's tiles reuse this buffer set only after these MMAs
+    __syncthreads();
+  }
+  if (prev >= 0) {
+    int jl = 0;
+    for (int ww = blockIdx.x; ww + (int)gridDim.x < a.nslab; ww += gridDim.x) ++jl;
+    drain(prev, jl);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(256));
+  }
+}
+
+// out = A Coef over one slab without prior blocks: K = (digit t, column q)
+// = 7 S values per row (padded to KK), N = (class j, output n) = 8 NC with
+// the coefficient image of k_oz_coef<MODE 2>, M = 128 rows per MMA group of
+// KK / 16 instructions.  D[row][(j, n)] is the pair sum S_v (v = j + 2, or
+// the two pair groups of v = 8) of the recombination, exact since it adds at
+// most 7 S digit products.
+template <int S, int NOUT>
+struct Upd0Layout {
+  static constexpr int NC = NOUT * S, KK = umma_round16(7 * S), NCOL = 8 * NC;
+  static constexpr int SBO = (KK / 8) * 128, ATILE = 16 * SBO, BIMG = NC * SBO;
+  static constexpr int X = 0;                        // 2 slabs x 256 rows x S float64
+  static constexpr int AT = X + 2 * 256 * S * 8;     // 2 row tiles
+  static constexpr int BI = AT + 2 * ATILE;          // the chunk's coefficient image
+  static constexpr int CTL = BI + BIMG;
+  static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
+};
+
+template <int S, int NOUT>
+__global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_update0(StepArgs a, const double* src_fixed,
+                                                                    int64_t lds_fixed, int pass) {
+  using L = Upd0Layout<S, NOUT>;
+  constexpr int NC = L::NC, KK = L::KK, NCOL = L::NCOL, SBO = L::SBO, ATILE = L::ATILE, BIMG = L::BIMG;
+  if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
+  if (umma_timed_out(a.flags)) return;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* src = src_fixed;
+  int64_t lds = lds_fixed;
+  double* slot = a.V;  // nb = 0
+  if (NOUT == 2) {
+    int Lp = 1;
+    for (int t = 2; t <= kMaxPass; ++t)
+      if (a.flags[kFlagPass + t - 1]) Lp = t;
+    src = (Lp == 1) ? a.W : slot;
+    lds = (Lp == 1) ? a.ldw : S;
+  }
+  const uint32_t mmad0 = su32(&ctl.mmad[0]);
+  if (tid == 0) {
+    mbar_init(mmad0, 1);
+    mbar_init(mmad0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ctl.abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if constexpr (KK > 7 * S) {  // K pad columns of both row tiles stay zero
+    for (int i = tid; i < 2 * 128; i += kUmma0Threads) {
+      const int tl = i >> 7, m = i & 127;
+      for (int kk = 7 * S; kk < KK; kk += 4)
+        *reinterpret_cast<uint2*>(sm + L::AT + tl * ATILE + (m & 7) * 16 + (m >> 3) * SBO + (kk & 7) * 2 + (kk >> 3) * 128) =
+            make_uint2(0u, 0u);
+    }
+  }
+  int w = blockIdx.x;
+  if (w < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X), a, w, src, lds);
+  cp_async_commit();
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = ctl.tslot;
+  const uint32_t idesc = umma_idesc(128, NCOL, 0, 0);
+
+  // outputs of row tile g (rows rt .. rt + 127 of slab wp, chunk cp): warp w
+  // drains TMEM lanes 32 (w % 4) .. + 31, output columns of half w / 4
+  struct Tile {
+    int w, rt, rows, chunk;
+    int64_t row0;
+  };
+  auto drain = [&](const Tile& tl, int g) {
+    const int b = g & 1;
+    const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * b, (uint32_t)((g >> 1) & 1)));
+    if (!ok) umma_timeout(ctl, a.flags);
+    tc_fence_after();
+    if (!__all_sync(0xffffffffu, ctl.abort == 0)) return;  // warp-uniform around the TMEM loads
+    const int r = tl.rt + (warp & 3) * 32 + lane;
+    const bool in = r < tl.rows;
+    const int64_t row = tl.row0 + (in ? r : 0);
+    const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 256);
+#pragma unroll
+    for (int c4 = 0; c4 < NC / 8; ++c4) {
+      const int n0 = (warp >> 2) * (NC / 2) + c4 * 4;
+      uint32_t x[8][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) tmem_ld4(tlane + (uint32_t)(j * NC + n0), x[j]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = __float2int_rn(__uint_as_float(x[j][e]) * 0x1p48f);
+        long long rest = (long long)d[1] * (1LL << 37);
+        rest += (long long)d[2] * (1LL << 29);
+        rest += (long long)d[3] * (1LL << 21);
+        rest += (long long)d[4] * (1LL << 13);
+        rest += (long long)d[5] * (1LL << 5);
+        rest += (long long)((d[6] + 4) >> 3) + (long long)((d[7] + 4) >> 3);
+        const int n = n0 + e;
+        const double val = scale_exp(partial_to_double(d[0], rest), a.coefexp[(int64_t)tl.chunk * 64 + n] - 1022 - 16);
+        if (n < S) {
+          if (in) slot[row * S + n] = val;
+          const int ex = __reduce_max_sync(0xffffffffu, in ? bexp(val) : 0);
+          if (lane == 0) {
+            if (NOUT == 2)
+              atomicMax(&a.colexp[(int64_t)n * a.p + tl.chunk], ex);
+            else
+              atomicMax(&a.srcexp_slab[(int64_t)tl.w * 32 + n], ex);
+          }
+        } else if (in) {
+          a.U[row * a.ldu + (n - S)] = val;
+        }
+      }
+    }
+  };
+
+  int g = 0, bchunk = -1;
+  Tile prev{-1, 0, 0, 0, 0};
+  for (int j = 0; w < a.nslab; ++j, w += gridDim.x) {
+    const int b = j & 1;
+    double* X = reinterpret_cast<double*>(sm + L::X) + b * 256 * S;
+    const int wn = w + gridDim.x;
+    if (wn < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X) + (b ^ 1) * 256 * S, a, wn, src, lds);
+    cp_async_commit();
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    const SlabInfo si = a.slabs[w];
+    if (si.chunk != bchunk) {
+      // a new chunk's coefficient image, once the MMAs reading the old one are done
+      if (g > 0) {
+        const bool ok = ctl.abort ? true : mbar_wait(mmad0 + 8 * ((g - 1) & 1), (uint32_t)(((g - 1) >> 1) & 1));
+        if (!ok) umma_timeout(ctl, a.flags);
+      }
+      tc_fence_after();
+      const uint4* gsrc = reinterpret_cast<const uint4*>(a.coefdig + (int64_t)si.chunk * a.coefdig_stride);
+      for (int i = tid; i < BIMG / 16; i += kUmma0Threads) reinterpret_cast<uint4*>(sm + L::BI)[i] = gsrc[i];
+      bchunk = si.chunk;
+    }
+    __syncthreads();
+    const int ntr = (si.rows + 127) / 128;
+    for (int rtile = 0; rtile < ntr; ++rtile, ++g) {
+      const int ab = g & 1;
+      unsigned char* A = sm + L::AT + ab * ATILE;
+      // A buffer ab last served row tile g - 2
+      if (g >= 2) {
+        const bool ok = ctl.abort ? true : mbar_wait(mmad0 + 8 * ab, (uint32_t)(((g - 2) >> 1) & 1));
+        if (!ok) umma_timeout(ctl, a.flags);
+      }
+      // items (row m, 4 columns): the 7 digits of 4 values
+      for (int it = tid; it < 128 * (S / 4); it += kUmma0Threads) {
+        const int m = it / (S / 4), c4 = it - m * (S / 4), rr = rtile * 128 + m;
+        const double* x = X + rr * S + 4 * c4;
+        unsigned h[4], l[4], gg[4];
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          bad |= oz_split(rr < si.rows ? x[e] : 0.0, a.srcexp[(int64_t)si.chunk * 32 + 4 * c4 + e], h[e], l[e], gg[e]);
+        if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
+        unsigned char* base = A + (m & 7) * 16 + (m >> 3) * SBO;
+#pragma unroll
+        for (int t = 1; t <= kOzDigits; ++t) {
+          const int kk = (t - 1) * S + 4 * c4;
+          const unsigned w0 = oz_pack(t, h[0], l[0], h[1], l[1], (gg[0] >> 16) | gg[1]);
+          const unsigned w1 = oz_pack(t, h[2], l[2], h[3], l[3], (gg[2] >> 16) | gg[3]);
+          *reinterpret_cast<uint2*>(base + (kk & 7) * 2 + (kk >> 3) * 128) = make_uint2(w0, w1);
+        }
+      }
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0 && !ctl.abort && !umma_timed_out(a.flags)) {
+        tc_fence_after();
+        const uint64_t da0 = umma_sdesc(su32(A), 128, SBO), db0 = umma_sdesc(su32(sm + L::BI), 128, SBO);
+#pragma unroll
+        for (int kb = 0; kb < KK / 16; ++kb)
+          umma_f16(tbase + (uint32_t)(ab * 256), da0 + (uint64_t)((kb * 256) >> 4), db0 + (uint64_t)((kb * 256) >> 4),
+                   idesc, kb > 0 ? 1u : 0u);
+        umma_commit(mmad0 + 8 * ab);
+      } else if (tid == 0) {
+        umma_timeout(ctl, a.flags);
+      }
+      // the previous row tile's outputs while these MMAs run
+      if (prev.w >= 0) drain(prev, g - 1);
+      prev = Tile{w, rtile * 128, si.rows, si.chunk, si.row0};
+    }
+  }
+  if (prev.w >= 0) drain(prev, g - 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+  }
+}
+
 bool g_umma_attr = false;
 
 int umma_sms() {
@@ -981,6 +1377,22 @@ cudaError_t umma_set_attrs() {
   LO_UMMA_ATTR(16)
   LO_UMMA_ATTR(32)
 #undef LO_UMMA_ATTR
+  if ((e = cudaFuncSetAttribute(k_umma_gram0<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gram0Layout<8>::BYTES)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_umma_gram0<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, Gram0Layout<16>::BYTES)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_umma_update0<8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Upd0Layout<8, 1>::BYTES)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_umma_update0<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Upd0Layout<8, 2>::BYTES)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_umma_update0<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Upd0Layout<16, 1>::BYTES)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_umma_update0<16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Upd0Layout<16, 2>::BYTES)))
+    return e;
   g_umma_attr = true;
   return cudaSuccess;
 }
@@ -1006,6 +1418,48 @@ cudaError_t launch_umma_update(const StepArgs& a, int nout, int pass, cudaStream
   }
 }
 
+bool umma0_enabled(const StepArgs& a) { return a.nb == 0 && (a.s == 8 || a.s == 16); }
+
+template <int S>
+cudaError_t umma_gram0_for(const StepArgs& a, int pass, cudaStream_t st) {
+  const double* src = (pass == 1) ? a.W : a.V;
+  const int64_t lds = (pass == 1) ? a.ldw : S;
+  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
+  k_umma_gram0<S><<<grid, kUmma0Threads, Gram0Layout<S>::BYTES, st>>>(a, src, lds, pass);
+  return cudaGetLastError();
+}
+
+template <int S, int NOUT>
+cudaError_t umma_update0_for(const StepArgs& a, int pass, cudaStream_t st) {
+  const double* src = nullptr;
+  int64_t lds = 0;
+  if (NOUT == 1) {
+    src = (pass == 2) ? a.W : a.V;
+    lds = (pass == 2) ? a.ldw : S;
+  }
+  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
+  k_umma_update0<S, NOUT><<<grid, kUmma0Threads, Upd0Layout<S, NOUT>::BYTES, st>>>(a, src, lds, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_umma_gram0(const StepArgs& a, int pass, cudaStream_t st) {
+  switch (a.s) {
+    case 8: return umma_gram0_for<8>(a, pass, st);
+    case 16: return umma_gram0_for<16>(a, pass, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_umma_update0(const StepArgs& a, int nout, int pass, cudaStream_t st) {
+  switch (a.s * 4 + nout) {
+    case 8 * 4 + 1: return umma_update0_for<8, 1>(a, pass, st);
+    case 8 * 4 + 2: return umma_update0_for<8, 2>(a, pass, st);
+    case 16 * 4 + 1: return umma_update0_for<16, 1>(a, pass, st);
+    case 16 * 4 + 2: return umma_update0_for<16, 2>(a, pass, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_umma_digitize(const StepArgs& a, cudaStream_t st) {
   switch (a.s) {
     case 8: k_umma_digitize<8><<<a.nslab, 256, 0, st>>>(a); break;
@@ -1019,6 +1473,8 @@ cudaError_t launch_umma_digitize(const StepArgs& a, cudaStream_t st) {
 int64_t umma_coef_words(int Kmax, int s) {
   const int64_t KS = (Kmax + 15) / 16;
   int64_t best = 0;
+  if (s == 8 || s == 16)  // the image of the step without prior blocks (k_umma_update0)
+    best = (int64_t)2 * s * (umma_round16(7 * s) / 8) * 128 / 4;
   for (int nout = 1; nout <= 2; ++nout) {
     const int nc = nout * s, nb = nc < 16 ? nc : 16, nspl = nc / nb, rb = umma_round16(7 * nb);
     const int64_t w = (int64_t)nspl * KS * rb * 32 / 4;

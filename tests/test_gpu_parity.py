@@ -462,3 +462,20 @@ def test_saturated_digits_long_slab(planes):
     _, _, Ro = ora.orthogonalize(X, "hh", "hh")
     assert rel(host(R), Ro) <= TOL_REL
     assert O.e_perp(host(U)) <= TOL_PERP
+
+
+@pytest.mark.parametrize("s", [8, 16])
+@pytest.mark.parametrize("kappa", [1e2, 1e8])
+def test_single_block_tensor_core_tsqr(s, kappa):
+    """A basis of one block (no digit planes) as a fresh process would build
+    it first: the k = 0 tensor-core kernels on their own, against the oracle."""
+    n, cr = 40000, 4096
+    A = I.stewart(n, s, kappa, 5300 + s + int(np.log10(kappa)))
+    b = lo().Basis(n, s, 1, cr, precision="fp64_tc")
+    U, _, R = b.orthogonalize(dev(A))
+    Uh, Rh = host(U), host(R)
+    assert O.e_perp(Uh) <= TOL_PERP
+    assert O.residual(A, Uh, Rh) <= TOL_RES
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    _, _, Ro = ora.orthogonalize(A, "hh", "hh")
+    assert rel(Rh, Ro) <= max(TOL_REL, 100 * kappa * np.finfo(float).eps)
