@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "lo_internal.h"
+#include "lo_recombine.h"
 
 namespace lo {
 namespace {
@@ -144,15 +145,6 @@ __device__ __forceinline__ void group_mma(float (&acc)[kGroupPairs][4], const un
     bf[u - 1][0] = w.x; bf[u - 1][1] = w.y;
   }
   for_group_pairs<G>([&](int idx, int t, int u) { mma_f16(acc[idx], af[t - 1], bf[u - 1][0], bf[u - 1][1]); });
-}
-
-// v * 2^X for an integer X in a wide range (two exact power-of-two factors).
-__device__ __forceinline__ double scale2(double v, int X) {
-  if (X < -2044) return 0.0;
-  const int X1 = X / 2, X2 = X - X1;
-  const double f1 = __longlong_as_double((long long)(X1 + 1023) << 52);
-  const double f2 = __longlong_as_double((long long)(X2 + 1023) << 52);
-  return (v * f1) * f2;
 }
 
 // v * 2^X by adding X to the exponent field when the result stays normal

@@ -45,7 +45,7 @@ namespace lo {
 namespace {
 
 constexpr int kUmmaThreads = 288;     // 8 worker warps + 1 issuer warp
-constexpr int kUmma0Threads = 256;    // the k = 0 kernels
+constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (warps 0..7)
 constexpr int kIssuer = 256;          // lane 0 of warp 8 issues every load and MMA
 constexpr int kStages = 5;            // TMA ring depth
 constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
@@ -925,45 +925,95 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 // one MMA per 16 rows: D[(t, q)][(u, n)] = sum_rows d_t(A_q) d_u(A_n), M = 7 S
 // rows padded to 64 / 128, N = 7 S.  The pairs t + u <= 8 are summed per
 // (q, n) into the integer pair sums of the recombination.
+// Shared-memory layout of k_umma_gram0.  A slab's digits (K = its rows, M = N
+// = (digit t, column q)) are 16 steps of 16 rows; a step tile holds the BLK
+// digit rows of one step (7 S used, the rest zero) as 8 x 16-byte core
+// matrices, K-major, 256 bytes apart along M.  At s = 8 one MMA takes two
+// consecutive steps (M = N = 128, the two 64-row halves being the two steps'
+// digits) and only its two diagonal 64 x 64 blocks are kept; at s = 16 one
+// MMA takes one step (M = 128, N = 112).  A slab's 16 steps are written as
+// two halves of 8 steps into two tile buffers, each released by the commit
+// of its own MMAs.
 template <int S>
 struct Gram0Layout {
-  static constexpr int M = S == 8 ? 64 : 128, N = 7 * S, TILE = (M / 8) * 256, STEPS = 16;
-  static constexpr int X = 0;                               // 2 slabs x 256 rows x S float64
-  static constexpr int TL = X + 2 * 256 * S * 8;            // 2 slabs x STEPS tiles
-  static constexpr int SV = TL + 2 * STEPS * TILE;          // pair sums: S x 8 x S ints
-  static constexpr int HS = SV + S * 8 * S * 4;             // column exponents: 2 x 32 ints
-  static constexpr int CTL = HS + 2 * 32 * 4;
+  static constexpr int BLK = S == 8 ? 64 : 128;   // digit rows of one step
+  static constexpr int CH = 128 / BLK;             // steps per MMA
+  static constexpr int N = CH == 2 ? 128 : 7 * S;  // MMA N (a multiple of 16)
+  static constexpr int TILE = BLK * 32;            // bytes of one step tile (16 rows of K)
+  static constexpr int HALF = 8 * TILE;            // 8 steps
+  static constexpr int NX = 3, DIST = 2;           // float64 slab ring, slabs loaded ahead
+  static constexpr int SS = S * S;
+  static constexpr int CS = 28 * SS + 16;          // int stride of a step set in the pair sums
+  static constexpr int X = 0;                      // NX slabs x 256 rows x S float64
+  static constexpr int TL = X + NX * 256 * S * 8;  // 2 half-slab tile buffers
+  static constexpr int P = TL + 2 * HALF;          // pair sums: CH x 28 pairs x S x S ints
+  static constexpr int HW = P + CH * CS * 4;       // per-warp column exponents: 2 x 8 x S ints
+  static constexpr int HS = HW + 2 * 8 * S * 4;    // slab column exponents: 2 x S ints
+  static constexpr int CTL = HS + 2 * S * 4;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
 };
 
-// Slab w's rows of src, float64, into X (rows past the slab zero).
-template <int S>
-__device__ __forceinline__ void stage_slab(double* X, const StepArgs& a, int w, const double* src, int64_t lds) {
-  const SlabInfo si = a.slabs[w];
-  for (int i = threadIdx.x; i < 256 * S; i += kUmma0Threads) {
-    const int r = i / S, c = i - r * S;
-    const bool ok = r < si.rows;
-    cp_async8(X + i, src + (si.row0 + (ok ? r : 0)) * lds + c, ok);
-  }
+// The values of column q, rows r0 .. r0 + R - 1 of both 128-row halves of a
+// slab (rows past the slab zero): each thread stages exactly what it reads.
+template <int S, int R>
+__device__ __forceinline__ void stage_cols(double* X, const SlabInfo& si, const double* src, int64_t lds, int q,
+                                           int r0) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int r = 128 * h + r0 + i;
+      const bool ok = r < si.rows;
+      cp_async8(X + r * S + q, src + (si.row0 + (ok ? r : 0)) * lds + q, ok);
+    }
 }
 
+// CTAs of the k = 0 kernels per SM: two at s = 8 (registers, shared memory
+// and TMEM allow it), so one CTA's phases overlap the other's.
+__host__ __device__ constexpr int umma0_ctas(int s, int nout) { return s == 8 ? 2 : 1; }
+
+// Barrier of the 256 worker threads (warps 0..7); warp 8 issues the MMAs.
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+// Index of digit pair (t, u), t + u <= 8, among the 28 pairs (t-major).
+__host__ __device__ constexpr int pair_index(int t, int u) { return (t - 1) * 8 - (t - 1) * t / 2 + (u - 1); }
+
+// Contiguous slab range of CTA `cta` among `ctas`.
+__device__ __forceinline__ void slab_range(int nslab, int cta, int ctas, int& w0, int& w1) {
+  w0 = (int)((int64_t)nslab * cta / ctas);
+  w1 = (int)((int64_t)nslab * (cta + 1) / ctas);
+}
+
+// Gram partial of every slab of the step without prior blocks (Alg. 7 stage
+// 1, k = 0): part[slab] = X_slab^T X_slab in the digit arithmetic, with the
+// slab's column exponents in srcexp_slab.  Worker warps 0..7 stage the
+// slabs (cp.async, DIST ahead), take the column exponents, split the digits
+// into the step tiles, and drain the accumulators of the previous slab; lane
+// 0 of warp 8 issues the MMAs of each half slab as soon as its tiles are
+// written.
 template <int S>
-__global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_gram0(StepArgs a, const double* src, int64_t lds,
-                                                                  int pass) {
+__global__ void __launch_bounds__(kUmmaThreads, umma0_ctas(S, 1)) k_umma_gram0(StepArgs a, const double* src,
+                                                                                int64_t lds, int pass) {
   using L = Gram0Layout<S>;
-  constexpr int M = L::M, N = L::N, TILE = L::TILE;
+  constexpr int BLK = L::BLK, CH = L::CH, TILE = L::TILE, NX = L::NX, DIST = L::DIST, SS = L::SS, CS = L::CS;
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   UmmaCtl& ctl = *reinterpret_cast<UmmaCtl*>(sm + L::CTL);
-  int* Sv = reinterpret_cast<int*>(sm + L::SV);
+  int* P = reinterpret_cast<int*>(sm + L::P);
+  int* Hw = reinterpret_cast<int*>(sm + L::HW);
   int* Hs = reinterpret_cast<int*>(sm + L::HS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t mmad0 = su32(&ctl.mmad[0]);
+  // ready[h]: half h of a slab's tiles written (8 warp arrivals); full[h]:
+  // the MMAs reading half h are done; mmad[b]: the MMAs of a slab are done
+  const uint32_t ready0 = su32(&ctl.ready[0]), free0 = su32(&ctl.full[0]), mmad0 = su32(&ctl.mmad[0]);
   if (tid == 0) {
-    mbar_init(mmad0, 1);
-    mbar_init(mmad0 + 8, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(ready0 + 8 * h, 8);
+      mbar_init(free0 + 8 * h, 1);
+      mbar_init(mmad0 + 8 * h, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -971,141 +1021,207 @@ __global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_gram0(StepArgs a, con
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // pad rows of every tile stay zero; pair sums start at zero
-  for (int i = tid; i < 2 * L::STEPS * (M - N) * 2; i += kUmma0Threads) {
-    const int h = i & 1, rest = i >> 1, r = N + rest % (M - N), tl = rest / (M - N);
-    *reinterpret_cast<uint4*>(sm + L::TL + tl * TILE + (r & 7) * 16 + (r >> 3) * 256 + h * 128) = make_uint4(0u, 0u, 0u, 0u);
+  // digit rows past 7 S of every step tile stay zero
+  for (int i = tid; i < 2 * 8 * (BLK - 7 * S) * 2; i += kUmmaThreads) {
+    const int kh = i & 1, rest = i >> 1, r = 7 * S + rest % (BLK - 7 * S), tl = rest / (BLK - 7 * S);
+    *reinterpret_cast<uint4*>(sm + L::TL + tl * TILE + (r & 7) * 16 + (r >> 3) * 256 + kh * 128) = make_uint4(0u, 0u, 0u, 0u);
   }
-  for (int i = tid; i < S * 8 * S; i += kUmma0Threads) Sv[i] = 0;
-  int w = blockIdx.x;
-  if (w < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X), a, w, src, lds);
-  cp_async_commit();
+  int w0, w1;
+  slab_range(a.nslab, blockIdx.x, gridDim.x, w0, w1);
+  // split item of a worker: column q, rows r0 .. r0 + R - 1 of each half (R = S / 2)
+  constexpr int R = S / 2;
+  const int q = tid % S, r0 = (tid / S) * R;
+  SlabInfo pf{};  // slab info of the next slab to stage
+  if (tid < kUmma0Threads) {
+    for (int d = 0; d < DIST; ++d) {
+      if (w0 + d < w1)
+        stage_cols<S, R>(reinterpret_cast<double*>(sm + L::X) + d * 256 * S, a.slabs[w0 + d], src, lds, q, r0);
+      cp_async_commit();
+    }
+    if (w0 + DIST < w1) pf = a.slabs[w0 + DIST];
+  }
   fence_async_smem();
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
-  const uint32_t idesc = umma_idesc(M, N, 0, 0);
 
-  // recombine and write the partial of slab wp (TMEM buffer b)
-  auto drain = [&](int wp, int j) {
-    const int b = j & 1;
-    const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * b, (uint32_t)((j >> 1) & 1)));
-    if (!ok) umma_timeout(ctl, a.flags);
-    tc_fence_after();
-    const bool alive = __all_sync(0xffffffffu, ctl.abort == 0);  // warp-uniform around the TMEM loads
-    if (warp < 4 && alive) {
-      const int R = (M == 64) ? (lane < 16 ? 16 * warp + lane : -1) : 32 * warp + lane;
-      const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 128);
-      const int t = R >= 0 ? R / S + 1 : 0, q = R >= 0 ? R % S : 0;
+  if (warp == 8) {
+    // MMA issuer: per slab, half 0 then half 1 as their tiles are ready
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc(128, L::N, 0, 0);
+      const uint64_t d0 = umma_sdesc(su32(sm + L::TL), 128, 256);
+      int rows_next = w0 < w1 ? a.slabs[w0].rows : 0;
+      for (int j = 0, w = w0; w < w1; ++j, ++w) {
+        const int nsteps = (rows_next + 15) / 16;
+        if (w + 1 < w1) rows_next = a.slabs[w + 1].rows;
+        const uint32_t acc_col = (uint32_t)((j & 1) * 128);
+        int issued = 0;
+        for (int h = 0; h < 2; ++h) {
+          const bool ok = ctl.abort ? false : mbar_wait(ready0 + 8 * h, (uint32_t)(j & 1));
+          if (!ok && !ctl.abort) umma_timeout(ctl, a.flags);
+          tc_fence_after();
+          if (!ctl.abort) {
+            for (int st = 8 * h; st < 8 * h + 8 && st < nsteps; st += CH) {
+              const uint64_t d = d0 + (uint64_t)((h * L::HALF + (st - 8 * h) * TILE) >> 4);
+              umma_f16(tbase + acc_col, d, d, idesc, issued > 0 ? 1u : 0u);
+              ++issued;
+            }
+          }
+          umma_commit(free0 + 8 * h);
+        }
+        umma_commit(mmad0 + 8 * (j & 1));
+      }
+    }
+  } else {
+    // ---- workers ----
+    const int qq = warp & 3, hcol = warp >> 2;
+    // drain role: TMEM lanes 32 qq + lane = digit row (step set c, t, q)
+    const int mrow = 32 * qq + lane, dc = mrow / BLK, dr = mrow % BLK, dt = dr / S + 1, dq = dr % S;
+    auto drain = [&](int wp, int jj) {
+      const int b = jj & 1;
+      const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * b, (uint32_t)((jj >> 1) & 1)));
+      if (!ok) umma_timeout(ctl, a.flags);
+      tc_fence_after();
+      if (__all_sync(0xffffffffu, ctl.abort == 0)) {  // warp-uniform around the TMEM loads
+        // columns (u, n) of this warp's half: u = 4 hcol + 1 .. 4 hcol + NU
+        constexpr int NU0 = 4;
+        const uint32_t ta = tbase + ((uint32_t)(32 * qq) << 16) + (uint32_t)(b * 128 + dc * BLK + hcol * NU0 * S);
+        uint32_t r[NU0 * S];
 #pragma unroll
-      for (int c8 = 0; c8 < N / 8; ++c8) {
-        uint32_t r8[8];
-        tmem_ld8(tl + (uint32_t)(c8 * 8), r8);
+        for (int c8 = 0; c8 < NU0 * S / 8; ++c8) {
+          if (hcol == 0 || c8 < 3 * S / 8)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[c8 * 8 + 0]), "=r"(r[c8 * 8 + 1]), "=r"(r[c8 * 8 + 2]), "=r"(r[c8 * 8 + 3]),
+                           "=r"(r[c8 * 8 + 4]), "=r"(r[c8 * 8 + 5]), "=r"(r[c8 * 8 + 6]), "=r"(r[c8 * 8 + 7])
+                         : "r"(ta + (uint32_t)(c8 * 8)));
+        }
         tmem_wait_ld();
-        if (R >= 0 && R < N) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int col = c8 * 8 + e, u = col / S + 1, n = col % S, v = t + u;
-            if (v > 8) continue;
-            const int d = __float2int_rn(__uint_as_float(r8[e]) * 0x1p48f);
-            const int slotv = v < 8 ? v - 2 : (pair_group_has(0, t) ? 6 : 7);
-            atomicAdd(&Sv[(q * 8 + slotv) * S + n], d);
+        for (int ui = 0; ui < NU0; ++ui) {
+          const int u = hcol * NU0 + ui + 1;
+          if (u <= 7 && dt <= 7 && dt + u <= 8) {
+            int* dst = P + dc * CS + pair_index(dt, u) * SS + dq * S;
+#pragma unroll
+            for (int n4 = 0; n4 < S / 4; ++n4) {
+              int4 v;
+              v.x = __float2int_rn(__uint_as_float(r[ui * S + 4 * n4 + 0]) * 0x1p48f);
+              v.y = __float2int_rn(__uint_as_float(r[ui * S + 4 * n4 + 1]) * 0x1p48f);
+              v.z = __float2int_rn(__uint_as_float(r[ui * S + 4 * n4 + 2]) * 0x1p48f);
+              v.w = __float2int_rn(__uint_as_float(r[ui * S + 4 * n4 + 3]) * 0x1p48f);
+              reinterpret_cast<int4*>(dst)[n4] = v;
+            }
           }
         }
       }
-    }
-    tc_fence_before();
-    __syncthreads();
-    const int* hs = Hs + 32 * (j & 1);
-    for (int i = tid; i < S * S && !ctl.abort; i += kUmma0Threads) {
-      const int q = i / S, n = i - q * S;
-      const int* sv = Sv + q * 8 * S + n;
-      long long rest = (long long)sv[1 * S] * (1LL << 37);
-      rest += (long long)sv[2 * S] * (1LL << 29);
-      rest += (long long)sv[3 * S] * (1LL << 21);
-      rest += (long long)sv[4 * S] * (1LL << 13);
-      rest += (long long)sv[5 * S] * (1LL << 5);
-      rest += (long long)((sv[6 * S] + 4) >> 3) + (long long)((sv[7 * S] + 4) >> 3);
-      const double v = partial_to_double(sv[0], rest);
-      a.part[(int64_t)wp * a.Kmax * S + q * S + n] = scale_exp(v, hs[q] + hs[n] - 2044 - 16);
-    }
-    if (tid < S && !ctl.abort) a.srcexp_slab[(int64_t)wp * 32 + tid] = hs[tid];
-    __syncthreads();
-    for (int i = tid; i < S * 8 * S; i += kUmma0Threads) Sv[i] = 0;
-  };
+      tc_fence_before();
+      workers_sync();
+      // pair sums S_v of output (qo, no), one step set per thread, then added
+      const bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
+      if (tid < CH * SS && alive) {
+        const int qn = CH == 2 ? tid >> 1 : tid, c = CH == 2 ? tid & 1 : 0;
+        int sv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sv[i] = 0;
+#pragma unroll
+        for (int t = 1; t <= 7; ++t)
+#pragma unroll
+          for (int u = 1; u + t <= 8; ++u) {
+            const int x = P[c * CS + pair_index(t, u) * SS + qn];
+            sv[t + u < 8 ? t + u - 2 : (pair_group_has(0, t) ? 6 : 7)] += x;
+          }
+        if (CH == 2) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sv[i] += __shfl_xor_sync(0xffffffffu, sv[i], 1);
+        }
+        if (c == 0) {
+          const int qo = qn / S, no = qn % S;
+          long long rest = (long long)sv[1] * (1LL << 37);
+          rest += (long long)sv[2] * (1LL << 29);
+          rest += (long long)sv[3] * (1LL << 21);
+          rest += (long long)sv[4] * (1LL << 13);
+          rest += (long long)sv[5] * (1LL << 5);
+          rest += (long long)((sv[6] + 4) >> 3) + (long long)((sv[7] + 4) >> 3);
+          const int* hs = Hs + S * b;
+          a.part[(int64_t)wp * a.Kmax * S + qo * S + no] = oz_recombine(sv[0], rest, hs[qo] + hs[no] - 2044 - 16);
+        }
+      }
+      if (tid < S && alive) a.srcexp_slab[(int64_t)wp * 32 + tid] = Hs[S * b + tid];
+    };
 
-  int prev = -1;
-  for (int j = 0; w < a.nslab; ++j, w += gridDim.x) {
-    const int b = j & 1;
-    double* X = reinterpret_cast<double*>(sm + L::X) + b * 256 * S;
-    const int wn = w + gridDim.x;
-    if (wn < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X) + (b ^ 1) * 256 * S, a, wn, src, lds);
-    cp_async_commit();
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    if (tid < 32) Hs[32 * b + tid] = 0;
-    __syncthreads();
-    const int rows = a.slabs[w].rows, nsteps = (rows + 15) / 16;
-    // items (step, column, quad of 4 rows): exponents first, then the digits
-    constexpr int ITEMS = L::STEPS * S * 4;
-    int mx = 0;
-    for (int it = tid; it < ITEMS; it += kUmma0Threads) {
-      const int q = it % S, r0 = (it / S) * 4;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) mx = max(mx, bexp(X[(r0 + r) * S + q]));
-      if (it + kUmma0Threads >= ITEMS || (it + kUmma0Threads) % S != q) {
-        atomicMax(&Hs[32 * b + q], mx);
-        mx = 0;
+    for (int j = 0, w = w0; w < w1; ++j, ++w) {
+      const int b = j & 1;
+      asm volatile("cp.async.wait_group %0;" ::"n"(DIST - 1) : "memory");  // own copies of slab j
+      if (w + DIST < w1) {
+        stage_cols<S, R>(reinterpret_cast<double*>(sm + L::X) + ((j + DIST) % NX) * 256 * S, pf, src, lds, q, r0);
+        if (w + DIST + 1 < w1) pf = a.slabs[w + DIST + 1];
       }
-    }
-    __syncthreads();
-    unsigned char* tiles = sm + L::TL + b * L::STEPS * TILE;
-    for (int it = tid; it < ITEMS; it += kUmma0Threads) {
-      const int q = it % S, qd = (it / S) & 3, st = it / (4 * S);
-      if (st >= nsteps) continue;
-      const double* x = X + (st * 16 + qd * 4) * S + q;
-      unsigned h[4], l[4], g[4];
-      bool bad = false;
-      const int e = Hs[32 * b + q];
+      cp_async_commit();
+      const double* X = reinterpret_cast<const double*>(sm + L::X) + (j % NX) * 256 * S;
+      double x[2][R];
+      int mx = 0;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) bad |= oz_split(x[r * S], e, h[r], l[r], g[r]);
-      if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-      unsigned char* tb = tiles + st * TILE + (qd & 1) * 8 + (qd >> 1) * 128;
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) {
-        const int row = (t - 1) * S + q;
-        const unsigned w0 = oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
-        const unsigned w1 = oz_pack(t, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
-        *reinterpret_cast<uint2*>(tb + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
+        for (int i = 0; i < R; ++i) {
+          x[h][i] = X[(128 * h + r0 + i) * S + q];
+          mx = max(mx, bexp(x[h][i]));
+        }
+#pragma unroll
+      for (int o = S; o < 32; o <<= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane < S) Hw[(b * 8 + warp) * S + lane] = mx;
+      workers_sync();
+      int e = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) e = max(e, Hw[(b * 8 + i) * S + q]);
+      if (tid < S) Hs[S * b + tid] = e;
+      // the digits, half by half, each once the MMAs of slab j - 1 that read
+      // its tile buffer are done
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (j > 0 && !ctl.abort) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(free0 + 8 * h, (uint32_t)((j - 1) & 1)));
+          if (!ok) umma_timeout(ctl, a.flags);
+        }
+        unsigned hh[R], ll[R], gg[R];
+        bool bad = false;
+#pragma unroll
+        for (int i = 0; i < R; ++i) bad |= oz_split(x[h][i], e, hh[i], ll[i], gg[i]);
+        if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
+        // rows r0 .. r0 + R - 1: step r0 / 16, K offset r0 % 16
+        unsigned char* tb = sm + L::TL + h * L::HALF + (r0 >> 4) * TILE + ((r0 >> 3) & 1) * 128 + (r0 & 7) * 2;
+#pragma unroll
+        for (int t = 1; t <= kOzDigits; ++t) {
+          const int m = (t - 1) * S + q;
+          unsigned char* dst = tb + (m & 7) * 16 + (m >> 3) * 256;
+          if constexpr (R == 4) {
+            const unsigned wa = oz_pack(t, hh[0], ll[0], hh[1], ll[1], (gg[0] >> 16) | gg[1]);
+            const unsigned wb = oz_pack(t, hh[2], ll[2], hh[3], ll[3], (gg[2] >> 16) | gg[3]);
+            *reinterpret_cast<uint2*>(dst) = make_uint2(wa, wb);
+          } else {
+            uint4 v;
+            v.x = oz_pack(t, hh[0], ll[0], hh[1], ll[1], (gg[0] >> 16) | gg[1]);
+            v.y = oz_pack(t, hh[2], ll[2], hh[3], ll[3], (gg[2] >> 16) | gg[3]);
+            v.z = oz_pack(t, hh[4], ll[4], hh[5], ll[5], (gg[4] >> 16) | gg[5]);
+            v.w = oz_pack(t, hh[6], ll[6], hh[7], ll[7], (gg[6] >> 16) | gg[7]);
+            *reinterpret_cast<uint4*>(dst) = v;
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(ready0 + 8 * h);
       }
+      // the previous slab's accumulators, while these MMAs run
+      if (j > 0) drain(w - 1, j - 1);
     }
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0 && !ctl.abort && !umma_timed_out(a.flags)) {
-      tc_fence_after();
-      const uint64_t d0 = umma_sdesc(su32(tiles), 128, 256);
-      for (int st = 0; st < nsteps; ++st) {
-        const uint64_t d = d0 + (uint64_t)((st * TILE) >> 4);
-        umma_f16(tbase + (uint32_t)(b * 128), d, d, idesc, st > 0 ? 1u : 0u);
-      }
-      umma_commit(mmad0 + 8 * b);
-    } else if (tid == 0) {
-      umma_timeout(ctl, a.flags);
+    if (w1 > w0) {
+      workers_sync();
+      drain(w1 - 1, w1 - w0 - 1);
     }
-    // the previous slab's accumulators drain while these MMAs run
-    if (prev >= 0) drain(prev, j - 1);
-    prev = w;
-    // the next slab's tiles reuse this buffer set only after these MMAs
-    __syncthreads();
-  }
-  if (prev >= 0) {
-    int jl = 0;
-    for (int ww = blockIdx.x; ww + (int)gridDim.x < a.nslab; ww += gridDim.x) ++jl;
-    drain(prev, jl);
   }
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(256));
@@ -1122,18 +1238,44 @@ template <int S, int NOUT>
 struct Upd0Layout {
   static constexpr int NC = NOUT * S, KK = umma_round16(7 * S), NCOL = 8 * NC;
   static constexpr int SBO = (KK / 8) * 128, ATILE = 16 * SBO, BIMG = NC * SBO;
-  static constexpr int X = 0;                        // 2 slabs x 256 rows x S float64
-  static constexpr int AT = X + 2 * 256 * S * 8;     // 2 row tiles
-  static constexpr int BI = AT + 2 * ATILE;          // the chunk's coefficient image
+  static constexpr int TBUF = NCOL <= 128 ? 128 : 256;  // TMEM columns of one half's accumulators
+  static constexpr int NX = 3, DIST = 2;                 // float64 slab ring, slabs loaded ahead
+  static constexpr int X = 0;                            // NX slabs x 256 rows x S float64
+  static constexpr int AT = X + NX * 256 * S * 8;        // A tiles of the two 128-row halves
+  static constexpr int BI = AT + 2 * ATILE;              // the chunk's coefficient image
   static constexpr int CTL = BI + BIMG;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;
 };
 
+// Row `row` of slab si, float64, into X (zero past the slab), by its own thread.
+template <int S>
+__device__ __forceinline__ void stage_row(double* X, const SlabInfo& si, const double* src, int64_t lds, int row,
+                                          bool vec16) {
+  const bool ok = row < si.rows;
+  const double* g = src + (si.row0 + (ok ? row : 0)) * lds;
+  if (vec16) {
+#pragma unroll
+    for (int c = 0; c < S; c += 2) cp_async16(X + row * S + c, g + c, ok);
+  } else {
+#pragma unroll
+    for (int c = 0; c < S; ++c) cp_async8(X + row * S + c, g + c, ok);
+  }
+}
+
+// Assembly products of the step without prior blocks: out = X Coef per slab
+// (NOUT = 1: the pass product into the basis slot; NOUT = 2: the slot and U).
+// Worker thread i owns row i of every slab of its CTA: it stages the row
+// (cp.async, DIST slabs ahead), splits it into the A tile of its 128-row half
+// (K-major digits), and reads its outputs back from TMEM lane i % 128 of the
+// half's accumulators one slab later; no barrier joins the workers.  Lane 0
+// of warp 8 issues the KK / 16 MMAs of each half as its 4 warps finish, with
+// the chunk's coefficient image resident until the chunk changes.
 template <int S, int NOUT>
-__global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_update0(StepArgs a, const double* src_fixed,
-                                                                    int64_t lds_fixed, int pass) {
+__global__ void __launch_bounds__(kUmmaThreads, umma0_ctas(S, NOUT)) k_umma_update0(StepArgs a, const double* src_fixed,
+                                                                                     int64_t lds_fixed, int pass) {
   using L = Upd0Layout<S, NOUT>;
   constexpr int NC = L::NC, KK = L::KK, NCOL = L::NCOL, SBO = L::SBO, ATILE = L::ATILE, BIMG = L::BIMG;
+  constexpr int TBUF = L::TBUF, TCOLS = 2 * TBUF, NX = L::NX, DIST = L::DIST;
   if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
@@ -1150,162 +1292,201 @@ __global__ void __launch_bounds__(kUmma0Threads, 1) k_umma_update0(StepArgs a, c
     src = (Lp == 1) ? a.W : slot;
     lds = (Lp == 1) ? a.ldw : S;
   }
-  const uint32_t mmad0 = su32(&ctl.mmad[0]);
+  // ready[h]: the 4 warps of half h wrote its A tile; mmad[h]: its MMAs are
+  // done; empty[0]: every MMA issued so far is done (before a new image)
+  const uint32_t ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]), cfree = su32(&ctl.empty[0]);
   if (tid == 0) {
-    mbar_init(mmad0, 1);
-    mbar_init(mmad0 + 8, 1);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(ready0 + 8 * h, 4);
+      mbar_init(mmad0 + 8 * h, 1);
+    }
+    mbar_init(cfree, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)), "r"(512));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&ctl.tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if constexpr (KK > 7 * S) {  // K pad columns of both row tiles stay zero
-    for (int i = tid; i < 2 * 128; i += kUmma0Threads) {
+  if constexpr (KK > 7 * S) {  // K pad columns of both A tiles stay zero
+    static_assert(KK - 7 * S == 8, "one 16-byte pad row");
+    for (int i = tid; i < 2 * 128; i += kUmmaThreads) {
       const int tl = i >> 7, m = i & 127;
-      for (int kk = 7 * S; kk < KK; kk += 4)
-        *reinterpret_cast<uint2*>(sm + L::AT + tl * ATILE + (m & 7) * 16 + (m >> 3) * SBO + (kk & 7) * 2 + (kk >> 3) * 128) =
-            make_uint2(0u, 0u);
+      *reinterpret_cast<uint4*>(sm + L::AT + tl * ATILE + (m & 7) * 16 + (m >> 3) * SBO + (7 * S / 8) * 128) =
+          make_uint4(0u, 0u, 0u, 0u);
     }
   }
-  int w = blockIdx.x;
-  if (w < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X), a, w, src, lds);
-  cp_async_commit();
+  int w0, w1;
+  slab_range(a.nslab, blockIdx.x, gridDim.x, w0, w1);
+  const bool vec16 = ((reinterpret_cast<uintptr_t>(src) & 15) == 0) && ((lds & 1) == 0);
+  SlabInfo pf{};  // the next slab to stage
+  if (tid < kUmma0Threads) {
+    for (int d = 0; d < DIST; ++d) {
+      if (w0 + d < w1) stage_row<S>(reinterpret_cast<double*>(sm + L::X) + d * 256 * S, a.slabs[w0 + d], src, lds, tid, vec16);
+      cp_async_commit();
+    }
+    if (w0 + DIST < w1) pf = a.slabs[w0 + DIST];
+  }
   fence_async_smem();
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
-  const uint32_t idesc = umma_idesc(128, NCOL, 0, 0);
 
-  // outputs of row tile g (rows rt .. rt + 127 of slab wp, chunk cp): warp w
-  // drains TMEM lanes 32 (w % 4) .. + 31, output columns of half w / 4
-  struct Tile {
-    int w, rt, rows, chunk;
-    int64_t row0;
-  };
-  auto drain = [&](const Tile& tl, int g) {
-    const int b = g & 1;
-    const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * b, (uint32_t)((g >> 1) & 1)));
-    if (!ok) umma_timeout(ctl, a.flags);
-    tc_fence_after();
-    if (!__all_sync(0xffffffffu, ctl.abort == 0)) return;  // warp-uniform around the TMEM loads
-    const int r = tl.rt + (warp & 3) * 32 + lane;
-    const bool in = r < tl.rows;
-    const int64_t row = tl.row0 + (in ? r : 0);
-    const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 256);
+  if (warp == 8) {
+    // ---- MMA issuer (lane 0; the warp copies coefficient images) ----
+    const uint32_t idesc = umma_idesc(128, NCOL, 0, 0);
+    const uint64_t db0 = umma_sdesc(su32(sm + L::BI), 128, SBO);
+    int chunk = -1;
+    uint32_t nimg = 0;
+    SlabInfo nxt{};
+    if (w0 < w1) nxt = a.slabs[w0];
+    for (int j = 0, w = w0; w < w1; ++j, ++w) {
+      const SlabInfo si = nxt;
+      if (w + 1 < w1) nxt = a.slabs[w + 1];
+      if (si.chunk != chunk) {
+        if (chunk >= 0) {  // the MMAs reading the old image are done
+          if (lane == 0) umma_commit(cfree);
+          __syncwarp();
+          const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(cfree, nimg & 1));
+          if (!ok && lane == 0) umma_timeout(ctl, a.flags);
+          ++nimg;
+        }
+        const uint4* g = reinterpret_cast<const uint4*>(a.coefdig + (int64_t)si.chunk * a.coefdig_stride);
+        for (int i = lane; i < BIMG / 16; i += 32) reinterpret_cast<uint4*>(sm + L::BI)[i] = g[i];
+        fence_async_smem();
+        __syncwarp();
+        chunk = si.chunk;
+      }
+      for (int h = 0; h < 2; ++h) {
+        if (lane == 0) {
+          const bool ok = ctl.abort ? false : mbar_wait(ready0 + 8 * h, (uint32_t)(j & 1));
+          if (!ok && !ctl.abort) umma_timeout(ctl, a.flags);
+          tc_fence_after();
+          if (!ctl.abort && 128 * h < si.rows) {
+            const uint64_t da0 = umma_sdesc(su32(sm + L::AT + h * ATILE), 128, SBO);
 #pragma unroll
-    for (int c4 = 0; c4 < NC / 8; ++c4) {
-      const int n0 = (warp >> 2) * (NC / 2) + c4 * 4;
-      uint32_t x[8][4];
+            for (int kb = 0; kb < KK / 16; ++kb)
+              umma_f16(tbase + (uint32_t)(h * TBUF), da0 + (uint64_t)((kb * 256) >> 4),
+                       db0 + (uint64_t)((kb * 256) >> 4), idesc, kb > 0 ? 1u : 0u);
+          }
+          umma_commit(mmad0 + 8 * h);
+        }
+        __syncwarp();
+      }
+    }
+  } else {
+    // ---- workers: thread tid owns row tid of each slab ----
+    const int h = warp >> 2, m = tid & 127;
+    const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * TBUF);
+    unsigned char* arow = sm + L::AT + h * ATILE + (m & 7) * 16 + (m >> 3) * SBO;
+    int ex[S];            // split exponents of the current chunk's columns
+    int xchunk = -1;
+    // outputs of row tid of slab sd (its accumulators in this half's TMEM)
+    auto drain = [&](const SlabInfo& sd, int wd) {
+      const bool in = tid < sd.rows;
+      const int64_t row = sd.row0 + (in ? tid : 0);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) tmem_ld4(tlane + (uint32_t)(j * NC + n0), x[j]);
-      tmem_wait_ld();
+      for (int g4 = 0; g4 < NC / 4; ++g4) {
+        uint32_t x[8][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        int d[8];
+        for (int jj = 0; jj < 8; ++jj) tmem_ld4(tl + (uint32_t)(jj * NC + 4 * g4), x[jj]);
+        tmem_wait_ld();
+        double val[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) d[j] = __float2int_rn(__uint_as_float(x[j][e]) * 0x1p48f);
-        long long rest = (long long)d[1] * (1LL << 37);
-        rest += (long long)d[2] * (1LL << 29);
-        rest += (long long)d[3] * (1LL << 21);
-        rest += (long long)d[4] * (1LL << 13);
-        rest += (long long)d[5] * (1LL << 5);
-        rest += (long long)((d[6] + 4) >> 3) + (long long)((d[7] + 4) >> 3);
-        const int n = n0 + e;
-        const double val = scale_exp(partial_to_double(d[0], rest), a.coefexp[(int64_t)tl.chunk * 64 + n] - 1022 - 16);
-        if (n < S) {
-          if (in) slot[row * S + n] = val;
-          const int ex = __reduce_max_sync(0xffffffffu, in ? bexp(val) : 0);
-          if (lane == 0) {
-            if (NOUT == 2)
-              atomicMax(&a.colexp[(int64_t)n * a.p + tl.chunk], ex);
-            else
-              atomicMax(&a.srcexp_slab[(int64_t)tl.w * 32 + n], ex);
+        for (int e = 0; e < 4; ++e) {
+          int d[8];
+          // a class sums at most 6 S digit products (< 2^22 at s = 8)
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            d[jj] = S == 8 ? oz_f2i_small(__uint_as_float(x[jj][e])) : __float2int_rn(__uint_as_float(x[jj][e]) * 0x1p48f);
+          // integer recombination, rounded once: float64 arithmetic (a
+          // small fraction of the integer rate here) would bound this loop
+          val[e] = oz_recombine8(d, a.coefexp[(int64_t)sd.chunk * 64 + 4 * g4 + e] - 1022 - 16);
+        }
+        if (4 * g4 < S) {
+          if (in) {
+            double2* o = reinterpret_cast<double2*>(slot + row * S + 4 * g4);
+            o[0] = make_double2(val[0], val[1]);
+            o[1] = make_double2(val[2], val[3]);
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int mx = __reduce_max_sync(0xffffffffu, in ? bexp(val[e]) : 0);
+            if (lane == 0) {
+              if (NOUT == 2)
+                atomicMax(&a.colexp[(int64_t)(4 * g4 + e) * a.p + sd.chunk], mx);
+              else
+                atomicMax(&a.srcexp_slab[(int64_t)wd * 32 + 4 * g4 + e], mx);
+            }
           }
         } else if (in) {
-          a.U[row * a.ldu + (n - S)] = val;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) a.U[row * a.ldu + (4 * g4 + e - S)] = val[e];
         }
       }
-    }
-  };
-
-  int g = 0, bchunk = -1;
-  Tile prev{-1, 0, 0, 0, 0};
-  for (int j = 0; w < a.nslab; ++j, w += gridDim.x) {
-    const int b = j & 1;
-    double* X = reinterpret_cast<double*>(sm + L::X) + b * 256 * S;
-    const int wn = w + gridDim.x;
-    if (wn < a.nslab) stage_slab<S>(reinterpret_cast<double*>(sm + L::X) + (b ^ 1) * 256 * S, a, wn, src, lds);
-    cp_async_commit();
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    const SlabInfo si = a.slabs[w];
-    if (si.chunk != bchunk) {
-      // a new chunk's coefficient image, once the MMAs reading the old one are done
-      if (g > 0) {
-        const bool ok = ctl.abort ? true : mbar_wait(mmad0 + 8 * ((g - 1) & 1), (uint32_t)(((g - 1) >> 1) & 1));
-        if (!ok) umma_timeout(ctl, a.flags);
+    };
+    SlabInfo cur{}, prev{};
+    if (w0 < w1) cur = a.slabs[w0];
+    for (int j = 0, w = w0; w < w1; ++j, ++w) {
+      const SlabInfo si = cur;
+      if (w + 1 < w1) cur = a.slabs[w + 1];
+      asm volatile("cp.async.wait_group %0;" ::"n"(DIST - 1) : "memory");  // own row of slab j
+      if (w + DIST < w1) {
+        stage_row<S>(reinterpret_cast<double*>(sm + L::X) + ((j + DIST) % NX) * 256 * S, pf, src, lds, tid, vec16);
+        if (w + DIST + 1 < w1) pf = a.slabs[w + DIST + 1];
       }
-      tc_fence_after();
-      const uint4* gsrc = reinterpret_cast<const uint4*>(a.coefdig + (int64_t)si.chunk * a.coefdig_stride);
-      for (int i = tid; i < BIMG / 16; i += kUmma0Threads) reinterpret_cast<uint4*>(sm + L::BI)[i] = gsrc[i];
-      bchunk = si.chunk;
-    }
-    __syncthreads();
-    const int ntr = (si.rows + 127) / 128;
-    for (int rtile = 0; rtile < ntr; ++rtile, ++g) {
-      const int ab = g & 1;
-      unsigned char* A = sm + L::AT + ab * ATILE;
-      // A buffer ab last served row tile g - 2
-      if (g >= 2) {
-        const bool ok = ctl.abort ? true : mbar_wait(mmad0 + 8 * ab, (uint32_t)(((g - 2) >> 1) & 1));
-        if (!ok) umma_timeout(ctl, a.flags);
-      }
-      // items (row m, 4 columns): the 7 digits of 4 values
-      for (int it = tid; it < 128 * (S / 4); it += kUmma0Threads) {
-        const int m = it / (S / 4), c4 = it - m * (S / 4), rr = rtile * 128 + m;
-        const double* x = X + rr * S + 4 * c4;
-        unsigned h[4], l[4], gg[4];
-        bool bad = false;
+      cp_async_commit();
+      if (si.chunk != xchunk) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          bad |= oz_split(rr < si.rows ? x[e] : 0.0, a.srcexp[(int64_t)si.chunk * 32 + 4 * c4 + e], h[e], l[e], gg[e]);
-        if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-        unsigned char* base = A + (m & 7) * 16 + (m >> 3) * SBO;
+        for (int c = 0; c < S; ++c) ex[c] = a.srcexp[(int64_t)si.chunk * 32 + c];
+        xchunk = si.chunk;
+      }
+      // the A tile and the accumulators of this half are free once the MMAs
+      // of slab j - 1 are done; its outputs first
+      if (j > 0) {
+        const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * h, (uint32_t)((j - 1) & 1)));
+        if (!ok) umma_timeout(ctl, a.flags);
+        tc_fence_after();
+        if (__all_sync(0xffffffffu, ctl.abort == 0)) drain(prev, w - 1);
+      }
+      const double* xr = reinterpret_cast<const double*>(sm + L::X) + (j % NX) * 256 * S + tid * S;
+      bool bad = false;
+#pragma unroll
+      for (int c8 = 0; c8 < S / 8; ++c8) {
+        unsigned hh[8], ll[8], gg[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bad |= oz_split(xr[8 * c8 + i], ex[8 * c8 + i], hh[i], ll[i], gg[i]);
 #pragma unroll
         for (int t = 1; t <= kOzDigits; ++t) {
-          const int kk = (t - 1) * S + 4 * c4;
-          const unsigned w0 = oz_pack(t, h[0], l[0], h[1], l[1], (gg[0] >> 16) | gg[1]);
-          const unsigned w1 = oz_pack(t, h[2], l[2], h[3], l[3], (gg[2] >> 16) | gg[3]);
-          *reinterpret_cast<uint2*>(base + (kk & 7) * 2 + (kk >> 3) * 128) = make_uint2(w0, w1);
+          uint4 v;
+          v.x = oz_pack(t, hh[0], ll[0], hh[1], ll[1], (gg[0] >> 16) | gg[1]);
+          v.y = oz_pack(t, hh[2], ll[2], hh[3], ll[3], (gg[2] >> 16) | gg[3]);
+          v.z = oz_pack(t, hh[4], ll[4], hh[5], ll[5], (gg[4] >> 16) | gg[5]);
+          v.w = oz_pack(t, hh[6], ll[6], hh[7], ll[7], (gg[6] >> 16) | gg[7]);
+          *reinterpret_cast<uint4*>(arow + ((t - 1) * (S / 8) + c8) * 128) = v;
         }
       }
+      if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
       fence_async_smem();
       tc_fence_before();
-      __syncthreads();
-      if (tid == 0 && !ctl.abort && !umma_timed_out(a.flags)) {
-        tc_fence_after();
-        const uint64_t da0 = umma_sdesc(su32(A), 128, SBO), db0 = umma_sdesc(su32(sm + L::BI), 128, SBO);
-#pragma unroll
-        for (int kb = 0; kb < KK / 16; ++kb)
-          umma_f16(tbase + (uint32_t)(ab * 256), da0 + (uint64_t)((kb * 256) >> 4), db0 + (uint64_t)((kb * 256) >> 4),
-                   idesc, kb > 0 ? 1u : 0u);
-        umma_commit(mmad0 + 8 * ab);
-      } else if (tid == 0) {
-        umma_timeout(ctl, a.flags);
-      }
-      // the previous row tile's outputs while these MMAs run
-      if (prev.w >= 0) drain(prev, g - 1);
-      prev = Tile{w, rtile * 128, si.rows, si.chunk, si.row0};
+      __syncwarp();
+      if (lane == 0) mbar_arrive(ready0 + 8 * h);
+      prev = si;
+    }
+    if (w1 > w0) {
+      const int j = w1 - w0;
+      const bool ok = __all_sync(0xffffffffu, ctl.abort ? true : mbar_wait(mmad0 + 8 * h, (uint32_t)((j - 1) & 1)));
+      if (!ok) umma_timeout(ctl, a.flags);
+      tc_fence_after();
+      if (__all_sync(0xffffffffu, ctl.abort == 0)) drain(prev, w1 - 1);
     }
   }
-  if (prev.w >= 0) drain(prev, g - 1);
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TCOLS));
   }
 }
 
@@ -1424,8 +1605,9 @@ template <int S>
 cudaError_t umma_gram0_for(const StepArgs& a, int pass, cudaStream_t st) {
   const double* src = (pass == 1) ? a.W : a.V;
   const int64_t lds = (pass == 1) ? a.ldw : S;
-  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
-  k_umma_gram0<S><<<grid, kUmma0Threads, Gram0Layout<S>::BYTES, st>>>(a, src, lds, pass);
+  const int ctas = umma_sms() * umma0_ctas(S, 1);
+  dim3 grid(a.nslab < ctas ? a.nslab : ctas);
+  k_umma_gram0<S><<<grid, kUmmaThreads, Gram0Layout<S>::BYTES, st>>>(a, src, lds, pass);
   return cudaGetLastError();
 }
 
@@ -1437,8 +1619,9 @@ cudaError_t umma_update0_for(const StepArgs& a, int pass, cudaStream_t st) {
     src = (pass == 2) ? a.W : a.V;
     lds = (pass == 2) ? a.ldw : S;
   }
-  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
-  k_umma_update0<S, NOUT><<<grid, kUmma0Threads, Upd0Layout<S, NOUT>::BYTES, st>>>(a, src, lds, pass);
+  const int ctas = umma_sms() * umma0_ctas(S, NOUT);
+  dim3 grid(a.nslab < ctas ? a.nslab : ctas);
+  k_umma_update0<S, NOUT><<<grid, kUmmaThreads, Upd0Layout<S, NOUT>::BYTES, st>>>(a, src, lds, pass);
   return cudaGetLastError();
 }
 
