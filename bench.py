@@ -44,7 +44,8 @@ S = 8
 M_RESTART = 30
 CHUNK = 4096
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", f) for f in ("lo_kernels.cu", "lo_ozaki.cu")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", f)
+               for f in ("lo_kernels.cu", "lo_ozaki.cu", "lo_umma.cu", "lo_oz_common.cuh", "lo_recombine.h")]
 # DRAM bytes of one launch of the dominant kernel from one ncu capture (bench.py
 # --case profile: n = 2^20, s = 8, k = 120), with that launch's algorithmic bytes,
 # keyed by (kernel group, precision, sha256 prefix of the kernel sources).  The
@@ -252,12 +253,15 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     events = []
+    # the timed cycles are the profiler window (ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     t0 = time.perf_counter()
     with Clocks(local) as clk:
         for _ in range(args.steps):
             gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events)
         torch.cuda.synchronize()
     wall = time.perf_counter() - t0
+    torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
     launches = lo.launch_count() - launches0
@@ -292,7 +296,9 @@ def run_gpu(args):
     traffic = (round(cap["dram_bytes"] / cap["algorithmic_bytes"] * bsum / launches_dom)
                if cap else None)
     if tc:
-        kernel_name = {"update": "k_oz_update", "gram": "k_oz_gram"}[dom]
+        # s = 8, 16, 32 keep digit planes of the prior panels: tcgen05 kernels
+        kernel_name = ({"update": "k_umma_update", "gram": "k_umma_gram"} if s in (8, 16, 32)
+                       else {"update": "k_oz_update", "gram": "k_oz_gram"})[dom]
         # tensor work: 28 fp16 digit-pair products per float64 product, 2 flops each
         tens_tf = 28 * fsum / t_dom / 1e12
         tens_peak = peaks_bf16()
@@ -463,8 +469,8 @@ def run_reference(args):
 def run_profile_case(args):
     """A single mid-cycle orthogonalization (n = 2^20, s = 8, k = 120 prior
     columns from Gaussian blocks, 4096-row chunks) for ncu captures: the basis
-    (1 GB) is larger than L2.  The last step is the one to capture: it is the
-    16th launch of the stage-2 kernel and the 46th of the Gram kernel."""
+    (1 GB) is larger than L2.  The last step runs between cudaProfilerStart and
+    cudaProfilerStop (ncu --profile-from-start off captures only it)."""
     import torch
 
     from paper_2204_13393_gb300 import inputs as I
@@ -479,7 +485,10 @@ def run_profile_case(args):
     W = torch.from_numpy(I.gaussian(n, s, I.seed_for(9, kb))).to(dev)
     torch.cuda.synchronize()
     b.set_profiling(True)
+    torch.cuda.profiler.start()
     b.orthogonalize(W)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     prof = b.profile_read()
     print(json.dumps({"case": "profile", "precision": args.precision, "n": n, "s": s, "k": kb * s,
                       "chunks": b.num_chunks,
@@ -621,6 +630,18 @@ def run_mixed_case(args):
     print(json.dumps(out), flush=True)
 
 
+def orthonormal_columns(torch, X):
+    """Q of X = QR by CholeskyQR2: two passes of X <- X L^-T with L the
+    Cholesky factor of X^T X (the s x s factor on the host), so only matrix
+    products run on the device.  For a Gaussian X (condition ~1) the result
+    is orthonormal to rounding."""
+    for _ in range(2):
+        G = (X.T @ X).cpu().numpy()
+        Linv_t = np.linalg.inv(np.linalg.cholesky(G)).T
+        X = X @ torch.from_numpy(np.ascontiguousarray(Linv_t)).to(X.device)
+    return X
+
+
 def run_tsqr_case(args):
     """Tall-skinny QR (k = 0 step) at n = 2^24 rows (--tsqr-n): A = U diag(sigma)
     V^T with Haar U, V (QR of Gaussians on the device) and sigma log-spaced from
@@ -628,7 +649,9 @@ def run_tsqr_case(args):
     float64 and float64 on the tensor cores) gets the autotuned chunk size; one
     step is timed with CUDA events (min over --steps repetitions after one
     warm-up).  Algorithmic bytes 32ns: read A twice, write the local panel and
-    U.  Reported with e_perp = |U^T U - I|_F and |A - UR|_F / |A|_F."""
+    U.  Reported with e_perp = |U^T U - I|_F and |A - UR|_F / |A|_F.  The
+    profiled step of each form runs between cudaProfilerStart and
+    cudaProfilerStop (for ncu --profile-from-start off)."""
     import torch
 
     from paper_2204_13393_gb300 import lo
@@ -642,15 +665,15 @@ def run_tsqr_case(args):
     g.manual_seed(2204133930 + 3000)
     for s in [int(x) for x in args.tsqr_s.split(",")]:
         nbytes = 32 * n * s
-        for kappa in (1e2, 1e6, 1e10):
-            Uh, _ = torch.linalg.qr(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
-            Vh, _ = torch.linalg.qr(torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+        for kappa in [float(x) for x in args.tsqr_kappas.split(",")]:
+            Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+            Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
             sig = torch.tensor([kappa ** (-j / max(s - 1.0, 1.0)) for j in range(s)], dtype=torch.float64,
                                device=dev)
             A = (Uh * sig) @ Vh.T
             del Uh
             row = {"s": s, "kappa": kappa}
-            for prec in ("fp64", "fp64_tc"):
+            for prec in args.tsqr_precisions.split(","):
                 cr = args.tsqr_cr or lo.tune_chunk_rows(n, s, 1, precision=prec)
                 b = lo.Basis(n, s, 1, cr, precision=prec, sync=True)
                 U = torch.empty_like(A)
@@ -668,7 +691,10 @@ def run_tsqr_case(args):
                 ms = min(times[1:])
                 b.truncate(0)
                 b.set_profiling(True)
+                torch.cuda.profiler.start()
                 b.orthogonalize(A, U=U)
+                torch.cuda.synchronize()
+                torch.cuda.profiler.stop()
                 prof = {g: round(v[0], 4) for g, v in b.profile_read().items() if v[0] > 0}
                 b.set_profiling(False)
                 eye = torch.eye(s, dtype=torch.float64, device=dev)
@@ -703,6 +729,8 @@ def main():
     ap.add_argument("--tsqr-n", type=int, default=2 ** 24)
     ap.add_argument("--tsqr-s", default="8", help="comma-separated block widths for --case tsqr")
     ap.add_argument("--tsqr-cr", type=int, default=0, help="chunk rows for --case tsqr (0: autotuned)")
+    ap.add_argument("--tsqr-kappas", default="1e2,1e6,1e10", help="condition numbers for --case tsqr")
+    ap.add_argument("--tsqr-precisions", default="fp64,fp64_tc", help="forms for --case tsqr")
     args = ap.parse_args()
     if args.case == "profile":
         run_profile_case(args)

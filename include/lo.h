@@ -102,9 +102,11 @@ typedef enum lo_leaf {
  * once per pass; the tensor cores take each float64 value as 7 exact 8-bit
  * digits aligned to its column's largest exponent.  With digit planes the
  * digits are made once, when the panel is created, and kept beside the
- * float64 values as 8 byte planes (7 digits and a sign), 8 bytes per value:
- * the basis takes twice the memory and the passes stream bytes instead of
+ * float64 values as fp16 digits (7 per value, the sign in each, 14 bytes per
+ * value) in the tensor cores' operand order: the panels take 2.75 times the
+ * memory of float64 alone and the passes stream MMA operands instead of
  * re-splitting float64 values.  Results are bitwise the same either way.
+ * Memory per basis with planes: max_blocks * s * (8 + 14) bytes per row.
  */
 typedef enum lo_digit_planes {
   LO_PLANES_AUTO = 0, /* planes for the tensor-core forms when s is 8, 16 or 32  */

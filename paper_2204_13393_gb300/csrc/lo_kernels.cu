@@ -852,14 +852,17 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       count_launches(pass >= 2 ? 3 : (umma_enabled(a) ? 2 : 1));
     } else if (pass == 1 && gram1_supported(s)) {
       if ((e = mixed ? launch_gram1<float>(a, st) : launch_gram1<double>(a, st))) return e;
+      count_launches(1);
     } else if (pass == 1 && mixed) {
       const int tr = gram_tile_rows(Kt, s, 4);
       const size_t sm = (((size_t)4 * tr * Kt + 15) & ~(size_t)15) + 8 * (size_t)tr * s + 8 * kThreads;
       k_gram<float, float><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
+      count_launches(1);
     } else {
       const int tr = gram_tile_rows(Kt, s, 8);
       const size_t sm = (size_t)8 * tr * Kt + 8 * (size_t)tr * s + 8 * kThreads;
       k_gram<double, double><<<a.nslab, kThreads, sm, st>>>(a, pass, tr);
+      count_launches(1);
     }
     mark(hook, pass == 1 ? kKindGram : kKindRefine, false, st);
     // shifted Cholesky for the float32 first pass: relative shift of the trace
@@ -869,7 +872,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     const int allow_shift = (pass == 1 && !mixed && a.leaf != LO_LEAF_PIP) ? 1 : 0;
     k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift, allow_shift);
     mark(hook, kKindLeaf, false, st);
-    count_launches(2);
+    count_launches(1);
   }
   // reduction
   const int ngroups = (a.p + kTreeGroup - 1) / kTreeGroup;
