@@ -49,6 +49,7 @@ constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (wa
 constexpr int kIssuer = 256;          // lane 0 of warp 8 issues every load and MMA
 constexpr int kStages = 5;            // TMA ring depth
 constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
+constexpr int kBBuf = 4;              // steps the producer warps may run ahead of the MMAs
 constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
 constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
 
@@ -160,9 +161,10 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t (&r)[N]) {
 // Per-CTA control block at the end of dynamic shared memory.
 struct UmmaCtl {
   uint64_t full[kStages];   // loads of a stage landed (the issuer arms them every step)
-  uint64_t ready[kStages];  // the workers wrote their part of a step's operands (8 warp arrivals)
-  uint64_t mmad[2];         // MMAs of a step done (commit), alternating by step parity
-  uint64_t empty[2];        // a TMEM accumulator buffer was drained (8 warp arrivals)
+  uint64_t ready[kStages];  // the producer warps wrote their part of a step's operands
+  uint64_t mmad[kBBuf];     // MMAs of a step done (commit), by step modulo kBBuf
+  uint64_t empty[2];        // a TMEM accumulator buffer was drained (drainer warp arrivals)
+  uint64_t accf[2];         // the last MMAs of an accumulation interval in a buffer are done
   uint32_t tslot;           // TMEM base written by tcgen05.alloc
   int abort;                // a bounded wait gave up: no further TMA or MMA is issued
 };
@@ -319,11 +321,11 @@ struct GramLayout {
   static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
   static constexpr int RB = umma_round16(7 * NB);
   static constexpr int STG = 0;                                 // kStages x [2][16][7][128 B]
-  static constexpr int BBUF = STG + kStages * kStageBytes;      // 2 x RB x 32 B
+  static constexpr int BBUF = STG + kStages * kStageBytes;      // kBBuf x RB x 32 B
   // private cp.async slots (3 steps) of the float64 values a thread splits:
   // the block's own columns of the A tile (2 S units of 8 rows) and the B
   // operand (4 NB units of 4 rows)
-  static constexpr int SRCA = BBUF + 2 * RB * 32;
+  static constexpr int SRCA = BBUF + kBBuf * RB * 32;
   static constexpr int SRCB = SRCA + 3 * 2 * S * 8 * 8;
   static constexpr int CTL = SRCB + 3 * 4 * NB * 4 * 8;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
@@ -362,6 +364,18 @@ struct GramCursor {
   }
 };
 
+// The role of a thread of the persistent k > 0 kernels: warps 0..3 split the
+// pass block into the operands of each step (producers), warps 4..7 read the
+// accumulators of each finished interval back from TMEM (drainers), lane 0
+// of warp 8 issues the loads and MMAs.  Producers run up to kBBuf steps ahead
+// of the MMAs and never wait for a drain; drainers wait on accf, a commit of
+// the interval's last MMAs into that TMEM buffer.
+constexpr int kProducers = 128;
+
+// Whether step st (of nsteps in its item) closes an accumulation interval:
+// exact float32 sums cover 16 steps.
+__device__ __forceinline__ bool interval_end(int st, int nsteps) { return ((st + 1) & 15) == 0 || st + 1 == nsteps; }
+
 template <int S>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass) {
@@ -377,17 +391,18 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   const int gtot = a.M * (S / 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
-  const uint32_t empty0 = su32(&ctl.empty[0]);
+  const uint32_t empty0 = su32(&ctl.empty[0]), accf0 = su32(&ctl.accf[0]);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(full0 + 8 * i, 1);
-      mbar_init(ready0 + 8 * i, 8);
+      mbar_init(ready0 + 8 * i, 4);
     }
-    mbar_init(mmad0, 1);
-    mbar_init(mmad0 + 8, 1);
-    mbar_init(empty0, 8);
-    mbar_init(empty0 + 8, 8);
+    for (int i = 0; i < kBBuf; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(empty0 + 8 * i, 4);
+      mbar_init(accf0 + 8 * i, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -397,7 +412,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if constexpr (RB > 7 * NB) {  // B pad rows stay zero
-    for (int i = tid; i < 2 * (RB - 7 * NB) * 2; i += kUmmaThreads) {
+    for (int i = tid; i < kBBuf * (RB - 7 * NB) * 2; i += kUmmaThreads) {
       const int h = i & 1, rest = i >> 1, r = 7 * NB + rest % (RB - 7 * NB), bb = rest / (RB - 7 * NB);
       *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
           make_uint4(0u, 0u, 0u, 0u);
@@ -441,10 +456,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       int64_t committed = -1;
       for (; issued < kDist && ld.valid; ++issued, ld.next(a, nitems, ngroups)) issue(ld, issued);
       for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-        const int s = g % kStages, bb = g & 1;
+        const int s = g % kStages, bb = g % kBBuf;
         bool ok = true;
         // the stage of global step g + kDist last served step g - 2
-        if (g >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1));
+        if (g >= 2) ok = mbar_wait(mmad0 + 8 * ((g - 2) % kBBuf), (uint32_t)(((g - 2) / kBBuf) & 1));
         if (ok && ld.valid) {
           issue(ld, issued++);
           ld.next(a, nitems, ngroups);
@@ -454,14 +469,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           if (ok) landed = g + 1;
         }
         if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((g / kStages) & 1));
-        int buf = 0;
         if ((cur.st & 15) == 0) {  // a new accumulation interval: its buffer must be drained
-          buf = intervals % NACC;
-          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * buf, (uint32_t)(((intervals / NACC) - 1) & 1));
+          const int b = intervals % NACC;
+          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1));
           ++intervals;
         }
-        buf = (intervals - 1) % NACC;
-        if (!ok || umma_timed_out(a.flags)) {
+        const int buf = (intervals - 1) % NACC;
+        if (!ok || ctl.abort) {
           umma_timeout(ctl, a.flags);
           break;
         }
@@ -474,22 +488,23 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
         umma_commit(mmad0 + 8 * bb);
+        if (interval_end(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
       // what is still in flight completes before the CTA's memory is released
       for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
-      if (committed >= 0) mbar_wait(mmad0 + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
+      if (committed >= 0)
+        mbar_wait(mmad0 + 8 * (int)(committed % kBBuf), (uint32_t)((committed / kBBuf) & 1));
     }
     __syncwarp();
-  } else {
-    // ---- workers (warps 0..7) ------------------------------------------------
+  } else if (warp < 4) {
+    // ---- producers (warps 0..3) -----------------------------------------------
     // threads 0 .. 2S - 1 split the block's own columns into the A tile
     // (column l = tid / 2, rows 8 (tid % 2) .. + 7; only in the group that
-    // holds them); threads 128 .. 128 + 4 NB - 1 split the B operand (column
-    // n, rows 4 q .. 4 q + 3); warp w drains TMEM lanes 32 (w % 4) .. + 31,
-    // columns (w / 4) NB / 2 .. + NB / 2 - 1
+    // holds them); threads 64 .. 64 + 4 NB - 1 split the B operand (column
+    // n, rows 4 q .. 4 q + 3) into B buffer g % kBBuf
     const int al = tid >> 1, ah = tid & 1;
-    const int bi = tid - 128;
+    const int bi = tid - 64;
     const bool b_role = bi >= 0 && bi < 4 * NB;
     const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
     double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (tid < 2 * S ? tid : 0) * 8;
@@ -530,17 +545,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     ahead.next(a, nitems, ngroups);
     load_src(ahead, 1);
     ahead.next(a, nitems, ngroups);
-    double acc[NB / 2];
-#pragma unroll
-    for (int j = 0; j < NB / 2; ++j) acc[j] = 0.0;
-    int intervals = 0;
     for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-      const int s = g % kStages, bb = g & 1;
+      const int s = g % kStages, bb = g % kBBuf;
       load_src(ahead, g + 2);
       ahead.next(a, nitems, ngroups);
       asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
-      // MMAs of step g - 2 done: B buffer bb is free (and no warp runs ahead)
-      if (g >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1)))
+      // MMAs of step g - kBBuf done: B buffer bb is free (and no warp runs further ahead)
+      if (g >= kBBuf && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - kBBuf) / kBBuf) & 1)))
         umma_timeout(ctl, a.flags);
       unsigned char* stage = sm + L::STG + s * kStageBytes;
       if (is_asrc(cur)) {
@@ -569,42 +580,50 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
-      // exact float32 sums cover 16 steps (256 rows): drain the accumulators
-      const bool item_end = cur.st + 1 == cur.nsteps;
-      if (((cur.st + 1) & 15) == 0 || item_end) {
-        const int buf = intervals % NACC;
-        ++intervals;
-        // warp-uniform decisions around the warp-collective TMEM loads
-        bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
-        if (alive) {
-          alive = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((g >> 1) & 1)));
-          if (!alive) {
-            umma_timeout(ctl, a.flags);
-          } else {
-            tc_fence_after();
-            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
+    }
+  } else {
+    // ---- drainers (warps 4..7): TMEM lanes 32 (w % 4) .. + 31 = columns
+    // col0 + m of the item, all NB block columns, once per interval ----------
+    GramCursor cur;
+    cur.start(a, nitems, ngroups);
+    double acc[NB];
 #pragma unroll
-            for (int c4 = 0; c4 < NB / 8; ++c4)
-              umma_drain<NB, 4>(tlane, (warp >> 2) * (NB / 2) + c4 * 4, acc + c4 * 4);
-          }
+    for (int j = 0; j < NB; ++j) acc[j] = 0.0;
+    int intervals = 0;
+    for (; cur.valid; cur.next(a, nitems, ngroups)) {
+      if (!interval_end(cur.st, cur.nsteps)) continue;
+      const int buf = intervals % NACC;
+      const uint32_t use = (uint32_t)(intervals / NACC);
+      ++intervals;
+      // warp-uniform decisions around the warp-collective TMEM loads
+      bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
+      if (alive) {
+        alive = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, use & 1));
+        if (!alive) {
+          umma_timeout(ctl, a.flags);
+        } else {
+          tc_fence_after();
+          const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll
+          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty0 + 8 * buf);
-        if (item_end) {
-          // partial of this slab: column col0 + m, block columns z NB + (w / 4) NB / 2 ..
-          const int m = (warp & 3) * 32 + lane, colm = cur.col0 + m;
-          if (colm < Kt && alive) {
-            const int n0 = cur.z * NB + (warp >> 2) * (NB / 2);
-            const int* hs = a.srcexp_slab + (int64_t)cur.slab * 32;
-            const int F = colm < k ? a.colexp[(int64_t)colm * a.p + cur.chunk] : hs[colm - k];
-            double* out = a.part + (int64_t)cur.slab * a.Kmax * S + (int64_t)colm * S + n0;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+      if (cur.st + 1 == cur.nsteps) {
+        // partial of this slab: column col0 + m, block columns z NB .. z NB + NB - 1
+        const int m = (warp & 3) * 32 + lane, colm = cur.col0 + m;
+        if (colm < Kt && alive) {
+          const int n0 = cur.z * NB;
+          const int* hs = a.srcexp_slab + (int64_t)cur.slab * 32;
+          const int F = colm < k ? a.colexp[(int64_t)colm * a.p + cur.chunk] : hs[colm - k];
+          double* out = a.part + (int64_t)cur.slab * a.Kmax * S + (int64_t)colm * S + n0;
 #pragma unroll
-            for (int j = 0; j < NB / 2; ++j) out[j] = scale_exp(acc[j], F + hs[n0 + j] - 2044 - 16);
-          }
-#pragma unroll
-          for (int j = 0; j < NB / 2; ++j) acc[j] = 0.0;
+          for (int j = 0; j < NB; ++j) out[j] = scale_exp(acc[j], F + hs[n0 + j] - 2044 - 16);
         }
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc[j] = 0.0;
       }
     }
   }
@@ -698,17 +717,18 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   }
   const int KS = (Kt + 15) / 16, KSMAX = (a.Kmax + 15) / 16, per_tile = NSPL * KS;
   const uint32_t full0 = su32(&ctl.full[0]), ready0 = su32(&ctl.ready[0]), mmad0 = su32(&ctl.mmad[0]);
-  const uint32_t empty0 = su32(&ctl.empty[0]);
+  const uint32_t empty0 = su32(&ctl.empty[0]), accf0 = su32(&ctl.accf[0]);
 
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(full0 + 8 * i, 1);
-      mbar_init(ready0 + 8 * i, 8);
+      mbar_init(ready0 + 8 * i, 4);
     }
-    mbar_init(mmad0, 1);
-    mbar_init(mmad0 + 8, 1);
-    mbar_init(empty0, 8);
-    mbar_init(empty0 + 8, 8);
+    for (int i = 0; i < kBBuf; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(empty0 + 8 * i, 4);
+      mbar_init(accf0 + 8 * i, 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -721,6 +741,11 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   cta_sync();
   tc_fence_after();
   const uint32_t tbase = ctl.tslot;
+  // a step closes an accumulation interval: exact float32 sums cover 256 columns
+  auto closes = [&](const UpdCursor& c) {
+    const int ks = c.st % KS;
+    return ((ks + 1) & 15) == 0 || ks + 1 == KS;
+  };
 
   if (warp == 8) {
     // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
@@ -752,10 +777,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       int64_t committed = -1;
       for (; issued < kDist && ld.valid; ++issued, ld.next(a, per_tile)) issue(ld, issued);
       for (int g = 0; cur.valid; ++g, cur.next(a, per_tile)) {
-        const int s = g % kStages, bb = g & 1, ks = cur.st % KS;
+        const int s = g % kStages, ks = cur.st % KS;
         bool ok = true;
         // the stage of global step g + kDist last served step g - 2
-        if (g >= 2) ok = mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1));
+        if (g >= 2) ok = mbar_wait(mmad0 + 8 * ((g - 2) % kBBuf), (uint32_t)(((g - 2) / kBBuf) & 1));
         if (ok && ld.valid) {
           issue(ld, issued++);
           ld.next(a, per_tile);
@@ -771,7 +796,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           ++intervals;
         }
         const int buf = (intervals - 1) % NACC;
-        if (!ok || umma_timed_out(a.flags)) {
+        if (!ok || ctl.abort) {
           umma_timeout(ctl, a.flags);
           break;
         }
@@ -783,30 +808,35 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
-        umma_commit(mmad0 + 8 * bb);
+        umma_commit(mmad0 + 8 * (g % kBBuf));
+        if (closes(cur)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
       for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
-      if (committed >= 0) mbar_wait(mmad0 + 8 * (int)(committed & 1), (uint32_t)((committed >> 1) & 1));
+      if (committed >= 0)
+        mbar_wait(mmad0 + 8 * (int)(committed % kBBuf), (uint32_t)((committed / kBBuf) & 1));
     }
     __syncwarp();
-  } else {
-    // ---- workers (warps 0..7): thread (column kk, 16-row tile tau, half h)
-    // of a step splits the block's own columns into the stage, and warp w
-    // drains TMEM lanes 32 (w % 4) .. + 31 and output columns
-    // (w / 4) NB / 2 .. + NB / 2 - 1 of the group
-    const int kk = tid & 15, tau = (tid >> 4) & 7, hh = (tid >> 7) & 1;
-    double* xs_slot = reinterpret_cast<double*>(sm + L::SRCU) + tid * 8;
+  } else if (warp < 4) {
+    // ---- producers (warps 0..3): thread (column kk, 16-row tile tau) of a
+    // step splits the block's own columns, both 8-row halves, into the stage
+    const int kk = tid & 15, tau = (tid >> 4) & 7;
+    auto xs_slot = [&](int hh, int j) {
+      return reinterpret_cast<double*>(sm + L::SRCU) + (j % 3) * 256 * 8 + (tid + 128 * hh) * 8;
+    };
     auto load_src = [&](const UpdCursor& c, int j) {
       if (c.valid) {
         const int rt = (c.st / per_tile) * 128, q = (c.st % KS) * 16 + kk;
         if (q >= k && q < Kt) {
-          double* d = xs_slot + (j % 3) * 256 * 8;
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int row = rt + 16 * tau + 8 * hh + r;
-            const bool ok = row < c.rows;
-            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+          for (int hh = 0; hh < 2; ++hh) {
+            double* d = xs_slot(hh, j);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+              const int row = rt + 16 * tau + 8 * hh + r;
+              const bool ok = row < c.rows;
+              cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + (q - k), ok);
+            }
           }
         }
       }
@@ -819,74 +849,84 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     ahead.next(a, per_tile);
     load_src(ahead, 1);
     ahead.next(a, per_tile);
-    constexpr int NH = NB / 2;
-    double acc[NH], res[NSPL][NH];
-#pragma unroll
-    for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-    int intervals = 0;
     for (int g = 0; cur.valid; ++g, cur.next(a, per_tile)) {
-      const int s = g % kStages, bb = g & 1;
-      const int rt = (cur.st / per_tile) * 128, ks = cur.st % KS, q = ks * 16 + kk, zs = (cur.st / KS) % NSPL;
+      const int s = g % kStages;
+      const int ks = cur.st % KS, q = ks * 16 + kk;
       load_src(ahead, g + 2);
       ahead.next(a, per_tile);
       asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
-      // no warp runs more than two steps ahead of the MMAs
-      if (g >= 2 && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - 2) >> 1) & 1)))
+      // no warp runs more than kBBuf steps ahead of the MMAs
+      if (g >= kBBuf && !ctl.abort &&
+          !mbar_wait(mmad0 + 8 * (g % kBBuf), (uint32_t)(((g - kBBuf) / kBBuf) & 1)))
         umma_timeout(ctl, a.flags);
-      unsigned char* stage = sm + L::STG + s * kStageBytes;
-      // the stage's loads landed (its previous step's MMAs finished before they were issued)
-      if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
-      if (q >= k) {  // the block's own columns, or zeros past Kt
-        unsigned char* dst =
-            stage + (2 * tau + hh) * (2 * kOzDigits * 128) + (kk >> 3) * (kOzDigits * 128) + (kk & 7) * 16;
-        if (q < Kt) {
-          split8_store(xs_slot + (g % 3) * 256 * 8, a.srcexp[(int64_t)cur.chunk * 32 + (q - k)], dst, 128, a.flags);
-        } else {
+      if (q >= k) {  // the block's own columns, or zeros past Kt, once the stage's loads landed
+        if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
+        unsigned char* stage = sm + L::STG + s * kStageBytes;
 #pragma unroll
-          for (int t = 0; t < kOzDigits; ++t) *reinterpret_cast<uint4*>(dst + t * 128) = make_uint4(0u, 0u, 0u, 0u);
+        for (int hh = 0; hh < 2; ++hh) {
+          unsigned char* dst =
+              stage + (2 * tau + hh) * (2 * kOzDigits * 128) + (kk >> 3) * (kOzDigits * 128) + (kk & 7) * 16;
+          if (q < Kt) {
+            split8_store(xs_slot(hh, g), a.srcexp[(int64_t)cur.chunk * 32 + (q - k)], dst, 128, a.flags);
+          } else {
+#pragma unroll
+            for (int t = 0; t < kOzDigits; ++t) *reinterpret_cast<uint4*>(dst + t * 128) = make_uint4(0u, 0u, 0u, 0u);
+          }
         }
       }
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
-      const bool last_k = (ks + 1 == KS);
-      if (((ks + 1) & 15) == 0 || last_k) {  // exact float32 sums cover <= 256 columns
-        const int buf = intervals % NACC;
-        ++intervals;
-        // warp-uniform decisions around the warp-collective operations
-        bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
-        if (alive) {
-          alive = __all_sync(0xffffffffu, mbar_wait(mmad0 + 8 * bb, (uint32_t)((g >> 1) & 1)));
-          if (!alive) {
-            umma_timeout(ctl, a.flags);
-          } else {
-            tc_fence_after();
-            const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
+    }
+  } else {
+    // ---- drainers (warps 4..7): TMEM lanes 32 (w % 4) .. + 31 = rows of the
+    // tile, all NB output columns of the group, once per interval; the tile
+    // is written after the last group -------------------------------------
+    UpdCursor cur;
+    cur.start(a, per_tile);
+    double acc[NB], res[NSPL][NB];
 #pragma unroll
-            for (int c4 = 0; c4 < NH / 4; ++c4) umma_drain<NB, 4>(tlane, (warp >> 2) * NH + c4 * 4, acc + c4 * 4);
-          }
+    for (int j = 0; j < NB; ++j) acc[j] = 0.0;
+    int intervals = 0;
+    for (; cur.valid; cur.next(a, per_tile)) {
+      if (!closes(cur)) continue;
+      const int rt = (cur.st / per_tile) * 128, ks = cur.st % KS, zs = (cur.st / KS) % NSPL;
+      const int buf = intervals % NACC;
+      const uint32_t use = (uint32_t)(intervals / NACC);
+      ++intervals;
+      // warp-uniform decisions around the warp-collective operations
+      bool alive = __all_sync(0xffffffffu, ctl.abort == 0);
+      if (alive) {
+        alive = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * buf, use & 1));
+        if (!alive) {
+          umma_timeout(ctl, a.flags);
+        } else {
+          tc_fence_after();
+          const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
+#pragma unroll
+          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4);
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty0 + 8 * buf);
-        if (last_k) {
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+      if (ks + 1 == KS) {
 #pragma unroll
-          for (int zz = 0; zz < NSPL; ++zz)
-            if (zz == zs)
+        for (int zz = 0; zz < NSPL; ++zz)
+          if (zz == zs)
 #pragma unroll
-              for (int j = 0; j < NH; ++j) res[zz][j] = acc[j];
+            for (int j = 0; j < NB; ++j) res[zz][j] = acc[j];
 #pragma unroll
-          for (int j = 0; j < NH; ++j) acc[j] = 0.0;
-        }
-        if (last_k && zs == NSPL - 1 && alive) {
+        for (int j = 0; j < NB; ++j) acc[j] = 0.0;
+        if (zs == NSPL - 1 && alive) {
           const int r = rt + (warp & 3) * 32 + lane;
           const bool in = r < cur.rows;
           const int64_t row = cur.row0 + (in ? r : 0);
 #pragma unroll
           for (int zz = 0; zz < NSPL; ++zz)
 #pragma unroll
-            for (int j = 0; j < NH; ++j) {
-              const int n = zz * NB + (warp >> 2) * NH + j;
+            for (int j = 0; j < NB; ++j) {
+              const int n = zz * NB + j;
               const double d = scale_exp(res[zz][j], a.coefexp[(int64_t)cur.chunk * 64 + n] - 1022 - 16);
               if (n < S) {
                 if (in) slot[row * S + n] = d;
