@@ -235,7 +235,8 @@ def run_gpu(args):
     lo.library()
     n, s, m = NX * NY, S, M_RESTART
     stream = torch.cuda.current_stream()
-    basis = lo.Basis(n, s, m + 1, CHUNK, sync=False, stream=stream, precision=args.precision)
+    chunk = args.chunk_rows or lo.tune_chunk_rows(n, s, m + 1, precision=args.precision, stream=stream)
+    basis = lo.Basis(n, s, m + 1, chunk, sync=False, stream=stream, precision=args.precision)
     p = basis.num_chunks
     B = torch.from_numpy(I.uniform(n, s, I.seed_for(2, rank))).to(dev)
     Hbuf = [torch.empty(((j + 1) * s, s), dtype=torch.float64, device=dev) for j in range(m)]
@@ -323,7 +324,7 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
-        e2e = run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, args.precision)
+        e2e = run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, args.precision, chunk)
         cpu = cpu_baseline(args.cpu_budget) if world == 1 or rank == 0 else None
         clocks = clk.summary()
         out = {
@@ -333,7 +334,8 @@ def run_gpu(args):
             "config": {"workload": "block-GMRes restart cycle, 2D 5-point Laplacian 1024x1024 (n=1048576), "
                                    "s=8 RHS U(-1,1), m=30: 31 orthogonalizations (k=0..240) + apply_Q; "
                                    "stencil and host least-squares untimed",
-                       "n": n, "s": s, "restart_blocks": m, "chunk_rows": CHUNK, "chunks": p,
+                       "n": n, "s": s, "restart_blocks": m, "chunk_rows": chunk,
+                       "chunk_rows_from": "fixed" if args.chunk_rows else "lo_tune_chunk_rows (measured)", "chunks": p,
                        "precision": args.precision, "leaf": "pip2", "reduction": "auto",
                        "arithmetic": ("float64-accurate products on fp16 tensor cores (exact 8-bit digit "
                                       "splitting, exact float32 sums, integer recombination); float64 "
@@ -357,7 +359,7 @@ def run_gpu(args):
     return out
 
 
-def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, basis_precision):
+def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, basis_precision, chunk):
     """The same cycle's orthogonalizations through the public API with pinned
     host buffers: each call copies W in, U/H/R out and waits (wall clock)."""
     rec = []
@@ -369,7 +371,7 @@ def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, basis_precision):
     Uh = torch.empty((n, s), dtype=torch.float64).pin_memory()
     Hh = torch.empty(((m + 1) * s, s), dtype=torch.float64).pin_memory()
     Rh = torch.empty((s, s), dtype=torch.float64).pin_memory()
-    hb = lo.Basis(n, s, m + 1, CHUNK, sync=True, stream=stream, precision=basis_precision)
+    hb = lo.Basis(n, s, m + 1, chunk, sync=True, stream=stream, precision=basis_precision)
     torch.cuda.synchronize()
     t = 0.0
     h2d = d2h = 0
@@ -642,6 +644,68 @@ def orthonormal_columns(torch, X):
     return X
 
 
+def run_step_case(args):
+    """The small block-Arnoldi step (n = 4096, s = 4, 8 prior blocks built by
+    orthogonalizing seeded N(0,1) blocks, 512-row chunks, new block N(0,1)):
+    launch-bound, so one step is captured once in a CUDA graph on the basis
+    stream and replayed 1000 times; reported as the median replay time (CUDA
+    events) and steps/s, with e_perp of the 9-block basis and the H, R of the
+    replays against an eager step."""
+    import torch
+
+    from paper_2204_13393_gb300 import inputs as I
+    from paper_2204_13393_gb300 import lo
+
+    n, s, kb, cr = 4096, 4, 8, 512
+    dev = torch.device("cuda", 0)
+    lo.library()
+    out = {"case": "step", "n": n, "s": s, "k": kb * s, "chunk_rows": cr, "results": {}}
+    for prec in args.step_precisions.split(","):
+        st = torch.cuda.Stream()
+        b = lo.Basis(n, s, kb + 1, cr, sync=False, stream=st, precision=prec)
+        with torch.cuda.stream(st):
+            for j in range(kb):
+                b.orthogonalize(torch.from_numpy(I.gaussian(n, s, I.seed_for(1, j))).to(dev))
+            W = torch.from_numpy(I.gaussian(n, s, I.seed_for(1, kb))).to(dev)
+            U = torch.empty(n, s, dtype=torch.float64, device=dev)
+            H = torch.empty(kb * s, s, dtype=torch.float64, device=dev)
+            R = torch.empty(s, s, dtype=torch.float64, device=dev)
+            l0 = lo.launch_count()
+            b.orthogonalize(W, U=U, H=H, R=R)       # eager step (also the warm-up)
+            launches = lo.launch_count() - l0
+        st.synchronize()
+        H0, R0 = H.clone(), R.clone()
+        b.truncate(kb)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            b.orthogonalize(W, U=U, H=H, R=R)   # the basis holds 9 blocks; each replay rewrites the 9th
+        times = []
+        with torch.cuda.stream(st):
+            for _ in range(20):
+                g.replay()
+            for _ in range(1000):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                g.replay()
+                e1.record(st)
+                times.append((e0, e1))
+        st.synchronize()
+        us = sorted(e0.elapsed_time(e1) * 1e3 for e0, e1 in times)
+        med = us[len(us) // 2]
+        Q = b.apply_Q(torch.eye((kb + 1) * s, dtype=torch.float64, device=dev))
+        st.synchronize()
+        eperp = float(torch.linalg.norm(Q.T @ Q - torch.eye((kb + 1) * s, dtype=torch.float64, device=dev)))
+        nbytes = orth_bytes(n, s, kb * s, n // cr)
+        out["results"][prec] = {
+            "us_median": round(med, 2), "us_p10": round(us[len(us) // 10], 2), "us_p90": round(us[9 * len(us) // 10], 2),
+            "steps_per_s": round(1e6 / med, 1), "gbs": round(nbytes / (med * 1e-6) / 1e9, 2),
+            "e_perp": eperp, "H_replay_vs_eager": float((H - H0).abs().max()),
+            "R_replay_vs_eager": float((R - R0).abs().max()), "launches_per_step": launches}
+        b.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_tsqr_case(args):
     """Tall-skinny QR (k = 0 step) at n = 2^24 rows (--tsqr-n): A = U diag(sigma)
     V^T with Haar U, V (QR of Gaussians on the device) and sigma log-spaced from
@@ -658,12 +722,11 @@ def run_tsqr_case(args):
 
     dev = torch.device("cuda", 0)
     lo.library()
-    n = args.tsqr_n
     hbm, _src = peaks()
-    out = {"case": "tsqr", "n": n, "results": []}
+    out = {"case": "tsqr", "n": args.tsqr_n, "results": []}
     g = torch.Generator(device=dev)
     g.manual_seed(2204133930 + 3000)
-    for s in [int(x) for x in args.tsqr_s.split(",")]:
+    for n, s in [(int(a), int(b)) for a in args.tsqr_n.split(",") for b in args.tsqr_s.split(",")]:
         nbytes = 32 * n * s
         for kappa in [float(x) for x in args.tsqr_kappas.split(",")]:
             Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
@@ -672,7 +735,7 @@ def run_tsqr_case(args):
                                device=dev)
             A = (Uh * sig) @ Vh.T
             del Uh
-            row = {"s": s, "kappa": kappa}
+            row = {"n": n, "s": s, "kappa": kappa}
             for prec in args.tsqr_precisions.split(","):
                 cr = args.tsqr_cr or lo.tune_chunk_rows(n, s, 1, precision=prec)
                 b = lo.Basis(n, s, 1, cr, precision=prec, sync=True)
@@ -721,12 +784,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for the CPU baseline")
     ap.add_argument("--precision", default="fp64_tc", choices=["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"],
                     help="fp64_tc (default): float64-accurate products on the tensor cores; fp64: native float64")
-    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed", "tsqr"],
+    ap.add_argument("--case", default="cycle", choices=["cycle", "profile", "batched", "mixed", "tsqr", "step"],
                     help="profile: one mid-cycle step for ncu captures; batched: 64 uneven instances; "
                          "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480; "
-                         "tsqr: k = 0 steps at n = 2^24")
+                         "tsqr: k = 0 steps at n = 2^24; step: the small step (n = 4096, s = 4, k = 32), "
+                         "graph-replayed")
     ap.add_argument("--mixed-n", type=int, default=2 ** 24)
-    ap.add_argument("--tsqr-n", type=int, default=2 ** 24)
+    ap.add_argument("--step-precisions", default="fp64,fp64_tc", help="forms for --case step")
+    ap.add_argument("--chunk-rows", type=int, default=CHUNK,
+                    help="chunk rows of the cycle's basis (0: lo_tune_chunk_rows, measured on this GPU)")
+    ap.add_argument("--tsqr-n", default=str(2 ** 24), help="comma-separated row counts for --case tsqr")
     ap.add_argument("--tsqr-s", default="8", help="comma-separated block widths for --case tsqr")
     ap.add_argument("--tsqr-cr", type=int, default=0, help="chunk rows for --case tsqr (0: autotuned)")
     ap.add_argument("--tsqr-kappas", default="1e2,1e6,1e10", help="condition numbers for --case tsqr")
@@ -743,6 +810,9 @@ def main():
         return
     if args.case == "tsqr":
         run_tsqr_case(args)
+        return
+    if args.case == "step":
+        run_step_case(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -74,11 +74,16 @@ typedef enum lo_precision {
                            /* products run as fp16 mma with exact float32        */
                            /* accumulation, and are recombined in 64-bit         */
                            /* integers.  Small factors stay float64.  Requires   */
-                           /* s in {1, 2, 4, 8, 16, 32}; values below 2^-1022    */
-                           /* (subnormals) count as zero.                        */
+                           /* s in {1, 2, 4, 8, 16, 32} (any s <= 4 when         */
+                           /* max_blocks = 1); values below 2^-1022              */
+                           /* (subnormals) count as zero.  A one-block basis     */
+                           /* (max_blocks = 1) with s <= 4 runs the native       */
+                           /* float64 kernels (its products are too narrow for   */
+                           /* the tensor cores to pay)                           */
   LO_PREC_MIXED_TC = 3     /* mixed form on the tensor-core path: the first Gram */
                            /* pass in float32 (shifted float64 Cholesky), every  */
                            /* further pass and the assembly as LO_PREC_FP64_TC   */
+                           /* (max_blocks = 1, s <= 4: as LO_PREC_MIXED_FP32)    */
 } lo_precision;
 
 /* Local sub-algorithm (the "local subalgorithm" of Alg. 9). */

@@ -315,6 +315,16 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
       o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1)
     return LO_ERR_INVALID_ARG;
+  // A one-block basis (tall-skinny QR) of at most kNativeMaxS columns runs
+  // the native float64 kernels in the tensor-core forms too: with no prior
+  // columns its products (s / 4 flop per streamed byte) are too narrow for a
+  // 128-row MMA tile to pay (measured at s = 1, 2, 4, n = 2^12 .. 2^22: native
+  // float64 1.0 - 2.2x faster).  With prior blocks the tensor-core form wins
+  // (n = 4096, s = 4, k = 32: 2.2x) and is kept.
+  if (s <= lo::kNativeMaxS && max_blocks == 1) {
+    if (o.precision == LO_PREC_FP64_TC) o.precision = LO_PREC_FP64;
+    if (o.precision == LO_PREC_MIXED_TC) o.precision = LO_PREC_MIXED_FP32;
+  }
   const bool tc = (o.precision == LO_PREC_FP64_TC || o.precision == LO_PREC_MIXED_TC);
   if (tc && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
   if (o.refine_tol <= 0) o.refine_tol = 1e-13;

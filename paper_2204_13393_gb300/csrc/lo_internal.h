@@ -197,6 +197,9 @@ cudaError_t umma_make_maps(uint8_t* dig, int s, int panels, int64_t dtiles, Umma
 // uint32 words of one chunk's coefficient images (both assembly products).
 int64_t umma_coef_words(int Kmax, int s);
 bool oz_supported(int s);
+// Widest block of a one-block basis that the tensor-core forms leave to the
+// native float64 kernels.
+constexpr int kNativeMaxS = 4;
 cudaError_t oz_set_attrs();
 
 cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,

@@ -152,7 +152,7 @@ __device__ __forceinline__ void group_mma(float (&acc)[kGroupPairs][4], const un
 __device__ __forceinline__ double scale_exp(double v, int X) {
   const long long b = __double_as_longlong(v);
   const int e = (int)((b >> 52) & 0x7FF);
-  if (v == 0.0) return 0.0;
+  if ((b << 1) == 0) return 0.0;  // +-0 (an integer test: float64 compares run at the float64 rate)
   if (e + X >= 1 && e + X <= 2046 && e != 0) return __longlong_as_double(b + ((long long)X << 52));
   return scale2(v, X);
 }

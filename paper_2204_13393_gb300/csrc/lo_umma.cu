@@ -208,9 +208,10 @@ struct PairSums {
 
 // Read the pair accumulators of NW consecutive output columns (starting at
 // column n0 of every pair block) for this thread's TMEM lane and add their
-// recombined values to acc[0 .. NW).
+// recombined values to acc[0 .. NW) (or set them: the first interval of an
+// output, which saves a float64 add).
 template <int NB, int NW>
-__device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc) {
+__device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, bool first) {
   PairSums ps[NW];
 #pragma unroll
   for (int j = 0; j < NW; ++j) ps[j].clear();
@@ -226,7 +227,10 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc) 
       for (int j = 0; j < NW; ++j) ps[j].add(t, u, __uint_as_float(r[u - 1][j]));
   }
 #pragma unroll
-  for (int j = 0; j < NW; ++j) acc[j] += ps[j].value();
+  for (int j = 0; j < NW; ++j) {
+    const double v = ps[j].value();
+    acc[j] = first ? v : acc[j] + v;
+  }
 }
 
 // Expand 16 digit bytes d (rows rho = 0..15 of one column) with their sign
@@ -605,7 +609,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           tc_fence_after();
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4);
+          const bool first = cur.st < 16;  // the item's first interval
+#pragma unroll
+          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
         }
       }
       tc_fence_before();
@@ -904,7 +910,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           tc_fence_after();
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4);
+          const bool first = ks < 16;  // the output group's first interval
+#pragma unroll
+          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
         }
       }
       tc_fence_before();

@@ -479,3 +479,29 @@ def test_single_block_tensor_core_tsqr(s, kappa):
     ora = O.LocallyOrthogonalBasis(n, s, cr)
     _, _, Ro = ora.orthogonalize(A, "hh", "hh")
     assert rel(Rh, Ro) <= max(TOL_REL, 100 * kappa * np.finfo(float).eps)
+
+
+@pytest.mark.parametrize("s", [3, 4])
+def test_narrow_one_block_basis_runs_native(s):
+    """A one-block tensor-core basis of at most 4 columns runs the native
+    float64 kernels (any s <= 4, s = 3 included): its QR matches the oracle and
+    is bit for bit the native form's; with prior blocks the tensor-core form
+    keeps its own width rule (s = 3 is unsupported there)."""
+    n, cr = 50000, 4096
+    A = I.stewart(n, s, 1e6, 7100 + s)
+    outs = {}
+    for prec in ("fp64", "fp64_tc"):
+        b = lo().Basis(n, s, 1, cr, precision=prec)
+        U, _, R = b.orthogonalize(dev(A))
+        outs[prec] = (host(U), host(R))
+    (Uf, Rf), (Ut, Rt) = outs["fp64"], outs["fp64_tc"]
+    assert np.array_equal(Uf, Ut) and np.array_equal(Rf, Rt)
+    assert O.e_perp(Ut) <= TOL_PERP
+    assert O.residual(A, Ut, Rt) <= TOL_RES
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    _, _, Ro = ora.orthogonalize(A, "hh", "hh")
+    assert rel(Rt, Ro) <= max(TOL_REL, 100 * 1e6 * np.finfo(float).eps)
+    if s == 3:
+        with pytest.raises(lo().LoError) as e:
+            lo().Basis(n, s, 2, cr, precision="fp64_tc")
+        assert "UNSUPPORTED" in str(e.value)
