@@ -671,7 +671,11 @@ def run_step_case(args):
             H = torch.empty(kb * s, s, dtype=torch.float64, device=dev)
             R = torch.empty(s, s, dtype=torch.float64, device=dev)
             l0 = lo.launch_count()
+            st.synchronize()
+            torch.cuda.profiler.start()              # the eager step is the profiler window
             b.orthogonalize(W, U=U, H=H, R=R)       # eager step (also the warm-up)
+            st.synchronize()
+            torch.cuda.profiler.stop()
             launches = lo.launch_count() - l0
         st.synchronize()
         H0, R0 = H.clone(), R.clone()
