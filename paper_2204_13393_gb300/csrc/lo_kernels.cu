@@ -344,6 +344,103 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
   }
 }
 
+// Stage-1 Gram of a step without prior blocks (k = 0) for narrow blocks
+// (S <= 4), every pass: the partial A_i^T A_i of each 256-row slab, with A_i
+// = W_i in pass 1 and, from pass 2 on, the iterate Y = A_prev N_last^{-1}
+// (Alg. 8, U_1; no projection at k = 0) formed on the fly and written into
+// the new local panel.  Four lanes share a slab, 64 rows each, with the S x S
+// products in registers; the four partials are added by two shuffle levels
+// in a fixed order.  Per row that is S^2 float64 multiply-adds (plus S(S+1)/2
+// for the iterate) and no row-group reduction: the float64 pipe, not a
+// serial sum, bounds the narrow widths.
+template <int S>
+__global__ void __launch_bounds__(128) k_gram_narrow(StepArgs a, int pass) {
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = gid >> 2, q = gid & 3;  // slab, quarter
+  const bool valid = w < a.nslab;
+  SlabInfo si{};
+  if (valid) si = a.slabs[w];
+  double acc[S][S];
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int l = 0; l < S; ++l) acc[i][l] = 0.0;
+  const int r0 = 64 * q, r1 = valid ? min(si.rows, r0 + 64) : 0;
+  if (pass == 1) {
+    const double* src = a.W + (si.row0 + r0) * a.ldw;
+#pragma unroll 4
+    for (int r = r0; r < r1; ++r, src += a.ldw) {
+      double x[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) x[l] = __ldg(src + l);
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int l = i; l < S; ++l) acc[i][l] = fma(x[i], x[l], acc[i][l]);
+    }
+  } else {
+    const double* src = (pass == 2) ? a.W : a.V;
+    const int64_t lds = (pass == 2) ? a.ldw : S;
+    double* slot = a.V;  // nb = 0
+    double ninv[S][S];
+    if (valid) {
+      const double* Ninv = chunk_small(a, si.chunk) + SmallLayout::make(a.Kmax, S).Ninv_last;
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+#pragma unroll
+        for (int l = 0; l < S; ++l) ninv[j][l] = Ninv[j * S + l];
+    }
+    for (int r = r0; r < r1; ++r) {
+      const int64_t row = si.row0 + r;
+      double x[S], y[S];
+#pragma unroll
+      for (int l = 0; l < S; ++l) x[l] = src[row * lds + l];
+#pragma unroll
+      for (int l = 0; l < S; ++l) {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j <= l; ++j) v = fma(x[j], ninv[j][l], v);
+        y[l] = v;
+      }
+#pragma unroll
+      for (int l = 0; l < S; ++l) slot[row * S + l] = y[l];
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+#pragma unroll
+        for (int l = i; l < S; ++l) acc[i][l] = fma(y[i], y[l], acc[i][l]);
+    }
+  }
+  // the four quarters of a slab: (q0 + q1) + (q2 + q3)
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int l = i; l < S; ++l) {
+      acc[i][l] += __shfl_xor_sync(0xffffffffu, acc[i][l], 1);
+      acc[i][l] += __shfl_xor_sync(0xffffffffu, acc[i][l], 2);
+    }
+  if (valid && q == 0) {
+    double* out = a.part + (int64_t)w * a.Kmax * S;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int l = 0; l < S; ++l) out[i * S + l] = (l >= i) ? acc[i][l] : acc[l][i];
+  }
+}
+
+cudaError_t launch_gram_narrow(const StepArgs& a, int pass, cudaStream_t st) {
+  if (a.slab_rows > 256) return cudaErrorInvalidValue;  // four lanes x 64 rows per slab
+  const int blocks = (int)(((int64_t)a.nslab * 4 + 127) / 128);
+  switch (a.s) {
+    case 1: k_gram_narrow<1><<<blocks, 128, 0, st>>>(a, pass); break;
+    case 2: k_gram_narrow<2><<<blocks, 128, 0, st>>>(a, pass); break;
+    case 3: k_gram_narrow<3><<<blocks, 128, 0, st>>>(a, pass); break;
+    case 4: k_gram_narrow<4><<<blocks, 128, 0, st>>>(a, pass); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <typename Acc>
 cudaError_t launch_gram1(const StepArgs& a, cudaStream_t st) {
   const size_t sm = sizeof(double) * kThreads * 32;
@@ -689,6 +786,57 @@ __global__ void __launch_bounds__(kThreads) k_update(StepArgs a, int tile_rows) 
   }
 }
 
+// Stage 2 of a step without prior blocks for narrow blocks (S <= 4): per row
+// u = A_last N_last^{-1} (new local panel) and out = u Nt_i (caller's U),
+// one thread per row (coalesced rows of S values), the two triangular S x S
+// factors of the row's chunk in registers.
+template <int S>
+__global__ void __launch_bounds__(256) k_update_narrow(StepArgs a) {
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int r = threadIdx.x;
+  if (r >= si.rows) return;
+  const int L = passes_run(a);
+  double* slot = a.V;  // nb = 0
+  const double* src = (L == 1) ? a.W : slot;
+  const int64_t lds = (L == 1) ? a.ldw : S;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, S);
+  const double* smallc = a.small + (int64_t)si.chunk * SL.stride;
+  const double* Ninv = smallc + SL.Ninv_last;
+  const double* Nt = a.T + (int64_t)si.chunk * a.tstride + tblock_offset(0, S);
+  const int64_t row = si.row0 + r;
+  double x[S], u[S];
+#pragma unroll
+  for (int l = 0; l < S; ++l) x[l] = src[row * lds + l];
+#pragma unroll
+  for (int l = 0; l < S; ++l) {
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j <= l; ++j) v = fma(x[j], __ldg(Ninv + j * S + l), v);
+    u[l] = v;
+  }
+#pragma unroll
+  for (int l = 0; l < S; ++l) slot[row * S + l] = u[l];
+#pragma unroll
+  for (int l = 0; l < S; ++l) {
+    double o = 0.0;
+#pragma unroll
+    for (int j = 0; j <= l; ++j) o = fma(u[j], __ldg(Nt + j * S + l), o);
+    a.U[row * a.ldu + l] = o;
+  }
+}
+
+cudaError_t launch_update_narrow(const StepArgs& a, cudaStream_t st) {
+  if (a.slab_rows > 256) return cudaErrorInvalidValue;  // one thread per row of a slab
+  switch (a.s) {
+    case 1: k_update_narrow<1><<<a.nslab, 256, 0, st>>>(a); break;
+    case 2: k_update_narrow<2><<<a.nslab, 256, 0, st>>>(a); break;
+    case 3: k_update_narrow<3><<<a.nslab, 256, 0, st>>>(a); break;
+    case 4: k_update_narrow<4><<<a.nslab, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // apply_Q: Z_i = T_i C (k x m) per chunk, then Y_i = Q_i Z_i.
 __global__ void __launch_bounds__(kThreads) k_apply_z(StepArgs a, const double* C, int m,
@@ -850,6 +998,9 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       if (pass >= 2 && (e = launch_oz_ypass(a, pass, st))) return e;
       if ((e = launch_oz_gram(a, pass, st))) return e;
       count_launches(pass >= 2 ? 3 : (umma_enabled(a) ? 2 : 1));
+    } else if (a.nb == 0 && s <= 4 && !(pass == 1 && mixed)) {
+      if ((e = launch_gram_narrow(a, pass, st))) return e;
+      count_launches(1);
     } else if (pass == 1 && gram1_supported(s)) {
       if ((e = mixed ? launch_gram1<float>(a, st) : launch_gram1<double>(a, st))) return e;
       count_launches(1);
@@ -895,6 +1046,9 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       if ((e = launch_umma_digitize(a, st))) return e;
       count_launches(1);
     }
+  } else if (a.nb == 0 && s <= 4) {
+    if ((e = launch_update_narrow(a, st))) return e;
+    count_launches(1);
   } else {
     const int tu = update_tile_rows(k, s);
     k_update<<<a.nslab, kThreads, (size_t)8 * tu * (k + 2 * s), st>>>(a, tu);
