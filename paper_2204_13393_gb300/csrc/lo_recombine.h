@@ -205,6 +205,34 @@ LO_HD double oz_recombine8(const int (&d)[8], int X) {
   return scale2(oz_from_bits(sign | ((uint64_t)e << 52) | frac), X);
 }
 
+// The float64 of a nonzero integer m 2^e2 (|m| < 2^53) built from its bits.
+LO_HD double oz_exact_double(long long m, int e2) {
+  if (m == 0) return 0.0;
+  const uint64_t sign = m < 0 ? (1ull << 63) : 0ull;
+  const uint64_t a = m < 0 ? (uint64_t)0 - (uint64_t)m : (uint64_t)m;
+  const int p = 63 - oz_clz64(a);  // leading bit, <= 52
+  return oz_from_bits(sign | ((uint64_t)(1023 + p + e2) << 52) | ((a << (52 - p)) & ((1ull << 52) - 1)));
+}
+
+// oz_recombine8 with one float64 addition: T = A1 2^37 + lo with |A1| < 2^31
+// and |lo| < 2^53, both exact as float64 (built from their bits), so their
+// rounded sum is RN(T) -- the same single rounding, bit for bit.
+LO_HD double oz_recombine8_add(const int (&d)[8], int X) {
+  const int a1 = d[0] * 256 + d[1], a2 = d[2] * 256 + d[3], a3 = d[4] * 256 + d[5];
+  const long long lo = (long long)a2 * (1ll << 21) + (long long)a3 * 32 + ((d[6] + 4) >> 3) + ((d[7] + 4) >> 3);
+  const double v = oz_exact_double(a1, 37) + oz_exact_double(lo, 0);  // RN(T), T 2^0
+  uint64_t b;
+#ifdef __CUDA_ARCH__
+  b = (uint64_t)__double_as_longlong(v);
+#else
+  std::memcpy(&b, &v, sizeof b);
+#endif
+  if ((b << 1) == 0) return 0.0;
+  const int e = (int)((b >> 52) & 0x7FF), E = e + X - 45;
+  if (E >= 1 && E <= 2046) return oz_from_bits(b + ((uint64_t)(int64_t)(X - 45) << 52));
+  return scale2(oz_from_bits(b - (45ull << 52)), X);  // T 2^-45 (normal: e >= 1023), as the others scale it
+}
+
 // d of a float32 x = d 2^-48 with d an integer, |d| < 2^22: one add of the
 // constant 1.5 2^-25 puts d + 1.5 2^23 in the significand exactly.
 LO_HD int oz_f2i_small(float x) {

@@ -1448,9 +1448,10 @@ __global__ void __launch_bounds__(kUmmaThreads, umma0_ctas(S, NOUT)) k_umma_upda
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj)
             d[jj] = S == 8 ? oz_f2i_small(__uint_as_float(x[jj][e])) : __float2int_rn(__uint_as_float(x[jj][e]) * 0x1p48f);
-          // integer recombination, rounded once: float64 arithmetic (a
-          // small fraction of the integer rate here) would bound this loop
-          val[e] = oz_recombine8(d, a.coefexp[(int64_t)sd.chunk * 64 + 4 * g4 + e] - 1022 - 16);
+          // recombination rounded once: the two exact halves of the integer
+          // sum built from their bits and added in one float64 operation
+          // (|class sum| <= 6 S digit products < 2^23 - 2^16 at s <= 16)
+          val[e] = oz_recombine8_add(d, a.coefexp[(int64_t)sd.chunk * 64 + 4 * g4 + e] - 1022 - 16);
         }
         if (4 * g4 < S) {
           if (in) {

@@ -4,7 +4,8 @@
 //   oz_recombine_exact: v = the exact s2 + rest 2^-45 rounded once
 //                       (a 128-bit integer converted to double),
 //   oz_recombine8:      oz_recombine_exact of the 8 class sums, rest formed
-//                       from them as its definition states,
+//                       from them as its definition states (and
+//                       oz_recombine8_add, the same with one float64 add),
 // each then scaled by 2^X (an exponent shift when the result stays normal,
 // else (v * 2^X1) * 2^X2); oz_f2i_small: the integer d of d 2^-48, all d
 // in [-2^22, 2^22).  Random inputs over all magnitudes plus constructed ties,
@@ -137,6 +138,12 @@ int main() {
     const double a = lo::oz_recombine8(d, X), b = reference_exact(d[0], rest, X);
     if (bits(a) != bits(b)) {
       if (bad < 10) std::printf("mismatch (8) d0=%d d1=%d X=%d: %a vs %a\n", d[0], d[1], X, a, b);
+      ++bad;
+    }
+    ++cases;
+    const double c = lo::oz_recombine8_add(d, X);
+    if (bits(c) != bits(b)) {
+      if (bad < 10) std::printf("mismatch (8 add) d0=%d d1=%d X=%d: %a vs %a\n", d[0], d[1], X, c, b);
       ++bad;
     }
   }
