@@ -574,8 +574,8 @@ def run_batched_case(args):
 def run_mixed_case(args):
     """Mixed-precision workload: n = 2^24 rows (--mixed-n), s = 16, 30 prior
     blocks (480 columns, Gaussian, built untimed), new block a Stewart-type
-    matrix U diag(sigma) V^T with kappa in {1e2, 1e4, 1e6} (Haar factors from
-    torch.linalg.qr on the device).  Each step is timed with CUDA events for
+    matrix U diag(sigma) V^T with kappa in {1e2, 1e4, 1e6} (orthonormal factors
+    by CholeskyQR2 of Gaussians).  Each step is timed with CUDA events for
     the float64 tensor-core form and the mixed tensor-core form; the step's
     orthogonality is sqrt(|U^T U - I|^2 + 2 |Q^T U|^2), with Q^T U measured by
     one more projection of U (the H output of a PQR step of U)."""
@@ -586,15 +586,18 @@ def run_mixed_case(args):
     dev = torch.device("cuda", 0)
     lo.library()
     n, s, kb = args.mixed_n, 16, 30
-    cr = 8192
-    out = {"case": "mixed", "n": n, "s": s, "k": kb * s, "chunk_rows": cr, "results": []}
+    # chunk rows: measured by the tuner for the float64 form (the reduction's
+    # float64 work grows with the number of chunks), or --mixed-cr
+    cr = args.mixed_cr or lo.tune_chunk_rows(n, s, kb + 2, precision="fp64_tc")
+    out = {"case": "mixed", "n": n, "s": s, "k": kb * s, "chunk_rows": cr,
+           "chunk_rows_from": "option" if args.mixed_cr else "lo_tune_chunk_rows (measured)", "results": []}
     g = torch.Generator(device=dev)
     g.manual_seed(2204133930 + 4000)
     prior = [torch.randn(n, s, dtype=torch.float64, device=dev, generator=g) for _ in range(kb)]
     nbytes = orth_bytes(n, s, kb * s, max(1, n // cr))
     for kappa in (1e2, 1e4, 1e6):
-        Uh, _ = torch.linalg.qr(torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
-        Vh, _ = torch.linalg.qr(torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+        Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+        Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
         sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device=dev)
         W = (Uh * sig) @ Vh.T
         # the block also has components along the basis, like a Krylov block
@@ -616,6 +619,11 @@ def run_mixed_case(args):
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
             passes = b.last_step_info()
+            b.truncate(kb)
+            b.set_profiling(True)
+            U, _, R = b.orthogonalize(W)
+            prof = {gname: round(v[0], 3) for gname, v in b.profile_read().items() if v[0] > 0}
+            b.set_profiling(False)
             UtU = U.T @ U
             b.truncate(kb)
             _, QtU, _ = b.orthogonalize(U.clone())   # H = Q^T U against the kb prior blocks
@@ -624,7 +632,7 @@ def run_mixed_case(args):
             eperp = float(torch.sqrt(torch.linalg.norm(UtU - eye) ** 2 + 2 * torch.linalg.norm(qtu) ** 2))
             ms = min(times[1:]) if len(times) > 1 else times[0]
             row[prec] = {"ms": round(ms, 3), "gbs": round(nbytes / ms / 1e6, 1), "e_perp": eperp,
-                         "passes": passes[0], "tree_iterations": passes[1]}
+                         "passes": passes[0], "tree_iterations": passes[1], "kernel_ms": prof}
             b.close()
             del U, R
         row["speedup_mixed_vs_fp64"] = round(row["fp64_tc"]["ms"] / row["mixed_tc"]["ms"], 3)
@@ -794,6 +802,7 @@ def main():
                          "tsqr: k = 0 steps at n = 2^24; step: the small step (n = 4096, s = 4, k = 32), "
                          "graph-replayed")
     ap.add_argument("--mixed-n", type=int, default=2 ** 24)
+    ap.add_argument("--mixed-cr", type=int, default=0, help="chunk rows for --case mixed (0: lo_tune_chunk_rows)")
     ap.add_argument("--step-precisions", default="fp64,fp64_tc", help="forms for --case step")
     ap.add_argument("--chunk-rows", type=int, default=CHUNK,
                     help="chunk rows of the cycle's basis (0: lo_tune_chunk_rows, measured on this GPU)")
