@@ -51,7 +51,13 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", f)
 # keyed by (kernel group, precision, sha256 prefix of the kernel sources).  The
 # reported traffic scales the measured ratio to the average launch of the cycle;
 # a source change invalidates the entry (traffic: null).
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+    #     --clock-control none --profile-from-start off -k regex:k_umma_update -s 2 -c 1
+    #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 659.8 us)
+    ("update", "fp64_tc", "e8707ef1579b69d9"): {"dram_bytes": 1955182592 + 129818624,
+                                                "algorithmic_bytes": 1210056704},
+}
 
 
 def peaks():

@@ -27,7 +27,7 @@ __device__ __forceinline__ int bexp(double x) {
 // returns true for Inf/NaN.
 __device__ __forceinline__ bool oz_split(double x, int emax, unsigned& yhi, unsigned& ylo, unsigned& sgn) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned hi = (unsigned)(b >> 32);
   const int e = (int)((hi >> 20) & 0x7FFu);
   sgn = hi & 0x80000000u;
   unsigned long long m = ((b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull) << 3;

@@ -351,20 +351,21 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
       for (int i = tid; i < (a.chunk_slab0[c + 1] - a.chunk_slab0[c]) * 32; i += 256)
         a.srcexp_slab[(int64_t)a.chunk_slab0[c] * 32 + i] = 0;
     return;
+  } else {
+    // pairs (q even, q+1) for each column n
+    for (int pi = tid; pi < ksteps * 8 * NT * 8; pi += 256) {
+      const int n = pi % (NT * 8), qp = pi / (NT * 8), q = 2 * qp;
+      const double x0 = (n < NC && q < Kt) ? Cf[q * NC + n] : 0.0;
+      const double x1 = (n < NC && q + 1 < Kt) ? Cf[(q + 1) * NC + n] : 0.0;
+      const int e = (n < NC) ? Gs[n] : 0;
+      const int ks = q >> 4, kk = q & 15, nt = n >> 3;
+      const int ln = (n & 7) * 4 + ((kk & 7) >> 1), rg = (kk >> 3) & 1;
+      // layout: [kstep][ntile][plane][lane][2]
+      unsigned* base = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;
+      oz_store_pair(base, 64, ln * 2 + rg, x0, e, x1, e, a.flags);
+    }
+    for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
   }
-  // pairs (q even, q+1) for each column n
-  for (int pi = tid; pi < ksteps * 8 * NT * 8; pi += 256) {
-    const int n = pi % (NT * 8), qp = pi / (NT * 8), q = 2 * qp;
-    const double x0 = (n < NC && q < Kt) ? Cf[q * NC + n] : 0.0;
-    const double x1 = (n < NC && q + 1 < Kt) ? Cf[(q + 1) * NC + n] : 0.0;
-    const int e = (n < NC) ? Gs[n] : 0;
-    const int ks = q >> 4, kk = q & 15, nt = n >> 3;
-    const int ln = (n & 7) * 4 + ((kk & 7) >> 1), rg = (kk >> 3) & 1;
-    // layout: [kstep][ntile][plane][lane][2]
-    unsigned* base = dig + ((int64_t)(ks * NT + nt) * kOzDigits) * 64;
-    oz_store_pair(base, 64, ln * 2 + rg, x0, e, x1, e, a.flags);
-  }
-  for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
 }
 
 // ---------------------------------------------------------------------------

@@ -46,7 +46,6 @@ namespace {
 
 constexpr int kUmmaThreads = 288;     // 8 worker warps + 1 issuer warp
 constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (warps 0..7)
-constexpr int kIssuer = 256;          // lane 0 of warp 8 issues every load and MMA
 constexpr int kStages = 5;            // TMA ring depth
 constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
 constexpr int kBBuf = 4;              // steps the producer warps may run ahead of the MMAs
@@ -143,19 +142,10 @@ __device__ __forceinline__ void tmem_ld4(uint32_t ta, uint32_t (&r)[4]) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(ta));
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(ta));
-}
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t (&r)[N]) {
-  if constexpr (N == 4) {
-    tmem_ld4(ta, r);
-  } else {
-    static_assert(N == 8, "tmem_ld: 4 or 8 columns");
-    tmem_ld8(ta, r);
-  }
+  static_assert(N == 4, "tmem_ld: 4 columns");
+  tmem_ld4(ta, r);
 }
 
 // Per-CTA control block at the end of dynamic shared memory.
@@ -231,15 +221,6 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, 
     const double v = ps[j].value();
     acc[j] = first ? v : acc[j] + v;
   }
-}
-
-// Expand 16 digit bytes d (rows rho = 0..15 of one column) with their sign
-// bytes g into 16 fp16 digits: out[0..3] rows 0..7, out[4..7] rows 8..15.
-__device__ __forceinline__ void expand16(const uint4& d, const uint4& g, uint4& lo, uint4& hi) {
-  lo.x = __byte_perm(d.x, g.x, 0x5140); lo.y = __byte_perm(d.x, g.x, 0x7362);
-  lo.z = __byte_perm(d.y, g.y, 0x5140); lo.w = __byte_perm(d.y, g.y, 0x7362);
-  hi.x = __byte_perm(d.z, g.z, 0x5140); hi.y = __byte_perm(d.z, g.z, 0x7362);
-  hi.z = __byte_perm(d.w, g.w, 0x5140); hi.w = __byte_perm(d.w, g.w, 0x7362);
 }
 
 // Split 8 float64 values x[0..7] (8 consecutive rows of one column) against
@@ -374,7 +355,6 @@ struct GramCursor {
 // of warp 8 issues the loads and MMAs.  Producers run up to kBBuf steps ahead
 // of the MMAs and never wait for a drain; drainers wait on accf, a commit of
 // the interval's last MMAs into that TMEM buffer.
-constexpr int kProducers = 128;
 
 // Whether step st (of nsteps in its item) closes an accumulation interval:
 // exact float32 sums cover 16 steps.
@@ -608,7 +588,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         } else {
           tc_fence_after();
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
-#pragma unroll
           const bool first = cur.st < 16;  // the item's first interval
 #pragma unroll
           for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
@@ -909,7 +888,6 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         } else {
           tc_fence_after();
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
-#pragma unroll
           const bool first = ks < 16;  // the output group's first interval
 #pragma unroll
           for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
