@@ -998,6 +998,11 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       if (pass >= 2 && (e = launch_oz_ypass(a, pass, st))) return e;
       if ((e = launch_oz_gram(a, pass, st))) return e;
       count_launches(pass >= 2 ? 3 : (umma_enabled(a) ? 2 : 1));
+    } else if (tc && pass == 1 && mixed && umma_enabled(a)) {
+      // the mixed form's first pass on the tensor cores: the leading three
+      // digits (24 bits) of both factors, 3 of the 7 planes read
+      if ((e = launch_umma_gram_split3(a, st))) return e;
+      count_launches(2);
     } else if (a.nb == 0 && s <= 4 && !(pass == 1 && mixed)) {
       if ((e = launch_gram_narrow(a, pass, st))) return e;
       count_launches(1);

@@ -55,14 +55,14 @@ constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
 __host__ __device__ constexpr int umma_round16(int x) { return (x + 15) / 16 * 16; }
 // N of the MMA of digit t (pairs u = 1 .. 8 - t, nb columns each), and its
 // first TMEM column.
-__host__ __device__ constexpr int umma_nt(int t, int nb) { return umma_round16((8 - t) * nb); }
-__host__ __device__ constexpr int umma_col(int t, int nb) {
+__host__ __device__ constexpr int umma_nt(int t, int nb, int nd = kOzDigits) { return umma_round16((nd + 1 - t) * nb); }
+__host__ __device__ constexpr int umma_col(int t, int nb, int nd = kOzDigits) {
   int c = 0;
-  for (int i = 1; i < t; ++i) c += umma_nt(i, nb);
+  for (int i = 1; i < t; ++i) c += umma_nt(i, nb, nd);
   return c;
 }
 // TMEM accumulator buffers (256 columns apart) that fit in the 512 columns.
-__host__ __device__ constexpr int umma_nacc(int nb) { return umma_col(8, nb) <= 256 ? 2 : 1; }
+__host__ __device__ constexpr int umma_nacc(int nb, int nd = kOzDigits) { return umma_col(nd + 1, nb, nd) <= 256 ? 2 : 1; }
 constexpr int kTmemCols = 512;
 
 // --- PTX wrappers -------------------------------------------------------------
@@ -110,6 +110,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm,
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           dst),
       "l"(tm), "r"(c0), "r"(c1), "r"(mb)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint32_t mb) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(mb)
       : "memory");
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb) {
@@ -200,19 +208,20 @@ struct PairSums {
 // column n0 of every pair block) for this thread's TMEM lane and add their
 // recombined values to acc[0 .. NW) (or set them: the first interval of an
 // output, which saves a float64 add).
-template <int NB, int NW>
+template <int NB, int NW, int ND = kOzDigits>
 __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, bool first) {
   PairSums ps[NW];
 #pragma unroll
   for (int j = 0; j < NW; ++j) ps[j].clear();
 #pragma unroll
-  for (int t = 1; t <= kOzDigits; ++t) {
-    uint32_t r[8 - 1][NW];
+  for (int t = 1; t <= ND; ++t) {
+    uint32_t r[ND][NW];
 #pragma unroll
-    for (int u = 1; u <= 8 - t; ++u) tmem_ld<NW>(tlane + (uint32_t)(umma_col(t, NB) + (u - 1) * NB + n0), r[u - 1]);
+    for (int u = 1; u <= ND + 1 - t; ++u)
+      tmem_ld<NW>(tlane + (uint32_t)(umma_col(t, NB, ND) + (u - 1) * NB + n0), r[u - 1]);
     tmem_wait_ld();
 #pragma unroll
-    for (int u = 1; u <= 8 - t; ++u)
+    for (int u = 1; u <= ND + 1 - t; ++u)
 #pragma unroll
       for (int j = 0; j < NW; ++j) ps[j].add(t, u, __uint_as_float(r[u - 1][j]));
   }
@@ -225,9 +234,10 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, 
 
 // Split 8 float64 values x[0..7] (8 consecutive rows of one column) against
 // exponent e and store their fp16 digits as one 16-byte core-matrix row of
-// each of the 7 planes at dst + t * plane.
+// each of the first ND planes at dst + t * plane.
+template <int ND = kOzDigits>
 __device__ __forceinline__ void split8_store(const double* x, int e, unsigned char* dst, int plane, int* flags) {
-  unsigned w[kOzDigits][4];
+  unsigned w[ND][4];
   bool bad = false;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -236,11 +246,11 @@ __device__ __forceinline__ void split8_store(const double* x, int e, unsigned ch
     bad |= oz_split(x[2 * i + 1], e, h1, l1, s1);
     const unsigned sb = (s0 >> 16) | s1;
 #pragma unroll
-    for (int t = 1; t <= kOzDigits; ++t) w[t - 1][i] = oz_pack(t, h0, l0, h1, l1, sb);
+    for (int t = 1; t <= ND; ++t) w[t - 1][i] = oz_pack(t, h0, l0, h1, l1, sb);
   }
   if (bad) oz_status(flags, LO_ERR_NONFINITE);
 #pragma unroll
-  for (int t = 0; t < kOzDigits; ++t)
+  for (int t = 0; t < ND; ++t)
     *reinterpret_cast<uint4*>(dst + t * plane) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
@@ -301,12 +311,16 @@ __global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* s
 // [t][128 B]: K-major, SBO = 7 x 128, LBO = 16 x 7 x 128); the block's own
 // columns are split into it after the load.  B operand (K-major): row
 // (u - 1) NB + n holds digit u of column n of A.
-template <int S>
+// ND = 7: every digit (float64 accuracy); ND = 3: the leading three digits
+// of both factors and the pairs t + u <= 4 (a 24-bit split: the first pass
+// of the mixed form), which reads 3 of the 7 planes.
+template <int S, int ND = kOzDigits>
 struct GramLayout {
   static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
-  static constexpr int RB = umma_round16(7 * NB);
-  static constexpr int STG = 0;                                 // kStages x [2][16][7][128 B]
-  static constexpr int BBUF = STG + kStages * kStageBytes;      // kBBuf x RB x 32 B
+  static constexpr int RB = umma_round16(ND * NB);
+  static constexpr int STAGE = ND * 4096;                       // [2][16][ND][128 B]
+  static constexpr int STG = 0;                                 // kStages stages
+  static constexpr int BBUF = STG + kStages * STAGE;            // kBBuf x RB x 32 B
   // private cp.async slots (3 steps) of the float64 values a thread splits:
   // the block's own columns of the A tile (2 S units of 8 rows) and the B
   // operand (4 NB units of 4 rows)
@@ -360,11 +374,11 @@ struct GramCursor {
 // exact float32 sums cover 16 steps.
 __device__ __forceinline__ bool interval_end(int st, int nsteps) { return ((st + 1) & 15) == 0 || st + 1 == nsteps; }
 
-template <int S>
+template <int S, int ND>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
-    k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass) {
-  using L = GramLayout<S>;
-  constexpr int NB = L::NB, RB = L::RB, NSPL = L::NSPL, NACC = umma_nacc(NB);
+    k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass, const __grid_constant__ CUtensorMap tm) {
+  using L = GramLayout<S, ND>;
+  constexpr int NB = L::NB, RB = L::RB, NSPL = L::NSPL, NACC = umma_nacc(NB, ND), STAGE = L::STAGE;
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
@@ -395,9 +409,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if constexpr (RB > 7 * NB) {  // B pad rows stay zero
-    for (int i = tid; i < kBBuf * (RB - 7 * NB) * 2; i += kUmmaThreads) {
-      const int h = i & 1, rest = i >> 1, r = 7 * NB + rest % (RB - 7 * NB), bb = rest / (RB - 7 * NB);
+  if constexpr (RB > ND * NB) {  // B pad rows stay zero
+    for (int i = tid; i < kBBuf * (RB - ND * NB) * 2; i += kUmmaThreads) {
+      const int h = i & 1, rest = i >> 1, r = ND * NB + rest % (RB - ND * NB), bb = rest / (RB - ND * NB);
       *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
           make_uint4(0u, 0u, 0u, 0u);
     }
@@ -411,24 +425,31 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   if (warp == 8) {
     // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
     if (lane == 0) {
-      uint32_t idesc[kOzDigits];
+      uint32_t idesc[ND];
 #pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 0, 0);
+      for (int t = 1; t <= ND; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB, ND), 0, 0);
       // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
-      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kStageBytes / 2, kOzDigits * 128);
+      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
       // loads of global step j (cursor c): the digit planes of the group's prior
-      // panels, or a bare arrival when it has none
+      // panels (all 7: two contiguous runs; the leading 3: one 3D TMA box that
+      // skips the other 4 planes of every group), or a bare arrival when it
+      // has none
       auto issue = [&](const GramCursor& c, int j) {
         const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, gtot - g0);
         if (k > c.col0 && ng > 0) {
-          const uint32_t run = (uint32_t)ng * kOzDigits * 128;
           const int64_t eta = 2 * (int64_t)(c.tile0 + c.st);
-          const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
-          mbar_expect_tx(full0 + 8 * sj, 2 * run);
-          bulk_load(su32(sm + L::STG + sj * kStageBytes), gsrc, run, full0 + 8 * sj);
-          bulk_load(su32(sm + L::STG + sj * kStageBytes + kStageBytes / 2), gsrc + (int64_t)gtot * kOzDigits * 128,
-                    run, full0 + 8 * sj);
+          if constexpr (ND == kOzDigits) {
+            const uint32_t run = (uint32_t)ng * kOzDigits * 128;
+            const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
+            mbar_expect_tx(full0 + 8 * sj, 2 * run);
+            bulk_load(su32(sm + L::STG + sj * STAGE), gsrc, run, full0 + 8 * sj);
+            bulk_load(su32(sm + L::STG + sj * STAGE + STAGE / 2), gsrc + (int64_t)gtot * kOzDigits * 128, run,
+                      full0 + 8 * sj);
+          } else {
+            mbar_expect_tx(full0 + 8 * sj, STAGE);  // the whole box (groups past gtot arrive as zeros)
+            tma_load_3d(su32(sm + L::STG + sj * STAGE), &tm, 0, g0, (int)eta, full0 + 8 * sj);
+          }
         } else {
           mbar_arrive(full0 + 8 * sj);
         }
@@ -467,9 +488,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         const uint64_t db = dB0 + (uint64_t)((bb * (RB * 32)) >> 4);
         const uint32_t accum = (cur.st & 15) ? 1u : 0u;
 #pragma unroll
-        for (int t = 1; t <= kOzDigits; ++t) {
-          const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
-          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
+        for (int t = 1; t <= ND; ++t) {
+          const uint64_t da = dA0 + (uint64_t)((s * STAGE + (t - 1) * 128) >> 4);
+          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB, ND)), da, db, idesc[t - 1], accum);
         }
         umma_commit(mmad0 + 8 * bb);
         if (interval_end(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
@@ -537,12 +558,12 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       // MMAs of step g - kBBuf done: B buffer bb is free (and no warp runs further ahead)
       if (g >= kBBuf && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - kBBuf) / kBBuf) & 1)))
         umma_timeout(ctl, a.flags);
-      unsigned char* stage = sm + L::STG + s * kStageBytes;
+      unsigned char* stage = sm + L::STG + s * STAGE;
       if (is_asrc(cur)) {
         const int am = k - cur.col0 + al;
         if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
-        split8_store(xa_slot + (g % 3) * 2 * S * 8, a.srcexp_slab[(int64_t)cur.slab * 32 + al],
-                     stage + ah * (kStageBytes / 2) + (am >> 3) * (kOzDigits * 128) + (am & 7) * 16, 128, a.flags);
+        split8_store<ND>(xa_slot + (g % 3) * 2 * S * 8, a.srcexp_slab[(int64_t)cur.slab * 32 + al],
+                         stage + ah * (STAGE / 2) + (am >> 3) * (ND * 128) + (am & 7) * 16, 128, a.flags);
       }
       if (b_role) {
         unsigned h[4], l[4], gg[4];
@@ -554,7 +575,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
         unsigned char* bbuf = sm + L::BBUF + bb * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
 #pragma unroll
-        for (int u = 1; u <= kOzDigits; ++u) {
+        for (int u = 1; u <= ND; ++u) {
           const int row = (u - 1) * NB + bn;
           const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (gg[0] >> 16) | gg[1]);
           const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (gg[2] >> 16) | gg[3]);
@@ -590,7 +611,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
           const bool first = cur.st < 16;  // the item's first interval
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
+          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4, ND>(tlane, c4 * 4, acc + c4 * 4, first);
         }
       }
       tc_fence_before();
@@ -1529,9 +1550,9 @@ int umma_sms() {
   return sms;
 }
 
-template <int S>
+template <int S, int ND = kOzDigits>
 cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
-  using L = GramLayout<S>;
+  using L = GramLayout<S, ND>;
   const int Kt = a.nb * S + S;
   const int nitems = a.nslab * ((Kt + 127) / 128) * L::NSPL;
   dim3 grid(nitems < umma_sms() ? nitems : umma_sms());
@@ -1540,7 +1561,7 @@ cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   // the pass block's exponents per slab: from a small pass over W for pass 1,
   // from the reiteration's assembly (k_umma_update<S, 1>) afterwards
   if (pass == 1) k_umma_srcexp<S><<<a.nslab, 256, 0, st>>>(a, src, lds);
-  k_umma_gram<S><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass);
+  k_umma_gram<S, ND><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram3);
   return cudaGetLastError();
 }
 
@@ -1572,8 +1593,11 @@ cudaError_t umma_set_attrs() {
   if (g_umma_attr) return cudaSuccess;
   cudaError_t e;
 #define LO_UMMA_ATTR(S)                                                                                          \
-  if ((e = cudaFuncSetAttribute(k_umma_gram<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
-                                GramLayout<S>::BYTES)))                                                         \
+  if ((e = cudaFuncSetAttribute(k_umma_gram<S, kOzDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                GramLayout<S, kOzDigits>::BYTES)))                                              \
+    return e;                                                                                                   \
+  if ((e = cudaFuncSetAttribute(k_umma_gram<S, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                                GramLayout<S, 3>::BYTES)))                                                      \
     return e;                                                                                                   \
   if ((e = cudaFuncSetAttribute(k_umma_update<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                 UpdLayout<S, 1>::BYTES)))                                                       \
@@ -1610,6 +1634,15 @@ cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st) {
     case 8: return umma_gram_for<8>(a, pass, st);
     case 16: return umma_gram_for<16>(a, pass, st);
     case 32: return umma_gram_for<32>(a, pass, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_umma_gram_split3(const StepArgs& a, cudaStream_t st) {
+  switch (a.s) {
+    case 8: return umma_gram_for<8, 3>(a, 1, st);
+    case 16: return umma_gram_for<16, 3>(a, 1, st);
+    case 32: return umma_gram_for<32, 3>(a, 1, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1706,9 +1739,20 @@ cudaError_t umma_make_maps(uint8_t* dig, int s, int panels, int64_t dtiles, Umma
   const cuuint64_t strides[1] = {gtot * kOzDigits * 128};
   const cuuint32_t es[2] = {1, 1};
   const cuuint32_t box[2] = {2 * kOzDigits * 128 / 8, 16};
-  const CUresult r = encode(&maps->upd, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, dig, dims, strides, box, es,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(&maps->upd, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, dig, dims, strides, box, es,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // 3D view for the Gram's leading three digits: (the 7 x 128 bytes of one
+  // group of one 8-row block, groups, 8-row blocks); box = the first 3 x 128
+  // bytes of 16 groups of 2 blocks (one 16-row step of 128 columns)
+  const cuuint64_t dims3[3] = {kOzDigits * 128 / 8, gtot, (cuuint64_t)(2 * dtiles)};
+  const cuuint64_t strides3[2] = {kOzDigits * 128, gtot * kOzDigits * 128};
+  const cuuint32_t es3[3] = {1, 1, 1};
+  const cuuint32_t box3[3] = {3 * 128 / 8, 16, 2};
+  r = encode(&maps->gram3, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, dig, dims3, strides3, box3, es3,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -425,10 +425,14 @@ def test_full_size_sampled_rows(precision):
 def test_digit_planes_bitwise(n, s, cr, M, precision):
     """Panels kept as digit planes give bit-for-bit the products of re-splitting
     the float64 panels in every pass: every output of every step, with the
-    reiteration passes included, and the final basis against the oracle."""
+    reiteration passes included, and the final basis against the oracle.  The
+    mixed form's first pass differs on purpose (with planes: the leading three
+    digits on the tensor cores; without: float32 on the CUDA cores), so there
+    both bases must agree within the float64 tolerances instead."""
     L = lo()
     on = L.Basis(n, s, M, cr, precision=precision)
     off = L.Basis(n, s, M, cr, precision=precision, digit_planes=False)
+    bitwise = precision == "fp64_tc"
     A = []
     for j in range(M):
         Wh = I.gaussian(n, s, 5000 + j)
@@ -439,13 +443,19 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
         r1 = [host(x) for x in on.orthogonalize(W) if x is not None]
         r2 = [host(x) for x in off.orthogonalize(W) if x is not None]
         for x, y in zip(r1, r2):
-            assert np.array_equal(x, y), j
+            if bitwise:
+                assert np.array_equal(x, y), j
+            else:
+                assert rel(x, y) <= TOL_REL, j
     Q = host(on.apply_Q(dev(np.eye(on.k))))
     assert O.e_perp(Q) <= TOL_PERP
     for c in (0, on.num_chunks - 1):
         Qa, Ta = on.export_chunk(c)
         Qb, Tb = off.export_chunk(c)
-        assert np.array_equal(Qa, Qb) and np.array_equal(Ta, Tb)
+        if bitwise:
+            assert np.array_equal(Qa, Qb) and np.array_equal(Ta, Tb)
+        else:
+            assert rel(Qa, Qb) <= TOL_REL and rel(Ta, Tb) <= TOL_REL
 
 
 @pytest.mark.parametrize("planes", [True, False])
