@@ -127,7 +127,7 @@ struct StepArgs {
 // TMA descriptors of a basis's digit planes: one box shape per kernel.
 struct UmmaMaps {
   CUtensorMap upd;    // 16 8-row blocks (128 rows) of the 16 columns of one step, all planes
-  CUtensorMap gram3;  // 2 8-row blocks of 16 column groups, the leading 3 planes
+  CUtensorMap gram_lead;  // 2 8-row blocks of 16 column groups, the mixed Gram's leading planes
 };
 
 // Digit planes of the tensor-core form: 7 planes of 8-bit digits per value.
@@ -185,8 +185,8 @@ cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, int mode,
 // step has prior blocks (nb >= 1).
 bool umma_enabled(const StepArgs& a);
 cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st);
-// The mixed form's first Gram pass: the leading three digits of both factors.
-cudaError_t launch_umma_gram_split3(const StepArgs& a, cudaStream_t st);
+// The mixed form's first Gram pass: the leading digits of both factors.
+cudaError_t launch_umma_gram_mixed(const StepArgs& a, cudaStream_t st);
 cudaError_t launch_umma_update(const StepArgs& a, int nout, int pass, cudaStream_t st);
 // tcgen05 forms of a step without prior blocks (k = 0, s in {8, 16}); no digit planes needed.
 bool umma0_enabled(const StepArgs& a);

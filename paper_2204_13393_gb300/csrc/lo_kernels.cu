@@ -462,8 +462,12 @@ bool gram1_supported(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s =
 // Leaf factorization of pass `pass`, one CTA per chunk: sum the slab partials
 // in slab order, then N = chol(G - P^T P) (Alg. 7), N^{-1}, and the
 // reiteration bookkeeping of Alg. 8: P_comb <- P_comb + P N_comb,
-// N_comb <- N N_comb.  Decides on the next pass from kappa_F(N).
-__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel, int allow_shift) {
+// N_comb <- N N_comb.  Decides on the next pass from kappa_F(N).  u_gram is
+// the unit roundoff of this pass's Gram (float64: DBL_EPSILON; the mixed
+// form's digit Gram: 2^-31): the breakdown test and the shift of the retry
+// scale with it.
+__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel, int allow_shift,
+                                                   double u_gram) {
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   extern __shared__ __align__(16) double sm[];
   const int c = blockIdx.x, s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s, ss = s * s;
@@ -505,9 +509,9 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     for (int i = threadIdx.x; i < s; i += blockDim.x) M[i * s + i] += shift_rel * trG;
     __syncthreads();
   }
-  const double tol = (double)s * DBL_EPSILON * trG;
+  const double tol = (double)s * u_gram * trG;
   const int64_t rows = a.chunk_row0[c + 1] - a.chunk_row0[c];
-  const double sigma = 11.0 * ((double)rows * s + (double)s * (s + 1)) * DBL_EPSILON * trG;
+  const double sigma = 11.0 * ((double)rows * s + (double)s * (s + 1)) * u_gram * trG;
   const bool shifted = cta_cholesky_shifted(M, tmp, s, tol, sigma, allow_shift != 0, a.flags,
                                             reinterpret_cast<int*>(red + 2));
   if (shifted && threadIdx.x == 0)
@@ -999,9 +1003,9 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       if ((e = launch_oz_gram(a, pass, st))) return e;
       count_launches(pass >= 2 ? 3 : (umma_enabled(a) ? 2 : 1));
     } else if (tc && pass == 1 && mixed && umma_enabled(a)) {
-      // the mixed form's first pass on the tensor cores: the leading three
-      // digits (24 bits) of both factors, 3 of the 7 planes read
-      if ((e = launch_umma_gram_split3(a, st))) return e;
+      // the mixed form's first pass on the tensor cores: the leading digits
+      // of both factors, only their planes read
+      if ((e = launch_umma_gram_mixed(a, st))) return e;
       count_launches(2);
     } else if (a.nb == 0 && s <= 4 && !(pass == 1 && mixed)) {
       if ((e = launch_gram_narrow(a, pass, st))) return e;
@@ -1021,12 +1025,18 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       count_launches(1);
     }
     mark(hook, pass == 1 ? kKindGram : kKindRefine, false, st);
-    // shifted Cholesky for the float32 first pass: relative shift of the trace
-    const double shift = (pass == 1 && mixed) ? 1e-5 : 0.0;
+    // the reduced-precision first pass of the mixed form: above a float32
+    // Gram a fixed shift of 1e-5 of the trace; above the 32-bit digit Gram on
+    // the tensor cores the plain Cholesky, with the shifted retry (and two
+    // more passes) only on breakdown, both scaled to its unit roundoff, so a
+    // moderately conditioned block needs no third pass
+    const bool digit_first = pass == 1 && mixed && tc && umma_enabled(a) && a.leaf != LO_LEAF_PIP;
+    const double shift = (pass == 1 && mixed && !digit_first) ? 1e-5 : 0.0;
+    const double u_gram = digit_first ? 0x1p-31 : DBL_EPSILON;
     const size_t smleaf = 8 * ((size_t)Kt * s + 4 * ss + 4);
     mark(hook, kKindLeaf, true, st);
-    const int allow_shift = (pass == 1 && !mixed && a.leaf != LO_LEAF_PIP) ? 1 : 0;
-    k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift, allow_shift);
+    const int allow_shift = (pass == 1 && (!mixed || digit_first) && a.leaf != LO_LEAF_PIP) ? 1 : 0;
+    k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift, allow_shift, u_gram);
     mark(hook, kKindLeaf, false, st);
     count_launches(1);
   }

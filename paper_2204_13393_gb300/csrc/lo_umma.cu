@@ -49,6 +49,7 @@ constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (wa
 constexpr int kStages = 5;            // TMA ring depth
 constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
 constexpr int kBBuf = 4;              // steps the producer warps may run ahead of the MMAs
+constexpr int kMixedDigits = 4;       // leading digits of the mixed form's first Gram (8 bits each)
 constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
 constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
 
@@ -311,9 +312,9 @@ __global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* s
 // [t][128 B]: K-major, SBO = 7 x 128, LBO = 16 x 7 x 128); the block's own
 // columns are split into it after the load.  B operand (K-major): row
 // (u - 1) NB + n holds digit u of column n of A.
-// ND = 7: every digit (float64 accuracy); ND = 3: the leading three digits
-// of both factors and the pairs t + u <= 4 (a 24-bit split: the first pass
-// of the mixed form), which reads 3 of the 7 planes.
+// ND = 7: every digit (float64 accuracy); ND < 7: the leading ND digits of
+// both factors and the pairs t + u <= ND + 1 (an 8 ND-bit split: the first
+// pass of the mixed form), which reads ND of the 7 planes.
 template <int S, int ND = kOzDigits>
 struct GramLayout {
   static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
@@ -432,9 +433,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
       // loads of global step j (cursor c): the digit planes of the group's prior
-      // panels (all 7: two contiguous runs; the leading 3: one 3D TMA box that
-      // skips the other 4 planes of every group), or a bare arrival when it
-      // has none
+      // panels (all 7: two contiguous runs; the leading ND: one 3D TMA box
+      // that skips the other planes of every group), or a bare arrival when
+      // it has none
       auto issue = [&](const GramCursor& c, int j) {
         const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, gtot - g0);
         if (k > c.col0 && ng > 0) {
@@ -1561,7 +1562,7 @@ cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   // the pass block's exponents per slab: from a small pass over W for pass 1,
   // from the reiteration's assembly (k_umma_update<S, 1>) afterwards
   if (pass == 1) k_umma_srcexp<S><<<a.nslab, 256, 0, st>>>(a, src, lds);
-  k_umma_gram<S, ND><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram3);
+  k_umma_gram<S, ND><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram_lead);
   return cudaGetLastError();
 }
 
@@ -1596,8 +1597,8 @@ cudaError_t umma_set_attrs() {
   if ((e = cudaFuncSetAttribute(k_umma_gram<S, kOzDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                 GramLayout<S, kOzDigits>::BYTES)))                                              \
     return e;                                                                                                   \
-  if ((e = cudaFuncSetAttribute(k_umma_gram<S, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
-                                GramLayout<S, 3>::BYTES)))                                                      \
+  if ((e = cudaFuncSetAttribute(k_umma_gram<S, kMixedDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                GramLayout<S, kMixedDigits>::BYTES)))                                           \
     return e;                                                                                                   \
   if ((e = cudaFuncSetAttribute(k_umma_update<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                 UpdLayout<S, 1>::BYTES)))                                                       \
@@ -1638,11 +1639,11 @@ cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_umma_gram_split3(const StepArgs& a, cudaStream_t st) {
+cudaError_t launch_umma_gram_mixed(const StepArgs& a, cudaStream_t st) {
   switch (a.s) {
-    case 8: return umma_gram_for<8, 3>(a, 1, st);
-    case 16: return umma_gram_for<16, 3>(a, 1, st);
-    case 32: return umma_gram_for<32, 3>(a, 1, st);
+    case 8: return umma_gram_for<8, kMixedDigits>(a, 1, st);
+    case 16: return umma_gram_for<16, kMixedDigits>(a, 1, st);
+    case 32: return umma_gram_for<32, kMixedDigits>(a, 1, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1743,14 +1744,15 @@ cudaError_t umma_make_maps(uint8_t* dig, int s, int panels, int64_t dtiles, Umma
                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  // 3D view for the Gram's leading three digits: (the 7 x 128 bytes of one
-  // group of one 8-row block, groups, 8-row blocks); box = the first 3 x 128
-  // bytes of 16 groups of 2 blocks (one 16-row step of 128 columns)
+  // 3D view for the mixed Gram's leading digits: (the 7 x 128 bytes of one
+  // group of one 8-row block, groups, 8-row blocks); box = the first
+  // kMixedDigits x 128 bytes of 16 groups of 2 blocks (one 16-row step of 128
+  // columns)
   const cuuint64_t dims3[3] = {kOzDigits * 128 / 8, gtot, (cuuint64_t)(2 * dtiles)};
   const cuuint64_t strides3[2] = {kOzDigits * 128, gtot * kOzDigits * 128};
   const cuuint32_t es3[3] = {1, 1, 1};
-  const cuuint32_t box3[3] = {3 * 128 / 8, 16, 2};
-  r = encode(&maps->gram3, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, dig, dims3, strides3, box3, es3,
+  const cuuint32_t box3[3] = {kMixedDigits * 128 / 8, 16, 2};
+  r = encode(&maps->gram_lead, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, dig, dims3, strides3, box3, es3,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
