@@ -601,7 +601,7 @@ def run_mixed_case(args):
     g.manual_seed(2204133930 + 4000)
     prior = [torch.randn(n, s, dtype=torch.float64, device=dev, generator=g) for _ in range(kb)]
     nbytes = orth_bytes(n, s, kb * s, max(1, n // cr))
-    for kappa in (1e2, 1e4, 1e6):
+    for kappa in [float(x) for x in args.mixed_kappas.split(",")]:
         Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
         Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
         sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device=dev)
@@ -627,7 +627,11 @@ def run_mixed_case(args):
             passes = b.last_step_info()
             b.truncate(kb)
             b.set_profiling(True)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()       # the profiled step of each form (ncu --profile-from-start off)
             U, _, R = b.orthogonalize(W)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
             prof = {gname: round(v[0], 3) for gname, v in b.profile_read().items() if v[0] > 0}
             b.set_profiling(False)
             UtU = U.T @ U
@@ -809,6 +813,7 @@ def main():
                          "graph-replayed")
     ap.add_argument("--mixed-n", type=int, default=2 ** 24)
     ap.add_argument("--mixed-cr", type=int, default=0, help="chunk rows for --case mixed (0: lo_tune_chunk_rows)")
+    ap.add_argument("--mixed-kappas", default="1e2,1e4,1e6", help="condition numbers for --case mixed")
     ap.add_argument("--step-precisions", default="fp64,fp64_tc", help="forms for --case step")
     ap.add_argument("--chunk-rows", type=int, default=CHUNK,
                     help="chunk rows of the cycle's basis (0: lo_tune_chunk_rows, measured on this GPU)")

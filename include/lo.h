@@ -81,8 +81,12 @@ typedef enum lo_precision {
                            /* float64 kernels (its products are too narrow for   */
                            /* the tensor cores to pay)                           */
   LO_PREC_MIXED_TC = 3     /* mixed form on the tensor-core path: the first Gram */
-                           /* pass in float32 (shifted float64 Cholesky), every  */
-                           /* further pass and the assembly as LO_PREC_FP64_TC   */
+                           /* pass reduced (with digit planes and prior blocks:  */
+                           /* the leading four digits of both factors on the     */
+                           /* tensor cores, a 32-bit split, unshifted float64    */
+                           /* Cholesky with a shifted retry on breakdown; else   */
+                           /* float32 with a fixed shift), every further pass    */
+                           /* and the assembly as LO_PREC_FP64_TC                */
                            /* (max_blocks = 1, s <= 4: as LO_PREC_MIXED_FP32)    */
 } lo_precision;
 
