@@ -515,3 +515,70 @@ def test_narrow_one_block_basis_runs_native(s):
         with pytest.raises(lo().LoError) as e:
             lo().Basis(n, s, 2, cr, precision="fp64_tc")
         assert "UNSUPPORTED" in str(e.value)
+
+
+def _orthonormal_columns(X):
+    """Q of X = QR by CholeskyQR2 (the s x s Cholesky on the host), for
+    device-side test inputs of full size."""
+    for _ in range(2):
+        G = (X.T @ X).cpu().numpy()
+        Linv_t = np.linalg.inv(np.linalg.cholesky(G)).T
+        X = X @ torch.from_numpy(np.ascontiguousarray(Linv_t)).to(X.device)
+    return X
+
+
+def test_full_cycle_every_step_properties():
+    """The block-GMRes workload in the benchmark's launch configuration
+    (n = 2^20, s = 8, 31 blocks, 4096-row chunks, float64 on the tensor cores):
+    every step k = 0 .. 240 satisfies W = Q H + U R to float64 accuracy, and
+    the final 248-column basis is orthonormal.  Properties that hold at any
+    size; the oracle at these sizes is the CPU baseline's minutes."""
+    n, s, m, cr = 2 ** 20, 8, 31, 4096
+    L = lo()
+    b = L.Basis(n, s, m, cr, precision="fp64_tc")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2204133930 + 2000)
+    worst = 0.0
+    for j in range(m):
+        W = torch.randn(n, s, dtype=torch.float64, device="cuda", generator=g)
+        if j:  # a Krylov-like block: a component along the basis
+            W = W + b.apply_Q(torch.randn(b.k, s, dtype=torch.float64, device="cuda", generator=g))
+        k = b.k
+        U, H, R = b.orthogonalize(W)
+        recon = U @ R
+        if k:
+            C = torch.zeros(b.k, s, dtype=torch.float64, device="cuda")
+            C[:k] = H
+            recon = recon + b.apply_Q(C)
+        res = float(torch.linalg.norm(W - recon) / torch.linalg.norm(W))
+        worst = max(worst, res)
+        assert res <= TOL_RES, (j, res)
+    Q = b.apply_Q(torch.eye(b.k, dtype=torch.float64, device="cuda"))
+    G = Q.T @ Q
+    eperp = float(torch.linalg.norm(G - torch.eye(b.k, dtype=torch.float64, device="cuda")))
+    assert eperp <= TOL_PERP, eperp
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6, 1e10])
+def test_tsqr_target_size_properties(kappa):
+    """The tall-skinny QR at the target size (n = 2^24, s = 8, one block,
+    chunk rows from the tuner, float64 on the tensor cores), A = U diag(sigma)
+    V^T with orthonormal U, V and sigma log-spaced to 1/kappa: U^T U = I and
+    A = U R to float64 accuracy, R upper triangular with a positive diagonal."""
+    n, s = 2 ** 24, 8
+    L = lo()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2204133930 + 3000 + int(np.log10(kappa)))
+    Uh = _orthonormal_columns(torch.randn(n, s, dtype=torch.float64, device="cuda", generator=g))
+    Vh = _orthonormal_columns(torch.randn(s, s, dtype=torch.float64, device="cuda", generator=g))
+    sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device="cuda")
+    A = (Uh * sig) @ Vh.T
+    del Uh
+    cr = L.tune_chunk_rows(n, s, 1, precision="fp64_tc")
+    b = L.Basis(n, s, 1, cr, precision="fp64_tc")
+    U, _, R = b.orthogonalize(A)
+    eye = torch.eye(s, dtype=torch.float64, device="cuda")
+    assert float(torch.linalg.norm(U.T @ U - eye)) <= TOL_PERP
+    assert float(torch.linalg.norm(A - U @ R) / torch.linalg.norm(A)) <= TOL_RES
+    Rh = host(R)
+    assert np.allclose(np.tril(Rh, -1), 0.0) and np.all(np.diag(Rh) > 0)
