@@ -138,7 +138,12 @@ typedef struct lo_options {
                        /* normalizer N (the Gram cancellation factor).          */
                        /* <= 0 selects the default 1e-13.                        */
   int32_t digit_planes;  /* lo_digit_planes, default LO_PLANES_AUTO              */
-  int32_t reserved_;     /* set to 0                                             */
+  int32_t test_stall;    /* test hook, default 0.  1: in a step with prior       */
+                         /* blocks, the tensor-core Gram's issuing thread issues */
+                         /* no loads and no MMAs, so the kernel's bounded waits  */
+                         /* (about 0.25 s each) expire and the step returns      */
+                         /* LO_ERR_TIMEOUT with the basis unchanged (the timeout */
+                         /* path; no fault, nothing left in flight)              */
 } lo_options;
 
 typedef struct lo_basis lo_basis;

@@ -138,9 +138,10 @@ lo_status from_cuda(cudaError_t e) {
 }
 
 lo_status status_from_bits(int bits) {
+  // a wait that gave up leaves the step's later factors meaningless: report it first
+  if (bits & (1 << LO_ERR_TIMEOUT)) return LO_ERR_TIMEOUT;
   if (bits & (1 << LO_ERR_NONFINITE)) return LO_ERR_NONFINITE;
   if (bits & (1 << LO_ERR_BREAKDOWN)) return LO_ERR_BREAKDOWN;
-  if (bits & (1 << LO_ERR_TIMEOUT)) return LO_ERR_TIMEOUT;
   if (bits) return LO_ERR_CUDA;
   return LO_OK;
 }
@@ -180,6 +181,7 @@ StepArgs make_args(const lo_basis* b) {
   a.chunk_row0 = b->d_chunk_row0;
   a.nslab = b->nslab;
   a.slab_rows = b->slab_rows;
+  a.test_stall = b->opt.test_stall;
   a.precision = b->opt.precision;
   a.leaf = b->opt.leaf;
   a.reduction = b->opt.reduction;
@@ -283,7 +285,7 @@ void lo_options_default(lo_options* opt) {
   opt->sync = 1;
   opt->refine_tol = 1e-13;
   opt->digit_planes = LO_PLANES_AUTO;
-  opt->reserved_ = 0;
+  opt->test_stall = 0;
 }
 
 const char* lo_status_string(lo_status st) {
@@ -313,7 +315,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options_default(&o);
   if (opt) o = *opt;
   if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
-      o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1)
+      o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1 || o.test_stall < 0 || o.test_stall > 1)
     return LO_ERR_INVALID_ARG;
   // A one-block basis (tall-skinny QR) of at most kNativeMaxS columns runs
   // the native float64 kernels in the tensor-core forms too: with no prior

@@ -122,6 +122,7 @@ struct StepArgs {
   uint8_t* dig;
   int64_t dtiles;            // 16-row tiles of the slab tiling
   const struct UmmaMaps* maps;  // host-side TMA descriptors of dig (lo_umma.cu)
+  int32_t test_stall;           // test hook: the k > 0 tensor-core Gram issues nothing (lo_options)
 };
 
 // TMA descriptors of a basis's digit planes: one box shape per kernel.

@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 
   if (warp == 8) {
     // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
-    if (lane == 0) {
+    // (the test hook withholds all of it: every bounded wait then expires)
+    if (lane == 0 && !a.test_stall) {
       uint32_t idesc[ND];
 #pragma unroll
       for (int t = 1; t <= ND; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB, ND), 0, 0);

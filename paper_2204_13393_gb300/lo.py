@@ -56,7 +56,7 @@ class LoError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("leaf", c_int32), ("reduction", c_int32),
                 ("sync", c_int32), ("refine_tol", c_double), ("digit_planes", c_int32),
-                ("reserved_", c_int32)]
+                ("test_stall", c_int32)]
 
 
 _L = None
@@ -179,7 +179,7 @@ class Basis:
 
     def __init__(self, n: int, s: int, max_blocks: int, chunk_rows: int, precision: str = "fp64",
                  leaf: str = "pip2", reduction: str = "auto", sync: bool = True,
-                 refine_tol: float = 0.0, stream=None, digit_planes: bool = True):
+                 refine_tol: float = 0.0, stream=None, digit_planes: bool = True, test_stall: bool = False):
         L = _lib()
         o = Options()
         L.lo_options_default(ctypes.byref(o))
@@ -190,6 +190,7 @@ class Basis:
         if refine_tol > 0:
             o.refine_tol = refine_tol
         o.digit_planes = 0 if digit_planes else 1
+        o.test_stall = 1 if test_stall else 0
         h = c_void_p()
         self._h = None
         _check(L.lo_basis_create(int(n), int(s), int(max_blocks), int(chunk_rows), ctypes.byref(o),

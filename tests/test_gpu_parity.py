@@ -582,3 +582,28 @@ def test_tsqr_target_size_properties(kappa):
     assert float(torch.linalg.norm(A - U @ R) / torch.linalg.norm(A)) <= TOL_RES
     Rh = host(R)
     assert np.allclose(np.tril(Rh, -1), 0.0) and np.all(np.diag(Rh) > 0)
+
+
+def test_bounded_wait_expires_cleanly():
+    """The timeout path of the tcgen05 kernels without a fault: with the test
+    hook the k > 0 Gram's issuer issues nothing, so its producers' and
+    drainers' bounded waits expire.  The step reports LO_ERR_TIMEOUT, the basis
+    keeps its blocks, and the context stays usable: the same basis without the
+    hook's effect (a fresh one) and this one's next step on k = 0 work."""
+    n, s, cr = 65536, 8, 4096
+    L = lo()
+    W0, W1 = (dev(I.gaussian(n, s, 7200 + j)) for j in range(2))
+    b = L.Basis(n, s, 3, cr, precision="fp64_tc", test_stall=True)
+    b.orthogonalize(W0)                       # k = 0: the k = 0 kernels, no hook
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(W1)                   # k = 8: the Gram's issuer withholds its work
+    assert e.value.name == "LO_ERR_TIMEOUT"
+    assert b.num_blocks == 1
+    b.truncate(0)                             # the status word was read and cleared
+    U, _, R = b.orthogonalize(W0)
+    assert O.e_perp(host(U)) <= TOL_PERP
+    ok = L.Basis(n, s, 3, cr, precision="fp64_tc")
+    for W in (W0, W1):
+        ok.orthogonalize(W)
+    Q = host(ok.apply_Q(dev(np.eye(ok.k))))
+    assert O.e_perp(Q) <= TOL_PERP

@@ -78,6 +78,9 @@ def test_create_rejects_bad_arguments_without_device(lib):
     lib.lo_options_default(ctypes.byref(bad))
     bad.digit_planes = 2
     assert lib.lo_basis_create(4096, 4, 8, 512, ctypes.byref(bad), None, ctypes.byref(h)) == 1
+    lib.lo_options_default(ctypes.byref(bad))
+    bad.test_stall = 2
+    assert lib.lo_basis_create(4096, 4, 8, 512, ctypes.byref(bad), None, ctypes.byref(h)) == 1
 
 
 def test_null_handles_are_rejected(lib):
@@ -94,5 +97,5 @@ def test_options_default(lib):
     lib.lo_options_default(ctypes.byref(o))
     assert (o.precision, o.leaf, o.reduction, o.sync) == (0, 2, 0, 1)
     assert o.refine_tol == pytest.approx(1e-13)
-    assert (o.digit_planes, o.reserved_) == (0, 0)
+    assert (o.digit_planes, o.test_stall) == (0, 0)
     assert ctypes.sizeof(o) == 32
