@@ -14,7 +14,8 @@ beyond what the cited definition or algorithm states.
 
 Contents (paper section / equation / algorithm each function follows):
 
-* ``cholesky_upper``       textbook Cholesky, N^T N = M (Sec. 3, CholQR).
+* ``cholesky_upper``       textbook Cholesky, N^T N = M (Sec. 3, CholQR); an
+                           exactly zero component gives a zero row.
 * ``solve_upper_right``    Y N^{-1} by column-wise substitution.
 * ``householder_qr``       column-wise Householder QR (Sec. 2.2, eq. (hh),
                            Alg. 6 with an empty prior basis).
@@ -67,8 +68,9 @@ __all__ = [
 
 
 class Breakdown(ArithmeticError):
-    """A Cholesky pivot was not positive (rank deficiency / deflation, which
-    the oracle, like the library, does not handle; Sec. 3 last paragraph)."""
+    """A Cholesky pivot was not positive and the block was not exactly zero
+    there (rank deficiency / deflation, which the oracle, like the library,
+    does not handle; Sec. 3 last paragraph)."""
 
 
 def _sgn(x: float) -> float:
@@ -80,29 +82,42 @@ def cholesky_upper(M: np.ndarray) -> np.ndarray:
     """Upper-triangular N with N^T N = M (textbook Cholesky, row by row).
 
     This is the factorization CholQR and BCGS-PIP use (Sec. 3): for the PQR
-    Gram matrix it is applied to G - P^T P.  Raises ``Breakdown`` on a
-    non-positive or non-finite pivot.
+    Gram matrix it is applied to G - P^T P.  A pivot that is exactly zero
+    while the rest of its row is exactly zero too (the block has an exactly
+    zero component there, e.g. a column that vanishes on one chunk) gives a
+    zero row of N: Sec. 3 allows keeping t = s and carrying the rank
+    deficiency in N, and with exact zeros no tolerance is involved.  Any other
+    non-positive or non-finite pivot raises ``Breakdown``.
     """
     M = np.asarray(M, dtype=np.float64)
     s = M.shape[0]
     N = np.zeros((s, s))
     for i in range(s):
         d = M[i, i] - sum(N[l, i] * N[l, i] for l in range(i))
+        rest = [M[i, j] - sum(N[l, i] * N[l, j] for l in range(i)) for j in range(i + 1, s)]
+        if d == 0.0 and all(r == 0.0 for r in rest):
+            continue  # exactly zero component: zero row
         if not (d > 0.0) or not np.isfinite(d):
             raise Breakdown(f"Cholesky pivot {i} = {d!r}")
         N[i, i] = np.sqrt(d)
         for j in range(i + 1, s):
-            N[i, j] = (M[i, j] - sum(N[l, i] * N[l, j] for l in range(i))) / N[i, i]
+            N[i, j] = rest[j - i - 1] / N[i, i]
     return N
 
 
 def solve_upper_right(Y: np.ndarray, N: np.ndarray) -> np.ndarray:
     """Return Y N^{-1} for upper-triangular N, by substitution over columns
-    (column j of the result solves sum_{l<=j} X[:, l] N[l, j] = Y[:, j])."""
+    (column j of the result solves sum_{l<=j} X[:, l] N[l, j] = Y[:, j]).
+
+    For a zero row j of N (an exactly zero component, see ``cholesky_upper``)
+    column j of the result is zero: X N = Y then holds for every Y whose
+    columns lie in the row space of N."""
     Y = np.asarray(Y, dtype=np.float64)
     s = N.shape[0]
     X = np.zeros_like(Y)
     for j in range(s):
+        if N[j, j] == 0.0:
+            continue
         acc = Y[:, j].copy()
         for l in range(j):
             acc -= X[:, l] * N[l, j]
@@ -259,6 +274,12 @@ class LocallyOrthogonalBasis:
     Q = diag(Q_1, .., Q_p) [T_1; ..; T_p] where Q_i (n_i x k) has orthonormal
     columns and the stacked T_i (k x k each, upper triangular) are orthonormal,
     sum_i T_i^T T_i = I.  ``orthogonalize`` runs Alg. 9 (TreeTSPQR).
+
+    With a Cholesky-based local solver ('pip', 'pip2') a block that is
+    exactly zero in some column of a chunk gives that chunk a zero column in
+    Q_i (Q_i^T Q_i is then diagonal with entries 0 and 1) and a zero row in
+    T_i, so Q itself stays orthonormal; the Householder solver completes Q_i
+    with unit directions instead.
     """
 
     def __init__(self, n: int, s: int, chunk_rows: int):
@@ -295,6 +316,10 @@ class LocallyOrthogonalBasis:
         Qs = np.vstack([np.vstack([Ti, np.zeros((s, k))]) for Ti in self.T])
         Xs = np.vstack([np.vstack([Pi, Ni]) for (_, Pi, Ni) in loc])
         Us, P, N = pqr(Qs, Xs, reduction)
+        if np.any(np.diag(N) == 0.0):
+            # the block has an exactly zero component on every chunk: a global
+            # rank deficiency (the deflation case of Sec. 3, not handled)
+            raise Breakdown("the block is rank deficient against the basis")
         U = np.zeros((self.n, s))
         for i, ((b, e), (Ui, _, _)) in enumerate(zip(self.bounds, loc)):
             blk = Us[i * (k + s):(i + 1) * (k + s)]

@@ -12,6 +12,8 @@ float64 data.
   (Mezzadri 2007), computed with LAPACK through numpy (input generation only).
 * The uneven batch of the batched workload: n log-uniform, s from {4, 8, 16},
   prior blocks uniform in [1, 30].
+* Localized blocks: Gaussian columns that are exactly zero outside given row
+  ranges (the degenerate case of a block that vanishes on whole chunks).
 """
 
 from __future__ import annotations
@@ -60,6 +62,19 @@ def stewart(n: int, s: int, kappa: float, seed: int) -> np.ndarray:
     else:
         sig = np.asarray(float(kappa)) ** (-np.arange(s) / (s - 1.0))
     return np.ascontiguousarray((U * sig[None, :]) @ V.T)
+
+
+def localized(n: int, s: int, seed: int, supports) -> np.ndarray:
+    """n x s block whose column j is N(0, 1) on the row ranges supports[j]
+    (a list of (begin, end) pairs) and exactly zero elsewhere: a block of
+    point-source-like right-hand sides, which vanishes on most row chunks."""
+    X = gaussian(n, s, seed)
+    keep = np.zeros((n, s), dtype=bool)
+    for j, ranges in enumerate(supports):
+        for b, e in ranges:
+            keep[b:e, j] = True
+    X[~keep] = 0.0
+    return np.ascontiguousarray(X)
 
 
 def batch_instances(count: int, seed: int, n_lo: float = 1e4, n_hi: float = 2.0 ** 20,

@@ -355,3 +355,92 @@ def test_error_law_slopes(alg, slope):
         errs.append(O.e_perp(Q))
     fit = np.polyfit(np.log10(ks), np.log10(errs), 1)[0]
     assert abs(fit - slope) < 0.6, (alg, fit, errs)
+
+
+# ------------------------------------------------ exactly zero components
+
+def test_cholesky_zero_rows_match_lapack_on_the_rest():
+    """An exactly zero column of the factored block gives a zero row of N;
+    the other rows are LAPACK's Cholesky of the matrix without that index."""
+    B = I.gaussian(60, 6, 5)
+    B[:, [1, 4]] = 0.0
+    M = B.T @ B
+    N = O.cholesky_upper(M)
+    J = [0, 2, 3, 5]
+    assert np.all(N[[1, 4]] == 0.0) and np.all(N[:, [1, 4]] == 0.0)
+    L = np.linalg.cholesky(M[np.ix_(J, J)])
+    np.testing.assert_allclose(N[np.ix_(J, J)], L.T, rtol=0, atol=1e-13 * np.abs(L).max())
+    np.testing.assert_allclose(N.T @ N, M, rtol=0, atol=1e-12 * np.abs(M).max())
+    assert np.all(O.cholesky_upper(np.zeros((3, 3))) == 0.0)
+    # a zero pivot whose row is not zero (indefinite) still breaks down
+    with pytest.raises(O.Breakdown):
+        O.cholesky_upper(np.array([[0.0, 1.0], [1.0, 1.0]]))
+
+
+def test_solve_upper_right_zero_rows():
+    """Columns of the result at zero rows of N are zero, and X N = Y for Y in
+    the row space of N (checked against a least-squares solve)."""
+    N = np.triu(I.gaussian(5, 5, 6)) + 4 * np.eye(5)
+    N[2] = 0.0
+    Y = I.gaussian(30, 5, 7) @ N
+    X = O.solve_upper_right(Y, N)
+    assert np.all(X[:, 2] == 0.0)
+    np.testing.assert_allclose(X @ N, Y, atol=1e-12 * np.abs(Y).max())
+    Xl = np.linalg.lstsq(np.delete(N, 2, axis=0).T, Y.T, rcond=None)[0].T
+    np.testing.assert_allclose(np.delete(X, 2, axis=1), Xl, atol=1e-12)
+
+
+@pytest.mark.parametrize("local,reduction", [("pip2", "pip2"), ("pip", "pip2"), ("pip2", "hh"),
+                                             ("hh", "hh")])
+@pytest.mark.parametrize("n,chunk", [(1000, 128), (777, 100)])
+def test_tree_tspqr_blocks_vanishing_on_chunks(local, reduction, n, chunk):
+    """Blocks that are exactly zero on whole chunks or on some columns of a
+    chunk (globally of full rank): Alg. 9 still gives the unique U, P, N of
+    the direct PQR and LAPACK's QR of all blocks; Q_i^T Q_i is diagonal with
+    entries 0 and 1 for the Cholesky leaves and sum T_i^T T_i = I."""
+    s, steps = 4, 4
+    B = O.LocallyOrthogonalBasis(n, s, chunk)
+    bounds = B.bounds
+    p = len(bounds)
+    Xs = []
+    for j in range(steps):
+        # column c lives on chunks c, c + s, ... (plus the first half of chunk
+        # p - 1 for the odd steps); chunk 1 is empty for every column
+        sup = [[bounds[i] for i in range(c, p, s) if i != 1] for c in range(s)]
+        if j % 2:
+            b, e = bounds[p - 1]
+            sup = [r + [(b, (b + e) // 2)] for r in sup]
+        Xs.append(I.localized(n, s, 700 + j, sup))
+    Rfull = np.zeros((s * steps, s * steps))
+    for j, X in enumerate(Xs):
+        Ud, Pd, Nd = O.pqr_householder(B.explicit(), X)
+        U, P, N = B.orthogonalize(X, local, reduction)
+        np.testing.assert_allclose(U, Ud, atol=1e-13)
+        np.testing.assert_allclose(P, Pd, atol=1e-13)
+        np.testing.assert_allclose(N, Nd, atol=1e-12)
+        Rfull[:j * s, j * s:(j + 1) * s] = P
+        Rfull[j * s:(j + 1) * s, j * s:(j + 1) * s] = N
+        np.testing.assert_allclose(B.tree_gram(), np.eye(B.k), atol=1e-13)
+        if local != "hh":
+            G1 = B.Qloc[1].T @ B.Qloc[1]
+            assert np.all(G1 == 0.0)  # chunk 1 never saw a nonzero value
+            for Qi in B.Qloc:
+                G = Qi.T @ Qi
+                d = np.diag(G)
+                assert np.all((np.abs(d - 1) < 1e-13) | (d == 0.0))
+                np.testing.assert_allclose(G - np.diag(d), 0, atol=1e-13)
+    A = np.hstack(Xs)
+    Ql, Rl = _lapack_qr(A)
+    np.testing.assert_allclose(B.explicit(), Ql, atol=1e-12)
+    np.testing.assert_allclose(Rfull, Rl, atol=1e-11 * np.abs(Rl).max())
+    assert O.e_perp(B.explicit()) < 1e-13
+
+
+def test_block_vanishing_everywhere_in_one_column_breaks_down():
+    """A column that is zero on every chunk is a global rank deficiency (the
+    deflation case), which the Cholesky reduction reports."""
+    n, s = 512, 3
+    B = O.LocallyOrthogonalBasis(n, s, 128)
+    X = I.localized(n, s, 9, [[(0, 512)], [], [(100, 300)]])
+    with pytest.raises(O.Breakdown):
+        B.orthogonalize(X, "pip2", "pip2")
