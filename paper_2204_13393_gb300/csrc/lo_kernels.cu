@@ -36,14 +36,22 @@ __device__ __forceinline__ int passes_run(const StepArgs& a) {
 
 // In-place upper Cholesky of the s x s symmetric matrix M (row-major, smem):
 // afterwards the upper triangle holds N with N^T N = M, the lower is zero.
-// A pivot <= tol (or non-finite) sets *fail (shared memory, zeroed by the
-// caller) and, when flags is not null, latches LO_ERR_BREAKDOWN /
-// LO_ERR_NONFINITE; the pivot is replaced by 1 so that no NaN propagates.
+// A pivot that is exactly zero with the rest of its row exactly zero (the
+// block is exactly zero in that component, e.g. a column that vanishes on a
+// chunk) leaves a zero row of N: Sec. 3 allows keeping t = s and carrying the
+// rank deficiency in N.  Any other pivot <= tol (or non-finite) sets *fail
+// (shared memory, zeroed by the caller) and, when flags is not null, latches
+// LO_ERR_BREAKDOWN / LO_ERR_NONFINITE; the pivot is replaced by 1 so that no
+// NaN propagates.
 __device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail) {
   for (int i = 0; i < s; ++i) {
     if (threadIdx.x == 0) {
       double d = M[i * s + i];
-      if (!isfinite(d)) {
+      bool zero_row = d == 0.0;
+      for (int j = i + 1; j < s && zero_row; ++j) zero_row = M[i * s + j] == 0.0;
+      if (zero_row) {
+        d = 0.0;
+      } else if (!isfinite(d)) {
         if (flags) set_status(flags, LO_ERR_NONFINITE);
         *fail = 1;
         d = 1.0;
@@ -56,6 +64,10 @@ __device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail
     }
     __syncthreads();
     const double piv = M[i * s + i];
+    if (piv == 0.0) {  // zero row: nothing to divide, nothing to eliminate
+      __syncthreads();
+      continue;
+    }
     for (int j = i + 1 + threadIdx.x; j < s; j += blockDim.x) M[i * s + j] /= piv;
     __syncthreads();
     const int rem = s - i - 1;
@@ -93,12 +105,17 @@ __device__ bool cta_cholesky_shifted(double* M, double* save, int s, double tol,
   return true;
 }
 
-// X = N^{-1} for upper-triangular N (smem), column by column.
+// X = N^{-1} for upper-triangular N (smem), column by column.  Zero rows of
+// N (exactly zero components, see cta_cholesky) give zero rows and columns
+// of X: X = (N + E)^{-1} with those columns cleared (E: ones on the zero
+// rows' diagonal), so that Y X has zero columns there and Y X N = Y for Y in
+// the row space of N.
 __device__ void cta_upper_inverse(const double* N, double* X, int s) {
   for (int l = threadIdx.x; l < s; l += blockDim.x) {
+    const bool zero_col = N[l * s + l] == 0.0;
     for (int i = s - 1; i >= 0; --i) {
       double v = (i == l) ? 1.0 : 0.0;
-      if (i <= l) {
+      if (i <= l && !zero_col && N[i * s + i] != 0.0) {
         for (int j = i + 1; j <= l; ++j) v -= N[i * s + j] * X[j * s + l];
         v /= N[i * s + i];
       } else {

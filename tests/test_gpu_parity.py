@@ -607,3 +607,91 @@ def test_bounded_wait_expires_cleanly():
         ok.orthogonalize(W)
     Q = host(ok.apply_Q(dev(np.eye(ok.k))))
     assert O.e_perp(Q) <= TOL_PERP
+
+
+def vanishing_blocks(n, s, cr, count, seed0):
+    """Blocks that are exactly zero on whole chunks: column c lives on two
+    chunks, chunk 1 is empty for every column, and odd blocks add the first
+    half of the last chunk (so its local panel mixes zero and full columns)."""
+    bounds = O.chunk_bounds(n, cr)
+    p = len(bounds)
+    out = []
+    for j in range(count):
+        sup = []
+        for c in range(s):
+            chunks = {(2 + c + j) % p, (2 + c + j + p // 2) % p} - {1}
+            sup.append([bounds[i] for i in sorted(chunks)])
+        if j % 2:
+            b, e = bounds[p - 1]
+            sup = [r + [(b, (b + e) // 2)] for r in sup]
+        out.append(I.localized(n, s, seed0 + j, sup))
+    return out
+
+
+@pytest.mark.parametrize("n,s,cr,M,precision", [
+    (40000, 8, 4096, 4, "fp64"),
+    (40000, 8, 4096, 4, "fp64_tc"),
+    (20000, 4, 2048, 4, "fp64"),
+    (20000, 4, 2048, 4, "fp64_tc"),
+    (20000, 4, 2048, 1, "fp64"),      # one-block basis: the narrow k = 0 kernels
+    (70000, 16, 8192, 3, "fp64_tc"),
+    (70000, 16, 8192, 3, "mixed_tc"),
+    (40000, 8, 4096, 3, "mixed_fp32"),
+])
+def test_blocks_vanishing_on_chunks(n, s, cr, M, precision):
+    """Exactly zero components of a block on some chunks (globally of full
+    rank) give zero normalizer rows locally and zero columns in the local
+    panels; U, H, R match the unique solution of the oracle, the local
+    representation matches the oracle's Cholesky leaf, and Q is orthonormal."""
+    blocks = vanishing_blocks(n, s, cr, M, 4100 + s)
+    b = lo().Basis(n, s, M, cr, precision=precision)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    ora_loc = O.LocallyOrthogonalBasis(n, s, cr)
+    A = np.hstack(blocks)
+    Rfull = np.zeros((A.shape[1], A.shape[1]))
+    for j, Wh in enumerate(blocks):
+        U, H, R = b.orthogonalize(dev(Wh))
+        Uo, Po, No = ora.orthogonalize(Wh, "hh", "hh")
+        ora_loc.orthogonalize(Wh, "pip2", "hh")
+        assert rel(host(U), Uo) <= TOL_REL, (j, rel(host(U), Uo))
+        assert rel(host(R), No) <= TOL_REL, (j, rel(host(R), No))
+        if j > 0:
+            assert rel(host(H), Po) <= TOL_REL, (j, rel(host(H), Po))
+            Rfull[:j * s, j * s:(j + 1) * s] = host(H)
+        Rfull[j * s:(j + 1) * s, j * s:(j + 1) * s] = host(R)
+    Q = host(b.apply_Q(dev(np.eye(b.k))))
+    assert O.e_perp(Q) <= TOL_PERP
+    assert O.residual(A, Q, Rfull) <= TOL_RES
+    if precision in ("fp64", "fp64_tc"):
+        for c in range(b.num_chunks):
+            Qi, Ti = b.export_chunk(c)
+            assert rel(Qi, ora_loc.Qloc[c]) <= TOL_REL, c
+            assert rel(Ti, np.triu(ora_loc.T[c])) <= TOL_REL, c
+            G = Qi.T @ Qi
+            d = np.diag(G)
+            assert np.all((np.abs(d - 1) <= TOL_PERP) | (d == 0.0)), c
+            assert np.abs(G - np.diag(d)).max() <= TOL_PERP, c
+        Qi, _ = b.export_chunk(1)
+        assert np.all(Qi == 0.0)  # chunk 1 never saw a nonzero value
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+def test_component_vanishing_everywhere_is_a_breakdown(precision):
+    """A column that is zero on every chunk is a global rank deficiency (the
+    unsupported deflation case): LO_ERR_BREAKDOWN, basis unchanged."""
+    L = lo()
+    n, s, cr = 16384, 8, 2048
+    b = L.Basis(n, s, 3, cr, precision=precision)
+    b.orthogonalize(dev(I.gaussian(n, s, 4200)))
+    Wz = I.gaussian(n, s, 4201)
+    Wz[:, 5] = 0.0
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(dev(Wz))
+    assert e.value.name == "LO_ERR_BREAKDOWN"
+    assert b.num_blocks == 1
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    ora.orthogonalize(I.gaussian(n, s, 4200), "hh", "hh")
+    Wg = I.gaussian(n, s, 4202)
+    U, H, R = b.orthogonalize(dev(Wg))
+    Uo, Po, No = ora.orthogonalize(Wg, "hh", "hh")
+    assert rel(host(U), Uo) <= TOL_REL and rel(host(H), Po) <= TOL_REL and rel(host(R), No) <= TOL_REL
