@@ -44,19 +44,25 @@ S = 8
 M_RESTART = 30
 CHUNK = 4096
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2204_13393_gb300", "csrc", f)
-               for f in ("lo_kernels.cu", "lo_ozaki.cu", "lo_umma.cu", "lo_oz_common.cuh", "lo_recombine.h")]
+# The translation unit (with the headers it includes) of each kernel whose DRAM
+# traffic was captured: a change to any of these files invalidates the capture.
+KERNEL_TU = {
+    "k_umma_update": ["paper_2204_13393_gb300/csrc/lo_umma.cu", "paper_2204_13393_gb300/csrc/lo_oz_common.cuh",
+                      "paper_2204_13393_gb300/csrc/lo_recombine.h", "paper_2204_13393_gb300/csrc/lo_internal.h",
+                      "include/lo.h"],
+}
 # DRAM bytes of one launch of the dominant kernel from one ncu capture (bench.py
 # --case profile: n = 2^20, s = 8, k = 120), with that launch's algorithmic bytes,
-# keyed by (kernel group, precision, sha256 prefix of the kernel sources).  The
-# reported traffic scales the measured ratio to the average launch of the cycle;
-# a source change invalidates the entry (traffic: null).
+# keyed by (kernel group, precision); "src" is the sha256 prefix of the kernel's
+# translation unit when the counters were taken.  The reported traffic scales the
+# measured ratio to the average launch of the cycle; a source change invalidates
+# the entry (traffic: null).
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #     --clock-control none --profile-from-start off -k regex:k_umma_update -s 2 -c 1
     #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 659.2 us)
-    ("update", "fp64_tc", "ca23dfef1ab44755"): {"dram_bytes": 1955506432 + 129825024,
-                                                "algorithmic_bytes": 1210056704},
+    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "98dd4f59a2e47380",
+                            "dram_bytes": 1955506432 + 129825024, "algorithmic_bytes": 1210056704},
 }
 
 
@@ -96,12 +102,18 @@ def gram_bytes_flops(n, s, k):
     return 8 * n * (k + s), 2 * n * (k + s) * s
 
 
-def src_hash():
+def src_hash(kernel):
     h = hashlib.sha256()
-    for path in KERNEL_SRCS:
-        with open(path, "rb") as f:
+    for rel in KERNEL_TU[kernel]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def traffic_capture(group, precision):
+    """The ncu capture of this kernel group's dominant kernel, if its sources are unchanged."""
+    cap = TRAFFIC.get((group, precision))
+    return cap if cap and cap["src"] == src_hash(cap["kernel"]) else None
 
 
 class Clocks:
@@ -298,7 +310,7 @@ def run_gpu(args):
     t_dom = kinds[dom][0] * 1e-3
     ach_gbs = bsum / t_dom / 1e9
     ach_tf = fsum / t_dom / 1e12
-    cap = TRAFFIC.get((dom, args.precision, src_hash()))
+    cap = traffic_capture(dom, args.precision)
     launches_dom = kinds[dom][1]
     traffic = (round(cap["dram_bytes"] / cap["algorithmic_bytes"] * bsum / launches_dom)
                if cap else None)
