@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "lo_internal.h"
+#include "lo_recombine.h"
 
 namespace lo {
 namespace {
@@ -165,6 +166,68 @@ __global__ void k_step_begin(int* flags, int force_pass2, int force_tree2) {
   }
 }
 
+// float64 -> float32 with integer operations only (round toward zero; |x| below
+// 2^-126 flushes to a signed zero, above the float32 range becomes a signed
+// infinity).  Used by the float32 first pass of the mixed form so that it never
+// issues work to GB300's narrow float64 pipe.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned r = sign | ((unsigned)(e - 896) << 23) | mant;
+  if (e < 897) r = sign;
+  if (e > 1150) r = sign | 0x7F800000u;
+  return __uint_as_float(r);
+}
+
+// f32_trunc(x * 2^sh) for an integer sh, by moving the exponent field
+// (zero and subnormal x give a signed zero).  The float32 first pass scales
+// each column of the block by a power of two so that its largest entry on
+// the slab lies in [1, 2): the float32 products then neither overflow nor
+// underflow whatever the block's magnitude, and the scaling is undone
+// exactly in float64 on the partial.
+__device__ __forceinline__ float f32_trunc_shift(double x, int sh) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu), es = e + sh;
+  if (e == 0 || es < 897) return __uint_as_float(sign);
+  if (es > 1150) return __uint_as_float(sign | 0x7F800000u);
+  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  return __uint_as_float(sign | ((unsigned)(es - 896) << 23) | mant);
+}
+
+// Largest biased exponent of each of the S columns of the block over the
+// slab's rows (0 for a zero column), into hs[0 .. S).  Whole CTA.
+template <typename F>
+__device__ __forceinline__ void slab_col_exponents(int* hs, int S, int rows, F&& value) {
+  if ((int)threadIdx.x < S) hs[threadIdx.x] = 0;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rows * S; idx += blockDim.x) {
+    const int r = idx / S, l = idx - r * S;
+    atomicMax(&hs[l], (int)((((unsigned long long)__double_as_longlong(value(r, l))) >> 52) & 0x7FF));
+  }
+  __syncthreads();
+}
+
+// The shift that brings a column with largest biased exponent h to [1, 2).
+__device__ __forceinline__ int col_shift(int h) { return h == 0 ? 0 : 1023 - h; }
+
+template <typename Acc>
+__device__ __forceinline__ Acc load_as(const double* p);
+template <>
+__device__ __forceinline__ double load_as<double>(const double* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_as<float>(const double* p) { return f32_trunc(__ldg(p)); }
+template <typename Acc>
+__device__ __forceinline__ Acc load_scaled(const double* p, int sh);
+template <>
+__device__ __forceinline__ double load_scaled<double>(const double* p, int) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_scaled<float>(const double* p, int sh) { return f32_trunc_shift(__ldg(p), sh); }
+
 // ---------------------------------------------------------------------------
 // Stage 1, Gram pass `pass` over one row slab of one chunk (Alg. 7 first line,
 // "at once"): the partial of C_i = [Q_i A_i]^T A_i where A_i is the block of
@@ -196,6 +259,11 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
   const double* Plast = smallc + SL.P_last;
   const double* Ninv = smallc + SL.Ninv_last;
   double* slot = a.V + (int64_t)a.nb * a.n * s;
+  // float32 first pass: the block's columns scaled per slab (see f32_trunc_shift)
+  constexpr bool kF32 = sizeof(TileT) == 4;
+  __shared__ int hs[32];
+  if (kF32) slab_col_exponents(hs, s, si.rows, [&](int r, int l) { return a.W[(si.row0 + r) * a.ldw + l]; });
+  auto out_scale = [&](int e) { return kF32 ? -col_shift(hs[e % s]) - (e / s >= k ? col_shift(hs[e / s - k]) : 0) : 0; };
 
   for (int r0 = 0; r0 < si.rows; r0 += tile_rows) {
     const int rows = min(tile_rows, si.rows - r0);
@@ -208,7 +276,8 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
     if (pass == 1) {
       for (int idx = tid; idx < rows * s; idx += kThreads) {
         const int r = idx / s, l = idx - r * s;
-        A[r * Kt + k + l] = (TileT)a.W[(grow0 + r) * a.ldw + l];
+        const double w = a.W[(grow0 + r) * a.ldw + l];
+        A[r * Kt + k + l] = kF32 ? (TileT)f32_trunc_shift(w, col_shift(hs[l])) : (TileT)w;
       }
     } else {
       __syncthreads();
@@ -252,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int e = tid + j * kThreads;
-      if (j < J && e < E) out[e] = (double)acc[j];
+      if (j < J && e < E) out[e] = kF32 ? scale2((double)acc[j], out_scale(e)) : (double)acc[j];
     }
   } else {
     // fixed-order sum over the G row groups
@@ -262,33 +331,11 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
     if (tid < E) {
       double v = 0.0;
       for (int gg = 0; gg < G; ++gg) v += red[gg * E + tid];
-      out[tid] = v;
+      out[tid] = kF32 ? scale2(v, out_scale(tid)) : v;
     }
   }
 }
 
-// float64 -> float32 with integer operations only (round toward zero; |x| below
-// 2^-126 flushes to a signed zero, above the float32 range becomes a signed
-// infinity).  Used by the float32 first pass of the mixed form so that it never
-// issues work to GB300's narrow float64 pipe.
-__device__ __forceinline__ float f32_trunc(double x) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(bits >> 32), lo = (unsigned)bits;
-  const unsigned sign = hi & 0x80000000u;
-  const int e = (int)((hi >> 20) & 0x7FFu);
-  const unsigned mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  unsigned r = sign | ((unsigned)(e - 896) << 23) | mant;
-  if (e < 897) r = sign;
-  if (e > 1150) r = sign | 0x7F800000u;
-  return __uint_as_float(r);
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc load_as(const double* p);
-template <>
-__device__ __forceinline__ double load_as<double>(const double* p) { return __ldg(p); }
-template <>
-__device__ __forceinline__ float load_as<float>(const double* p) { return f32_trunc(__ldg(p)); }
 
 // Stage 1, first Gram pass, for block widths S in {1, 2, 4, 8, 16, 32}: the
 // partial of C_i = [Q_i W_i]^T W_i over one slab.  Each thread keeps a
@@ -306,18 +353,17 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
   const int tid = threadIdx.x, g = tid / T, t = tid - g * T;
   const bool active = g < G;
   const int q0 = t * TQ;
-  if (a.srcexp_slab) {  // tensor-core assembly follows: the block's column exponents per slab
-    __shared__ int hs[32];
-    if (tid < 32) hs[tid] = 0;
-    __syncthreads();
-    for (int idx = tid; idx < si.rows * S; idx += kThreads) {
-      const int r = idx / S, l = idx - r * S;
-      const int ex = (int)((((unsigned long long)__double_as_longlong(a.W[(si.row0 + r) * a.ldw + l])) >> 52) & 0x7FF);
-      atomicMax(&hs[l], ex);
-    }
-    __syncthreads();
-    if (tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = hs[tid];
+  constexpr bool kF32 = sizeof(Acc) == 4;
+  __shared__ int hs[32];
+  if (a.srcexp_slab || kF32) {
+    // the block's column exponents on this slab: for a tensor-core assembly
+    // that follows, and for the scaling of the float32 pass
+    slab_col_exponents(hs, S, si.rows, [&](int r, int l) { return a.W[(si.row0 + r) * a.ldw + l]; });
+    if (a.srcexp_slab && tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = hs[tid];
   }
+  int sh[S];
+#pragma unroll
+  for (int l = 0; l < S; ++l) sh[l] = kF32 ? col_shift(hs[l]) : 0;
   Acc acc[TQ][S];
 #pragma unroll
   for (int i = 0; i < TQ; ++i)
@@ -329,7 +375,7 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
       const double* wr = a.W + row * a.ldw;
       Acc b[S];
 #pragma unroll
-      for (int l = 0; l < S; ++l) b[l] = load_as<Acc>(wr + l);
+      for (int l = 0; l < S; ++l) b[l] = load_scaled<Acc>(wr + l, sh[l]);
       Acc av[TQ];
 #pragma unroll
       for (int i = 0; i < TQ; ++i) {
@@ -337,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
         if (q < k)
           av[i] = load_as<Acc>(a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S));
         else if (q < Kt)
-          av[i] = load_as<Acc>(wr + (q - k));
+          av[i] = load_scaled<Acc>(wr + (q - k), kF32 ? col_shift(hs[q - k]) : 0);
         else
           av[i] = Acc(0);
       }
@@ -357,6 +403,7 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
     const int q = e / S, l = e - q * S, tt = q / TQ, i = q - tt * TQ;
     double v = 0.0;
     for (int gg = 0; gg < G; ++gg) v += red[(gg * T + tt) * (TQ * S) + i * S + l];
+    if (kF32) v = scale2(v, -col_shift(hs[l]) - (q >= k ? col_shift(hs[q - k]) : 0));
     out[e] = v;
   }
 }

@@ -695,3 +695,46 @@ def test_component_vanishing_everywhere_is_a_breakdown(precision):
     U, H, R = b.orthogonalize(dev(Wg))
     Uo, Po, No = ora.orthogonalize(Wg, "hh", "hh")
     assert rel(host(U), Uo) <= TOL_REL and rel(host(H), Po) <= TOL_REL and rel(host(R), No) <= TOL_REL
+
+
+@pytest.mark.parametrize("n,s,cr,M,precision", [
+    (40000, 8, 4096, 3, "fp64"),
+    (40000, 8, 4096, 3, "fp64_tc"),
+    (20000, 4, 2048, 3, "fp64"),
+    (20000, 4, 2048, 1, "fp64_tc"),
+    (70000, 16, 8192, 3, "fp64_tc"),
+    (70000, 16, 8192, 3, "mixed_tc"),
+    (40000, 8, 4096, 3, "mixed_fp32"),
+    (30000, 3, 4096, 3, "mixed_fp32"),
+])
+def test_power_of_two_scaling_is_exact(n, s, cr, M, precision):
+    """The PQR of 2^j W is (U, 2^j H, 2^j R).  Every form scales by exponent
+    (float64 arithmetic, the digit splits against column exponents, the
+    float32 pass's per-slab column scaling), so blocks scaled by 2^300 and
+    2^-300 -- whose products overflow or underflow float32 -- give the same
+    U and Q bit for bit and H, R scaled bit for bit; the unscaled run
+    matches the oracle."""
+    blocks = gaussian_blocks(n, s, M, 4300 + s)
+    runs = {}
+    for j in (0, 300, -300):
+        b = lo().Basis(n, s, M, cr, precision=precision)
+        res = []
+        for Wh in blocks:
+            U, H, R = b.orthogonalize(dev(np.ldexp(Wh, j)))
+            res.append((host(U), np.zeros((0, s)) if H is None else host(H), host(R)))
+        runs[j] = (res, host(b.apply_Q(dev(np.eye(b.k)))))
+        b.close()
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    for (U, H, R), Wh in zip(runs[0][0], blocks):
+        Uo, Po, No = ora.orthogonalize(Wh, "hh", "hh")
+        assert rel(U, Uo) <= TOL_REL and rel(R, No) <= TOL_REL
+        if Po.size:
+            assert rel(H, Po) <= TOL_REL
+    assert O.e_perp(runs[0][1]) <= TOL_PERP
+    for j in (300, -300):
+        res, Q = runs[j]
+        assert np.array_equal(Q, runs[0][1]), j
+        for i, ((U, H, R), (U0, H0, R0)) in enumerate(zip(res, runs[0][0])):
+            assert np.array_equal(U, U0), (j, i, rel(U, U0))
+            assert np.array_equal(H, np.ldexp(H0, j)), (j, i)
+            assert np.array_equal(R, np.ldexp(R0, j)), (j, i, rel(R, np.ldexp(R0, j)))

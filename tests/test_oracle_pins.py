@@ -444,3 +444,21 @@ def test_block_vanishing_everywhere_in_one_column_breaks_down():
     X = I.localized(n, s, 9, [[(0, 512)], [], [(100, 300)]])
     with pytest.raises(O.Breakdown):
         B.orthogonalize(X, "pip2", "pip2")
+
+
+@pytest.mark.parametrize("local,reduction", [("hh", "hh"), ("pip2", "pip2")])
+def test_power_of_two_scaling_commutes(local, reduction):
+    """The PQR of 2^j X is (U, 2^j P, 2^j N) (eq. (pqr) is homogeneous in X);
+    products, sums, quotients and square roots commute with power-of-two
+    scaling, so the oracle's results scale bit for bit."""
+    n, s, cr = 600, 3, 128
+    Xs = [I.gaussian(n, s, 4400 + j) for j in range(3)]
+    runs = {}
+    for j in (0, 300, -300):
+        B = O.LocallyOrthogonalBasis(n, s, cr)
+        runs[j] = [B.orthogonalize(np.ldexp(X, j), local, reduction) for X in Xs]
+    for j in (300, -300):
+        for (U, P, N), (U0, P0, N0) in zip(runs[j], runs[0]):
+            assert np.array_equal(U, U0)
+            assert np.array_equal(P, np.ldexp(P0, j))
+            assert np.array_equal(N, np.ldexp(N0, j))
