@@ -196,7 +196,12 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw,
  * stage), computed chunk-wise as Y_i = Q_i (T_i C).  C is k x m row-major
  * (k = num_blocks*s, row stride ldc >= m), host or device; Y is n x m
  * (row stride ldy >= m), host or device.  With C = I_k this materializes the
- * explicit basis.  1 <= m <= 1024.
+ * explicit basis.  1 <= m <= 1024.  A basis with digit planes (tensor-core
+ * forms, s in {8, 16, 32}, at least two blocks) computes the products on the
+ * tensor cores with float64 accuracy, one assembly per s columns of C; other
+ * bases use float64 arithmetic.  Errors latched by the device (a non-finite C:
+ * LO_ERR_NONFINITE; LO_ERR_TIMEOUT) are returned when the call synchronizes
+ * (host Y or the sync option), else by the next call or lo_basis_sync.
  */
 lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc,
                      double* Y, int64_t ldy);

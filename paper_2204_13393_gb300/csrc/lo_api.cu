@@ -739,10 +739,7 @@ lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc, doubl
                           st);
     if (e != cudaSuccess) return from_cuda(e);
   }
-  if (b->opt.sync || !y_dev) {
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return from_cuda(e);
-  }
+  if (b->opt.sync || !y_dev) return read_status(b, st);  // the tensor-core form can latch a status
   return LO_OK;
 }
 

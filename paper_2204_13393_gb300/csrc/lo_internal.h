@@ -123,6 +123,12 @@ struct StepArgs {
   int64_t dtiles;            // 16-row tiles of the slab tiling
   const struct UmmaMaps* maps;  // host-side TMA descriptors of dig (lo_umma.cu)
   int32_t test_stall;           // test hook: the k > 0 tensor-core Gram issues nothing (lo_options)
+  // apply_Q on the tensor cores: k_umma_update<S, 1> writes columns
+  // apply_n0 .. apply_n0 + S - 1 (those below apply_m) of Y = apply_y (device,
+  // row stride apply_ldy) instead of the new panel; null in the steps
+  double* apply_y;
+  int64_t apply_ldy;
+  int apply_m, apply_n0;
 };
 
 // TMA descriptors of a basis's digit planes: one box shape per kernel.
@@ -172,6 +178,12 @@ cudaError_t launch_fill_pattern(double* X, int64_t count, cudaStream_t st);
 
 // Launchers (lo_kernels.cu).  All enqueue on `st` and return the launch error.
 cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook);
+// Y = Q C on the tensor cores (digit planes of every panel but the last, which
+// is split on the fly); false when the basis has no such form (then the
+// float64 kernels run).
+bool umma_apply_supported(const StepArgs& a);
+cudaError_t launch_umma_apply(const StepArgs& a, const double* C, int64_t ldc, int m, double* Y, int64_t ldy,
+                              cudaStream_t st);
 cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ldc, double* Z,
                            double* Y, int64_t ldy, cudaStream_t st, ProfHook* hook);
 // Tensor-core (Ozaki) launchers (lo_ozaki.cu).

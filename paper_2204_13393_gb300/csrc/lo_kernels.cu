@@ -1142,6 +1142,14 @@ cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ld
   cudaError_t e = set_attrs();
   if (e) return e;
   const int k = a.nb * a.s;
+  if (umma_apply_supported(a)) {  // digit planes of the panels: the tensor-core assembly
+    if ((e = umma_set_attrs())) return e;
+    mark(hook, kKindApply, true, st);
+    e = launch_umma_apply(a, C, ldc, m, Y, ldy, st);
+    mark(hook, kKindApply, false, st);
+    count_launches(2 * ((m + a.s - 1) / a.s));
+    return e;
+  }
   mark(hook, kKindApply, true, st);
   k_apply_z<<<a.p, kThreads, 0, st>>>(a, C, m, ldc, Z);
   int tr = kTileSmem / (8 * (k > 0 ? k : 1));

@@ -147,6 +147,50 @@ __device__ __forceinline__ void group_mma(float (&acc)[kGroupPairs][4], const un
   for_group_pairs<G>([&](int idx, int t, int u) { mma_f16(acc[idx], af[t - 1], bf[u - 1][0], bf[u - 1][1]); });
 }
 
+// The B operand of k_umma_update for one chunk: the scaled coefficient Cf
+// (Kt x NC, row-major) split against its column exponents Gs into 7 digits.
+// Per (output group z of NB columns, 16-column step ks) one R x 16 K-major
+// no-swizzle tile, R = round16(7 NB): row (u - 1) NB + n holds digit u of
+// coefficient (16 ks + kk, z NB + n); rows past 7 NB and columns past Kt are
+// zero.  KS: steps per output group in the image.  Whole CTA.
+template <int NC>
+__device__ void umma_coef_image(const double* Cf, const int* Gs, int Kt, int KS, unsigned char* img, int* flags) {
+  constexpr int NB = NC < 16 ? NC : 16, NSPL = NC / NB, R = (7 * NB + 15) / 16 * 16;
+  const int ksteps = (Kt + 15) / 16, tid = threadIdx.x;
+  // one item = (split z, step ks, row n of the split, K quad kq): 4 coefficients
+  for (int it = tid; it < NSPL * ksteps * NB * 4; it += blockDim.x) {
+    const int kq = it & 3, rest = it >> 2;
+    const int n = rest % NB, zks = rest / NB, ks = zks % ksteps, z = zks / ksteps;
+    const int col = z * NB + n, q0 = ks * 16 + kq * 4;
+    double x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = (q0 + j < Kt) ? Cf[(q0 + j) * NC + col] : 0.0;
+    const int e = Gs[col];
+    unsigned h[4], l[4], g[4];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bad |= oz_split(x[j], e, h[j], l[j], g[j]);
+    if (bad) oz_status(flags, LO_ERR_NONFINITE);
+    unsigned char* base = img + (int64_t)(z * KS + ks) * R * 32 + (kq & 1) * 8 + (kq >> 1) * 128;
+#pragma unroll
+    for (int u = 1; u <= kOzDigits; ++u) {
+      const int row = (u - 1) * NB + n;
+      const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
+      const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
+      *reinterpret_cast<uint2*>(base + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
+    }
+  }
+  if constexpr (R > 7 * NB) {  // pad rows
+    for (int it = tid; it < NSPL * ksteps * (R - 7 * NB) * 4; it += blockDim.x) {
+      const int kq = it & 3, rest = it >> 2;
+      const int pr = rest % (R - 7 * NB), zks = rest / (R - 7 * NB), ks = zks % ksteps, z = zks / ksteps;
+      const int row = 7 * NB + pr;
+      unsigned char* base = img + (int64_t)(z * KS + ks) * R * 32 + (kq & 1) * 8 + (kq >> 1) * 128;
+      *reinterpret_cast<uint2*>(base + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(0u, 0u);
+    }
+  }
+}
+
 // v * 2^X by adding X to the exponent field when the result stays normal
 // (integer work only); otherwise through scale2.
 __device__ __forceinline__ double scale_exp(double v, int X) {

@@ -310,41 +310,7 @@ __global__ void __launch_bounds__(256) k_oz_coef(StepArgs a, int pass) {
     return;
   }
   if constexpr (MODE == 1) {
-    constexpr int NB = NC < 16 ? NC : 16, NSPL = NC / NB, R = (7 * NB + 15) / 16 * 16;
-    const int KS = (a.Kmax + 15) / 16;
-    unsigned char* img = reinterpret_cast<unsigned char*>(dig);
-    // one item = (split z, step ks, row n of the split, K quad kq): 4 coefficients
-    for (int it = tid; it < NSPL * ksteps * NB * 4; it += 256) {
-      const int kq = it & 3, rest = it >> 2;
-      const int n = rest % NB, zks = rest / NB, ks = zks % ksteps, z = zks / ksteps;
-      const int col = z * NB + n, q0 = ks * 16 + kq * 4;
-      double x[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) x[j] = (q0 + j < Kt) ? Cf[(q0 + j) * NC + col] : 0.0;
-      const int e = Gs[col];
-      unsigned h[4], l[4], g[4];
-      bool bad = false;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) bad |= oz_split(x[j], e, h[j], l[j], g[j]);
-      if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-      unsigned char* base = img + (int64_t)(z * KS + ks) * R * 32 + (kq & 1) * 8 + (kq >> 1) * 128;
-#pragma unroll
-      for (int u = 1; u <= kOzDigits; ++u) {
-        const int row = (u - 1) * NB + n;
-        const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
-        const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]);
-        *reinterpret_cast<uint2*>(base + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
-      }
-    }
-    if constexpr (R > 7 * NB) {  // pad rows
-      for (int it = tid; it < NSPL * ksteps * (R - 7 * NB) * 4; it += 256) {
-        const int kq = it & 3, rest = it >> 2;
-        const int pr = rest % (R - 7 * NB), zks = rest / (R - 7 * NB), ks = zks % ksteps, z = zks / ksteps;
-        const int row = 7 * NB + pr;
-        unsigned char* base = img + (int64_t)(z * KS + ks) * R * 32 + (kq & 1) * 8 + (kq >> 1) * 128;
-        *reinterpret_cast<uint2*>(base + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(0u, 0u);
-      }
-    }
+    umma_coef_image<NC>(Cf, Gs, Kt, (a.Kmax + 15) / 16, reinterpret_cast<unsigned char*>(dig), a.flags);
     for (int n = tid; n < NC; n += 256) a.coefexp[(int64_t)c * 64 + n] = Gs[n];
     // the new iterate's exponents per slab are maxima k_umma_update accumulates
     if (NOUT == 1)

@@ -656,7 +656,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 // U may alias W), so no row is written before every group has read it.
 // NOUT = 1: the reiteration's new iterate into the new panel, and its column
 // exponents per slab; NOUT = 2: U_i into the panel and U to the caller, and
-// the panel's column exponents.
+// the panel's column exponents.  APPLY (apply_Q, NOUT = 1, a.apply_y set):
+// [Q_i A] is the basis itself -- A the last panel, whose digits are never
+// stored -- and the coefficient T_i C; the result goes to the caller's Y.
 template <int S, int NOUT>
 struct UpdLayout {
   static constexpr int NC = NOUT * S, NB = NC < 16 ? NC : 16, NSPL = NC / NB;
@@ -700,13 +702,14 @@ struct UpdCursor {
   }
 };
 
-template <int S, int NOUT>
+template <int S, int NOUT, bool APPLY = false>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_umma_update(StepArgs a, const double* src_fixed, int64_t lds_fixed, int pass,
                   const __grid_constant__ CUtensorMap tm) {
   using L = UpdLayout<S, NOUT>;
   constexpr int NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL, NACC = umma_nacc(NB);
-  if (NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
+  static_assert(!APPLY || NOUT == 1, "apply_Q has one output");
+  if (!APPLY && NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -937,7 +940,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
             for (int j = 0; j < NB; ++j) {
               const int n = zz * NB + j;
               const double d = scale_exp(res[zz][j], a.coefexp[(int64_t)cur.chunk * 64 + n] - 1022 - 16);
-              if (n < S) {
+              if constexpr (APPLY) {  // apply_Q: the caller's Y, no exponent bookkeeping
+                if (in && a.apply_n0 + n < a.apply_m) a.apply_y[row * a.apply_ldy + a.apply_n0 + n] = d;
+              } else if (n < S) {
                 if (in) slot[row * S + n] = d;
                 // the column's largest exponent over the slab (NOUT = 1) or chunk (NOUT = 2)
                 const int ex = __reduce_max_sync(0xffffffffu, in ? bexp(d) : 0);
@@ -1585,10 +1590,87 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// apply_Q on the tensor cores (Sec. 5.1, the product Q C, chunk-wise as
+// Y_i = Q_i (T_i C)): the coefficient of chunk c for the output columns
+// apply_n0 .. + S - 1 is Z_c = T_c C (Kt x S, Kt = (a.nb + 1) S: a.nb panels
+// with digit planes and the last panel), each row scaled by the exponent its
+// local column is aligned to, split into the image k_umma_update reads.  The
+// last panel is the assembly's own block: its per-chunk column exponents go
+// to srcexp, from where the producers split it.
+template <int S>
+__global__ void __launch_bounds__(256) k_apply_coef(StepArgs a, const double* C, int64_t ldc) {
+  extern __shared__ __align__(16) double smc[];
+  const int c = blockIdx.x, nbf = a.nb + 1, Kt = nbf * S, k = a.nb * S, tid = threadIdx.x;
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* Cf = smc;                                       // Kt x S
+  int* Gs = reinterpret_cast<int*>(Cf + (size_t)Kt * S);  // S
+  if (tid < S) {
+    Gs[tid] = 0;
+    a.srcexp[(int64_t)c * 32 + tid] = a.colexp[(int64_t)(k + tid) * a.p + c];
+  }
+  __syncthreads();
+  for (int e = tid; e < Kt * S; e += 256) {
+    const int r = e / S, j = e - r * S, col = a.apply_n0 + j;
+    double v = 0.0;
+    if (col < a.apply_m)
+      for (int cb = r / S; cb < nbf; ++cb) {  // T_c is block upper triangular
+        const double* Tb = Tc + tblock_offset(cb, S);
+        for (int qq = 0; qq < S; ++qq) v += Tb[r * S + qq] * C[(int64_t)(cb * S + qq) * ldc + col];
+      }
+    const int F = a.colexp[(int64_t)r * a.p + c];
+    v = (F == 0 || v == 0.0) ? 0.0 : scale2(v, F - 1022);
+    Cf[e] = v;
+    atomicMax(&Gs[j], bexp(v));
+  }
+  __syncthreads();
+  umma_coef_image<S>(Cf, Gs, Kt, (a.Kmax + 15) / 16,
+                     reinterpret_cast<unsigned char*>(a.coefdig + (int64_t)c * a.coefdig_stride), a.flags);
+  if (tid < S) a.coefexp[(int64_t)c * 64 + tid] = Gs[tid];
+}
+
+template <int S>
+size_t apply_coef_smem(int Kt) {
+  return sizeof(double) * (size_t)Kt * S + sizeof(int) * 64;
+}
+
+template <int S>
+cudaError_t umma_apply_for(const StepArgs& a0, const double* C, int64_t ldc, int m, double* Y, int64_t ldy,
+                           cudaStream_t st) {
+  using L = UpdLayout<S, 1>;
+  StepArgs a = a0;
+  a.nb = a0.nb - 1;  // panels with digit planes; the last is split on the fly
+  a.apply_y = Y;
+  a.apply_ldy = ldy;
+  a.apply_m = m;
+  const double* last = a0.V + (int64_t)(a0.nb - 1) * a0.n * S;
+  dim3 grid(a.nslab < umma_sms() ? a.nslab : umma_sms());
+  for (int n0 = 0; n0 < m; n0 += S) {
+    a.apply_n0 = n0;
+    k_apply_coef<S><<<a.p, 256, apply_coef_smem<S>(a0.nb * S), st>>>(a, C, ldc);
+    k_umma_update<S, 1, true><<<grid, kUmmaThreads, L::BYTES, st>>>(a, last, S, 0, a.maps->upd);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 bool umma_enabled(const StepArgs& a) {
   return a.dig != nullptr && a.nb >= 1 && (a.s == 8 || a.s == 16 || a.s == 32);
+}
+
+bool umma_apply_supported(const StepArgs& a) {
+  return a.dig != nullptr && a.colexp != nullptr && a.maps != nullptr && a.nb >= 2 &&
+         (a.s == 8 || a.s == 16 || a.s == 32);
+}
+
+cudaError_t launch_umma_apply(const StepArgs& a, const double* C, int64_t ldc, int m, double* Y, int64_t ldy,
+                              cudaStream_t st) {
+  switch (a.s) {
+    case 8: return umma_apply_for<8>(a, C, ldc, m, Y, ldy, st);
+    case 16: return umma_apply_for<16>(a, C, ldc, m, Y, ldy, st);
+    case 32: return umma_apply_for<32>(a, C, ldc, m, Y, ldy, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t umma_set_attrs() {
@@ -1606,6 +1688,12 @@ cudaError_t umma_set_attrs() {
     return e;                                                                                                   \
   if ((e = cudaFuncSetAttribute(k_umma_update<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
                                 UpdLayout<S, 2>::BYTES)))                                                       \
+    return e;                                                                                                   \
+  if ((e = cudaFuncSetAttribute(k_umma_update<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                UpdLayout<S, 1>::BYTES)))                                                       \
+    return e;                                                                                                   \
+  if ((e = cudaFuncSetAttribute(k_apply_coef<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
+                                (int)apply_coef_smem<S>(kMaxKS / S))))                                          \
     return e;
   LO_UMMA_ATTR(8)
   LO_UMMA_ATTR(16)

@@ -738,3 +738,44 @@ def test_power_of_two_scaling_is_exact(n, s, cr, M, precision):
             assert np.array_equal(U, U0), (j, i, rel(U, U0))
             assert np.array_equal(H, np.ldexp(H0, j)), (j, i)
             assert np.array_equal(R, np.ldexp(R0, j)), (j, i, rel(R, np.ldexp(R0, j)))
+
+
+@pytest.mark.parametrize("n,s,cr,M,nb,precision", [
+    (40000, 8, 4096, 5, 5, "fp64_tc"),      # full basis: the last panel has no digit planes
+    (40000, 8, 4096, 5, 3, "fp64_tc"),      # the last panel has planes but is split all the same
+    (70001, 16, 8192, 4, 4, "fp64_tc"),     # ragged slabs and last chunk
+    (50000, 32, 8192, 3, 3, "fp64_tc"),     # two output groups per assembly
+    (40000, 8, 4096, 4, 4, "mixed_tc"),
+])
+def test_apply_Q_tensor_cores(n, s, cr, M, nb, precision):
+    """apply_Q of a basis with digit planes runs the tensor-core assembly:
+    Y = Q C matches the float64 product of the basis's own representation
+    (sum over chunks of Q_i (T_i C), evaluated on the host) to float64
+    accuracy and the oracle's basis within the parity tolerance, for m below,
+    equal to and above s, host and device buffers, and a strided Y."""
+    L = lo()
+    b = L.Basis(n, s, M, cr, precision=precision)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    for j in range(nb):
+        Wh = I.gaussian(n, s, 4500 + j)
+        b.orthogonalize(dev(Wh))
+        ora.orthogonalize(Wh, "hh", "hh")
+    rep = O.LocallyOrthogonalBasis(n, s, cr)  # the GPU basis's own representation
+    for c in range(b.num_chunks):
+        rep.Qloc[c], rep.T[c] = b.export_chunk(c)
+    before = L.launch_count()
+    for m in (1, s - 3, s, s + 5, 2 * s + 1):
+        C = I.gaussian(b.k, m, 4600 + m)
+        Y = host(b.apply_Q(dev(C)))
+        want = rep.apply_Q(C)
+        assert rel(Y, want) <= 1e-14, (m, rel(Y, want))
+        assert rel(Y, ora.apply_Q(C)) <= TOL_REL, m
+        Yh = b.apply_Q(C)
+        assert np.array_equal(Yh, Y), m
+        Ys = torch.full((n, m + 3), 7.0, dtype=torch.float64, device="cuda")
+        b.apply_Q(dev(C), Ys[:, :m])
+        Ys = host(Ys)
+        assert np.array_equal(Ys[:, :m], Y) and np.all(Ys[:, m:] == 7.0), m
+    # one coefficient kernel and one assembly per s columns of C
+    groups = sum(3 * ((m + s - 1) // s) for m in (1, s - 3, s, s + 5, 2 * s + 1))
+    assert L.launch_count() - before == 2 * groups
