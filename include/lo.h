@@ -62,10 +62,11 @@ typedef enum lo_status {
 /* Arithmetic of the O(n) passes. */
 typedef enum lo_precision {
   LO_PREC_FP64 = 0,        /* every product in native float64                    */
-  LO_PREC_MIXED_FP32 = 1,  /* first-pass Gram/projection in float32, then float64 */
-                           /* shifted Cholesky, one float64 CholeskyQR2-style    */
-                           /* refinement pass, float64 tree and update (Alg. 8   */
-                           /* pattern)                                            */
+  LO_PREC_MIXED_FP32 = 1,  /* first-pass Gram/projection in float32 (each column */
+                           /* of W scaled per slab by a power of two), then      */
+                           /* float64 shifted Cholesky, one float64 CholeskyQR2- */
+                           /* style refinement pass, float64 tree and update     */
+                           /* (Alg. 8 pattern)                                    */
   LO_PREC_FP64_TC = 2,     /* float64-accurate products of the O(n) passes on the */
                            /* tensor cores: every float64 value is split into 7   */
                            /* 8-bit digits against its column's largest exponent */
@@ -186,7 +187,12 @@ int32_t lo_basis_num_chunks(const lo_basis* b);
  *   R (s x s, row-major)       the normalizer N, upper triangular, diag > 0,
  * and appends the block to the basis.  U may alias W (same pointer, same ld).
  * H and R may be NULL if not wanted.  On any error the basis is unchanged
- * (its block count is not advanced) and U, H, R are undefined.
+ * (its block count is not advanced) and U, H, R are undefined.  A block that
+ * is exactly zero on some chunks, or in some of its columns there, is
+ * supported as long as it has full rank against the basis overall: the
+ * chunk's local panel then keeps zero columns (Sec. 3, t = s with the rank
+ * deficiency carried in the normalizer).  The results are homogeneous in W:
+ * W scaled by 2^j gives the same U and H, R scaled by 2^j, bit for bit.
  */
 lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw,
                            double* U, int64_t ldu, double* H, double* R);

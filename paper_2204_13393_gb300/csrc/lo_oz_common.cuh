@@ -71,17 +71,6 @@ __device__ __forceinline__ void mma_f16(float (&d)[4], const unsigned (&a)[4], u
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// The 28 digit pairs (t, u), t + u <= 8, as a compile-time walk.
-template <typename F>
-__device__ __forceinline__ void for_pairs(F&& f) {
-  int idx = 0;
-#pragma unroll
-  for (int t = 1; t <= kOzDigits; ++t)
-#pragma unroll
-    for (int u = 1; u <= kOzDigits; ++u)
-      if (t + u <= 8) f(idx++, t, u);
-}
-
 // Recombination of one output's 28 pair sums D_tu (exact integers, |D| < 2^24):
 //   sum_{t,u} D_tu 2^(-8(t+u)) = 2^-16 (S_2 + rest 2^-45),  S_v = sum_{t+u=v} D_tu,
 //   rest = S_3 2^37 + S_4 2^29 + S_5 2^21 + S_6 2^13 + S_7 2^5 + round(S_8 / 8)

@@ -97,114 +97,6 @@ LO_HD double oz_recombine(int s2, long long rest, int X) {
   return scale2(oz_from_bits(sign | ((uint64_t)e << 52) | frac), X);
 }
 
-// RN(s2 2^45 + rest) 2^(X - 45), the exact integer sum rounded once (to
-// nearest, ties to even), with 64-bit integer operations only; the result
-// outside the normal range after the scaling as scale2.  One rounding where
-// oz_recombine keeps the two of the float64 expression: used by kernels whose
-// results are compared with no other form bit for bit.
-LO_HD double oz_recombine_exact(int s2, long long rest, int X) {
-  // T = th 2^45 + tl, 0 <= tl < 2^45
-  const long long th = (long long)s2 + (rest >> 45);
-  const uint64_t tl = (uint64_t)rest & ((1ull << 45) - 1);
-  if (th == 0 && tl == 0) return 0.0;
-  const bool neg = th < 0;
-  // |T| = mh 2^45 + ml, ml < 2^45
-  uint64_t mh, ml;
-  if (!neg) {
-    mh = (uint64_t)th;
-    ml = tl;
-  } else if (tl == 0) {
-    mh = (uint64_t)(-th);
-    ml = 0;
-  } else {
-    mh = (uint64_t)(-th) - 1;
-    ml = (1ull << 45) - tl;
-  }
-  // the leading 64 bits of |T| (leading bit at 63) and the bits below them
-  int p;  // position of the leading bit of |T|
-  uint64_t top;
-  bool sticky = false;
-  if (mh == 0) {
-    p = 63 - oz_clz64(ml);
-    top = ml << (63 - p);
-  } else {
-    p = 45 + 63 - oz_clz64(mh);  // 45 .. 77
-    if (p >= 63) {
-      const int sh = p - 63;  // 0 .. 14
-      top = (mh << (45 - sh)) | (ml >> sh);
-      sticky = (ml & ((1ull << sh) - 1)) != 0;
-    } else {
-      const int sh = 63 - p;  // 1 .. 18
-      top = (mh << (45 + sh)) | (ml << sh);
-    }
-  }
-  uint64_t mant = top >> 11;
-  const uint64_t low = top & 0x7FF;
-  if (low > 0x400 || (low == 0x400 && (sticky || (mant & 1)))) {
-    if (++mant == (1ull << 53)) {
-      mant >>= 1;
-      ++p;
-    }
-  }
-  const uint64_t sign = neg ? (1ull << 63) : 0ull, frac = mant & ((1ull << 52) - 1);
-  const int e = p - 45 + 1023, E = e + X;
-  if (E >= 1 && E <= 2046) return oz_from_bits(sign | ((uint64_t)E << 52) | frac);
-  return scale2(oz_from_bits(sign | ((uint64_t)e << 52) | frac), X);
-}
-
-// oz_recombine_exact of the class sums d[0..7] of one output (d[0] = S_2,
-// d[1..5] = S_3 .. S_7, d[6], d[7] = S_8 of the two pair groups), from the
-// exact integer T = S_2 2^45 + rest with
-//   rest = S_3 2^37 + S_4 2^29 + S_5 2^21 + S_6 2^13 + S_7 2^5
-//          + floor((S_8a + 4) / 8) + floor((S_8b + 4) / 8),
-// for |d| <= 2^23 - 2^16: adjacent classes pair exactly in 32 bits
-// (A = S_v 2^8 + S_(v+1)), T = A1 2^37 + (A2 2^21 + A3 2^5 + r8), and the
-// conversion works on a 32-bit high word and a 37-bit low word.
-LO_HD double oz_recombine8(const int (&d)[8], int X) {
-  const int a1 = d[0] * 256 + d[1], a2 = d[2] * 256 + d[3], a3 = d[4] * 256 + d[5];
-  const long long lo = (long long)a2 * (1ll << 21) + (long long)a3 * 32 + ((d[6] + 4) >> 3) + ((d[7] + 4) >> 3);
-  // T = th 2^37 + tl, 0 <= tl < 2^37
-  const long long th = (long long)a1 + (lo >> 37);
-  const uint64_t tl = (uint64_t)lo & ((1ull << 37) - 1);
-  const bool neg = th < 0;
-  uint64_t mh = neg ? (uint64_t)(-th) : (uint64_t)th, ml = tl;
-  if (neg && tl != 0) {
-    mh -= 1;
-    ml = (1ull << 37) - tl;
-  }
-  // |T| = mh 2^37 + ml: its leading 64 bits and whether bits below them are set
-  int p;
-  uint64_t top;
-  bool sticky = false;
-  if (mh != 0) {
-    const int k = 63 - oz_clz64(mh);  // 0 .. 32
-    p = 37 + k;
-    top = mh << (63 - k);
-    if (k <= 26) {
-      top |= ml << (26 - k);
-    } else {
-      top |= ml >> (k - 26);
-      sticky = (ml & ((1ull << (k - 26)) - 1)) != 0;
-    }
-  } else {
-    if (ml == 0) return 0.0;
-    p = 63 - oz_clz64(ml);
-    top = ml << (63 - p);
-  }
-  uint64_t mant = top >> 11;
-  const uint64_t low = top & 0x7FF;
-  if (low > 0x400 || (low == 0x400 && (sticky || (mant & 1)))) {
-    if (++mant == (1ull << 53)) {
-      mant >>= 1;
-      ++p;
-    }
-  }
-  const uint64_t sign = neg ? (1ull << 63) : 0ull, frac = mant & ((1ull << 52) - 1);
-  const int e = p - 45 + 1023, E = e + X;
-  if (E >= 1 && E <= 2046) return oz_from_bits(sign | ((uint64_t)E << 52) | frac);
-  return scale2(oz_from_bits(sign | ((uint64_t)e << 52) | frac), X);
-}
-
 // The float64 of a nonzero integer m 2^e2 (|m| < 2^53) built from its bits.
 LO_HD double oz_exact_double(long long m, int e2) {
   if (m == 0) return 0.0;
@@ -214,9 +106,16 @@ LO_HD double oz_exact_double(long long m, int e2) {
   return oz_from_bits(sign | ((uint64_t)(1023 + p + e2) << 52) | ((a << (52 - p)) & ((1ull << 52) - 1)));
 }
 
-// oz_recombine8 with one float64 addition: T = A1 2^37 + lo with |A1| < 2^31
-// and |lo| < 2^53, both exact as float64 (built from their bits), so their
-// rounded sum is RN(T) -- the same single rounding, bit for bit.
+// The class sums d[0..7] of one output (d[0] = S_2, d[1..5] = S_3 .. S_7,
+// d[6], d[7] = S_8 of the two pair groups) recombined with one rounding:
+// RN(T) 2^(X - 45) for the exact integer T = S_2 2^45 + rest,
+//   rest = S_3 2^37 + S_4 2^29 + S_5 2^21 + S_6 2^13 + S_7 2^5
+//          + floor((S_8a + 4) / 8) + floor((S_8b + 4) / 8),
+// for |d| <= 2^23 - 2^16.  Adjacent classes pair exactly in 32 bits
+// (A = S_v 2^8 + S_(v+1)), so T = A1 2^37 + lo with |A1| < 2^31 and
+// |lo| < 2^53, both exact as float64 (built from their bits), and their one
+// float64 addition is RN(T).  A result outside the normal range after the
+// scaling goes through scale2.
 LO_HD double oz_recombine8_add(const int (&d)[8], int X) {
   const int a1 = d[0] * 256 + d[1], a2 = d[2] * 256 + d[3], a3 = d[4] * 256 + d[5];
   const long long lo = (long long)a2 * (1ll << 21) + (long long)a3 * 32 + ((d[6] + 4) >> 3) + ((d[7] + 4) >> 3);
