@@ -60,9 +60,9 @@ KERNEL_TU = {
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #     --clock-control none --profile-from-start off -k regex:k_umma_update -s 2 -c 1
-    #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 661.0 us)
-    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "dd19e147f11c8287",
-                            "dram_bytes": 1955145728 + 129702912, "algorithmic_bytes": 1210056704},
+    #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 659.4 us)
+    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "b85f8ba4496e96b8",
+                            "dram_bytes": 1955405824 + 129437696, "algorithmic_bytes": 1210056704},
 }
 
 
