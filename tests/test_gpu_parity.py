@@ -779,3 +779,51 @@ def test_apply_Q_tensor_cores(n, s, cr, M, nb, precision):
     # one coefficient kernel and one assembly per s columns of C
     groups = sum(3 * ((m + s - 1) // s) for m in (1, s - 3, s, s + 5, 2 * s + 1))
     assert L.launch_count() - before == 2 * groups
+
+
+@pytest.mark.parametrize("s,precision", [(8, "fp64_tc"), (16, "fp64_tc"), (32, "fp64_tc"), (8, "mixed_tc"),
+                                         (8, "mixed_fp32"), (4, "fp64_tc")])
+def test_strided_and_aliased_tensor_cores(s, precision):
+    """The tensor-core and mixed forms, at k = 0 and with digit planes at
+    k > 0 (two output groups at s = 32): W as a strided view whose rows start
+    off 16-byte alignment gives the same results bit for bit as a contiguous
+    copy orthogonalized in place (U written over W)."""
+    n, cr, M = 20000, 2048, 4
+    b1 = lo().Basis(n, s, M, cr, precision=precision)
+    b2 = lo().Basis(n, s, M, cr, precision=precision)
+    for j in range(3):
+        big = I.gaussian(n, s + 3, 4700 + j)
+        Wd = torch.from_numpy(big).cuda()[:, 1:1 + s]
+        assert Wd.stride(0) == s + 3
+        Wc = dev(big[:, 1:1 + s])
+        U1, H1, R1 = b1.orthogonalize(Wd)
+        U2, H2, R2 = b2.orthogonalize(Wc, U=Wc)
+        assert np.array_equal(host(U1), host(Wc)), j
+        assert np.array_equal(host(R1), host(R2)), j
+        if j > 0:
+            assert np.array_equal(host(H1), host(H2)), j
+    Q = host(b1.apply_Q(dev(np.eye(b1.k))))
+    assert O.e_perp(Q) <= TOL_PERP
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc", "mixed_fp32", "mixed_tc"])
+def test_gram_overflow_is_nonfinite(precision):
+    """A block whose Gram matrix leaves the float64 range (entries 2^520, the
+    Gram 2^1040) is reported as LO_ERR_NONFINITE with the basis unchanged,
+    and the basis goes on working; 2^500 (Gram 2^1000) is in range and
+    matches the oracle."""
+    L = lo()
+    n, s, cr = 16384, 8, 2048
+    b = L.Basis(n, s, 3, cr, precision=precision)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    W0 = I.gaussian(n, s, 4800)
+    b.orthogonalize(dev(W0))
+    ora.orthogonalize(W0, "hh", "hh")
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(dev(np.ldexp(I.gaussian(n, s, 4801), 520)))
+    assert e.value.name == "LO_ERR_NONFINITE"
+    assert b.num_blocks == 1
+    W1 = np.ldexp(I.gaussian(n, s, 4802), 500)
+    U, H, R = b.orthogonalize(dev(W1))
+    Uo, Po, No = ora.orthogonalize(W1, "hh", "hh")
+    assert rel(host(U), Uo) <= TOL_REL and rel(host(H), Po) <= TOL_REL and rel(host(R), No) <= TOL_REL
