@@ -11,8 +11,18 @@ import os
 import numpy as np
 import pytest
 
-from oracle import lo_oracle as O
 from paper_2204_13393_gb300 import inputs as I
+
+if os.environ.get("LO_ORACLE_MUTANT"):
+    # test_oracle_mutations.py runs these pins against a copy of the oracle
+    # with one planted mistake
+    import importlib.util
+
+    _spec = importlib.util.spec_from_file_location("lo_oracle_mutant", os.environ["LO_ORACLE_MUTANT"])
+    O = importlib.util.module_from_spec(_spec)
+    _spec.loader.exec_module(O)
+else:
+    from oracle import lo_oracle as O
 
 ALGS = ["hh", "mgs2", "pip", "pip2"]
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -341,10 +351,12 @@ def test_paper_stability_table(alg):
     assert res <= g[("residual", alg)][1] * 10, (alg, res)
 
 
-@pytest.mark.parametrize("alg,slope", [("pip", 2.0), ("pip2", 0.0), ("hh", 0.0)])
+@pytest.mark.parametrize("alg,slope", [("pip", 2.0), ("pip2", 0.0), ("hh", 0.0), ("mgs2", 0.0)])
 def test_error_law_slopes(alg, slope):
     """Sec. 3 / Sec. 6.1: e_perp = O(eps kappa^2) for PIP, O(eps) for PIP+
-    (while eps kappa^2 <= 1/2) and for HH.  Fit log e_perp over kappa = 1e2..1e6."""
+    (while eps kappa^2 <= 1/2) and for HH; O(eps) for Gram-Schmidt with one
+    reorthogonalization (Sec. 2, Alg. 5; a single sweep loses orthogonality
+    in proportion to kappa).  Fit log e_perp over kappa = 1e2..1e6."""
     n, m, s = 4096, 16, 4
     ks = [1e2, 1e3, 1e4, 1e5, 1e6] if alg != "pip" else [1e2, 1e3, 1e4, 1e5]
     errs = []
@@ -462,3 +474,29 @@ def test_power_of_two_scaling_commutes(local, reduction):
             assert np.array_equal(U, U0)
             assert np.array_equal(P, np.ldexp(P0, j))
             assert np.array_equal(N, np.ldexp(N0, j))
+
+
+# ------------------------------------------------ definitions in closed form
+
+def test_chunk_bounds_reading():
+    """p = max(1, floor(n / chunk_rows)) chunks of chunk_rows rows, the
+    remainder joining the last (the reading of Sec. 5.1.3 for other n)."""
+    assert O.chunk_bounds(777, 100) == [(0, 100), (100, 200), (200, 300), (300, 400), (400, 500),
+                                        (500, 600), (600, 777)]
+    assert O.chunk_bounds(800, 100)[-1] == (700, 800) and len(O.chunk_bounds(800, 100)) == 8
+    assert O.chunk_bounds(99, 100) == [(0, 99)]
+
+
+def test_error_measures_closed_form():
+    """e_perp = ||I - Q^T Q||_F (eq. (ortho_error)) and the residual is
+    ||A - QR||_F / ||A||_F: values where the Frobenius and spectral norms, and
+    the relative and absolute residuals, differ."""
+    Q = 2.0 * np.eye(3)[:, :2]                  # I - Q^T Q = -3 I_2
+    assert O.e_perp(Q) == pytest.approx(3.0 * np.sqrt(2.0), rel=1e-15)
+    A = 2.0 * np.eye(2)
+    assert O.residual(A, np.eye(2), np.eye(2)) == pytest.approx(0.5, rel=1e-15)
+    Qw = np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    R = np.array([[1.0, 2.0], [0.0, 3.0]])
+    Aw = Qw @ R
+    Aw[2, 1] = 4.0                              # A - QR = 4 e_3 e_2^T
+    assert O.residual(Aw, Qw, R) == pytest.approx(4.0 / np.sqrt(1 + 4 + 9 + 16), rel=1e-15)
