@@ -25,3 +25,14 @@ def test_reference_arm_json_line():
     cfg = line["config"]
     assert cfg["n"] == 1024 * 1024 and cfg["s"] == 8 and cfg["restart_blocks"] == 30
     assert cfg["workload"].startswith("block-GMRes restart cycle")
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun the reference arm runs on rank 0 alone: any other rank
+    exits 0 without work and prints no JSON line."""
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "0", "--cpu-budget", "2"], capture_output=True, text=True,
+                         timeout=300, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [l for l in out.stdout.splitlines() if l.strip().startswith("{")], out.stdout
