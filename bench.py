@@ -54,14 +54,14 @@ KERNEL_TU = {
 # DRAM bytes of one launch of the dominant kernel from one ncu capture (bench.py
 # --case profile: n = 2^20, s = 8, k = 120), with that launch's algorithmic bytes,
 # keyed by (kernel group, precision); "src" is the sha256 prefix of the kernel's
-# translation unit when the counters were taken.  The reported traffic scales the
-# measured ratio to the average launch of the cycle; a source change invalidates
-# the entry (traffic: null).
+# translation unit (comments stripped) when the counters were taken.  The
+# reported traffic scales the measured ratio to the average launch of the cycle;
+# a code change in that unit invalidates the entry (traffic: null).
 TRAFFIC = {
     # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
     #     --clock-control none --profile-from-start off -k regex:k_umma_update -s 2 -c 1
     #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 659.4 us)
-    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "b85f8ba4496e96b8",
+    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "0d97e169f48f294b",
                             "dram_bytes": 1955405824 + 129437696, "algorithmic_bytes": 1210056704},
 }
 
@@ -102,11 +102,49 @@ def gram_bytes_flops(n, s, k):
     return 8 * n * (k + s), 2 * n * (k + s) * s
 
 
+def strip_comments(text):
+    """C/C++ source without its comments, with every run of whitespace outside
+    string and character literals as one space (the literals kept as they
+    are), so that a comment- or layout-only edit does not invalidate a capture."""
+    out, i, n = [], 0, len(text)
+    space = False
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            if space:
+                out.append(" ")
+                space = False
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+            space = True
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            space = True
+        elif c.isspace():
+            space = True
+            i += 1
+        else:
+            if space:
+                out.append(" ")
+                space = False
+            out.append(c)
+            i += 1
+    return "".join(out).strip()
+
+
 def src_hash(kernel):
+    """sha256 prefix of the kernel's translation unit, comments stripped."""
     h = hashlib.sha256()
     for rel in KERNEL_TU[kernel]:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:16]
 
 

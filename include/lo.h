@@ -18,9 +18,10 @@
  *   whose stack is orthonormal.
  *
  *   TreeTSPQR, Alg. 9: a local PQR per chunk (BCGS-PIP, Alg. 7, reiterated as
- *   BCGS-PIP+, Alg. 8, when the block is ill-conditioned), a reduction PQR of
- *   the stacked small factors (BCGS-PIP+), and the assembly of U from the
- *   block-wise products of Sec. 4.1.
+ *   BCGS-PIP+, Alg. 8: by default always, optionally only when the block is
+ *   ill-conditioned), a reduction PQR of the stacked small factors
+ *   (BCGS-PIP+), and the assembly of U from the block-wise products of
+ *   Sec. 4.1.
  *
  * Conventions for every entry point:
  *   - All matrices are float64, row-major.  "ld" is the row stride in
@@ -32,8 +33,9 @@
  *   - The small outputs H and R are written to device or host memory as the
  *     pointer's kind says.
  *   - Functions return an lo_status; they never abort or throw across the ABI.
- *   - The library allocates only in lo_basis_create (and lazily, once, the
- *     host staging buffers).  Calls on one basis are not thread-safe.
+ *   - The library allocates only in lo_basis_create, and lazily the host
+ *     staging buffers and apply_Q's scratch (grown to the largest m seen).
+ *     Calls on one basis are not thread-safe.
  */
 #ifndef LO_H_
 #define LO_H_
@@ -50,8 +52,10 @@ typedef enum lo_status {
   LO_ERR_CAPACITY = 2,         /* basis already holds max_blocks blocks         */
   LO_ERR_CHUNK_TOO_SMALL = 3,  /* chunk_rows < max_blocks*s or n < max_blocks*s */
   LO_ERR_BREAKDOWN = 4,        /* a Cholesky pivot <= tolerance: the new block  */
-                               /* is (numerically) rank deficient; deflation    */
-                               /* (Sec. 3, last paragraph) is not supported     */
+                               /* is (numerically) rank deficient against the   */
+                               /* basis; deflation (Sec. 3, last paragraph) is  */
+                               /* not supported.  Exact zeros on some chunks    */
+                               /* are not a breakdown (see lo_orthogonalize)    */
   LO_ERR_NONFINITE = 5,        /* NaN or Inf reached a small factor             */
   LO_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                 */
   LO_ERR_CUDA = 7,             /* a CUDA runtime call failed                    */
@@ -115,7 +119,9 @@ typedef enum lo_leaf {
  * float64 values as fp16 digits (7 per value, the sign in each, 14 bytes per
  * value) in the tensor cores' operand order: the panels take 2.75 times the
  * memory of float64 alone and the passes stream MMA operands instead of
- * re-splitting float64 values.  Results are bitwise the same either way.
+ * re-splitting float64 values.  LO_PREC_FP64_TC gives bitwise the same
+ * results either way; LO_PREC_MIXED_TC's first pass needs the planes for its
+ * 32-bit digit split and otherwise runs in float32.
  * Memory per basis with planes: max_blocks * s * (8 + 14) bytes per row.
  */
 typedef enum lo_digit_planes {

@@ -36,3 +36,16 @@ def test_reference_arm_other_ranks_exit_quietly():
                          timeout=300, cwd=ROOT, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [l for l in out.stdout.splitlines() if l.strip().startswith("{")], out.stdout
+
+
+def test_strip_comments_keeps_code_and_literals():
+    """The traffic capture is keyed by the kernel's source without comments."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    src = 'int a = 1; // note\n/* block\n comment */ const char* s = "x//y  /*z*/"; char q = \'"\';\n'
+    assert bench.strip_comments(src) == 'int a = 1; const char* s = "x//y  /*z*/"; char q = \'"\';'
+    assert bench.strip_comments("a /* c */ b") == bench.strip_comments("a\n  b  // d")
+    assert bench.strip_comments("a /* c */ b") != bench.strip_comments("a b c")
