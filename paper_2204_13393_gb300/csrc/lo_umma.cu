@@ -1,12 +1,15 @@
 // The two O(n) products of a step (the stage-1 Gram partial of Alg. 7 and the
-// assembly products of Sec. 4.1) on the 5th-generation tensor cores, over the
-// digit planes that a tensor-core basis keeps for its prior panels.
+// assembly products of Sec. 4.1), and the product Q C of apply_Q, on the
+// 5th-generation tensor cores, over the digit planes that a tensor-core basis
+// keeps for its prior panels.
 //
 // Digit arithmetic as in lo_ozaki.cu: each float64 value is split exactly into
 // 7 8-bit digits aligned to its column's largest exponent, encoded as fp16
 // subnormals; the 28 digit pairs (t, u) with t + u <= 8 are multiplied with
 // float32 accumulation, exact for up to 256 products, and recombined in 64-bit
-// integers.  Results are bit for bit those of the mma.sync kernels.
+// integers.  With prior blocks the results are bit for bit those of the
+// mma.sync kernels; the k = 0 assembly rounds each output once
+// (lo_recombine.h).
 //
 // GB300 mapping:
 //   * one thread issues tcgen05.mma (M = 128, K = 16, kind::f16) with both
@@ -649,7 +652,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 // columns at a time, K = 16 columns of [Q_i A] per step.  The A operand of
 // digit t is the TMA stage itself ([8-row block][group][t][128 B]: MN-major,
 // SBO = 2 x 7 x 128, LBO = 7 x 128); the block's own columns are split into
-// it.  B operand: the coefficient image of the step (k_oz_coef<UMMA>).  With
+// it.  B operand: the coefficient image of the step (k_oz_coef<UMMA>; for
+// apply_Q, k_apply_coef).  With
 // more than NB outputs the K loop of a row tile runs once per group of NB
 // outputs and the tile is written only after the last group: the pass block
 // may share storage with an output (the new panel holds the last iterate;
