@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(512, 1) k_oz_gram(StepArgs a, const double* sr
 // step ks, a K-major no-swizzle tile of R = round16(7 NB) rows x 16 K, row
 // (u - 1) NB + n holding digit u of column z NB + n (rows past 7 NB zero):
 // byte ((row % 8) * 16 + (row / 8) * 256 + (kk % 8) * 2 + (kk / 8) * 128) of
-// image (z * ceil(Kmax / 16) + ks), images R * 32 bytes apart.
+// image (z * ceil(Kmax / 16) + ks), images R * 32 bytes apart
+// (umma_coef_image, shared with apply_Q's coefficient kernel).
 //
 // MODE 2 (no prior blocks, Kt = S) writes one image for k_umma_update0 whose
 // K index is (digit t of the block, block column) and whose N index is
