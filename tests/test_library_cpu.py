@@ -99,3 +99,34 @@ def test_options_default(lib):
     assert o.refine_tol == pytest.approx(1e-13)
     assert (o.digit_planes, o.test_stall) == (0, 0)
     assert ctypes.sizeof(o) == 32
+
+
+def test_tuner_and_noalloc_reject_bad_arguments_without_device(lib):
+    """lo_tune_chunk_rows and lo_tsqr_noalloc validate before any CUDA call."""
+    import numpy as np
+
+    out = ctypes.c_int32(-1)
+    assert lib.lo_tune_chunk_rows(4096, 4, 8, None, None, None) == 1                  # no output
+    for n, s, M, want in ((0, 4, 8, 1), (4096, 0, 8, 1), (4096, 33, 8, 1), (4096, 4, 0, 1),
+                          (4096, 32, 64, 3), (20, 4, 8, 3)):
+        assert lib.lo_tune_chunk_rows(n, s, M, None, None, ctypes.byref(out)) == want, (n, s, M)
+    W = np.zeros((64, 8))
+    U = np.zeros((64, 8))
+    R = np.zeros((8, 8))
+    w, u, r = W.ctypes.data, U.ctypes.data, R.ctypes.data
+    cases = [
+        ((0, 8, 16, w, 8, u, r), 1),           # n < 1
+        ((64, 0, 16, w, 8, u, r), 1),          # s < 1
+        ((64, 33, 16, w, 33, u, r), 1),        # s > 32
+        ((64, 8, 0, w, 8, u, r), 1),           # chunk_rows < 1
+        ((64, 8, 16, None, 8, u, r), 1),       # no W
+        ((64, 8, 16, w, 8, None, r), 1),       # no U
+        ((64, 8, 16, w, 8, u, None), 1),       # no R
+        ((64, 8, 16, w, 7, u, r), 1),          # ldw < s
+        ((32, 8, 16, w, 16, w, r), 1),         # in place with a strided block
+        ((64, 8, 16, w, 8, w + 8, r), 1),      # distinct but overlapping buffers
+        ((64, 8, 4, w, 8, u, r), 3),           # chunks shorter than s
+        ((4, 8, 16, w, 8, u, r), 3),           # one chunk shorter than s
+    ]
+    for args, want in cases:
+        assert lib.lo_tsqr_noalloc(*args, None) == want, args
