@@ -161,13 +161,16 @@ void lo_options_default(lo_options* opt);
 /*
  * Create an empty basis for n-row blocks of width s, holding up to max_blocks
  * blocks, with local row chunks of chunk_rows rows (p = max(1, n / chunk_rows)
- * chunks; the remainder rows join the last chunk).  Every chunk must have at
- * least max_blocks*s rows so that each local problem has full rank
- * (LO_ERR_CHUNK_TOO_SMALL otherwise).  Requires 1 <= s <= 32 and
- * max_blocks*s <= 1024.  cuda_stream is a cudaStream_t (NULL = legacy default
- * stream) of the current device.  opt may be NULL (defaults).
- * Allocates all device memory of the basis (local panels n*max_blocks*s
- * doubles, tree factors, scratch).  On failure *out is NULL.
+ * chunks; the remainder rows join the last chunk).  The basis is the locally
+ * orthogonal representation of Sec. 4.1 (one local factor Q_i per row chunk,
+ * the tree factors T_i), split into the local subproblems of Sec. 5.1.3
+ * (p = n / local size); the chunk size is the local problem size that
+ * Sec. 6.2 studies.  Every chunk must have at least max_blocks*s rows so that
+ * each local problem has full rank (LO_ERR_CHUNK_TOO_SMALL otherwise).
+ * Requires 1 <= s <= 32 and max_blocks*s <= 1024.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) of the current device.  opt may
+ * be NULL (defaults).  Allocates all device memory of the basis (local panels
+ * n*max_blocks*s doubles, tree factors, scratch).  On failure *out is NULL.
  */
 lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chunk_rows,
                           const lo_options* opt, void* cuda_stream, lo_basis** out);
@@ -178,7 +181,9 @@ void lo_basis_destroy(lo_basis* b);
 /* Drop all blocks (e.g. at a GMRes restart); keeps the allocations. */
 lo_status lo_basis_reset(lo_basis* b);
 
-/* Number of blocks currently in the basis (k = blocks * s columns). */
+/* Number of blocks currently in the basis (k = blocks * s columns): the
+ * number of PQR steps of Alg. 2 / Alg. 1 solved so far since create, reset or
+ * truncate.  -1 for NULL. */
 int32_t lo_basis_num_blocks(const lo_basis* b);
 
 /* Number of local chunks p. */
@@ -221,14 +226,21 @@ lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc,
 /*
  * Orthogonalize count independent problems (uneven n, s, k), one block each:
  * for j < count, the same as lo_orthogonalize(bases[j], W[j], ldw[j], U[j],
- * ldu[j], H[j], R[j]).  The steps of all problems are captured once into one
- * CUDA graph whose branches run concurrently (a fork over 8 internal streams,
- * joined back into the stream of bases[0]); the graph is cached under the
- * call's arguments (bases, their block counts, pointers, strides) and a repeat
- * call with the same arguments is a single graph launch.  All bases must live
- * on the same device and be distinct; W, U, H, R must be device pointers
- * (H[j], R[j], or H, R themselves may be NULL).  Waits for the work.  Returns
- * the first error; bases without error advance, the others are unchanged.
+ * ldu[j], H[j], R[j]) -- one PQR step (eq. (pqr), Alg. 9) per problem.  The
+ * paper solves one problem at a time; running many small ones together is
+ * this library's answer to Sec. 6.2's observation that small local problems
+ * leave the hardware idle.  The steps of all problems are captured once into
+ * one CUDA graph whose branches run concurrently (a fork over 8 internal
+ * streams, joined back into the stream of bases[0]); the graph is cached under
+ * the call's arguments (each basis by a process-unique id, its block count,
+ * the buffers and strides) and a repeat call with the same arguments is a
+ * single graph launch.  Destroying a basis evicts every cached graph that
+ * names it.  All bases must live on the same device and be distinct.  W, U,
+ * H, R may be device or host pointers, as in lo_orthogonalize (host W is
+ * staged through the basis's device buffer before the graph runs; host U, H,
+ * R are copied out after it, on the stream of bases[0]); H, R, H[j], R[j] may
+ * be NULL.  Waits for the work.  Returns the first error; bases without error
+ * advance, the others are unchanged.
  */
 lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count,
                                    const double* const* W, const int64_t* ldw,
@@ -251,6 +263,15 @@ lo_status lo_basis_truncate(lo_basis* b, int32_t num_blocks);
  */
 lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_options* opt,
                              void* cuda_stream, int32_t* chunk_rows);
+
+/*
+ * Inspection of the batched graph cache (for tests): lo_basis_id returns the
+ * basis's process-unique id (0 for NULL; ids are never reused);
+ * lo_batched_cache_entries returns how many cached graphs name the basis with
+ * that id (basis_id = 0: all cached graphs).  Host-only, no device work.
+ */
+uint64_t lo_basis_id(const lo_basis* b);
+int32_t lo_batched_cache_entries(uint64_t basis_id);
 
 /* Wait for the basis stream and return (and clear) any latched device error. */
 lo_status lo_basis_sync(lo_basis* b);
@@ -290,14 +311,15 @@ lo_status lo_basis_profile_read(lo_basis* b, double* ms, int64_t* intervals, int
 
 /*
  * Allocation-free tall-skinny QR: W = U R with the first step of the method
- * (empty basis, k = 0: local Gram per chunk, leaf Cholesky with reiteration
- * when needed, reduction of the stacked factors, assembly of U), for callers
- * that cannot allocate device memory: code that runs where the memory budget
- * is fixed up front (an application that owns every device allocation through
- * its own pool, a process that must not grow its footprint after start-up) or
- * a host thread for which cudaMalloc/cudaFree, with their implicit device
- * synchronization, are not permitted.  The paper has no counterpart; it is an
- * interface variant of the k = 0 step of lo_orthogonalize.
+ * (empty basis, k = 0: local Gram per chunk, leaf Cholesky with the BCGS-PIP+
+ * reiteration -- the library's default leaf, LO_LEAF_PIP2 --, reduction of the
+ * stacked factors, assembly of U), for callers that cannot allocate device
+ * memory: code that runs where the memory budget is fixed up front (an
+ * application that owns every device allocation through its own pool, a
+ * process that must not grow its footprint after start-up) or a host thread
+ * for which cudaMalloc/cudaFree, with their implicit device synchronization,
+ * are not permitted.  The paper has no counterpart; it is an interface
+ * variant of the k = 0 step of lo_orthogonalize.
  *
  *   n, s, chunk_rows  as for lo_basis_create with max_blocks = 1 (1 <= s <= 32,
  *                     every chunk at least s rows);
@@ -310,18 +332,30 @@ lo_status lo_basis_profile_read(lo_basis* b, double* ms, int64_t* intervals, int
  *
  * It allocates nothing: all scratch is one fixed 16 MiB array in device
  * memory that every device loading the library holds until the process exits.
- * A problem whose scratch does not fit (roughly p chunks * (8 s^2 + 1) doubles
- * plus one s x s tile per 256-row slab) returns LO_ERR_CAPACITY before any
- * device work.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) once for the device; make that first call
+ * A problem whose scratch does not fit (lo_tsqr_noalloc_scratch gives the
+ * size: roughly p chunks * (8 s^2 + 1) doubles plus one s x s tile per
+ * 256-row slab) returns LO_ERR_CAPACITY before any CUDA call.  Every call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress; after a device reset the module is reloaded, possibly
+ * elsewhere); the first call on a device also loads the module, so make it
  * before any stream capture.  Every call shares the array and leaves its
- * contents behind, so calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialized by the caller.  The call waits for its
- * stream and returns the step's status (LO_ERR_BREAKDOWN for a numerically
- * rank-deficient W, LO_ERR_NONFINITE for NaN/Inf).
+ * contents behind, so calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialized by the caller.  The call waits
+ * for its stream and returns the step's status (LO_ERR_BREAKDOWN for a
+ * numerically rank-deficient W, LO_ERR_NONFINITE for NaN/Inf).
  */
 lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, const double* W, int64_t ldw,
                           double* U, double* R, void* cuda_stream);
+
+/*
+ * Host-only size query for lo_tsqr_noalloc (no CUDA call): *need_bytes gets
+ * the scratch the problem (n, s, chunk_rows) needs, *capacity_bytes the size
+ * of the fixed array (either may be NULL).  Returns LO_OK if it fits,
+ * LO_ERR_CAPACITY if not, and the argument errors of lo_tsqr_noalloc
+ * (LO_ERR_INVALID_ARG, LO_ERR_CHUNK_TOO_SMALL) for bad sizes.
+ */
+lo_status lo_tsqr_noalloc_scratch(int64_t n, int32_t s, int32_t chunk_rows, uint64_t* need_bytes,
+                                  uint64_t* capacity_bytes);
 
 /* Human-readable name of a status code (static string). */
 const char* lo_status_string(lo_status st);

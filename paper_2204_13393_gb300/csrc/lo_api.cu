@@ -1,5 +1,6 @@
 // Host side of the C ABI (include/lo.h): basis object, argument validation,
 // staging of host buffers, kernel sequencing and status reporting.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -78,6 +79,7 @@ struct Profiler : lo::ProfHook {
 };
 
 struct lo_basis {
+  uint64_t id = 0;  // process-unique, never reused (keys of the batched graph cache)
   int64_t n = 0;
   int s = 0, M = 0, cr = 0, p = 0, nb = 0, Kmax = 0;
   lo_options opt{};
@@ -145,6 +147,8 @@ lo_status status_from_bits(int bits) {
   if (bits) return LO_ERR_CUDA;
   return LO_OK;
 }
+
+void evict_basis_graphs(uint64_t id);
 
 lo_status ensure(double** buf, size_t* cap, size_t need) {
   if (*cap >= need) return LO_OK;
@@ -233,8 +237,15 @@ lo_status copy_small_outputs(lo_basis* b, double* H, double* R, cudaStream_t st)
 }
 
 // Stream pool and graph cache of lo_orthogonalize_batched (one per process).
+// A cached graph bakes in the device buffers of the bases it was captured
+// for; its key names each basis by its process-unique id (never by address:
+// a new basis may be created at a destroyed one's address), and
+// lo_basis_destroy, or a reallocation of a staging buffer a graph may name,
+// evicts every entry that names the basis.
 constexpr int kPool = 8;
 constexpr size_t kGraphCache = 8;
+constexpr size_t kKeyHead = 2;    // count, stream
+constexpr size_t kKeyPer = 9;     // words per instance; the basis id comes first
 struct GraphEntry {
   std::vector<uintptr_t> key;
   cudaGraphExec_t exec;
@@ -246,7 +257,6 @@ struct BatchGraphs {
   cudaStream_t st[kPool] = {};
   cudaStream_t cap = nullptr;     // capture origin (the caller's stream may be the legacy one)
   cudaEvent_t fork = nullptr;
-  cudaEvent_t before = nullptr;
   cudaEvent_t join[kPool] = {};
   std::vector<GraphEntry> cache;
   unsigned long long clock = 0;
@@ -255,11 +265,49 @@ BatchGraphs& batch_graphs() {
   static BatchGraphs* g = new BatchGraphs();  // lives until process exit
   return *g;
 }
+bool key_names(const std::vector<uintptr_t>& key, uint64_t id) {
+  for (size_t i = kKeyHead; i < key.size(); i += kKeyPer)
+    if ((uint64_t)key[i] == id) return true;
+  return false;
+}
+// Caller holds bg.mu.
+void evict_locked(BatchGraphs& bg, uint64_t id) {
+  for (size_t i = 0; i < bg.cache.size();) {
+    if (key_names(bg.cache[i].key, id)) {
+      cudaGraphExecDestroy(bg.cache[i].exec);
+      bg.cache.erase(bg.cache.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+void evict_basis_graphs(uint64_t id) {
+  BatchGraphs& bg = batch_graphs();
+  std::lock_guard<std::mutex> lock(bg.mu);
+  evict_locked(bg, id);
+}
+// The pool lives on one device; a switch tears down the old pool (on its own
+// device) before creating the new one.
 cudaError_t ensure_pool(BatchGraphs& bg, int device) {
   if (bg.device == device) return cudaSuccess;
   if (bg.device >= 0) {
+    int cur = device;
+    cudaSetDevice(bg.device);
     for (auto& ent : bg.cache) cudaGraphExecDestroy(ent.exec);
     bg.cache.clear();
+    for (int i = 0; i < kPool; ++i) {
+      if (bg.st[i]) cudaStreamDestroy(bg.st[i]);
+      if (bg.join[i]) cudaEventDestroy(bg.join[i]);
+      bg.st[i] = nullptr;
+      bg.join[i] = nullptr;
+    }
+    if (bg.fork) cudaEventDestroy(bg.fork);
+    if (bg.cap) cudaStreamDestroy(bg.cap);
+    bg.fork = nullptr;
+    bg.cap = nullptr;
+    bg.device = -1;
+    cudaGetLastError();
+    cudaSetDevice(cur);
   }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < kPool && e == cudaSuccess; ++i) {
@@ -267,11 +315,20 @@ cudaError_t ensure_pool(BatchGraphs& bg, int device) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.join[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bg.before, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bg.cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) bg.device = device;
   return e;
 }
+
+// Grow one of the basis's lazily allocated buffers; a move evicts the
+// batched graphs of the basis (they may name the old buffer).
+lo_status ensure_owned(lo_basis* b, double** buf, size_t* cap, size_t need) {
+  if (*cap >= need) return LO_OK;
+  evict_basis_graphs(b->id);
+  return ensure(buf, cap, need);
+}
+
+std::atomic<uint64_t> g_next_basis_id{1};
 
 }  // namespace
 
@@ -338,6 +395,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
 
   lo_basis* b = new (std::nothrow) lo_basis();
   if (!b) return LO_ERR_OOM;
+  b->id = g_next_basis_id.fetch_add(1);
   b->n = n;
   b->s = s;
   b->M = max_blocks;
@@ -429,6 +487,8 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
 
 void lo_basis_destroy(lo_basis* b) {
   if (!b) return;
+  // no cached batched graph may outlive the buffers it names
+  evict_basis_graphs(b->id);
   cudaFree(b->V);
   cudaFree(b->T);
   cudaFree(b->part);
@@ -485,7 +545,7 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw, double* U,
   int64_t ldud = ldu;
   lo_status rs;
   if (!w_dev) {
-    if ((rs = ensure(&b->stage_in, &b->stage_in_cap, (size_t)n * s)) != LO_OK) return rs;
+    if ((rs = ensure_owned(b, &b->stage_in, &b->stage_in_cap, (size_t)n * s)) != LO_OK) return rs;
     cudaError_t e = cudaMemcpy2DAsync(b->stage_in, s * sizeof(double), W, ldw * sizeof(double),
                                       s * sizeof(double), n, cudaMemcpyDefault, st);
     if (e != cudaSuccess) return from_cuda(e);
@@ -493,7 +553,7 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw, double* U,
     ldwd = s;
   }
   if (!u_dev) {
-    if ((rs = ensure(&b->stage_out, &b->stage_out_cap, (size_t)n * s)) != LO_OK) return rs;
+    if ((rs = ensure_owned(b, &b->stage_out, &b->stage_out_cap, (size_t)n * s)) != LO_OK) return rs;
     Ud = b->stage_out;
     ldud = s;
   }
@@ -522,32 +582,71 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     if (!b || !W[j] || !U[j] || ldw[j] < b->s || ldu[j] < b->s) return LO_ERR_INVALID_ARG;
     if (b->nb >= b->M) return LO_ERR_CAPACITY;
     if (b->device != bases[0]->device) return LO_ERR_INVALID_ARG;
-    if (!is_device_ptr(W[j]) || !is_device_ptr(U[j])) return LO_ERR_INVALID_ARG;
-    if (H && H[j] && !is_device_ptr(H[j])) return LO_ERR_INVALID_ARG;
-    if (R && R[j] && !is_device_ptr(R[j])) return LO_ERR_INVALID_ARG;
     for (int i = 0; i < j; ++i)
       if (bases[i] == b) return LO_ERR_INVALID_ARG;  // one step per basis and call
   }
   cudaSetDevice(bases[0]->device);
   cudaStream_t cs = bases[0]->stream;
+  // Host buffers (as in lo_orthogonalize): W is staged into the basis's device
+  // buffer before the graph runs, U is written to a device buffer and copied
+  // out after it, and host H, R are copied from the basis's small outputs
+  // after it.  The graph itself only ever names device memory.
+  std::vector<const double*> Wd(count);
+  std::vector<int64_t> ldwd(count), ldud(count);
+  std::vector<double*> Ud(count), Hd(count), Rd(count);
+  std::vector<char> w_host(count), u_host(count), h_host(count), r_host(count);
+  for (int j = 0; j < count; ++j) {
+    lo_basis* b = bases[j];
+    w_host[j] = !is_device_ptr(W[j]);
+    u_host[j] = !is_device_ptr(U[j]);
+    double* hj = H ? H[j] : nullptr;
+    double* rj = R ? R[j] : nullptr;
+    h_host[j] = hj && !is_device_ptr(hj);
+    r_host[j] = rj && !is_device_ptr(rj);
+    Hd[j] = h_host[j] ? nullptr : hj;
+    Rd[j] = r_host[j] ? nullptr : rj;
+    Wd[j] = W[j];
+    ldwd[j] = ldw[j];
+    Ud[j] = U[j];
+    ldud[j] = ldu[j];
+    lo_status rs;
+    if (w_host[j]) {
+      if ((rs = ensure_owned(b, &b->stage_in, &b->stage_in_cap, (size_t)b->n * b->s)) != LO_OK) return rs;
+      Wd[j] = b->stage_in;
+      ldwd[j] = b->s;
+    }
+    if (u_host[j]) {
+      if ((rs = ensure_owned(b, &b->stage_out, &b->stage_out_cap, (size_t)b->n * b->s)) != LO_OK) return rs;
+      Ud[j] = b->stage_out;
+      ldud[j] = b->s;
+    }
+  }
+  // the staging copies of host W run on the caller's stream before the graph
+  for (int j = 0; j < count; ++j) {
+    if (!w_host[j]) continue;
+    lo_basis* b = bases[j];
+    cudaError_t e = cudaMemcpy2DAsync(b->stage_in, b->s * sizeof(double), W[j], ldw[j] * sizeof(double),
+                                      b->s * sizeof(double), b->n, cudaMemcpyDefault, cs);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
   BatchGraphs& bg = batch_graphs();
-  std::lock_guard<std::mutex> lock(bg.mu);
+  std::unique_lock<std::mutex> lock(bg.mu);
   cudaError_t e = ensure_pool(bg, bases[0]->device);
   if (e != cudaSuccess) return from_cuda(e);
-  // key: everything the captured work depends on
+  // key: everything the captured work depends on; a basis by its id
   std::vector<uintptr_t> key;
-  key.reserve(9 * (size_t)count + 2);
+  key.reserve(kKeyPer * (size_t)count + kKeyHead);
   key.push_back((uintptr_t)count);
   key.push_back((uintptr_t)cs);
   for (int j = 0; j < count; ++j) {
-    key.push_back((uintptr_t)bases[j]);
+    key.push_back((uintptr_t)bases[j]->id);
     key.push_back((uintptr_t)bases[j]->nb);
-    key.push_back((uintptr_t)W[j]);
-    key.push_back((uintptr_t)ldw[j]);
-    key.push_back((uintptr_t)U[j]);
-    key.push_back((uintptr_t)ldu[j]);
-    key.push_back((uintptr_t)(H ? H[j] : nullptr));
-    key.push_back((uintptr_t)(R ? R[j] : nullptr));
+    key.push_back((uintptr_t)Wd[j]);
+    key.push_back((uintptr_t)ldwd[j]);
+    key.push_back((uintptr_t)Ud[j]);
+    key.push_back((uintptr_t)ldud[j]);
+    key.push_back((uintptr_t)Hd[j]);
+    key.push_back((uintptr_t)Rd[j]);
     key.push_back((uintptr_t)bases[j]->h_flags);
   }
   cudaGraphExec_t exec = nullptr;
@@ -569,12 +668,12 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
       lo_basis* b = bases[j];
       cudaStream_t st = bg.st[j % kPool];
       StepArgs a = make_args(b);
-      a.W = W[j];
-      a.ldw = ldw[j];
-      a.U = U[j];
-      a.ldu = ldu[j];
+      a.W = Wd[j];
+      a.ldw = ldwd[j];
+      a.U = Ud[j];
+      a.ldu = ldud[j];
       rs = from_cuda(lo::launch_step(a, st, nullptr));
-      if (rs == LO_OK) rs = copy_small_outputs(b, H ? H[j] : nullptr, R ? R[j] : nullptr, st);
+      if (rs == LO_OK) rs = copy_small_outputs(b, Hd[j], Rd[j], st);
       if (rs == LO_OK)
         rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
@@ -602,6 +701,18 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
   }
   for (int j = 0; j < count; ++j) bases[j]->h_flags[0] = 0;
   e = cudaGraphLaunch(exec, cs);
+  lock.unlock();
+  // host outputs: after the graph, on the same stream
+  for (int j = 0; j < count && e == cudaSuccess; ++j) {
+    lo_basis* b = bases[j];
+    if (u_host[j])
+      e = cudaMemcpy2DAsync(U[j], ldu[j] * sizeof(double), b->stage_out, b->s * sizeof(double),
+                            b->s * sizeof(double), b->n, cudaMemcpyDefault, cs);
+    if (e == cudaSuccess && (h_host[j] || r_host[j])) {
+      lo_status rs = copy_small_outputs(b, h_host[j] ? H[j] : nullptr, r_host[j] ? R[j] : nullptr, cs);
+      if (rs != LO_OK) return rs;
+    }
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   if (e != cudaSuccess) return from_cuda(e);
   lo_status first = LO_OK;
@@ -616,6 +727,17 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     }
   }
   return first;
+}
+
+uint64_t lo_basis_id(const lo_basis* b) { return b ? b->id : 0; }
+
+int32_t lo_batched_cache_entries(uint64_t basis_id) {
+  BatchGraphs& bg = batch_graphs();
+  std::lock_guard<std::mutex> lock(bg.mu);
+  if (basis_id == 0) return (int32_t)bg.cache.size();
+  int32_t c = 0;
+  for (auto& ent : bg.cache) c += key_names(ent.key, basis_id) ? 1 : 0;
+  return c;
 }
 
 lo_status lo_basis_truncate(lo_basis* b, int32_t num_blocks) {
@@ -716,18 +838,18 @@ lo_status lo_apply_Q(lo_basis* b, const double* C, int32_t m, int64_t ldc, doubl
   const double* Cd = C;
   int64_t ldcd = ldc;
   if (!is_device_ptr(C)) {
-    if ((rs = ensure(&b->cdev, &b->cdev_cap, (size_t)k * m)) != LO_OK) return rs;
+    if ((rs = ensure_owned(b, &b->cdev, &b->cdev_cap, (size_t)k * m)) != LO_OK) return rs;
     cudaError_t e = cudaMemcpy2DAsync(b->cdev, m * sizeof(double), C, ldc * sizeof(double), m * sizeof(double), k,
                                       cudaMemcpyDefault, st);
     if (e != cudaSuccess) return from_cuda(e);
     Cd = b->cdev;
     ldcd = m;
   }
-  if ((rs = ensure(&b->zq, &b->zq_cap, (size_t)b->p * k * m)) != LO_OK) return rs;
+  if ((rs = ensure_owned(b, &b->zq, &b->zq_cap, (size_t)b->p * k * m)) != LO_OK) return rs;
   double* Yd = Y;
   int64_t ldyd = ldy;
   if (!y_dev) {
-    if ((rs = ensure(&b->stage_out, &b->stage_out_cap, (size_t)n * m)) != LO_OK) return rs;
+    if ((rs = ensure_owned(b, &b->stage_out, &b->stage_out_cap, (size_t)n * m)) != LO_OK) return rs;
     Yd = b->stage_out;
     ldyd = m;
   }

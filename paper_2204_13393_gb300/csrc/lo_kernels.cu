@@ -1185,9 +1185,6 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-std::atomic<void*> g_noalloc_ptr[kNoAllocMaxDevices];
-
 __global__ void k_noalloc_tables(int64_t n, int cr, int p, int slab_rows, int spc, int spl,
                                  SlabInfo* slabs, int32_t* chunk_slab0, int64_t* chunk_row0) {
   const int nslab = (p - 1) * spc + spl;
@@ -1224,6 +1221,68 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 }  // namespace lo
 
+namespace lo {
+namespace {
+
+// Scratch layout of one lo_tsqr_noalloc call (byte offsets into the array),
+// validated and computed on the host before any device work.
+struct NoAllocLayout {
+  int p, nslab, slab_rows, spc, spl, ngroups;
+  size_t o_flags, o_slabs, o_cs0, o_cr0, o_part, o_small, o_glob, o_tsum, o_T, bytes;
+};
+
+lo_status noalloc_layout(int64_t n, int32_t s, int32_t chunk_rows, NoAllocLayout* L) {
+  if (n < 1 || s < 1 || s > kMaxS || chunk_rows < 1) return LO_ERR_INVALID_ARG;
+  const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
+  if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
+  const int p = (int)p64;
+  const int64_t min_rows = (p == 1) ? n : chunk_rows;
+  if (min_rows < s) return LO_ERR_CHUNK_TOO_SMALL;
+  const int slab_rows = 16 * s > 256 ? 16 * s : 256;
+  const int64_t rows_last = n - (int64_t)(p - 1) * chunk_rows;
+  const int64_t spc = (chunk_rows + slab_rows - 1) / slab_rows;
+  const int64_t spl = (rows_last + slab_rows - 1) / slab_rows;
+  const int64_t nslab64 = (int64_t)(p - 1) * spc + spl;
+  if (nslab64 > (1 << 30) || spl > (1 << 30)) return LO_ERR_INVALID_ARG;
+  const int nslab = (int)nslab64;
+  const int ngroups = (p + kTreeGroup - 1) / kTreeGroup;
+  const SmallLayout SL = SmallLayout::make(s, s);
+  const GlobLayout GL = GlobLayout::make(s, s);
+  const size_t ss = (size_t)s * s;
+  size_t off = 0;
+  L->o_flags = off;   off = align256(off + sizeof(int) * kFlagCount);
+  L->o_slabs = off;   off = align256(off + sizeof(SlabInfo) * (size_t)nslab);
+  L->o_cs0 = off;     off = align256(off + sizeof(int32_t) * (size_t)(p + 1));
+  L->o_cr0 = off;     off = align256(off + sizeof(int64_t) * (size_t)(p + 1));
+  L->o_part = off;    off = align256(off + sizeof(double) * (size_t)nslab * ss);
+  L->o_small = off;   off = align256(off + sizeof(double) * (size_t)p * SL.stride);
+  L->o_glob = off;    off = align256(off + sizeof(double) * (size_t)GL.stride);
+  L->o_tsum = off;    off = align256(off + sizeof(double) * (size_t)ngroups * ss);
+  L->o_T = off;       off = align256(off + sizeof(double) * (size_t)p * ss);
+  L->bytes = off;
+  L->p = p;
+  L->nslab = nslab;
+  L->slab_rows = slab_rows;
+  L->spc = (int)spc;
+  L->spl = (int)spl;
+  L->ngroups = ngroups;
+  return LO_OK;
+}
+
+}  // namespace
+}  // namespace lo
+
+extern "C" lo_status lo_tsqr_noalloc_scratch(int64_t n, int32_t s, int32_t chunk_rows, uint64_t* need_bytes,
+                                             uint64_t* capacity_bytes) {
+  using namespace lo;
+  if (capacity_bytes) *capacity_bytes = kNoAllocScratchBytes;
+  NoAllocLayout L;
+  const lo_status st = noalloc_layout(n, s, chunk_rows, &L);
+  if (st != LO_OK) return st;
+  if (need_bytes) *need_bytes = L.bytes;
+  return L.bytes > kNoAllocScratchBytes ? LO_ERR_CAPACITY : LO_OK;
+}
+
 extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, const double* W,
                                      int64_t ldw, double* U, double* R, void* cuda_stream) {
   using namespace lo;
@@ -1235,51 +1294,25 @@ extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, c
     const double* uend = U + n * s;
     if (!(uend <= W || wend <= U)) return LO_ERR_INVALID_ARG;
   }
-  const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
-  if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
-  const int p = (int)p64;
-  const int64_t min_rows = (p == 1) ? n : chunk_rows;
-  if (min_rows < s) return LO_ERR_CHUNK_TOO_SMALL;
-  const int slab_rows = 16 * s > 256 ? 16 * s : 256;
-  const int64_t rows_last = n - (int64_t)(p - 1) * chunk_rows;
-  const int spc = (int)((chunk_rows + slab_rows - 1) / slab_rows);
-  const int spl = (int)((rows_last + slab_rows - 1) / slab_rows);
-  const int64_t nslab64 = (int64_t)(p - 1) * spc + spl;
-  if (nslab64 > (1 << 30)) return LO_ERR_INVALID_ARG;
-  const int nslab = (int)nslab64;
-  const int ngroups = (p + kTreeGroup - 1) / kTreeGroup;
-  const SmallLayout SL = SmallLayout::make(s, s);
+  // sizes first: a problem that does not fit is rejected before any CUDA call
+  NoAllocLayout lay;
+  lo_status st = noalloc_layout(n, s, chunk_rows, &lay);
+  if (st != LO_OK) return st;
+  if (lay.bytes > kNoAllocScratchBytes) return LO_ERR_CAPACITY;
+  const int p = lay.p, nslab = lay.nslab;
   const GlobLayout GL = GlobLayout::make(s, s);
   const size_t ss = (size_t)s * s;
-  // scratch layout
-  size_t off = 0;
-  const size_t o_flags = off;   off = align256(off + sizeof(int) * kFlagCount);
-  const size_t o_slabs = off;   off = align256(off + sizeof(SlabInfo) * (size_t)nslab);
-  const size_t o_cs0 = off;     off = align256(off + sizeof(int32_t) * (size_t)(p + 1));
-  const size_t o_cr0 = off;     off = align256(off + sizeof(int64_t) * (size_t)(p + 1));
-  const size_t o_part = off;    off = align256(off + sizeof(double) * (size_t)nslab * ss);
-  const size_t o_small = off;   off = align256(off + sizeof(double) * (size_t)p * SL.stride);
-  const size_t o_glob = off;    off = align256(off + sizeof(double) * (size_t)GL.stride);
-  const size_t o_tsum = off;    off = align256(off + sizeof(double) * (size_t)ngroups * ss);
-  const size_t o_T = off;       off = align256(off + sizeof(double) * (size_t)p * ss);
-  if (off > kNoAllocScratchBytes) return LO_ERR_CAPACITY;
 
-  // once per device: the device address of the scratch array
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+  // The device address of the scratch array in the current context, looked up
+  // on every call (cheap next to the synchronization below): after a device
+  // reset the module is loaded again, possibly at another address.
+  void* base = nullptr;
+  if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) {
     cudaGetLastError();
     return LO_ERR_CUDA;
   }
-  void* base = g_noalloc_ptr[dev].load();
-  if (!base) {
-    if (cudaGetSymbolAddress(&base, g_noalloc_scratch) != cudaSuccess || !base) {
-      cudaGetLastError();
-      return LO_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev].store(base);
-  }
   unsigned char* sc = static_cast<unsigned char*>(base);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
 
   StepArgs a{};
   a.n = n;
@@ -1289,20 +1322,20 @@ extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, c
   a.nb = 0;
   a.Kmax = s;
   a.V = U;                    // the local panel of block 0 is the caller's U
-  a.T = reinterpret_cast<double*>(sc + o_T);
+  a.T = reinterpret_cast<double*>(sc + lay.o_T);
   a.tstride = (int64_t)ss;
-  a.part = reinterpret_cast<double*>(sc + o_part);
-  a.small = reinterpret_cast<double*>(sc + o_small);
-  a.glob = reinterpret_cast<double*>(sc + o_glob);
-  a.tsum = reinterpret_cast<double*>(sc + o_tsum);
-  a.flags = reinterpret_cast<int*>(sc + o_flags);
-  a.slabs = reinterpret_cast<const SlabInfo*>(sc + o_slabs);
-  a.chunk_slab0 = reinterpret_cast<const int32_t*>(sc + o_cs0);
-  a.chunk_row0 = reinterpret_cast<const int64_t*>(sc + o_cr0);
+  a.part = reinterpret_cast<double*>(sc + lay.o_part);
+  a.small = reinterpret_cast<double*>(sc + lay.o_small);
+  a.glob = reinterpret_cast<double*>(sc + lay.o_glob);
+  a.tsum = reinterpret_cast<double*>(sc + lay.o_tsum);
+  a.flags = reinterpret_cast<int*>(sc + lay.o_flags);
+  a.slabs = reinterpret_cast<const SlabInfo*>(sc + lay.o_slabs);
+  a.chunk_slab0 = reinterpret_cast<const int32_t*>(sc + lay.o_cs0);
+  a.chunk_row0 = reinterpret_cast<const int64_t*>(sc + lay.o_cr0);
   a.nslab = nslab;
-  a.slab_rows = slab_rows;
+  a.slab_rows = lay.slab_rows;
   a.precision = LO_PREC_FP64;
-  a.leaf = LO_LEAF_AUTO;
+  a.leaf = LO_LEAF_PIP2;      // the library default (BCGS-PIP+, Alg. 8)
   a.reduction = 0;
   a.refine_tol = 1e-13;
   a.W = W;
@@ -1311,23 +1344,23 @@ extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, c
   a.ldu = s;
 
   // the status word must start at zero; everything else is written before it is read
-  cudaError_t e = cudaMemsetAsync(a.flags, 0, sizeof(int) * kFlagCount, st);
+  cudaError_t e = cudaMemsetAsync(a.flags, 0, sizeof(int) * kFlagCount, stream);
   if (e == cudaSuccess) {
     int blocks = (nslab + 255) / 256;
     if (blocks > 1024) blocks = 1024;
-    k_noalloc_tables<<<blocks, 256, 0, st>>>(n, chunk_rows, p, slab_rows, spc, spl,
-                                              reinterpret_cast<SlabInfo*>(sc + o_slabs),
-                                              reinterpret_cast<int32_t*>(sc + o_cs0),
-                                              reinterpret_cast<int64_t*>(sc + o_cr0));
+    k_noalloc_tables<<<blocks, 256, 0, stream>>>(n, chunk_rows, p, lay.slab_rows, lay.spc, lay.spl,
+                                                  reinterpret_cast<SlabInfo*>(sc + lay.o_slabs),
+                                                  reinterpret_cast<int32_t*>(sc + lay.o_cs0),
+                                                  reinterpret_cast<int64_t*>(sc + lay.o_cr0));
     count_launches(1);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = launch_step(a, st, nullptr);
+  if (e == cudaSuccess) e = launch_step(a, stream, nullptr);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(R, a.glob + GL.N_acc, sizeof(double) * ss, cudaMemcpyDeviceToDevice, st);
+    e = cudaMemcpyAsync(R, a.glob + GL.N_acc, sizeof(double) * ss, cudaMemcpyDeviceToDevice, stream);
   int bits = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, a.flags, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, a.flags, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return LO_ERR_CUDA;

@@ -41,7 +41,8 @@ EXPORTED = [
     "lo_basis_reset", "lo_basis_num_blocks", "lo_basis_num_chunks", "lo_basis_sync",
     "lo_orthogonalize", "lo_orthogonalize_batched", "lo_apply_Q", "lo_basis_export_chunk",
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
-    "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_basis_truncate", "lo_tune_chunk_rows",
+    "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_tsqr_noalloc_scratch", "lo_basis_truncate",
+    "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
@@ -109,6 +110,13 @@ def _lib():
     L.lo_basis_last_step_info.restype = c_int32
     L.lo_tsqr_noalloc.argtypes = [c_int64, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
     L.lo_tsqr_noalloc.restype = c_int32
+    L.lo_tsqr_noalloc_scratch.argtypes = [c_int64, c_int32, c_int32, POINTER(ctypes.c_uint64),
+                                          POINTER(ctypes.c_uint64)]
+    L.lo_tsqr_noalloc_scratch.restype = c_int32
+    L.lo_basis_id.argtypes = [c_void_p]
+    L.lo_basis_id.restype = ctypes.c_uint64
+    L.lo_batched_cache_entries.argtypes = [ctypes.c_uint64]
+    L.lo_batched_cache_entries.restype = c_int32
     L.lo_basis_truncate.argtypes = [c_void_p, c_int32]
     L.lo_basis_truncate.restype = c_int32
     L.lo_tune_chunk_rows.argtypes = [c_int64, c_int32, c_int32, POINTER(Options), c_void_p, POINTER(c_int32)]
@@ -214,6 +222,11 @@ class Basis:
         return self._h
 
     @property
+    def id(self) -> int:
+        """Process-unique id of the basis (never reused)."""
+        return int(_lib().lo_basis_id(self._h))
+
+    @property
     def num_blocks(self) -> int:
         return _lib().lo_basis_num_blocks(self._h)
 
@@ -287,7 +300,7 @@ class Basis:
 
 
 def orthogonalize_batched(bases, Ws, Us, Hs=None, Rs=None):
-    """lo_orthogonalize_batched over device tensors."""
+    """lo_orthogonalize_batched: torch tensors (device or host) or numpy arrays."""
     cnt = len(bases)
     arr = lambda vals, t: (t * cnt)(*vals)
     hb = arr([b.handle.value for b in bases], c_void_p)
@@ -298,6 +311,19 @@ def orthogonalize_batched(bases, Ws, Us, Hs=None, Rs=None):
     ph = arr([_ptr(h) for h in Hs], c_void_p) if Hs is not None else None
     pr = arr([_ptr(r) for r in Rs], c_void_p) if Rs is not None else None
     _check(_lib().lo_orthogonalize_batched(hb, cnt, pw, lw, pu, lu, ph, pr), "lo_orthogonalize_batched")
+
+
+def tsqr_noalloc_scratch(n: int, s: int, chunk_rows: int):
+    """(status name, bytes needed, bytes available) of lo_tsqr_noalloc's scratch
+    for this problem (host-only)."""
+    need, cap = ctypes.c_uint64(), ctypes.c_uint64()
+    code = _lib().lo_tsqr_noalloc_scratch(int(n), int(s), int(chunk_rows), ctypes.byref(need), ctypes.byref(cap))
+    return STATUS.get(code, str(code)), int(need.value), int(cap.value)
+
+
+def batched_cache_entries(basis_id: int = 0) -> int:
+    """Cached batched graphs that name the basis with this id (0: all)."""
+    return int(_lib().lo_batched_cache_entries(int(basis_id)))
 
 
 def tsqr_noalloc(W, U, R, chunk_rows: int, stream=None):

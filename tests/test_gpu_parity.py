@@ -367,6 +367,77 @@ def test_batched_graph_reuse_and_truncate():
         bases[0].truncate(bases[0].num_blocks + 1)
 
 
+def test_batched_cache_evicts_destroyed_bases():
+    """Cached batched graphs name their bases by process-unique ids: destroying
+    a basis evicts every graph that names it, and bases created afterwards
+    (their handles may reuse freed addresses) get new ids and new graphs whose
+    results match the oracle."""
+    L = lo()
+
+    def make(n, s, kb, seed):
+        b = L.Basis(n, s, kb + 1, 1000)
+        o = O.LocallyOrthogonalBasis(n, s, 1000)
+        for j in range(kb):
+            Wh = I.gaussian(n, s, seed + j)
+            b.orthogonalize(dev(Wh))
+            o.orthogonalize(Wh, "hh", "hh")
+        return b, o
+
+    seen = set()
+    for rnd, specs in enumerate([[(6000, 8, 2), (9000, 4, 3)], [(7000, 16, 1), (5000, 8, 3)],
+                                 [(6000, 8, 2), (9000, 4, 3)]]):
+        pairs = [make(n, s, kb, 8000 + 100 * rnd + 10 * i) for i, (n, s, kb) in enumerate(specs)]
+        bases = [b for b, _ in pairs]
+        ids = [b.id for b in bases]
+        assert not (set(ids) & seen)          # ids are never reused
+        seen |= set(ids)
+        Ws, Us, Hs, Rs, want = [], [], [], [], []
+        for i, ((b, o), (n, s, kb)) in enumerate(zip(pairs, specs)):
+            Wh = I.gaussian(n, s, 8090 + 100 * rnd + i)
+            want.append(o.orthogonalize(Wh, "hh", "hh"))
+            Ws.append(dev(Wh))
+            Us.append(torch.empty(n, s, dtype=torch.float64, device="cuda"))
+            Hs.append(torch.empty(kb * s, s, dtype=torch.float64, device="cuda"))
+            Rs.append(torch.empty(s, s, dtype=torch.float64, device="cuda"))
+        L.orthogonalize_batched(bases, Ws, Us, Hs, Rs)
+        for (Uo, Po, No), U, H, R in zip(want, Us, Hs, Rs):
+            assert rel(host(U), Uo) <= TOL_REL and rel(host(H), Po) <= TOL_REL and rel(host(R), No) <= TOL_REL
+        assert all(L.batched_cache_entries(i) == 1 for i in ids)
+        for b in bases:
+            b.close()
+        assert all(L.batched_cache_entries(i) == 0 for i in ids)
+
+
+def test_batched_host_buffers():
+    """Host W, U, H, R in the batched call: staged like lo_orthogonalize, with
+    the same results bit for bit as device buffers in a twin set of bases."""
+    L = lo()
+    specs = [(5000, 4, 2), (7000, 8, 1), (3001, 16, 2)]
+    bd, bh, Wd, Ud, Hd, Rd, Wh_, Uh_, Hh_, Rh_ = [], [], [], [], [], [], [], [], [], []
+    for i, (n, s, kb) in enumerate(specs):
+        b1, b2 = L.Basis(n, s, kb + 1, 1000), L.Basis(n, s, kb + 1, 1000)
+        for j in range(kb):
+            Wj = dev(I.gaussian(n, s, 8200 + 10 * i + j))
+            b1.orthogonalize(Wj)
+            b2.orthogonalize(Wj)
+        bd.append(b1)
+        bh.append(b2)
+        Wn = I.gaussian(n, s, 8290 + i)
+        Wd.append(dev(Wn))
+        Wh_.append(Wn)
+        Ud.append(torch.empty(n, s, dtype=torch.float64, device="cuda"))
+        Hd.append(torch.empty(kb * s, s, dtype=torch.float64, device="cuda"))
+        Rd.append(torch.empty(s, s, dtype=torch.float64, device="cuda"))
+        Uh_.append(np.zeros((n, s)))
+        Hh_.append(np.zeros((kb * s, s)))
+        Rh_.append(np.zeros((s, s)))
+    L.orthogonalize_batched(bd, Wd, Ud, Hd, Rd)
+    L.orthogonalize_batched(bh, Wh_, Uh_, Hh_, Rh_)
+    for U, H, R, Uh, Hh, Rh in zip(Ud, Hd, Rd, Uh_, Hh_, Rh_):
+        assert np.array_equal(host(U), Uh) and np.array_equal(host(H), Hh) and np.array_equal(host(R), Rh)
+    assert [b.num_blocks for b in bh] == [kb + 1 for (_, _, kb) in specs]
+
+
 def test_chunk_rows_tuner():
     L = lo()
     cr = L.tune_chunk_rows(200000, 8, 6)

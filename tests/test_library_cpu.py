@@ -130,3 +130,30 @@ def test_tuner_and_noalloc_reject_bad_arguments_without_device(lib):
     ]
     for args, want in cases:
         assert lib.lo_tsqr_noalloc(*args, None) == want, args
+
+
+def test_noalloc_scratch_query_without_device(lib):
+    """lo_tsqr_noalloc_scratch sizes the fixed scratch on the host alone: small
+    problems fit, tiny chunks of a wide block do not, and bad sizes give the
+    entry point's own argument errors."""
+    from paper_2204_13393_gb300 import lo
+
+    st, need, cap = lo.tsqr_noalloc_scratch(100000, 8, 4096)
+    assert st == "LO_OK" and 0 < need <= cap and cap == 16 << 20
+    st2, need2, _ = lo.tsqr_noalloc_scratch(200000, 8, 4096)
+    assert st2 == "LO_OK" and need2 > need            # more chunks and slabs, more scratch
+    st, need, cap = lo.tsqr_noalloc_scratch(65536, 32, 32)   # 2048 chunks of 32 x 32 factors
+    assert st == "LO_ERR_CAPACITY" and need > cap
+    st, need, cap = lo.tsqr_noalloc_scratch(2 ** 26, 32, 512)
+    assert st == "LO_ERR_CAPACITY" and need > cap
+    assert lo.tsqr_noalloc_scratch(0, 8, 16)[0] == "LO_ERR_INVALID_ARG"
+    assert lo.tsqr_noalloc_scratch(64, 33, 16)[0] == "LO_ERR_INVALID_ARG"
+    assert lo.tsqr_noalloc_scratch(64, 8, 4)[0] == "LO_ERR_CHUNK_TOO_SMALL"
+    assert lib.lo_tsqr_noalloc_scratch(64, 8, 16, None, None) == 0
+
+
+def test_batched_cache_hooks_without_device(lib):
+    """The cache inspection hooks are host-only: no basis, no entries."""
+    assert lib.lo_basis_id(None) == 0
+    assert lib.lo_batched_cache_entries(0) == 0
+    assert lib.lo_batched_cache_entries(12345) == 0

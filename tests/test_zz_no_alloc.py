@@ -88,10 +88,34 @@ def test_noalloc_in_place_and_repeat(L):
 
 
 def test_noalloc_rejects_oversized_problem(L):
+    """A problem whose scratch exceeds the fixed array is rejected before any
+    device work, with real buffers: 2048 chunks of a 32-column block need far
+    more than the array holds (the host-only size query says so too).  The
+    output buffers are left untouched."""
+    n, s, cr = 65536, 32, 32
+    st, need, cap = L.tsqr_noalloc_scratch(n, s, cr)
+    assert st == "LO_ERR_CAPACITY" and need > cap
+    W = torch.from_numpy(I.gaussian(n, s, I.seed_for(7, 30))).cuda()
+    U = torch.full((n, s), 3.0, dtype=torch.float64, device="cuda")
+    R = torch.full((s, s), 5.0, dtype=torch.float64, device="cuda")
     lib = L.library()
-    n, s = 2 ** 26, 32
-    W = ctypes.c_void_p(1 << 40)
-    U = ctypes.c_void_p(2 << 40)
-    R = ctypes.c_void_p(3 << 40)
-    # the scratch size check happens before any device work or pointer use
-    assert lib.lo_tsqr_noalloc(n, s, 512, W, s, U, R, None) == 2  # LO_ERR_CAPACITY
+    code = lib.lo_tsqr_noalloc(n, s, cr, ctypes.c_void_p(W.data_ptr()), s, ctypes.c_void_p(U.data_ptr()),
+                               ctypes.c_void_p(R.data_ptr()),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 2  # LO_ERR_CAPACITY
+    torch.cuda.synchronize()
+    assert bool((U == 3.0).all()) and bool((R == 5.0).all())
+
+
+def test_noalloc_ill_conditioned(L):
+    """kappa = 1e8 (the top of the float64 tolerance range): the reiterated
+    leaf keeps U^T U = I to 1e-12, and U, R agree with the allocating path."""
+    n, s, cr = 60000, 8, 4096
+    Wh = I.stewart(n, s, 1e8, I.seed_for(7, 40))
+    W = torch.from_numpy(Wh).cuda()
+    U0, R0 = _reference(L, W, cr)
+    U1, R1 = _noalloc(L, W, cr)
+    assert np.linalg.norm(U1.T @ U1 - np.eye(s)) <= 1e-12
+    assert np.linalg.norm(Wh - U1 @ R1) / np.linalg.norm(Wh) <= 1e-13
+    assert _rel(U1, U0) <= max(TOL_REL, 100 * 1e8 * np.finfo(float).eps)
+    assert _rel(R1, R0) <= max(TOL_REL, 100 * 1e8 * np.finfo(float).eps)
