@@ -102,6 +102,15 @@ def gram_bytes_flops(n, s, k):
     return 8 * n * (k + s), 2 * n * (k + s) * s
 
 
+def refine_bytes_flops(n, s, k, passes):
+    """Bytes and float64 flops the reiteration passes of one step must move and
+    do (BCGS-PIP+, Alg. 8): per pass >= 2 the iterate Y = (A - Q P) N^{-1} reads
+    [Q A] and writes Y (8nK + 8ns), and its Gram [Q Y]^T Y reads [Q Y] (8nK)."""
+    K = k + s
+    extra = max(0, int(passes) - 1)
+    return extra * (16 * n * K + 8 * n * s), extra * (4 * n * K * s)
+
+
 def strip_comments(text):
     """C/C++ source without its comments, with every run of whitespace outside
     string and character literals as one space (the literals kept as they
@@ -223,9 +232,11 @@ def replica_reduce(ms_local, bytes_local, dist=None, device=None):
     return float(t.item()), int(b.item())
 
 
-def gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events, record=None):
+def gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events, record=None, passes=None):
     """One restart cycle on the device.  events: list receiving (start, end)
-    CUDA event pairs around each hot-path call.  Returns the apply_Q result."""
+    CUDA event pairs around each hot-path call; passes (untimed cycles only):
+    list receiving the local Gram passes each step ran.  Returns the apply_Q
+    result."""
     n, s = B.shape
     m = M_RESTART
     basis.reset()
@@ -244,6 +255,8 @@ def gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events, record=None):
 
     # V_0 H_0 = R0 (x0 = 0, so R0 = B)
     timed(lambda: basis.orthogonalize(B, U=U, H=None, R=Rbuf[0]))
+    if passes is not None:
+        passes.append(basis.last_step_info()[0])
     if record is not None:
         record.append(B.clone())
     for j in range(m):
@@ -252,6 +265,8 @@ def gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, events, record=None):
             record.append(X.clone())
         k = (j + 1) * s
         timed(lambda: basis.orthogonalize(X, U=U, H=Hbuf[j][:k], R=Rbuf[j + 1]))
+        if passes is not None:
+            passes.append(basis.last_step_info()[0])
     # small least-squares on the host (harness; untimed)
     torch.cuda.current_stream().synchronize()
     basis.sync()
@@ -302,6 +317,9 @@ def run_gpu(args):
     for _ in range(args.warmup):
         ev = []
         gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, ev)
+    # the local passes of every step (the steps are bit for bit the same every cycle)
+    step_passes = []
+    gmres_cycle(lo, torch, basis, B, stream, Hbuf, Rbuf, [], passes=step_passes)
     torch.cuda.synchronize()
     basis.profile_read()
     basis.set_profiling(True)
@@ -335,14 +353,20 @@ def run_gpu(args):
     e_perp = float(torch.linalg.norm(G - torch.eye(G.shape[0], dtype=torch.float64, device=dev)))
     del Q, G
 
-    # dominant kernel group (pass-1 Gram or stage-2 assembly) and its roofline
+    # dominant kernel group (pass-1 Gram, stage-2 assembly or the reiteration
+    # passes) and its roofline
     hbm_peak, hbm_src = peaks()
     tc = args.precision in ("fp64_tc", "mixed_tc")
     kinds = {g: v for g, v in prof.items() if v[1] > 0}
-    dom = "update" if kinds.get("update", (0,))[0] >= kinds.get("gram", (0,))[0] else "gram"
+    dom = max((g for g in ("gram", "update", "refine") if g in kinds), key=lambda g: kinds[g][0])
     bsum = fsum = 0
     for j in range(m + 1):
-        b_, f_ = update_bytes_flops(n, s, j * s, p) if dom == "update" else gram_bytes_flops(n, s, j * s)
+        if dom == "update":
+            b_, f_ = update_bytes_flops(n, s, j * s, p)
+        elif dom == "gram":
+            b_, f_ = gram_bytes_flops(n, s, j * s)
+        else:
+            b_, f_ = refine_bytes_flops(n, s, j * s, step_passes[j])
         bsum += b_ * args.steps
         fsum += f_ * args.steps
     t_dom = kinds[dom][0] * 1e-3
@@ -354,8 +378,10 @@ def run_gpu(args):
                if cap else None)
     if tc:
         # s = 8, 16, 32 keep digit planes of the prior panels: tcgen05 kernels
-        kernel_name = ({"update": "k_umma_update", "gram": "k_umma_gram"} if s in (8, 16, 32)
-                       else {"update": "k_oz_update", "gram": "k_oz_gram"})[dom]
+        kernel_name = ({"update": "k_umma_update", "gram": "k_umma_gram",
+                        "refine": "k_umma_update<S,1> + k_umma_gram (passes >= 2)"} if s in (8, 16, 32)
+                       else {"update": "k_oz_update", "gram": "k_oz_gram",
+                             "refine": "k_oz_update + k_oz_gram (passes >= 2)"})[dom]
         # tensor work: 28 fp16 digit-pair products per float64 product, 2 flops each
         tens_tf = 28 * fsum / t_dom / 1e12
         tens_peak = peaks_bf16()
@@ -371,7 +397,7 @@ def run_gpu(args):
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 mma at the same rate)",
                     "hbm_achieved_gbs": round(ach_gbs, 1), "launches": kinds[dom][1]}
     else:
-        kernel_name = {"update": "k_update", "gram": "k_gram1"}[dom]
+        kernel_name = {"update": "k_update", "gram": "k_gram1", "refine": "k_gram (passes >= 2)"}[dom]
         roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                 "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                 "kernel": kernel_name, "peak_source": "float64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz",
@@ -383,6 +409,11 @@ def run_gpu(args):
         e2e = run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, args.precision, chunk)
         cpu = cpu_baseline(args.cpu_budget) if world == 1 or rank == 0 else None
         clocks = clk.summary()
+        targets = None
+        if not args.no_targets and world == 1:
+            basis.close()
+            torch.cuda.empty_cache()
+            targets = target_points(lo, torch, dev, args)
         out = {
             "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_local / args.steps, 4), "higher_is_better": True,
@@ -408,7 +439,10 @@ def run_gpu(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "e_perp_final": e_perp,
+            "step_passes": step_passes,
         }
+        if targets is not None:
+            out.update(targets)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -448,66 +482,127 @@ def run_e2e(lo, torch, dev, basis, B, stream, n, s, m, p, basis_precision, chunk
 
 # --------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(budget_s):
-    """Time the oracle (TreeTSPQR, BCGS-PIP+ sub-algorithms) on the first
-    orthogonalization steps of the same cycle at full n, until the budget is
-    spent.  Returns (bytes, seconds, steps done)."""
+# The cycle's 31 orthogonalization depths k = 8 j, j = 0..30, in bisection
+# order, so that any prefix of the sample spreads over the whole k range.
+SPREAD = [0, 30, 15, 7, 23, 3, 11, 19, 27, 1, 5, 9, 13, 17, 21, 25, 29,
+          2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 24, 26, 28]
+
+
+def oracle_basis_at_depth(O, n, s, cr, k):
+    """An oracle basis holding k columns, built without running k / s steps:
+    local factors Q_i = the first k unit vectors of the chunk (orthonormal) and
+    tree factors T_i = I / sqrt(p) (upper triangular, sum_i T_i^T T_i = I), a
+    valid locally orthogonal representation (Sec. 4.1) with the shapes of the
+    cycle's basis at that depth; the oracle's work per step depends on those
+    shapes only."""
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    p = len(ora.bounds)
+    for i, (b, e) in enumerate(ora.bounds):
+        Qi = np.zeros((e - b, k))
+        Qi[np.arange(k), np.arange(k)] = 1.0
+        ora.Qloc[i] = Qi
+        ora.T[i] = np.eye(k) / np.sqrt(p)
+    return ora
+
+
+def oracle_sample(budget_s, depths=None):
+    """Time the oracle (TreeTSPQR, BCGS-PIP+ local and reduction solvers, as
+    the GPU arm runs) on orthogonalization steps of the cycle at full n, at the
+    cycle's own depths (``depths``: indices j of k = 8 j; default: bisection
+    order until the budget is spent).  Returns (bytes, seconds, depths done)."""
     from oracle import lo_oracle as O
     from paper_2204_13393_gb300 import inputs as I
 
     n, s = NX * NY, S
-    B = I.uniform(n, s, I.seed_for(2, 0))
-    ora = O.LocallyOrthogonalBasis(n, s, CHUNK)
-    p = len(ora.bounds)
-
-    def lap(V):
-        G = V.reshape(NY, NX, -1)
-        out = 4 * G
-        out[:, 1:] -= G[:, :-1]
-        out[:, :-1] -= G[:, 1:]
-        out[1:] -= G[:-1]
-        out[:-1] -= G[1:]
-        return out.reshape(n, -1)
-
-    X = B
+    order = list(depths) if depths is not None else SPREAD
     t = 0.0
     nbytes = 0
-    steps = 0
-    for j in range(M_RESTART + 1):
+    done = []
+    for j in order:
         k = j * s
+        ora = oracle_basis_at_depth(O, n, s, CHUNK, k)
+        p = len(ora.bounds)
+        W = I.uniform(n, s, I.seed_for(2, 100 + j))
         t0 = time.perf_counter()
-        U, _, _ = ora.orthogonalize(X, "pip2", "pip2")
+        ora.orthogonalize(W, "pip2", "pip2")
         t += time.perf_counter() - t0
         nbytes += orth_bytes(n, s, k, p)
-        steps += 1
-        if t >= budget_s:
+        done.append(j)
+        del ora
+        if depths is None and t >= budget_s:
             break
-        X = lap(U)
-    return nbytes, t, steps
+    return nbytes, t, done
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def _depth_text(done):
+    ks = sorted(8 * j for j in done)
+    return f"{len(done)} of the cycle's 31 depths (k = {', '.join(map(str, ks))})"
 
 
 def cpu_baseline(budget_s):
-    nbytes, t, steps = oracle_sample(budget_s)
-    return {"value": round(nbytes / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {steps} of the 31 orthogonalizations of the cycle (k=0..{8 * (steps - 1)}) at "
-                      f"n=1048576, numpy oracle TreeTSPQR with BCGS-PIP+ local and reduction, "
-                      f"single-threaded BLAS; {t:.1f} s"}
+    """The oracle on this host's cores: single-threaded in this process, and
+    with every core's BLAS threads in a child process (the same sample)."""
+    nbytes, t, done = oracle_sample(budget_s)
+    out = {"value": round(nbytes / t / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"one orthogonalization step at each of {_depth_text(done)}, n=1048576, from a "
+                     f"locally orthogonal basis of that depth; numpy oracle TreeTSPQR with BCGS-PIP+ local "
+                     f"and reduction, single-threaded BLAS; {t:.1f} s"}
+    cores = _cores()
+    if cores > 1:
+        env = dict(os.environ)
+        for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(cores)
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample",
+                                ",".join(map(str, done))], env=env, capture_output=True, text=True,
+                               timeout=max(60.0, 4 * budget_s))
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            out["all_cores"] = {"value": round(d["bytes"] / d["seconds"] / 1e9, 4), "unit": "GB/s",
+                                "cores": cores, "seconds": round(d["seconds"], 2),
+                                "sample": "the same steps, BLAS with one thread per core"}
+        except Exception as exc:  # report, never fail the GPU line for the baseline
+            out["all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+    return out
+
+
+def run_cpu_sample(arg):
+    depths = [int(x) for x in arg.split(",") if x]
+    b, t, done = oracle_sample(0.0, depths)
+    print(json.dumps({"bytes": b, "seconds": t, "depths": done}), flush=True)
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on this host's cores, on the
+    cycle's metric; each step times two orthogonalizations of the cycle at
+    full n, the depths following the bisection order, so the steps together
+    sample the same k mix as the GPU arm's cycle."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    per = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    pos = 0
+
+    def step():
+        nonlocal pos
+        ds = [SPREAD[pos % len(SPREAD)], SPREAD[(pos + 1) % len(SPREAD)]]
+        pos += 2
+        return oracle_sample(0.0, ds)
+
     for _ in range(args.warmup):
-        oracle_sample(per)
+        step()
     tot_b = tot_t = 0.0
-    steps_done = []
+    depths = []
     for _ in range(args.steps):
-        b, t, k = oracle_sample(per)
+        b, t, d = step()
         tot_b += b
         tot_t += t
-        steps_done.append(k)
+        depths += d
     gbs = tot_b / tot_t / 1e9
     return {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
@@ -518,9 +613,9 @@ def run_reference(args):
                                    "stencil and host least-squares untimed",
                        "n": NX * NY, "s": S, "restart_blocks": M_RESTART, "chunk_rows": CHUNK},
             "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: the first {min(steps_done)}-{max(steps_done)} "
-                                       f"orthogonalizations of the cycle at full n (numpy oracle, "
-                                       f"single-threaded BLAS)"},
+                             "sample": f"each step: two orthogonalization steps of the cycle at full n "
+                                       f"(numpy oracle, single-threaded BLAS); timed steps covered "
+                                       f"{_depth_text(sorted(set(depths)))}"},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -627,76 +722,127 @@ def run_batched_case(args):
           flush=True)
 
 
+def mixed_measure(lo, torch, dev, n, cr, kappas, reps, check_n=8192):
+    """Mixed-precision workload: n rows, s = 16, 30 prior blocks (480 columns,
+    Gaussian, built untimed; regenerated from one seed for each form, so only
+    one basis is resident at a time), new block a Stewart-type matrix
+    U diag(sigma) V^T with kappa from ``kappas`` (orthonormal factors by
+    CholeskyQR2 of Gaussians) plus a component along the last prior block.
+    Each step is timed with CUDA events for the float64 tensor-core form and
+    the mixed tensor-core form.  Per result: the step's orthogonality
+    sqrt(|U^T U - I|^2 + 2 |Q^T U|^2) (Q^T U measured by one more projection
+    of U: the H output of a PQR step of U) and its residual
+    |W - Q H - U R| / |W|; and, on a sampled run of the same shape at
+    n = check_n rows (the oracle at full n would take hours), the U, H, R
+    error of each form against the CPU oracle (BCGS-PIP+ TreeTSPQR)."""
+    s, kb = 16, 30
+    out = {"n": n, "s": s, "k": kb * s, "chunk_rows": cr, "results": []}
+    Ws = {}
+    for kappa in kappas:
+        g = torch.Generator(device=dev)
+        g.manual_seed(2204133930 + 4100 + int(round(np.log10(kappa))))
+        Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+        Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+        sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device=dev)
+        Ws[kappa] = ((Uh * sig) @ Vh.T).cpu()
+        del Uh
+    rows = {kappa: {"kappa": kappa} for kappa in kappas}
+    nbytes = orth_bytes(n, s, kb * s, max(1, n // cr))
+    for prec in ("fp64_tc", "mixed_tc"):
+        b = lo.Basis(n, s, kb + 2, cr, precision=prec, sync=True)
+        g = torch.Generator(device=dev)
+        g.manual_seed(2204133930 + 4000)
+        last = None
+        for _ in range(kb):
+            last = torch.randn(n, s, dtype=torch.float64, device=dev, generator=g)
+            b.orthogonalize(last)
+        for kappa in kappas:
+            # the block also has components along the basis, like a Krylov block
+            W = Ws[kappa].to(dev) + 0.5 * last / float(n) ** 0.5
+            times = []
+            for rep in range(max(2, reps)):
+                b.truncate(kb)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                U, H, R = b.orthogonalize(W)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            passes = b.last_step_info()
+            C = torch.zeros(((kb + 1) * s, s), dtype=torch.float64, device=dev)
+            C[:kb * s] = H
+            res = float(torch.linalg.norm(W - b.apply_Q(C) - U @ R) / torch.linalg.norm(W))
+            UtU = U.T @ U
+            b.truncate(kb)
+            _, QtU, _ = b.orthogonalize(U.clone())   # H = Q^T U against the kb prior blocks
+            eye = torch.eye(s, dtype=torch.float64, device=dev)
+            eperp = float(torch.sqrt(torch.linalg.norm(UtU - eye) ** 2 + 2 * torch.linalg.norm(QtU) ** 2))
+            ms = min(times[1:])
+            rows[kappa][prec] = {"ms": round(ms, 3), "gbs": round(nbytes / ms / 1e6, 1), "e_perp": eperp,
+                                 "residual": res, "passes": passes[0], "tree_iterations": passes[1]}
+            del U, H, R, W, C
+        b.close()
+        del last
+        torch.cuda.empty_cache()
+    # the sampled run against the oracle
+    if check_n:
+        chk = mixed_oracle_check(lo, torch, dev, check_n, kappas)
+        for kappa in kappas:
+            for prec in ("fp64_tc", "mixed_tc"):
+                rows[kappa][prec]["oracle_sample"] = chk[kappa][prec]
+    for kappa in kappas:
+        r = rows[kappa]
+        r["speedup_mixed_vs_fp64"] = round(r["fp64_tc"]["ms"] / r["mixed_tc"]["ms"], 3)
+        r["speedup_stated"] = r["mixed_tc"]["e_perp"] <= 1e-12
+        out["results"].append(r)
+    return out
+
+
+def mixed_oracle_check(lo, torch, dev, n, kappas):
+    """U, H, R of both forms against the CPU oracle at n rows (s = 16, 30 prior
+    Gaussian blocks, 1024-row chunks, the same block recipe as mixed_measure)."""
+    from oracle import lo_oracle as O
+    from paper_2204_13393_gb300 import inputs as I
+
+    s, kb, cr = 16, 30, 1024
+    prior = [I.gaussian(n, s, I.seed_for(4, j)) for j in range(kb)]
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    for P in prior:
+        ora.orthogonalize(P, "pip2", "pip2")
+    out = {}
+    for kappa in kappas:
+        W = I.stewart(n, s, kappa, I.seed_for(4, 100 + int(round(np.log10(kappa))))) + 0.5 * prior[-1] / np.sqrt(n)
+        import copy
+        o = copy.deepcopy(ora)
+        Uo, Po, No = o.orthogonalize(W, "pip2", "pip2")
+        out[kappa] = {}
+        for prec in ("fp64_tc", "mixed_tc"):
+            b = lo.Basis(n, s, kb + 1, cr, precision=prec, sync=True)
+            for P in prior:
+                b.orthogonalize(torch.from_numpy(P).to(dev))
+            U, H, R = (x.cpu().numpy() for x in b.orthogonalize(torch.from_numpy(W).to(dev)))
+            b.close()
+
+            def rel(a, c):
+                return float(np.linalg.norm(a - c) / np.linalg.norm(c))
+            out[kappa][prec] = {"n": n, "U_rel": rel(U, Uo), "H_rel": rel(H, Po), "R_rel": rel(R, No)}
+    return out
+
+
 def run_mixed_case(args):
-    """Mixed-precision workload: n = 2^24 rows (--mixed-n), s = 16, 30 prior
-    blocks (480 columns, Gaussian, built untimed), new block a Stewart-type
-    matrix U diag(sigma) V^T with kappa in {1e2, 1e4, 1e6} (orthonormal factors
-    by CholeskyQR2 of Gaussians).  Each step is timed with CUDA events for
-    the float64 tensor-core form and the mixed tensor-core form; the step's
-    orthogonality is sqrt(|U^T U - I|^2 + 2 |Q^T U|^2), with Q^T U measured by
-    one more projection of U (the H output of a PQR step of U)."""
     import torch
 
     from paper_2204_13393_gb300 import lo
 
     dev = torch.device("cuda", 0)
     lo.library()
-    n, s, kb = args.mixed_n, 16, 30
-    # chunk rows: measured by the tuner for the float64 form (the reduction's
-    # float64 work grows with the number of chunks), or --mixed-cr
-    cr = args.mixed_cr or lo.tune_chunk_rows(n, s, kb + 2, precision="fp64_tc")
-    out = {"case": "mixed", "n": n, "s": s, "k": kb * s, "chunk_rows": cr,
-           "chunk_rows_from": "option" if args.mixed_cr else "lo_tune_chunk_rows (measured)", "results": []}
-    g = torch.Generator(device=dev)
-    g.manual_seed(2204133930 + 4000)
-    prior = [torch.randn(n, s, dtype=torch.float64, device=dev, generator=g) for _ in range(kb)]
-    nbytes = orth_bytes(n, s, kb * s, max(1, n // cr))
-    for kappa in [float(x) for x in args.mixed_kappas.split(",")]:
-        Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
-        Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
-        sig = torch.tensor([kappa ** (-j / (s - 1.0)) for j in range(s)], dtype=torch.float64, device=dev)
-        W = (Uh * sig) @ Vh.T
-        # the block also has components along the basis, like a Krylov block
-        W = W + 0.5 * prior[kb - 1] / float(n) ** 0.5
-        row = {"kappa": kappa}
-        for prec in ("fp64_tc", "mixed_tc"):
-            b = lo.Basis(n, s, kb + 2, cr, precision=prec, sync=True)
-            for P in prior:
-                b.orthogonalize(P)
-            times = []
-            for rep in range(max(2, args.steps)):
-                b.truncate(kb)
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                U, _, R = b.orthogonalize(W)
-                e1.record()
-                torch.cuda.synchronize()
-                times.append(e0.elapsed_time(e1))
-            passes = b.last_step_info()
-            b.truncate(kb)
-            b.set_profiling(True)
-            torch.cuda.synchronize()
-            torch.cuda.profiler.start()       # the profiled step of each form (ncu --profile-from-start off)
-            U, _, R = b.orthogonalize(W)
-            torch.cuda.synchronize()
-            torch.cuda.profiler.stop()
-            prof = {gname: round(v[0], 3) for gname, v in b.profile_read().items() if v[0] > 0}
-            b.set_profiling(False)
-            UtU = U.T @ U
-            b.truncate(kb)
-            _, QtU, _ = b.orthogonalize(U.clone())   # H = Q^T U against the kb prior blocks
-            eye = torch.eye(s, dtype=torch.float64, device=dev)
-            qtu = QtU[:kb * s]
-            eperp = float(torch.sqrt(torch.linalg.norm(UtU - eye) ** 2 + 2 * torch.linalg.norm(qtu) ** 2))
-            ms = min(times[1:]) if len(times) > 1 else times[0]
-            row[prec] = {"ms": round(ms, 3), "gbs": round(nbytes / ms / 1e6, 1), "e_perp": eperp,
-                         "passes": passes[0], "tree_iterations": passes[1], "kernel_ms": prof}
-            b.close()
-            del U, R
-        row["speedup_mixed_vs_fp64"] = round(row["fp64_tc"]["ms"] / row["mixed_tc"]["ms"], 3)
-        out["results"].append(row)
+    cr = args.mixed_cr or lo.tune_chunk_rows(args.mixed_n, 16, 32, precision="fp64_tc")
+    out = mixed_measure(lo, torch, dev, args.mixed_n, cr, [float(x) for x in args.mixed_kappas.split(",")],
+                        args.steps)
+    out["case"] = "mixed"
+    out["chunk_rows_from"] = "option" if args.mixed_cr else "lo_tune_chunk_rows (measured)"
     print(json.dumps(out), flush=True)
 
 
@@ -778,73 +924,107 @@ def run_step_case(args):
     print(json.dumps(out), flush=True)
 
 
+def tsqr_measure(lo, torch, dev, ns, ss, kappas, forms, reps, cr_fixed=0, verbose=False):
+    """Tall-skinny QR (k = 0 step): A = U diag(sigma) V^T with Haar U, V (QR of
+    Gaussians on the device) and sigma log-spaced from 1 to 1/kappa.  Each form
+    ("precision" or "precision:leaf") gets the autotuned chunk size (or
+    cr_fixed); one step is timed with CUDA events (min over ``reps``
+    repetitions after one warm-up).  Algorithmic bytes 32ns: read A twice,
+    write the local panel and U.  Reported with e_perp = |U^T U - I|_F and
+    |A - UR|_F / |A|_F.  The profiled step of each form runs between
+    cudaProfilerStart and cudaProfilerStop (for ncu --profile-from-start off)."""
+    hbm, _src = peaks()
+    rows = []
+    g = torch.Generator(device=dev)
+    g.manual_seed(2204133930 + 3000)
+    for n in ns:
+        for s in ss:
+            nbytes = 32 * n * s
+            for kappa in kappas:
+                Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
+                Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
+                sig = torch.tensor([kappa ** (-j / max(s - 1.0, 1.0)) for j in range(s)], dtype=torch.float64,
+                                   device=dev)
+                A = (Uh * sig) @ Vh.T
+                del Uh
+                row = {"n": n, "s": s, "kappa": kappa}
+                for form in forms:
+                    prec, _, leaf = form.partition(":")
+                    leaf = leaf or "pip2"
+                    cr = cr_fixed or lo.tune_chunk_rows(n, s, 1, precision=prec, leaf=leaf)
+                    b = lo.Basis(n, s, 1, cr, precision=prec, leaf=leaf, sync=True)
+                    U = torch.empty_like(A)
+                    times = []
+                    for rep in range(1 + max(1, reps)):
+                        b.truncate(0)
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        _, _, R = b.orthogonalize(A, U=U)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                    ms = min(times[1:])
+                    b.truncate(0)
+                    b.set_profiling(True)
+                    torch.cuda.profiler.start()
+                    b.orthogonalize(A, U=U)
+                    torch.cuda.synchronize()
+                    torch.cuda.profiler.stop()
+                    prof = {k_: round(v[0], 4) for k_, v in b.profile_read().items() if v[0] > 0}
+                    b.set_profiling(False)
+                    eye = torch.eye(s, dtype=torch.float64, device=dev)
+                    eperp = float(torch.linalg.norm(U.T @ U - eye))
+                    res = float(torch.linalg.norm(A - U @ R) / torch.linalg.norm(A))
+                    row[form] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                                 "frac_hbm": round(nbytes / ms / 1e6 / hbm, 3), "chunk_rows": cr,
+                                 "e_perp": eperp, "residual": res, "passes": b.last_step_info()[0],
+                                 "kernel_ms": prof}
+                    b.close()
+                    del U
+                rows.append(row)
+                if verbose:
+                    print(json.dumps(row), flush=True)
+                del A
+    return rows
+
+
 def run_tsqr_case(args):
-    """Tall-skinny QR (k = 0 step) at n = 2^24 rows (--tsqr-n): A = U diag(sigma)
-    V^T with Haar U, V (QR of Gaussians on the device) and sigma log-spaced from
-    1 to 1/kappa, kappa in {1e2, 1e6, 1e10}; s from --tsqr-s.  Each form (native
-    float64 and float64 on the tensor cores) gets the autotuned chunk size; one
-    step is timed with CUDA events (min over --steps repetitions after one
-    warm-up).  Algorithmic bytes 32ns: read A twice, write the local panel and
-    U.  Reported with e_perp = |U^T U - I|_F and |A - UR|_F / |A|_F.  The
-    profiled step of each form runs between cudaProfilerStart and
-    cudaProfilerStop (for ncu --profile-from-start off)."""
+    """--case tsqr: the tall-skinny QR sweep (--tsqr-n, --tsqr-s, --tsqr-kappas,
+    --tsqr-precisions)."""
     import torch
 
     from paper_2204_13393_gb300 import lo
 
     dev = torch.device("cuda", 0)
     lo.library()
-    hbm, _src = peaks()
-    out = {"case": "tsqr", "n": args.tsqr_n, "results": []}
-    g = torch.Generator(device=dev)
-    g.manual_seed(2204133930 + 3000)
-    for n, s in [(int(a), int(b)) for a in args.tsqr_n.split(",") for b in args.tsqr_s.split(",")]:
-        nbytes = 32 * n * s
-        for kappa in [float(x) for x in args.tsqr_kappas.split(",")]:
-            Uh = orthonormal_columns(torch, torch.randn(n, s, dtype=torch.float64, device=dev, generator=g))
-            Vh = orthonormal_columns(torch, torch.randn(s, s, dtype=torch.float64, device=dev, generator=g))
-            sig = torch.tensor([kappa ** (-j / max(s - 1.0, 1.0)) for j in range(s)], dtype=torch.float64,
-                               device=dev)
-            A = (Uh * sig) @ Vh.T
-            del Uh
-            row = {"n": n, "s": s, "kappa": kappa}
-            for prec in args.tsqr_precisions.split(","):
-                cr = args.tsqr_cr or lo.tune_chunk_rows(n, s, 1, precision=prec)
-                b = lo.Basis(n, s, 1, cr, precision=prec, sync=True)
-                U = torch.empty_like(A)
-                times = []
-                for rep in range(1 + max(1, args.steps)):
-                    b.truncate(0)
-                    torch.cuda.synchronize()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record()
-                    _, _, R = b.orthogonalize(A, U=U)
-                    e1.record()
-                    torch.cuda.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                ms = min(times[1:])
-                b.truncate(0)
-                b.set_profiling(True)
-                torch.cuda.profiler.start()
-                b.orthogonalize(A, U=U)
-                torch.cuda.synchronize()
-                torch.cuda.profiler.stop()
-                prof = {g: round(v[0], 4) for g, v in b.profile_read().items() if v[0] > 0}
-                b.set_profiling(False)
-                eye = torch.eye(s, dtype=torch.float64, device=dev)
-                eperp = float(torch.linalg.norm(U.T @ U - eye))
-                res = float(torch.linalg.norm(A - U @ R) / torch.linalg.norm(A))
-                row[prec] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
-                             "frac_hbm": round(nbytes / ms / 1e6 / hbm, 3), "chunk_rows": cr,
-                             "e_perp": eperp, "residual": res, "passes": b.last_step_info()[0],
-                             "kernel_ms": prof}
-                b.close()
-                del U
-            out["results"].append(row)
-            print(json.dumps(row), flush=True)
-            del A
-    print(json.dumps(out), flush=True)
+    rows = tsqr_measure(lo, torch, dev, [int(a) for a in args.tsqr_n.split(",")],
+                        [int(b) for b in args.tsqr_s.split(",")],
+                        [float(x) for x in args.tsqr_kappas.split(",")], args.tsqr_precisions.split(","),
+                        args.steps, args.tsqr_cr, verbose=True)
+    print(json.dumps({"case": "tsqr", "n": args.tsqr_n, "results": rows}), flush=True)
+
+
+def target_points(lo, torch, dev, args):
+    """The two measurements the benchmark spec states beside the cycle, on this
+    GPU in this run: the tall-skinny QR at n = 2^24, s = 8 (FP64 target: >= 70 %
+    of the HBM roofline, e_perp <= 1e-12) and the mixed form's speedup over
+    the float64 form at n = 2^24, s = 16, k = 480, kappa <= 1e6."""
+    hbm, _ = peaks()
+    out = {}
+    t0 = time.perf_counter()
+    rows = tsqr_measure(lo, torch, dev, [2 ** 24], [8], [1e2, 1e6, 1e10], args.target_forms.split(","), 3)
+    out["tsqr_2p24_s8"] = {
+        "roofline_time_ms_at_70pct": round(32 * 2 ** 24 * 8 / (0.7 * hbm * 1e9) * 1e3, 4),
+        "results": rows, "seconds": round(time.perf_counter() - t0, 1)}
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    mx = mixed_measure(lo, torch, dev, 2 ** 24, args.mixed_cr or 131072, [1e2, 1e4, 1e6], 3)
+    mx["chunk_rows_from"] = "option" if args.mixed_cr else "fixed (131072: the tuner's choice for the float64 form)"
+    mx["seconds"] = round(time.perf_counter() - t0, 1)
+    out["mixed_speedup"] = mx
+    return out
 
 
 def main():
@@ -872,7 +1052,15 @@ def main():
     ap.add_argument("--tsqr-cr", type=int, default=0, help="chunk rows for --case tsqr (0: autotuned)")
     ap.add_argument("--tsqr-kappas", default="1e2,1e6,1e10", help="condition numbers for --case tsqr")
     ap.add_argument("--tsqr-precisions", default="fp64,fp64_tc", help="forms for --case tsqr")
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-targets", action="store_true",
+                    help="skip the tall-skinny target point and the mixed speedup in the default line")
+    ap.add_argument("--target-forms", default="fp64_tc",
+                    help="forms of the tall-skinny target point in the default line")
     args = ap.parse_args()
+    if args.cpu_sample is not None:
+        run_cpu_sample(args.cpu_sample)
+        return
     if args.case == "profile":
         run_profile_case(args)
         return

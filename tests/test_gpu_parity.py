@@ -46,6 +46,23 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def close(a, b, tol=TOL_REL):
+    """Relative Frobenius error <= tol and, element by element,
+    |a - b| <= tol * max|b| (so no single entry hides in a small norm)."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = np.abs(b).max() if b.size else 0.0
+    ew = np.abs(a - b).max() / (scale if scale > 0 else 1.0) if b.size else 0.0
+    return rel(a, b) <= tol and ew <= tol
+
+
+def errs(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    scale = np.abs(b).max() if b.size else 1.0
+    return rel(a, b), (np.abs(a - b).max() / (scale if scale > 0 else 1.0) if b.size else 0.0)
+
+
 def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
@@ -67,10 +84,10 @@ def run_and_compare(n, s, M, cr, blocks, oracle_local="hh", oracle_reduction="hh
     for j, Wh in enumerate(blocks):
         U, H, R = b.orthogonalize(dev(Wh))
         Uo, Po, No = ora.orthogonalize(Wh, oracle_local, oracle_reduction)
-        assert rel(host(U), Uo) <= TOL_REL, (j, rel(host(U), Uo))
-        assert rel(host(R), No) <= TOL_REL, (j, rel(host(R), No))
+        assert close(host(U), Uo), (j, errs(host(U), Uo))
+        assert close(host(R), No), (j, errs(host(R), No))
         if j > 0:
-            assert rel(host(H), Po) <= TOL_REL, (j, rel(host(H), Po))
+            assert close(host(H), Po), (j, errs(host(H), Po))
             Rfull[:j * s, j * s:(j + 1) * s] = host(H)
         Rfull[j * s:(j + 1) * s, j * s:(j + 1) * s] = host(R)
         assert np.all(np.diag(host(R)) > 0)
@@ -79,13 +96,13 @@ def run_and_compare(n, s, M, cr, blocks, oracle_local="hh", oracle_reduction="hh
     Q = host(b.apply_Q(dev(np.eye(b.k))))
     assert O.e_perp(Q) <= TOL_PERP
     assert O.residual(A, Q, Rfull) <= TOL_RES
-    assert rel(Q, ora.explicit()) <= TOL_REL
+    assert close(Q, ora.explicit())
     if check_local:
         Tg = 0
         for c in range(b.num_chunks):
             Qi, Ti = b.export_chunk(c)
-            assert rel(Qi, ora.Qloc[c]) <= TOL_REL, c
-            assert rel(Ti, np.triu(ora.T[c])) <= TOL_REL, c
+            assert close(Qi, ora.Qloc[c]), c
+            assert close(Ti, np.triu(ora.T[c])), c
             assert O.e_perp(Qi) <= TOL_PERP
             Tg = Tg + Ti.T @ Ti
         assert np.abs(Tg - np.eye(b.k)).max() <= TOL_PERP
@@ -503,6 +520,7 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
     L = lo()
     on = L.Basis(n, s, M, cr, precision=precision)
     off = L.Basis(n, s, M, cr, precision=precision, digit_planes=False)
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
     bitwise = precision == "fp64_tc"
     A = []
     for j in range(M):
@@ -513,13 +531,20 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
         W = dev(Wh)
         r1 = [host(x) for x in on.orthogonalize(W) if x is not None]
         r2 = [host(x) for x in off.orthogonalize(W) if x is not None]
+        Uo, Po, No = ora.orthogonalize(Wh, "pip2", "pip2")
         for x, y in zip(r1, r2):
             if bitwise:
                 assert np.array_equal(x, y), j
             else:
                 assert rel(x, y) <= TOL_REL, j
+        # the planes-on outputs against the oracle: U, R (and H past the first block)
+        assert close(r1[0], Uo), (j, errs(r1[0], Uo))
+        assert close(r1[-1], No), (j, errs(r1[-1], No))
+        if j:
+            assert close(r1[1], Po), (j, errs(r1[1], Po))
     Q = host(on.apply_Q(dev(np.eye(on.k))))
     assert O.e_perp(Q) <= TOL_PERP
+    assert close(Q, ora.explicit()), errs(Q, ora.explicit())
     for c in (0, on.num_chunks - 1):
         Qa, Ta = on.export_chunk(c)
         Qb, Tb = off.export_chunk(c)
