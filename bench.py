@@ -1051,11 +1051,12 @@ def main():
     ap.add_argument("--tsqr-s", default="8", help="comma-separated block widths for --case tsqr")
     ap.add_argument("--tsqr-cr", type=int, default=0, help="chunk rows for --case tsqr (0: autotuned)")
     ap.add_argument("--tsqr-kappas", default="1e2,1e6,1e10", help="condition numbers for --case tsqr")
-    ap.add_argument("--tsqr-precisions", default="fp64,fp64_tc", help="forms for --case tsqr")
+    ap.add_argument("--tsqr-precisions", default="fp64,fp64_tc,fp64:hh",
+                    help="forms (precision[:leaf]) for --case tsqr")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-targets", action="store_true",
                     help="skip the tall-skinny target point and the mixed speedup in the default line")
-    ap.add_argument("--target-forms", default="fp64_tc",
+    ap.add_argument("--target-forms", default="fp64_tc,fp64:hh",
                     help="forms of the tall-skinny target point in the default line")
     args = ap.parse_args()
     if args.cpu_sample is not None:

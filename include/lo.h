@@ -104,10 +104,23 @@ typedef enum lo_leaf {
                            /* independent blocks; in a Krylov sequence the local */
                            /* losses below the estimate accumulate.               */
   LO_LEAF_PIP = 1,         /* BCGS-PIP, Alg. 7: one Gram pass                    */
-  LO_LEAF_PIP2 = 2         /* BCGS-PIP+, Alg. 8: two Gram passes (the default),  */
+  LO_LEAF_PIP2 = 2,        /* BCGS-PIP+, Alg. 8: two Gram passes (the default),  */
                            /* a third when the estimate still asks for it; a     */
                            /* first-pass breakdown retries with the shift of     */
                            /* shifted CholeskyQR3 and forces two more passes     */
+  LO_LEAF_HH = 3           /* Householder QR (Alg. 6, sign rule sigma = -sgn of  */
+                           /* the pivot) of each chunk in the step without prior */
+                           /* blocks (k = 0, the tall-skinny QR): one CTA holds  */
+                           /* the chunk tile in shared memory, so the block is   */
+                           /* read once and no Gram matrix is formed (stable at  */
+                           /* any condition number, no shifted retry); the      */
+                           /* reduction stays BCGS-PIP+ (the paper's choice at   */
+                           /* the level above the node, Sec. 5.3) and the local  */
+                           /* panel is the explicit Householder Q_i.  Steps with */
+                           /* prior blocks run BCGS-PIP+.  Every chunk (the last */
+                           /* one with the remainder rows included) must fit:    */
+                           /* rows * s * 8 <= 200 KiB, else lo_basis_create      */
+                           /* returns LO_ERR_UNSUPPORTED                         */
 } lo_leaf;
 
 /*

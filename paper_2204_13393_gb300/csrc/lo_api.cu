@@ -1,6 +1,7 @@
 // Host side of the C ABI (include/lo.h): basis object, argument validation,
 // staging of host buffers, kernel sequencing and status reporting.
 #include <atomic>
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -185,6 +186,8 @@ StepArgs make_args(const lo_basis* b) {
   a.chunk_row0 = b->d_chunk_row0;
   a.nslab = b->nslab;
   a.slab_rows = b->slab_rows;
+  for (int c = 0; c < b->p; ++c)
+    a.max_chunk_rows = std::max<int>(a.max_chunk_rows, (int)(b->chunk_row0[c + 1] - b->chunk_row0[c]));
   a.test_stall = b->opt.test_stall;
   a.precision = b->opt.precision;
   a.leaf = b->opt.leaf;
@@ -371,7 +374,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options o;
   lo_options_default(&o);
   if (opt) o = *opt;
-  if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 2 || o.reduction < 0 ||
+  if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 3 || o.reduction < 0 ||
       o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1 || o.test_stall < 0 || o.test_stall > 1)
     return LO_ERR_INVALID_ARG;
   // A one-block basis (tall-skinny QR) of at most kNativeMaxS columns runs
@@ -392,6 +395,11 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   const int p = (int)p64;
   const int64_t min_rows = (p == 1) ? n : chunk_rows;
   if (min_rows < Kmax) return LO_ERR_CHUNK_TOO_SMALL;
+  if (o.leaf == LO_LEAF_HH) {  // every chunk tile of the k = 0 step in one CTA's shared memory
+    const int64_t last = n - (int64_t)(p - 1) * chunk_rows;
+    const int64_t maxrows = (p > 1 && chunk_rows > last) ? chunk_rows : last;
+    if (maxrows * s * (int64_t)sizeof(double) > lo::kHHTileBytes) return LO_ERR_UNSUPPORTED;
+  }
 
   lo_basis* b = new (std::nothrow) lo_basis();
   if (!b) return LO_ERR_OOM;
@@ -813,6 +821,7 @@ lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_
   cudaFree(Wd);
   cudaFree(Ud);
   if (e != cudaSuccess) return from_cuda(e);
+  if (!(best_t < 1e300)) return LO_ERR_UNSUPPORTED;  // no candidate could run (e.g. Householder tiles too large)
   *chunk_rows = (int32_t)best;
   std::lock_guard<std::mutex> lock(mu);
   memo[mkey] = *chunk_rows;

@@ -17,6 +17,8 @@ constexpr int kThreads = 256;    // threads of the streaming kernels
 constexpr int kMaxPass = 3;      // local Gram passes (PIP, PIP+, one more)
 constexpr int kMaxTreeIter = 3;  // reduction iterations
 constexpr int kTreeGroup = 64;   // chunks summed per CTA in the tree's first level
+constexpr int kHHThreads = 256;  // threads of the Householder leaf (one CTA per chunk)
+constexpr int kHHTileBytes = 200 * 1024;  // shared memory for one chunk tile of the Householder leaf
 
 // Flag words (int) in device memory.
 enum Flag : int {
@@ -96,6 +98,7 @@ struct StepArgs {
   const int64_t* chunk_row0;    // first row of chunk c (p + 1 entries)
   int nslab;
   int slab_rows;
+  int max_chunk_rows;       // rows of the largest chunk (the last one holds the remainder)
   int precision;
   int leaf;
   int reduction;

@@ -7,6 +7,7 @@
 // the new local block).  Every reduction has a fixed order, so two runs give
 // bit-identical results.  No kernel waits on another CTA; breakdowns are
 // reported through the status flag word, never by trapping.
+#include <algorithm>
 #include <atomic>
 #include <cfloat>
 #include <cstdint>
@@ -966,6 +967,202 @@ __global__ void k_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Householder leaf of the step without prior blocks (Alg. 6 with an empty
+// basis, k = 0).  One CTA per chunk holds the chunk tile W_i (rows x s,
+// column-major in shared memory), reduces it to R_i by s reflections
+// H_j = I - tau_j v_j v_j^T (v_j[j] = 1, supported on rows j ..), with the
+// sign rule of Alg. 6: R_jj = sigma ||x||, sigma = -sgn(x_j), sgn(0) = +1, so
+// that x_j - R_jj never cancels.  It then forms the explicit
+// Q_i = H_0 ... H_{s-1} [I; 0] in place (the reflectors applied backwards to
+// the unit vectors) and normalizes the signs so that diag(R_i) >= 0.
+// Outputs: Q_i into the new local panel, R_i as the chunk's normalizer
+// (N_last = N_comb), N_last^{-1} recorded as the identity (the panel already
+// is the chunk's orthonormal factor), and for the tensor-core forms the
+// panel's column exponents.  A column that vanishes on and below the diagonal
+// gets no reflection (tau = 0): R_jj = 0 and Q_i keeps the unit direction e_j.
+
+// Sum over the CTA of v[0 .. cnt) of every thread, in a fixed order (lanes by
+// a butterfly, then warps in index order), into out[0 .. cnt).
+template <int SMAX>
+__device__ __forceinline__ void hh_block_sum(double (&v)[SMAX], int cnt, double* red, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < SMAX; ++c) {
+    if (c < cnt) {
+      double x = v[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      v[c] = x;
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < SMAX; ++c)
+      if (c < cnt) red[warp * 32 + c] = v[c];
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    double x = 0.0;
+    for (int w = 0; w < kHHThreads / 32; ++w) x += red[w * 32 + threadIdx.x];
+    out[threadIdx.x] = x;
+  }
+  __syncthreads();
+}
+
+// Apply H_j = I - t v v^T (v = column j of A below the diagonal, v_j = 1) to
+// columns j + 1 .. s - 1 of A (rows j ..): w_c = A[j][c] + sum_{r > j} v_r A[r][c],
+// A[., c] -= t v w_c.  Whole CTA; returns after a barrier.
+template <int SMAX>
+__device__ __forceinline__ void hh_apply(double* A, int rows, int s, int j, double t, double* red, double* vsum,
+                                         double* wsh) {
+  const int nc = s - j - 1, tid = threadIdx.x;
+  if (nc <= 0 || t == 0.0) return;
+  const double* x = A + (int64_t)j * rows;
+  double w[SMAX];
+#pragma unroll
+  for (int cc = 0; cc < SMAX; ++cc) w[cc] = 0.0;
+  for (int r = j + 1 + tid; r < rows; r += kHHThreads) {
+    const double vr = x[r];
+#pragma unroll
+    for (int cc = 0; cc < SMAX; ++cc)
+      if (cc < nc) w[cc] = fma(vr, A[(int64_t)(j + 1 + cc) * rows + r], w[cc]);
+  }
+  hh_block_sum<SMAX>(w, nc, red, vsum);
+  if (tid < nc) wsh[tid] = A[(int64_t)(j + 1 + tid) * rows + j] + vsum[tid];
+  __syncthreads();
+  if (tid < nc) A[(int64_t)(j + 1 + tid) * rows + j] -= t * wsh[tid];
+  for (int r = j + 1 + tid; r < rows; r += kHHThreads) {
+    const double tv = t * x[r];
+#pragma unroll
+    for (int cc = 0; cc < SMAX; ++cc)
+      if (cc < nc) A[(int64_t)(j + 1 + cc) * rows + r] -= tv * wsh[cc];
+  }
+  __syncthreads();
+}
+
+template <int SMAX>
+__global__ void __launch_bounds__(kHHThreads) k_hh_leaf(StepArgs a) {
+  extern __shared__ __align__(16) double A[];  // rows x s, column-major
+  __shared__ double red[(kHHThreads / 32) * 32];
+  __shared__ double vsum[32], wsh[32], tau[32], dsg[32];
+  __shared__ double Rs[32 * 32];
+  __shared__ int hs[32];
+  __shared__ int bad;
+  const int c = blockIdx.x, s = a.s, tid = threadIdx.x;
+  const int64_t r0 = a.chunk_row0[c];
+  const int rows = (int)(a.chunk_row0[c + 1] - r0);
+  if (tid == 0) bad = 0;
+  if (tid < 32) hs[tid] = 0;
+  __syncthreads();
+  for (int idx = tid; idx < rows * s; idx += kHHThreads) {
+    const int r = idx / s, l = idx - r * s;
+    const double x = a.W[(r0 + r) * a.ldw + l];
+    if (!isfinite(x)) bad = 1;
+    A[(int64_t)l * rows + r] = x;
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) set_status(a.flags, LO_ERR_NONFINITE);
+    return;
+  }
+  // R_i: one reflection per column
+  for (int j = 0; j < s; ++j) {
+    double* x = A + (int64_t)j * rows;
+    double v[SMAX];
+#pragma unroll
+    for (int cc = 0; cc < SMAX; ++cc) v[cc] = 0.0;
+    for (int r = j + tid; r < rows; r += kHHThreads) v[0] = fma(x[r], x[r], v[0]);
+    hh_block_sum<SMAX>(v, 1, red, vsum);
+    const double alpha = sqrt(vsum[0]);
+    const double x0 = x[j];
+    const double beta = (x0 >= 0.0) ? -alpha : alpha;
+    const double t = (alpha == 0.0) ? 0.0 : (beta - x0) / beta;
+    if (!isfinite(alpha)) {
+      if (tid == 0) set_status(a.flags, LO_ERR_NONFINITE);
+      return;
+    }
+    __syncthreads();  // every thread has read x_j
+    if (alpha != 0.0) {
+      const double scal = 1.0 / (x0 - beta);
+      for (int r = j + 1 + tid; r < rows; r += kHHThreads) x[r] *= scal;
+    }
+    if (tid == 0) {
+      x[j] = beta;
+      tau[j] = t;
+    }
+    __syncthreads();
+    hh_apply<SMAX>(A, rows, s, j, t, red, vsum, wsh);
+  }
+  for (int e = tid; e < s * s; e += kHHThreads) {
+    const int i = e / s, l = e - i * s;
+    Rs[e] = (i <= l) ? A[(int64_t)l * rows + i] : 0.0;
+  }
+  __syncthreads();
+  // Q_i = H_0 .. H_{s-1} [I; 0], formed in place from the last reflection back
+  for (int j = s - 1; j >= 0; --j) {
+    const double t = tau[j];
+    hh_apply<SMAX>(A, rows, s, j, t, red, vsum, wsh);
+    double* x = A + (int64_t)j * rows;
+    for (int r = tid; r < rows; r += kHHThreads) x[r] = (r < j) ? 0.0 : (r == j ? 1.0 - t : -t * x[r]);
+    __syncthreads();
+  }
+  // signs: D = diag(sgn(R_jj)), Q_i D and D R_i
+  if (tid < s) dsg[tid] = (Rs[tid * s + tid] >= 0.0) ? 1.0 : -1.0;
+  __syncthreads();
+  double* slot = a.V;  // the new local panel (k = 0)
+  for (int idx = tid; idx < rows * s; idx += kHHThreads) {
+    const int r = idx / s, l = idx - r * s;
+    slot[(r0 + r) * s + l] = A[(int64_t)l * rows + r] * dsg[l];
+  }
+  if (a.colexp) {  // largest biased exponent of each panel column on this chunk
+    for (int l = 0; l < s; ++l) {
+      int m = 0;
+      for (int r = tid; r < rows; r += kHHThreads)
+        m = max(m, (int)((((unsigned long long)__double_as_longlong(A[(int64_t)l * rows + r])) >> 52) & 0x7FF));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if ((tid & 31) == 0) atomicMax(&hs[l], m);
+    }
+    __syncthreads();
+    if (tid < s) a.colexp[(int64_t)tid * a.p + c] = hs[tid];
+  }
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  for (int e = tid; e < s * s; e += kHHThreads) {
+    const int i = e / s, l = e - i * s;
+    const double nv = Rs[e] * dsg[i];
+    smallc[SL.N_last + e] = nv;
+    smallc[SL.N_comb + e] = nv;
+    smallc[SL.Ninv_last + e] = (i == l) ? 1.0 : 0.0;
+  }
+}
+
+// Stage 2 after the Householder leaf: the local panel is Q_i already, so the
+// assembly is U = Q_i Nt_i (Sec. 4.1, with P empty at k = 0); one thread per
+// row, the row's s values in registers, Nt_i upper triangular.
+template <int SMAX>
+__global__ void __launch_bounds__(256) k_hh_assemble(StepArgs a) {
+  const SlabInfo si = a.slabs[blockIdx.x];
+  const int s = a.s;
+  const double* slot = a.V;
+  const double* Nt = a.T + (int64_t)si.chunk * a.tstride + tblock_offset(0, s);
+  for (int r = threadIdx.x; r < si.rows; r += 256) {
+    const int64_t row = si.row0 + r;
+    double q[SMAX];
+#pragma unroll
+    for (int l = 0; l < SMAX; ++l) q[l] = (l < s) ? slot[row * s + l] : 0.0;
+#pragma unroll
+    for (int l = 0; l < SMAX; ++l) {
+      if (l < s) {
+        double o = 0.0;
+#pragma unroll
+        for (int j = 0; j <= l; ++j) o = fma(q[j], __ldg(Nt + j * s + l), o);
+        a.U[row * a.ldu + l] = o;
+      }
+    }
+  }
+}
+
 // Shared-memory budget of the streaming kernels (bytes).
 constexpr int kTileSmem = 96 * 1024;
 
@@ -1002,6 +1199,10 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_tree_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_apply_y, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_leaf<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_leaf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_leaf<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_leaf<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   g_attr_done = true;
   return cudaSuccess;
 }
@@ -1045,15 +1246,74 @@ cudaError_t launch_fill_pattern(double* X, int64_t count, cudaStream_t st) {
 }
 void count_launches(int k) { g_launches += k; }
 
+// Reduction step (Sec. 4.1): BCGS-PIP on the stacked factors, reiterated.
+void launch_reduction(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
+  const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
+  const int ngroups = (a.p + kTreeGroup - 1) / kTreeGroup;
+  mark(hook, kKindTree, true, st);
+  for (int it = 1; it <= (a.reduction == 1 ? 1 : kMaxTreeIter); ++it) {
+    k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
+    k_tree_sum1<<<dim3(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, it);
+    k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
+    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
+    count_launches(4);
+  }
+  mark(hook, kKindTree, false, st);
+}
+
+// The step without prior blocks with the Householder leaf: k_hh_leaf per
+// chunk, the reduction, and the assembly U = Q_i Nt_i (plus the digit planes of
+// the new panel for a tensor-core basis that keeps them).
+cudaError_t launch_step_hh(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
+  const int s = a.s;
+  const size_t tile = sizeof(double) * (size_t)a.max_chunk_rows * s;
+  if (a.nb != 0 || tile > (size_t)kHHTileBytes) return cudaErrorInvalidValue;
+  const bool tc = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
+  cudaError_t e;
+  if (tc && (e = umma_set_attrs())) return e;
+  k_step_begin<<<1, 32, 0, st>>>(a.flags, 0, a.reduction != 1);
+  count_launches(1);
+  mark(hook, kKindLeaf, true, st);
+  if (s <= 4)
+    k_hh_leaf<4><<<a.p, kHHThreads, tile, st>>>(a);
+  else if (s <= 8)
+    k_hh_leaf<8><<<a.p, kHHThreads, tile, st>>>(a);
+  else if (s <= 16)
+    k_hh_leaf<16><<<a.p, kHHThreads, tile, st>>>(a);
+  else
+    k_hh_leaf<32><<<a.p, kHHThreads, tile, st>>>(a);
+  count_launches(1);
+  mark(hook, kKindLeaf, false, st);
+  launch_reduction(a, st, hook);
+  mark(hook, kKindUpdate, true, st);
+  if (s <= 4)
+    k_hh_assemble<4><<<a.nslab, 256, 0, st>>>(a);
+  else if (s <= 8)
+    k_hh_assemble<8><<<a.nslab, 256, 0, st>>>(a);
+  else if (s <= 16)
+    k_hh_assemble<16><<<a.nslab, 256, 0, st>>>(a);
+  else
+    k_hh_assemble<32><<<a.nslab, 256, 0, st>>>(a);
+  count_launches(1);
+  if (tc && a.dig && a.nb + 1 < a.M) {
+    if ((e = launch_umma_digitize(a, st))) return e;
+    count_launches(1);
+  }
+  mark(hook, kKindUpdate, false, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   cudaError_t e = set_attrs();
   if (e) return e;
+  if (a.leaf == LO_LEAF_HH && a.nb == 0) return launch_step_hh(a, st, hook);
   const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
   const bool mixed = (a.precision == LO_PREC_MIXED_FP32 || a.precision == LO_PREC_MIXED_TC);
   // The reduction always reiterates (BCGS-PIP+) unless plain PIP is asked for: its
   // projection uses the stacked tree factors of all earlier steps, whose rounding
   // errors a single pass amplifies step after step.
-  k_step_begin<<<1, 32, 0, st>>>(a.flags, (a.leaf == LO_LEAF_PIP2) || mixed, a.reduction != 1);
+  k_step_begin<<<1, 32, 0, st>>>(a.flags, (a.leaf == LO_LEAF_PIP2) || (a.leaf == LO_LEAF_HH) || mixed,
+                                 a.reduction != 1);
   count_launches(1);
   // stage 1
   const int maxpass = (a.leaf == LO_LEAF_PIP && !mixed) ? 1 : kMaxPass;
@@ -1104,17 +1364,7 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     mark(hook, kKindLeaf, false, st);
     count_launches(1);
   }
-  // reduction
-  const int ngroups = (a.p + kTreeGroup - 1) / kTreeGroup;
-  mark(hook, kKindTree, true, st);
-  for (int it = 1; it <= (a.reduction == 1 ? 1 : kMaxTreeIter); ++it) {
-    k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
-    k_tree_sum1<<<dim3(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, it);
-    k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
-    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
-    count_launches(4);
-  }
-  mark(hook, kKindTree, false, st);
+  launch_reduction(a, st, hook);
   // stage 2
   mark(hook, kKindUpdate, true, st);
   if (tc) {
@@ -1334,6 +1584,7 @@ extern "C" lo_status lo_tsqr_noalloc(int64_t n, int32_t s, int32_t chunk_rows, c
   a.chunk_row0 = reinterpret_cast<const int64_t*>(sc + lay.o_cr0);
   a.nslab = nslab;
   a.slab_rows = lay.slab_rows;
+  a.max_chunk_rows = (int)std::max<int64_t>(p > 1 ? chunk_rows : 0, n - (int64_t)(p - 1) * chunk_rows);
   a.precision = LO_PREC_FP64;
   a.leaf = LO_LEAF_PIP2;      // the library default (BCGS-PIP+, Alg. 8)
   a.reduction = 0;

@@ -33,7 +33,7 @@ STATUS = {
     9: "LO_ERR_UNSUPPORTED",
 }
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "fp64_tc": 2, "mixed_tc": 3}
-LEAF = {"auto": 0, "pip": 1, "pip2": 2}
+LEAF = {"auto": 0, "pip": 1, "pip2": 2, "hh": 3}
 REDUCTION = {"auto": 0, "pip": 1, "pip2": 2}
 
 EXPORTED = [

@@ -157,3 +157,20 @@ def test_batched_cache_hooks_without_device(lib):
     assert lib.lo_basis_id(None) == 0
     assert lib.lo_batched_cache_entries(0) == 0
     assert lib.lo_batched_cache_entries(12345) == 0
+
+
+def test_householder_leaf_tile_check_without_device(lib):
+    """LO_LEAF_HH needs every chunk tile (the last one with the remainder rows)
+    in one CTA's shared memory: rows * s * 8 <= 200 KiB, checked before any
+    CUDA call (LO_ERR_UNSUPPORTED = 9)."""
+    from paper_2204_13393_gb300 import lo
+
+    h = ctypes.c_void_p()
+    o = lo.Options()
+    lib.lo_options_default(ctypes.byref(o))
+    o.leaf = lo.LEAF["hh"]
+    for n, s, cr in ((2 ** 20, 8, 4096), (100000, 32, 1024), (30000, 8, 30000), (6000, 8, 4096)):
+        assert lib.lo_basis_create(n, s, 1, cr, ctypes.byref(o), None, ctypes.byref(h)) == 9, (n, s, cr)
+        assert h.value is None
+    o.leaf = 4
+    assert lib.lo_basis_create(4096, 4, 1, 512, ctypes.byref(o), None, ctypes.byref(h)) == 1
