@@ -24,6 +24,10 @@ Contents (paper section / equation / algorithm each function follows):
                            with a positive diagonal.  Oracle A.
 * ``pqr_mgs2``             PQR by modified Gram-Schmidt applied twice
                            (Alg. 4 reiterated as in Alg. 5).  Oracle B.
+* ``pqr_mgs2_deflate``     the deflated PQR of Sec. 3 (t < s; kept as t = s
+                           with zero rows of N and zero columns of U): oracle
+                           B with a column dropped when what remains of it
+                           is at most delta ||X||_F.
 * ``bcgs_pip``             Alg. 7 (BCGS-PIP).
 * ``bcgs_pip2``            Alg. 8 (BCGS-PIP+), with the combination step read
                            as P = P1 + P2 N1, N = N2 N1 (the printed formula is
@@ -54,6 +58,7 @@ __all__ = [
     "sign_normalize",
     "pqr_householder",
     "pqr_mgs2",
+    "pqr_mgs2_deflate",
     "bcgs_pip",
     "bcgs_pip2",
     "pqr",
@@ -69,8 +74,7 @@ __all__ = [
 
 class Breakdown(ArithmeticError):
     """A Cholesky pivot was not positive and the block was not exactly zero
-    there (rank deficiency / deflation, which the oracle, like the library,
-    does not handle; Sec. 3 last paragraph)."""
+    there: a rank deficiency while deflation (Sec. 3, t < s) is off."""
 
 
 def _sgn(x: float) -> float:
@@ -78,7 +82,7 @@ def _sgn(x: float) -> float:
     return 1.0 if x >= 0.0 else -1.0
 
 
-def cholesky_upper(M: np.ndarray) -> np.ndarray:
+def cholesky_upper(M: np.ndarray, deflate: float = 0.0) -> np.ndarray:
     """Upper-triangular N with N^T N = M (textbook Cholesky, row by row).
 
     This is the factorization CholQR and BCGS-PIP use (Sec. 3): for the PQR
@@ -88,6 +92,12 @@ def cholesky_upper(M: np.ndarray) -> np.ndarray:
     zero row of N: Sec. 3 allows keeping t = s and carrying the rank
     deficiency in N, and with exact zeros no tolerance is involved.  Any other
     non-positive or non-finite pivot raises ``Breakdown``.
+
+    With ``deflate`` > 0 a finite pivot d <= deflate is deflated as well (the
+    deflation case of Sec. 3: the column is, to that tolerance, in the span of
+    what came before it): row i of N is zero, and the later rows do not see
+    it.  The pivot is the squared distance of column i to the span of the
+    earlier columns, so ``deflate`` is a squared norm.
     """
     M = np.asarray(M, dtype=np.float64)
     s = M.shape[0]
@@ -97,6 +107,8 @@ def cholesky_upper(M: np.ndarray) -> np.ndarray:
         rest = [M[i, j] - sum(N[l, i] * N[l, j] for l in range(i)) for j in range(i + 1, s)]
         if d == 0.0 and all(r == 0.0 for r in rest):
             continue  # exactly zero component: zero row
+        if deflate > 0.0 and np.isfinite(d) and d <= deflate:
+            continue  # deflated: zero row
         if not (d > 0.0) or not np.isfinite(d):
             raise Breakdown(f"Cholesky pivot {i} = {d!r}")
         N[i, i] = np.sqrt(d)
@@ -223,24 +235,67 @@ def pqr_mgs2(Q: np.ndarray, X: np.ndarray):
     return U, P, N
 
 
-def bcgs_pip(Q: np.ndarray, X: np.ndarray):
+def pqr_mgs2_deflate(Q: np.ndarray, X: np.ndarray, delta: float):
+    """The deflated PQR problem (Sec. 3, t < s) by its plain definition.
+
+    Column j of X is treated as in ``pqr_mgs2`` (two sweeps of projections
+    against Q and the kept new columns, coefficients summed into P and N); if
+    the norm of what remains is at most delta ||X||_F, the column is in the
+    span of Q and the earlier columns to that tolerance: it is deflated,
+    U[:, j] = 0 and row j of N is zero (t = s is kept, the rank deficiency is
+    carried in N, as Sec. 3 allows), otherwise N[j, j] is that norm and
+    U[:, j] the normalized rest.  X = Q P + U N holds to the deflation
+    tolerance; the nonzero columns of U are orthonormal and orthogonal to Q.
+    """
+    Q = np.asarray(Q, dtype=np.float64).reshape(X.shape[0], -1)
+    n, k = Q.shape
+    s = X.shape[1]
+    thr = float(delta) * float(np.sqrt(np.sum(np.asarray(X, dtype=np.float64) ** 2)))
+    U = np.zeros((n, s))
+    P = np.zeros((k, s))
+    N = np.zeros((s, s))
+    for j in range(s):
+        v = X[:, j].astype(np.float64).copy()
+        for _pass in range(2):
+            for c in range(k):
+                coef = np.dot(Q[:, c], v)
+                v -= coef * Q[:, c]
+                P[c, j] += coef
+            for c in range(j):
+                if N[c, c] == 0.0:
+                    continue  # a deflated column of U is zero: nothing to project on
+                coef = np.dot(U[:, c], v)
+                v -= coef * U[:, c]
+                N[c, j] += coef
+        nrm = np.sqrt(np.dot(v, v))
+        if nrm <= thr:
+            continue  # deflated
+        N[j, j] = nrm
+        U[:, j] = v / nrm
+    return U, P, N
+
+
+def bcgs_pip(Q: np.ndarray, X: np.ndarray, deflate: float = 0.0):
     """Alg. 7 (BCGS-PIP): P = Q^T X and G = X^T X, N = chol(G - P^T P),
-    U = X N^{-1} - Q P N^{-1} (= (X - Q P) N^{-1})."""
+    U = X N^{-1} - Q P N^{-1} (= (X - Q P) N^{-1}).  ``deflate``: the squared
+    norm below which a Cholesky pivot is deflated (see ``cholesky_upper``)."""
     Q = np.asarray(Q, dtype=np.float64).reshape(X.shape[0], -1)
     P = Q.T @ X
     G = X.T @ X
-    N = cholesky_upper(G - P.T @ P)
+    N = cholesky_upper(G - P.T @ P, deflate)
     U = solve_upper_right(X - Q @ P, N)
     return U, P, N
 
 
-def bcgs_pip2(Q: np.ndarray, X: np.ndarray):
+def bcgs_pip2(Q: np.ndarray, X: np.ndarray, deflate: float = 0.0):
     """Alg. 8 (BCGS-PIP+): Alg. 7 applied to X, then to its output U1.
 
     From X = Q P1 + U1 N1 and U1 = Q P2 + U N2 it follows that
     X = Q (P1 + P2 N1) + U (N2 N1); hence P = P1 + P2 N1 and N = N2 N1.
+    Deflation (``deflate`` > 0) is decided in the first pass; the second
+    sees the deflated columns as exact zeros.
     """
-    U1, P1, N1 = bcgs_pip(Q, X)
+    U1, P1, N1 = bcgs_pip(Q, X, deflate)
     U, P2, N2 = bcgs_pip(Q, U1)
     return U, P1 + P2 @ N1, N2 @ N1
 
@@ -253,8 +308,13 @@ SUBALGORITHMS = {
 }
 
 
-def pqr(Q, X, alg: str = "hh"):
-    """Solve eq. (pqr) with the named sub-algorithm ('hh', 'mgs2', 'pip', 'pip2')."""
+def pqr(Q, X, alg: str = "hh", deflate: float = 0.0):
+    """Solve eq. (pqr) with the named sub-algorithm ('hh', 'mgs2', 'pip', 'pip2');
+    ``deflate`` (a squared norm) only for the Cholesky-based 'pip' and 'pip2'."""
+    if deflate > 0.0:
+        if alg not in ("pip", "pip2"):
+            raise ValueError("deflation needs a Cholesky-based sub-algorithm")
+        return SUBALGORITHMS[alg](Q, X, deflate)
     return SUBALGORITHMS[alg](Q, X)
 
 
@@ -296,9 +356,18 @@ class LocallyOrthogonalBasis:
     def num_blocks(self) -> int:
         return self.k // self.s
 
-    def orthogonalize(self, X: np.ndarray, local: str = "hh", reduction: str = "hh"):
+    def orthogonalize(self, X: np.ndarray, local: str = "hh", reduction: str = "hh", deflation: float = 0.0):
         """One PQR step, Alg. 9.  Returns (U, P, N) with P = H (k x s) and
         N = R (s x s).  The representation gains the new column block.
+
+        ``deflation`` = delta > 0: the deflated PQR (Sec. 3, t < s, kept as
+        t = s with zero rows of N): in the local first pass and in the
+        reduction a Cholesky pivot at most tau = max(delta^2, 64 s eps)
+        ||X||_F^2 (a column whose distance to the span of the earlier ones is
+        at most delta ||X||_F, ||X||_F the norm of the whole block) is
+        deflated.  The floor 64 s eps: a pivot of the Gram matrix G - P^T P
+        carries rounding noise of order eps ||X||_F^2 from the cancellation,
+        so distances below about sqrt(eps) ||X||_F cannot be told from zero.
 
         1. Local PQR per chunk: [Q_i X_i] = [Q_i U_i] [[I, P_i], [0, N_i]].
         2. Reduction PQR of the stacked factors:
@@ -309,14 +378,16 @@ class LocallyOrthogonalBasis:
         X = np.asarray(X, dtype=np.float64)
         s, k = self.s, self.k
         assert X.shape == (self.n, s)
+        eps = np.finfo(np.float64).eps
+        tau = max(float(deflation) ** 2, 64.0 * s * eps) * float(np.sum(X * X)) if deflation > 0.0 else 0.0
         loc = []
         for (b, e), Qi in zip(self.bounds, self.Qloc):
-            loc.append(pqr(Qi, X[b:e], local))
+            loc.append(pqr(Qi, X[b:e], local, tau if local in ("pip", "pip2") else 0.0))
         # stacked reduction problem: "Q" rows are [T_i; 0], "X" rows are [P_i; N_i]
         Qs = np.vstack([np.vstack([Ti, np.zeros((s, k))]) for Ti in self.T])
         Xs = np.vstack([np.vstack([Pi, Ni]) for (_, Pi, Ni) in loc])
-        Us, P, N = pqr(Qs, Xs, reduction)
-        if np.any(np.diag(N) == 0.0):
+        Us, P, N = pqr(Qs, Xs, reduction, tau)
+        if tau == 0.0 and np.any(np.diag(N) == 0.0):
             # the block has an exactly zero component on every chunk: a global
             # rank deficiency (the deflation case of Sec. 3, not handled)
             raise Breakdown("the block is rank deficient against the basis")

@@ -57,6 +57,14 @@ MUTATIONS = [
      "return float(np.linalg.norm(A - Q @ R) / np.linalg.norm(A))", "return float(np.linalg.norm(A - Q @ R))"),
     ("tree: projection block of T_i dropped",
      "Tn[:k, k:] = Pt", "Tn[:k, k:] = 0.0"),
+    ("deflation: threshold compared with the squared distance",
+     "        if nrm <= thr:\n            continue  # deflated", "        if nrm * nrm <= thr:\n            continue  # deflated"),
+    ("deflation: small Cholesky pivots kept",
+     "        if deflate > 0.0 and np.isfinite(d) and d <= deflate:",
+     "        if deflate > 0.0 and np.isfinite(d) and d < 0.0:"),
+    ("deflation: left out of the local solvers",
+     "loc.append(pqr(Qi, X[b:e], local, tau if local in (\"pip\", \"pip2\") else 0.0))",
+     "loc.append(pqr(Qi, X[b:e], local, 0.0))"),
     ("exact zero component: zero row not kept",
      "        if d == 0.0 and all(r == 0.0 for r in rest):\n            continue",
      "        if d == 0.0 and all(r == 0.0 for r in rest):\n            d = 1.0"),

@@ -500,3 +500,128 @@ def test_error_measures_closed_form():
     Aw = Qw @ R
     Aw[2, 1] = 4.0                              # A - QR = 4 e_3 e_2^T
     assert O.residual(Aw, Qw, R) == pytest.approx(4.0 / np.sqrt(1 + 4 + 9 + 16), rel=1e-15)
+
+
+# --- deflation (Sec. 3: t < s, kept as t = s with zero rows of N) ----------
+
+def _deficient_block(n, k, seed):
+    """Q (n x k orthonormal) and X (n x 6) whose column 2 = col 0 + 2 col 1,
+    column 4 lies in span(Q) and column 5 = col 3 - col 0 + Q c: rank 3
+    against Q, the dependent columns at 2, 4 and 5."""
+    Q = _orthonormal(n, k, seed)
+    G = I.gaussian(n, 6, seed + 1)
+    X = G.copy()
+    X[:, 2] = G[:, 0] + 2.0 * G[:, 1]
+    X[:, 4] = Q @ I.gaussian(k, 1, seed + 2)[:, 0]
+    X[:, 5] = G[:, 3] - G[:, 0] + Q @ I.gaussian(k, 1, seed + 3)[:, 0]
+    return Q, X
+
+
+def test_deflate_full_rank_is_mgs2():
+    Q = _orthonormal(300, 5, 901)
+    X = I.gaussian(300, 4, 902)
+    for a, b in zip(O.pqr_mgs2_deflate(Q, X, 1e-8), O.pqr_mgs2(Q, X)):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("k", [0, 7])
+def test_deflate_exact_dependencies(k):
+    """Exactly dependent columns: the kept count equals LAPACK's numerical
+    rank of (I - Q Q^T) X (an SVD), the dropped ones are the dependent
+    positions, kept columns of U are orthonormal and orthogonal to Q, dropped
+    ones and their rows of N are zero, and X = Q P + U N."""
+    n = 400
+    Q, X = _deficient_block(n, k, 903 + k)
+    if k == 0:
+        X[:, 4] = 0.5 * X[:, 1]
+        X[:, 5] = X[:, 3] - X[:, 0]
+    U, P, N = O.pqr_mgs2_deflate(Q, X, 1e-8)
+    Xp = X - Q @ (Q.T @ X) if k else X
+    rank = np.linalg.matrix_rank(Xp, tol=1e-8 * np.linalg.norm(X))
+    kept = np.flatnonzero(np.diag(N) != 0.0)
+    assert len(kept) == rank == 3
+    assert list(np.flatnonzero(np.diag(N) == 0.0)) == [2, 4, 5]
+    for j in (2, 4, 5):
+        assert np.all(U[:, j] == 0.0) and np.all(N[j, :] == 0.0)
+    assert np.allclose(np.triu(N), N, atol=0.0)
+    Uk = U[:, kept]
+    assert np.linalg.norm(Uk.T @ Uk - np.eye(len(kept))) < 1e-14
+    if k:
+        assert np.linalg.norm(Q.T @ U) < 1e-14
+    assert np.linalg.norm(X - Q @ P - U @ N) <= 1e-14 * np.linalg.norm(X)
+
+
+def test_deflate_spans_the_svd_truncated_normalizer():
+    """Sec. 3's deflation: the eigendecomposition G - P^T P = V S V^T with the
+    small values dropped gives U' = (X - Q P) V_t S_t^{-1/2}; the deflated
+    Gram-Schmidt spans the same space (projectors agree)."""
+    Q, X = _deficient_block(500, 6, 910)
+    U, P, N = O.pqr_mgs2_deflate(Q, X, 1e-8)
+    P0 = Q.T @ X
+    lam, V = np.linalg.eigh(X.T @ X - P0.T @ P0)
+    keep = lam > 1e-12 * lam.max()
+    Us = (X - Q @ P0) @ V[:, keep] / np.sqrt(lam[keep])[None, :]
+    Uk = U[:, np.diag(N) != 0.0]
+    assert Us.shape[1] == Uk.shape[1] == 3
+    assert np.linalg.norm(Uk @ Uk.T - Us @ Us.T) < 1e-12
+
+
+def test_deflate_threshold_closed_form():
+    """A column at distance eta from the span of the others is dropped iff
+    eta <= delta ||X||_F."""
+    n, delta = 256, 1e-6
+    X = I.gaussian(n, 3, 920)
+    e = I.gaussian(n, 1, 921)[:, 0]
+    B = X[:, :2]
+    e -= B @ np.linalg.lstsq(B, e, rcond=None)[0]
+    e /= np.linalg.norm(e)
+    for factor, dropped in ((0.5, True), (2.0, False)):
+        Y = X.copy()
+        Y[:, 2] = X[:, 0] - X[:, 1]
+        nrm = np.linalg.norm(Y)  # ||X||_F barely moves with eta this small
+        Y[:, 2] += factor * delta * nrm * e
+        _, _, N = O.pqr_mgs2_deflate(np.zeros((n, 0)), Y, delta)
+        assert (N[2, 2] == 0.0) == dropped, factor
+
+
+def test_cholesky_deflation_rows():
+    """cholesky_upper with a deflation threshold: the Gram of a block with a
+    dependent column gets a zero row exactly there, and N^T N reproduces the
+    Gram to rounding on the rest."""
+    X = I.gaussian(200, 4, 930)
+    X[:, 1] = 3.0 * X[:, 0]
+    G = X.T @ X
+    N = O.cholesky_upper(G, 1e-20 * np.trace(G) + 1e-12 * np.trace(G))
+    assert np.all(N[1] == 0.0) and np.all(np.diag(N)[[0, 2, 3]] > 0)
+    assert np.linalg.norm(N.T @ N - G) <= 1e-12 * np.linalg.norm(G)
+    N0 = O.cholesky_upper(G)           # without deflation: a rounding-level pivot, kept
+    assert N0[1, 1] ** 2 <= 1e-12 * np.trace(G)
+
+
+@pytest.mark.parametrize("chunk", [64, 150, 1000])
+def test_tree_tspqr_with_deflation_equals_the_definition(chunk):
+    """TreeTSPQR (Alg. 9) with deflating BCGS-PIP+ sub-algorithms (delta =
+    1e-6: the Gram pivots resolve distances down to about sqrt(eps) ||X||)
+    on a basis of two blocks, then the deficient block: U, P, N equal the
+    plain definition (pqr_mgs2_deflate on the explicit basis); the next
+    full-rank block still works and the representation stays orthonormal on
+    the kept columns."""
+    n, s = 1000, 6
+    ora = O.LocallyOrthogonalBasis(n, s, chunk)
+    for j in range(2):
+        ora.orthogonalize(I.gaussian(n, s, 940 + j), "pip2", "pip2")
+    Qx = ora.explicit()
+    _, X = _deficient_block(n, 12, 950)
+    X[:, 4] = Qx @ I.gaussian(12, 1, 951)[:, 0]
+    X[:, 5] = X[:, 3] - X[:, 0] + Qx @ I.gaussian(12, 1, 952)[:, 0]
+    Uo, Po, No = O.pqr_mgs2_deflate(Qx, X, 1e-8)
+    U, P, N = ora.orthogonalize(X, "pip2", "pip2", deflation=1e-6)
+    assert list(np.flatnonzero(np.diag(N) == 0.0)) == [2, 4, 5]
+    assert np.linalg.norm(U - Uo) <= 1e-12 and np.linalg.norm(P - Po) <= 1e-12 * np.linalg.norm(Po)
+    assert np.linalg.norm(N - No) <= 1e-12 * np.linalg.norm(No)
+    U2, _, N2 = ora.orthogonalize(I.gaussian(n, s, 953), "pip2", "pip2", deflation=1e-6)
+    assert np.all(np.diag(N2) > 0)
+    Q = ora.explicit()
+    kept = np.linalg.norm(Q, axis=0) > 0.5
+    assert kept.sum() == 4 * s - 3
+    assert np.linalg.norm(Q[:, kept].T @ Q[:, kept] - np.eye(kept.sum())) < 1e-13
