@@ -53,8 +53,8 @@ typedef enum lo_status {
   LO_ERR_CHUNK_TOO_SMALL = 3,  /* chunk_rows < max_blocks*s or n < max_blocks*s */
   LO_ERR_BREAKDOWN = 4,        /* a Cholesky pivot <= tolerance: the new block  */
                                /* is (numerically) rank deficient against the   */
-                               /* basis; deflation (Sec. 3, last paragraph) is  */
-                               /* not supported.  Exact zeros on some chunks    */
+                               /* basis and deflation (lo_options.deflation_tol,*/
+                               /* Sec. 3) is off.  Exact zeros on some chunks   */
                                /* are not a breakdown (see lo_orthogonalize)    */
   LO_ERR_NONFINITE = 5,        /* NaN or Inf reached a small factor             */
   LO_ERR_TIMEOUT = 6,          /* a bounded device wait gave up                 */
@@ -164,6 +164,22 @@ typedef struct lo_options {
                          /* (about 0.25 s each) expire and the step returns      */
                          /* LO_ERR_TIMEOUT with the basis unchanged (the timeout */
                          /* path; no fault, nothing left in flight)              */
+  double deflation_tol;  /* delta >= 0, default 0 (off).  delta > 0: the        */
+                         /* deflated PQR of Sec. 3 (t < s), kept as t = s: a    */
+                         /* column of W whose distance to the span of the basis */
+                         /* and of the earlier kept columns is at most          */
+                         /* delta ||W||_F is dropped -- its column of U is zero */
+                         /* and its row of R is zero -- instead of reporting    */
+                         /* LO_ERR_BREAKDOWN.  Decided by the Cholesky pivots   */
+                         /* (squared distances) of the local first pass and of  */
+                         /* the reduction against max(delta^2, 64 s eps)        */
+                         /* ||W||_F^2: the Gram pivots carry rounding noise of  */
+                         /* order eps ||W||_F^2, so delta below about 3e-7 acts */
+                         /* as that floor.  No shifted retry then.  Float64     */
+                         /* forms only (LO_PREC_FP64, LO_PREC_FP64_TC); the     */
+                         /* mixed forms return LO_ERR_UNSUPPORTED.  A deflated  */
+                         /* block still takes a slot of the basis (its dropped  */
+                         /* columns are zero columns of Q).                     */
 } lo_options;
 
 typedef struct lo_basis lo_basis;
@@ -317,6 +333,9 @@ lo_status lo_laplace5_apply(int32_t nx, int32_t ny, int32_t s, const double* X, 
  *   the last read (nkinds >= 6 entries in both arrays).
  */
 long long lo_launch_count(void);
+/* Rank t of the last step's normalizer R (the nonzero diagonal entries; t < s
+ * only with deflation).  Waits for the step. */
+lo_status lo_basis_last_rank(lo_basis* b, int32_t* rank);
 /* Local Gram passes and reduction iterations the last step ran (waits for it). */
 lo_status lo_basis_last_step_info(lo_basis* b, int32_t* passes, int32_t* tree_iterations);
 lo_status lo_basis_set_profiling(lo_basis* b, int32_t enable);

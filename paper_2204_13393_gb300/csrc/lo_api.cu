@@ -193,6 +193,7 @@ StepArgs make_args(const lo_basis* b) {
   a.leaf = b->opt.leaf;
   a.reduction = b->opt.reduction;
   a.refine_tol = b->opt.refine_tol > 0 ? b->opt.refine_tol : 1e-13;
+  a.deflation_tol = b->opt.deflation_tol;
   a.colexp = b->colexp;
   a.srcexp_slab = b->srcexp_slab;
   a.srcexp = b->srcexp;
@@ -346,6 +347,7 @@ void lo_options_default(lo_options* opt) {
   opt->refine_tol = 1e-13;
   opt->digit_planes = LO_PLANES_AUTO;
   opt->test_stall = 0;
+  opt->deflation_tol = 0.0;
 }
 
 const char* lo_status_string(lo_status st) {
@@ -389,6 +391,9 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   }
   const bool tc = (o.precision == LO_PREC_FP64_TC || o.precision == LO_PREC_MIXED_TC);
   if (tc && !lo::oz_supported(s)) return LO_ERR_UNSUPPORTED;
+  if (!(o.deflation_tol >= 0.0) || !std::isfinite(o.deflation_tol)) return LO_ERR_INVALID_ARG;
+  if (o.deflation_tol > 0.0 && (o.precision == LO_PREC_MIXED_FP32 || o.precision == LO_PREC_MIXED_TC))
+    return LO_ERR_UNSUPPORTED;
   if (o.refine_tol <= 0) o.refine_tol = 1e-13;
   const int64_t p64 = n / chunk_rows > 0 ? n / chunk_rows : 1;
   if (p64 > (1 << 30)) return LO_ERR_INVALID_ARG;
@@ -903,6 +908,21 @@ lo_status lo_basis_export_chunk(lo_basis* b, int32_t chunk, double* Qi_host, dou
 }
 
 long long lo_launch_count(void) { return lo::launches(); }
+
+lo_status lo_basis_last_rank(lo_basis* b, int32_t* rank) {
+  if (!b || !rank) return LO_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  const GlobLayout GL = GlobLayout::make(b->Kmax, b->s);
+  std::vector<double> N((size_t)b->s * b->s);
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(N.data(), b->glob + GL.N_acc, sizeof(double) * N.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return from_cuda(e);
+  int t = 0;
+  for (int i = 0; i < b->s; ++i) t += N[(size_t)i * b->s + i] != 0.0 ? 1 : 0;
+  *rank = t;
+  return LO_OK;
+}
 
 lo_status lo_basis_last_step_info(lo_basis* b, int32_t* passes, int32_t* tree_iterations) {
   if (!b) return LO_ERR_INVALID_ARG;

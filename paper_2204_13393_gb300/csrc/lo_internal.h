@@ -63,7 +63,8 @@ struct GlobLayout {
   int64_t P_it, N_it, Ninv_it;   // this tree iteration: Kmax x s, s x s, s x s
   int64_t P_acc, N_acc;          // combined over iterations (the outputs H, R)
   int64_t Zsum;                  // Kmax x s, the summed contributions
-  int64_t scal;                  // 8 scalars: [0] = |W|_F^2 of the step
+  int64_t scal;                  // 8 scalars: [0] = |W|_F^2 of the step (tree), [1] = the same from the
+                                 // pass-1 Gram partials (deflation thresholds of the local leaves)
   int64_t stride;
   __host__ __device__ static GlobLayout make(int Kmax, int s) {
     GlobLayout L;
@@ -103,6 +104,7 @@ struct StepArgs {
   int leaf;
   int reduction;
   double refine_tol;
+  double deflation_tol;     // delta of the deflated PQR (0: off)
   // the step's block and outputs
   const double* W;
   int64_t ldw;

@@ -45,12 +45,20 @@ __device__ __forceinline__ int passes_run(const StepArgs& a) {
 // (shared memory, zeroed by the caller) and, when flags is not null, latches
 // LO_ERR_BREAKDOWN / LO_ERR_NONFINITE; the pivot is replaced by 1 so that no
 // NaN propagates.
-__device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail) {
+//
+// defl > 0 (the deflated PQR of Sec. 3): a finite pivot d <= defl (the squared
+// distance of column i to the span of what precedes it) is deflated as well:
+// row i of N is set to zero and eliminates nothing.
+__device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail, double defl = 0.0) {
   for (int i = 0; i < s; ++i) {
     if (threadIdx.x == 0) {
       double d = M[i * s + i];
       bool zero_row = d == 0.0;
       for (int j = i + 1; j < s && zero_row; ++j) zero_row = M[i * s + j] == 0.0;
+      if (!zero_row && defl > 0.0 && isfinite(d) && d <= defl) {
+        for (int j = i + 1; j < s; ++j) M[i * s + j] = 0.0;
+        zero_row = true;
+      }
       if (zero_row) {
         d = 0.0;
       } else if (!isfinite(d)) {
@@ -92,11 +100,11 @@ __device__ void cta_cholesky(double* M, int s, double tol, int* flags, int* fail
 // caller then forces two further reiterations.  Without allow_shift a
 // breakdown latches the status.  save: s*s shared scratch.
 __device__ bool cta_cholesky_shifted(double* M, double* save, int s, double tol, double sigma, bool allow_shift,
-                                     int* flags, int* fail) {
+                                     int* flags, int* fail, double defl = 0.0) {
   if (threadIdx.x == 0) *fail = 0;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) save[e] = M[e];
   __syncthreads();
-  cta_cholesky(M, s, tol, allow_shift ? nullptr : flags, fail);
+  cta_cholesky(M, s, tol, allow_shift ? nullptr : flags, fail, defl);
   const bool failed = *fail != 0;
   __syncthreads();
   if (!failed || !allow_shift) return false;
@@ -577,8 +585,16 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
   const double tol = (double)s * u_gram * trG;
   const int64_t rows = a.chunk_row0[c + 1] - a.chunk_row0[c];
   const double sigma = 11.0 * ((double)rows * s + (double)s * (s + 1)) * u_gram * trG;
-  const bool shifted = cta_cholesky_shifted(M, tmp, s, tol, sigma, allow_shift != 0, a.flags,
-                                            reinterpret_cast<int*>(red + 2));
+  // deflation (first pass only; later passes see the dropped columns as exact
+  // zeros): pivots against the whole block's squared norm, floored at the
+  // Gram's rounding level
+  double defl = 0.0;
+  if (a.deflation_tol > 0.0 && pass == 1) {
+    const GlobLayout GLd = GlobLayout::make(a.Kmax, s);
+    defl = fmax(a.deflation_tol * a.deflation_tol, 64.0 * s * DBL_EPSILON) * a.glob[GLd.scal + 1];
+  }
+  const bool shifted = cta_cholesky_shifted(M, tmp, s, tol, sigma, allow_shift != 0 && a.deflation_tol <= 0.0,
+                                            a.flags, reinterpret_cast<int*>(red + 2), defl);
   if (shifted && threadIdx.x == 0)
     for (int t = pass + 1; t <= pass + 2 && t <= kMaxPass; ++t) atomicOr(&a.flags[kFlagPass + t - 1], 1);
   cta_upper_inverse(M, Ni, s);
@@ -615,6 +631,26 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
     if (auto_mode && !(DBL_EPSILON * kap * kap <= a.refine_tol))
       atomicOr(&a.flags[kFlagPass + pass], 1);
   }
+}
+
+// ||W||_F^2 of the step from the pass-1 Gram partials (the diagonal of each
+// slab's W^T W block, slabs in order), for the deflation thresholds of the
+// local leaves.  One CTA.
+__global__ void __launch_bounds__(kThreads) k_defl_trace(StepArgs a) {
+  __shared__ double red[kThreads];
+  const int s = a.s, k = a.nb * s;
+  double v = 0.0;
+  for (int e = threadIdx.x; e < a.nslab * s; e += kThreads) {
+    const int sl = e / s, i = e - sl * s;
+    v += a.part[(int64_t)sl * a.Kmax * s + (int64_t)(k + i) * s + i];
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.glob[GlobLayout::make(a.Kmax, s).scal + 1] = red[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -703,8 +739,12 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
   __syncthreads();
   const double trG = red[1];
   const double sigma = 11.0 * ((double)a.p * (k + s) * s + (double)s * (s + 1)) * DBL_EPSILON * trG;
+  const bool deflate = a.deflation_tol > 0.0;
+  const double defl =
+      (deflate && it == 1) ? fmax(a.deflation_tol * a.deflation_tol, 64.0 * s * DBL_EPSILON) * trG : 0.0;
   const bool shifted = cta_cholesky_shifted(M, tmp, s, (double)s * DBL_EPSILON * trG, sigma,
-                                            it == 1 && a.reduction != 1, a.flags, reinterpret_cast<int*>(red + 2));
+                                            it == 1 && a.reduction != 1 && !deflate, a.flags,
+                                            reinterpret_cast<int*>(red + 2), defl);
   if (shifted && threadIdx.x == 0)
     for (int t = it + 1; t <= it + 2 && t <= kMaxTreeIter; ++t) atomicOr(&a.flags[kFlagTree + t - 1], 1);
   if (it == 1 && threadIdx.x == 0) a.glob[GL.scal] = trG;  // |W|_F^2 of the step
@@ -739,7 +779,8 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
     // (the deflation case of Sec. 3, not supported) is a breakdown
     const double floor_ = 64.0 * s * DBL_EPSILON * sqrt(a.glob[GL.scal]);
     for (int i = 0; i < s; ++i)
-      if (!(fabs(N_acc[i * s + i]) > floor_)) set_status(a.flags, LO_ERR_BREAKDOWN);
+      if (!(fabs(N_acc[i * s + i]) > floor_) && !(deflate && N_acc[i * s + i] == 0.0))
+        set_status(a.flags, LO_ERR_BREAKDOWN);
   }
   if (threadIdx.x == 0 && it < kMaxTreeIter) {
     if (a.reduction == 0 && !(DBL_EPSILON * kap * kap <= a.refine_tol))
@@ -1358,6 +1399,10 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
     const double shift = (pass == 1 && mixed && !digit_first) ? 1e-5 : 0.0;
     const double u_gram = digit_first ? 0x1p-31 : DBL_EPSILON;
     const size_t smleaf = 8 * ((size_t)Kt * s + 4 * ss + 4);
+    if (pass == 1 && a.deflation_tol > 0.0) {
+      k_defl_trace<<<1, kThreads, 0, st>>>(a);
+      count_launches(1);
+    }
     mark(hook, kKindLeaf, true, st);
     const int allow_shift = (pass == 1 && (!mixed || digit_first) && a.leaf != LO_LEAF_PIP) ? 1 : 0;
     k_leaf<<<a.p, kThreads, smleaf, st>>>(a, pass, shift, allow_shift, u_gram);

@@ -42,7 +42,7 @@ EXPORTED = [
     "lo_orthogonalize", "lo_orthogonalize_batched", "lo_apply_Q", "lo_basis_export_chunk",
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
     "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_tsqr_noalloc_scratch", "lo_basis_truncate",
-    "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries",
+    "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries", "lo_basis_last_rank",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
@@ -57,7 +57,7 @@ class LoError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("leaf", c_int32), ("reduction", c_int32),
                 ("sync", c_int32), ("refine_tol", c_double), ("digit_planes", c_int32),
-                ("test_stall", c_int32)]
+                ("test_stall", c_int32), ("deflation_tol", c_double)]
 
 
 _L = None
@@ -108,6 +108,8 @@ def _lib():
     L.lo_basis_profile_read.restype = c_int32
     L.lo_basis_last_step_info.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32)]
     L.lo_basis_last_step_info.restype = c_int32
+    L.lo_basis_last_rank.argtypes = [c_void_p, POINTER(c_int32)]
+    L.lo_basis_last_rank.restype = c_int32
     L.lo_tsqr_noalloc.argtypes = [c_int64, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
     L.lo_tsqr_noalloc.restype = c_int32
     L.lo_tsqr_noalloc_scratch.argtypes = [c_int64, c_int32, c_int32, POINTER(ctypes.c_uint64),
@@ -187,7 +189,8 @@ class Basis:
 
     def __init__(self, n: int, s: int, max_blocks: int, chunk_rows: int, precision: str = "fp64",
                  leaf: str = "pip2", reduction: str = "auto", sync: bool = True,
-                 refine_tol: float = 0.0, stream=None, digit_planes: bool = True, test_stall: bool = False):
+                 refine_tol: float = 0.0, stream=None, digit_planes: bool = True, test_stall: bool = False,
+                 deflation_tol: float = 0.0):
         L = _lib()
         o = Options()
         L.lo_options_default(ctypes.byref(o))
@@ -199,6 +202,7 @@ class Basis:
             o.refine_tol = refine_tol
         o.digit_planes = 0 if digit_planes else 1
         o.test_stall = 1 if test_stall else 0
+        o.deflation_tol = float(deflation_tol)
         h = c_void_p()
         self._h = None
         _check(L.lo_basis_create(int(n), int(s), int(max_blocks), int(chunk_rows), ctypes.byref(o),
@@ -267,6 +271,12 @@ class Basis:
 
     def truncate(self, num_blocks: int):
         _check(_lib().lo_basis_truncate(self._h, int(num_blocks)), "lo_basis_truncate")
+
+    def last_rank(self) -> int:
+        """Rank of the last step's normalizer R (< s only with deflation)."""
+        t = c_int32()
+        _check(_lib().lo_basis_last_rank(self._h, ctypes.byref(t)), "lo_basis_last_rank")
+        return t.value
 
     def last_step_info(self):
         """(local Gram passes, reduction iterations) of the last step."""

@@ -98,7 +98,8 @@ def test_options_default(lib):
     assert (o.precision, o.leaf, o.reduction, o.sync) == (0, 2, 0, 1)
     assert o.refine_tol == pytest.approx(1e-13)
     assert (o.digit_planes, o.test_stall) == (0, 0)
-    assert ctypes.sizeof(o) == 32
+    assert o.deflation_tol == 0.0
+    assert ctypes.sizeof(o) == 40
 
 
 def test_tuner_and_noalloc_reject_bad_arguments_without_device(lib):
@@ -174,3 +175,19 @@ def test_householder_leaf_tile_check_without_device(lib):
         assert h.value is None
     o.leaf = 4
     assert lib.lo_basis_create(4096, 4, 1, 512, ctypes.byref(o), None, ctypes.byref(h)) == 1
+
+
+def test_deflation_option_checks_without_device(lib):
+    """deflation_tol must be finite and >= 0, and is for the float64 forms
+    only (the mixed forms' first pass cannot resolve the distances)."""
+    from paper_2204_13393_gb300 import lo
+
+    h = ctypes.c_void_p()
+    o = lo.Options()
+    for prec, tol, want in (("fp64", -1.0, 1), ("fp64", float("nan"), 1), ("fp64", float("inf"), 1),
+                            ("mixed_fp32", 1e-6, 9), ("mixed_tc", 1e-6, 9)):
+        lib.lo_options_default(ctypes.byref(o))
+        o.precision = lo.PRECISION[prec]
+        o.deflation_tol = tol
+        assert lib.lo_basis_create(4096, 8, 4, 512, ctypes.byref(o), None, ctypes.byref(h)) == want, (prec, tol)
+        assert h.value is None
