@@ -699,8 +699,16 @@ def run_batched_case(args):
             b.truncate(kb)
         lo.orthogonalize_batched(bases, Ws, Us, Hs, Rs)
 
+    def routed(mode):
+        def fn():
+            lo.set_batched_route(mode)
+            batched()
+        return fn
+
     res = {}
-    for name, fn in (("sequential", sequential), ("batched", batched)):
+    routes = {}
+    for name, fn in (("sequential", sequential), ("batched", routed("auto")), ("graph", routed("graph")),
+                     ("persistent", routed("persistent"))):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
@@ -712,7 +720,12 @@ def run_batched_case(args):
         e1.record(stream)
         torch.cuda.synchronize()
         res[name] = e0.elapsed_time(e1) / args.steps
+        if name != "sequential":
+            routes[name] = lo.batched_persistent_count()
+    lo.set_batched_route("auto")
     print(json.dumps({"case": "batched", "precision": args.precision, "instances": len(specs),
+                      "persistent_instances": routes,
+                      "ms_graph_only": round(res["graph"], 3), "ms_persistent_where_possible": round(res["persistent"], 3),
                       "bytes_per_step": nbytes, "ms_batched": round(res["batched"], 3),
                       "ms_sequential": round(res["sequential"], 3),
                       "gbs_batched": round(nbytes / res["batched"] / 1e6, 1),
@@ -911,6 +924,25 @@ def run_step_case(args):
         st.synchronize()
         us = sorted(e0.elapsed_time(e1) * 1e3 for e0, e1 in times)
         med = us[len(us) // 2]
+        # the same step as one persistent launch (lo_orthogonalize_batched with
+        # one instance, route 'persistent': init kernel + the persistent kernel)
+        lo.set_batched_route("persistent")
+        ptimes = []
+        with torch.cuda.stream(st):
+            for rep in range(220):
+                b.truncate(kb)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                lo.orthogonalize_batched([b], [W], [U], [H], [R])
+                e1.record(st)
+                if rep >= 20:
+                    ptimes.append((e0, e1))
+        st.synchronize()
+        lo.set_batched_route("auto")
+        pus = sorted(e0.elapsed_time(e1) * 1e3 for e0, e1 in ptimes)
+        pmed = pus[len(pus) // 2]
+        Hp, Rp = H.clone(), R.clone()
         Q = b.apply_Q(torch.eye((kb + 1) * s, dtype=torch.float64, device=dev))
         st.synchronize()
         eperp = float(torch.linalg.norm(Q.T @ Q - torch.eye((kb + 1) * s, dtype=torch.float64, device=dev)))
@@ -919,7 +951,14 @@ def run_step_case(args):
             "us_median": round(med, 2), "us_p10": round(us[len(us) // 10], 2), "us_p90": round(us[9 * len(us) // 10], 2),
             "steps_per_s": round(1e6 / med, 1), "gbs": round(nbytes / (med * 1e-6) / 1e9, 2),
             "e_perp": eperp, "H_replay_vs_eager": float((H - H0).abs().max()),
-            "R_replay_vs_eager": float((R - R0).abs().max()), "launches_per_step": launches}
+            "R_replay_vs_eager": float((R - R0).abs().max()), "launches_per_step": launches,
+            "persistent_launch": {"us_median": round(pmed, 2), "us_p10": round(pus[len(pus) // 10], 2),
+                                  "steps_per_s": round(1e6 / pmed, 1), "launches_per_step": 2,
+                                  "H_vs_eager": float((Hp - H0).abs().max() / H0.abs().max()),
+                                  "R_vs_eager": float((Rp - R0).abs().max() / R0.abs().max()),
+                                  "note": "device time between events around one lo_orthogonalize_batched "
+                                          "call (a cached graph: init + persistent kernel; float64 on the "
+                                          "CUDA cores)"}}
         b.close()
     print(json.dumps(out), flush=True)
 

@@ -277,6 +277,33 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count,
                                    double* const* H, double* const* R);
 
 /*
+ * Route of lo_orthogonalize_batched's instances (process-wide; part of the
+ * cached graphs' key):
+ *   0 (default) auto: an instance of at most 4e6 n (k + s) whose form the
+ *     persistent launch can run goes into it, every other one gets its own
+ *     branch of the graph;
+ *   1: the persistent launch for every instance it can run;
+ *   2: graph branches only (each instance's own kernel sequence).
+ * The persistent launch is one kernel (after a small init kernel) over a work
+ * list of (instance, row slab) and (instance, chunk) items of all its
+ * instances, with per-chunk and per-instance tickets handing the leaf and
+ * reduction factorizations to the CTA that finishes last (TreeTSPQR, Alg. 9,
+ * BCGS-PIP+ local and reduction solvers, float64 arithmetic on the CUDA cores;
+ * for a tensor-core basis the new panel's exponents and digit planes are
+ * kept current).  It runs instances created with the float64 forms
+ * (LO_PREC_FP64, LO_PREC_FP64_TC), the BCGS-PIP+ leaf (or the Householder
+ * leaf past the first block), a reiterating reduction, no deflation, and
+ * device buffers; an instance whose estimate asks for a third local pass or
+ * reduction iteration (or the shifted retry) is redone on the regular path
+ * within the same call.  Sec. 6.2 finds small local problems leave the
+ * hardware idle; many such steps fill it together.
+ * lo_batched_persistent_count: instances the last used cached graph runs in
+ * the persistent launch (for tests and the benchmark).
+ */
+lo_status lo_set_batched_route(int32_t mode);
+int32_t lo_batched_persistent_count(void);
+
+/*
  * Drop the trailing blocks so that num_blocks (<= the current count) remain.
  * The representation of the first num_blocks blocks is not affected by later
  * steps, so this is exact (a truncated restart, or re-running a step).

@@ -93,6 +93,7 @@ struct lo_basis {
   double* glob = nullptr;
   double* tsum = nullptr;
   int* flags = nullptr;
+  int* tick = nullptr;     // ticket area of the persistent batched launch
   int* h_flags = nullptr;  // pinned
   SlabInfo* d_slabs = nullptr;
   int32_t* d_chunk_slab0 = nullptr;
@@ -248,13 +249,24 @@ lo_status copy_small_outputs(lo_basis* b, double* H, double* R, cudaStream_t st)
 // evicts every entry that names the basis.
 constexpr int kPool = 8;
 constexpr size_t kGraphCache = 8;
-constexpr size_t kKeyHead = 2;    // count, stream
+constexpr size_t kKeyHead = 3;    // count, stream, route mode
 constexpr size_t kKeyPer = 9;     // words per instance; the basis id comes first
 struct GraphEntry {
   std::vector<uintptr_t> key;
   cudaGraphExec_t exec;
   unsigned long long stamp;
+  // the persistent launch's instance table, item prefix and counters (device)
+  lo::BatchInst* d_insts;
+  int* d_pref;
+  int* d_counters;
+  std::vector<char> persistent;  // per instance: run by the persistent launch
 };
+void free_entry(GraphEntry& ent) {
+  cudaGraphExecDestroy(ent.exec);
+  cudaFree(ent.d_insts);
+  cudaFree(ent.d_pref);
+  cudaFree(ent.d_counters);
+}
 struct BatchGraphs {
   std::mutex mu;
   int device = -1;
@@ -278,7 +290,7 @@ bool key_names(const std::vector<uintptr_t>& key, uint64_t id) {
 void evict_locked(BatchGraphs& bg, uint64_t id) {
   for (size_t i = 0; i < bg.cache.size();) {
     if (key_names(bg.cache[i].key, id)) {
-      cudaGraphExecDestroy(bg.cache[i].exec);
+      free_entry(bg.cache[i]);
       bg.cache.erase(bg.cache.begin() + i);
     } else {
       ++i;
@@ -297,7 +309,7 @@ cudaError_t ensure_pool(BatchGraphs& bg, int device) {
   if (bg.device >= 0) {
     int cur = device;
     cudaSetDevice(bg.device);
-    for (auto& ent : bg.cache) cudaGraphExecDestroy(ent.exec);
+    for (auto& ent : bg.cache) free_entry(ent);
     bg.cache.clear();
     for (int i = 0; i < kPool; ++i) {
       if (bg.st[i]) cudaStreamDestroy(bg.st[i]);
@@ -333,6 +345,15 @@ lo_status ensure_owned(lo_basis* b, double** buf, size_t* cap, size_t need) {
 }
 
 std::atomic<uint64_t> g_next_basis_id{1};
+
+// Route of the batched call's instances: 0 auto (the persistent launch for
+// instances of at most kPersistentWork n (k + s) that it can run, graph
+// branches for the rest), 1 the persistent launch wherever it can run,
+// 2 graph branches only.
+std::atomic<int> g_batch_route{0};
+// Crossover of the auto route, in n (k + s): below it one persistent float64
+// launch beats an instance's own kernel sequence (measured on GB300).
+constexpr double kPersistentWork = 4.0e6;
 
 }  // namespace
 
@@ -460,6 +481,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   alloc((void**)&b->glob, sizeof(double) * (size_t)GL.stride);
   alloc((void**)&b->tsum, sizeof(double) * (size_t)b->ngroups * Kmax * s);
   alloc((void**)&b->flags, sizeof(int) * lo::kFlagCount);
+  alloc((void**)&b->tick, sizeof(int) * lo::batch_tick_ints(p));
   alloc((void**)&b->d_slabs, sizeof(SlabInfo) * slabs.size());
   alloc((void**)&b->d_chunk_slab0, sizeof(int32_t) * cs0.size());
   alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
@@ -509,6 +531,7 @@ void lo_basis_destroy(lo_basis* b) {
   cudaFree(b->glob);
   cudaFree(b->tsum);
   cudaFree(b->flags);
+  cudaFree(b->tick);
   cudaFree(b->d_slabs);
   cudaFree(b->d_chunk_slab0);
   cudaFree(b->d_chunk_row0);
@@ -646,11 +669,13 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
   std::unique_lock<std::mutex> lock(bg.mu);
   cudaError_t e = ensure_pool(bg, bases[0]->device);
   if (e != cudaSuccess) return from_cuda(e);
+  const int route = g_batch_route.load();
   // key: everything the captured work depends on; a basis by its id
   std::vector<uintptr_t> key;
   key.reserve(kKeyPer * (size_t)count + kKeyHead);
   key.push_back((uintptr_t)count);
   key.push_back((uintptr_t)cs);
+  key.push_back((uintptr_t)route);
   for (int j = 0; j < count; ++j) {
     key.push_back((uintptr_t)bases[j]->id);
     key.push_back((uintptr_t)bases[j]->nb);
@@ -662,59 +687,160 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     key.push_back((uintptr_t)Rd[j]);
     key.push_back((uintptr_t)bases[j]->h_flags);
   }
-  cudaGraphExec_t exec = nullptr;
-  for (auto& ent : bg.cache)
-    if (ent.key == key) {
-      exec = ent.exec;
-      ent.stamp = ++bg.clock;
+  GraphEntry* ent = nullptr;
+  for (auto& en : bg.cache)
+    if (en.key == key) {
+      ent = &en;
+      en.stamp = ++bg.clock;
     }
-  if (!exec) {
-    // capture: fork onto the pool streams, one instance per stream round-robin, join
-    if ((e = lo::launch_prepare()) != cudaSuccess) return from_cuda(e);
+  if (!ent) {
+    // the route of every instance: the persistent launch (device buffers only) or its own branch
+    GraphEntry ne{key, nullptr, 0, nullptr, nullptr, nullptr, std::vector<char>(count, 0)};
+    std::vector<lo::BatchInst> insts;
+    std::vector<int> which;
+    for (int j = 0; j < count && route != 2; ++j) {
+      lo_basis* b = bases[j];
+      if (w_host[j] || u_host[j] || h_host[j] || r_host[j]) continue;
+      lo::BatchInst bi{};
+      bi.a = make_args(b);
+      bi.a.W = Wd[j];
+      bi.a.ldw = ldwd[j];
+      bi.a.U = Ud[j];
+      bi.a.ldu = ldud[j];
+      bi.tick = b->tick;
+      bi.H = (b->nb > 0) ? Hd[j] : nullptr;
+      bi.R = Rd[j];
+      if (!lo::batch_fill(&bi)) continue;
+      if (route == 0 && (double)b->n * (double)(b->nb * b->s + b->s) > kPersistentWork) continue;
+      ne.persistent[j] = 1;
+      insts.push_back(bi);
+      which.push_back(j);
+    }
+    const int ni = (int)insts.size();
+    size_t smem = 0;
+    if (ni > 0) {
+      // item prefix, phase-major: pass 1, pass 2, tree 1, tree 2, assembly, digit planes
+      std::vector<int> pref(6 * (size_t)(ni + 1));
+      int off = 0;
+      for (int ph = 0; ph < 6; ++ph) {
+        for (int q = 0; q < ni; ++q) {
+          pref[ph * (ni + 1) + q] = off;
+          const lo::StepArgs& a = insts[q].a;
+          const int cnt = (ph == 2 || ph == 3) ? a.p : (ph == 5 ? (insts[q].digitize ? a.nslab : 0) : a.nslab);
+          off += cnt;
+        }
+        pref[ph * (ni + 1) + ni] = off;
+      }
+      smem = lo::batch_smem(insts.data(), ni);
+      if (cudaMalloc(&ne.d_insts, sizeof(lo::BatchInst) * ni) != cudaSuccess ||
+          cudaMalloc(&ne.d_pref, sizeof(int) * pref.size()) != cudaSuccess ||
+          cudaMalloc(&ne.d_counters, 2 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(ne.d_insts);
+        cudaFree(ne.d_pref);
+        cudaFree(ne.d_counters);
+        return LO_ERR_OOM;
+      }
+      e = cudaMemcpy(ne.d_insts, insts.data(), sizeof(lo::BatchInst) * ni, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(ne.d_pref, pref.data(), sizeof(int) * pref.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        cudaFree(ne.d_insts);
+        cudaFree(ne.d_pref);
+        cudaFree(ne.d_counters);
+        return from_cuda(e);
+      }
+    }
+    // capture: fork onto the pool streams (the persistent launch on the first,
+    // the other instances round-robin on the rest), join
+    if ((e = lo::launch_prepare()) != cudaSuccess) {
+      cudaFree(ne.d_insts);
+      cudaFree(ne.d_pref);
+      cudaFree(ne.d_counters);
+      return from_cuda(e);
+    }
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(bg.cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return from_cuda(e);
-    lo_status rs = LO_OK;
-    cudaEventRecord(bg.fork, bg.cap);
-    for (int i = 0; i < kPool; ++i) cudaStreamWaitEvent(bg.st[i], bg.fork, 0);
-    for (int j = 0; j < count && rs == LO_OK; ++j) {
-      lo_basis* b = bases[j];
-      cudaStream_t st = bg.st[j % kPool];
-      StepArgs a = make_args(b);
-      a.W = Wd[j];
-      a.ldw = ldwd[j];
-      a.U = Ud[j];
-      a.ldu = ldud[j];
-      rs = from_cuda(lo::launch_step(a, st, nullptr));
-      if (rs == LO_OK) rs = copy_small_outputs(b, Hd[j], Rd[j], st);
-      if (rs == LO_OK)
-        rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    lo_status rs = from_cuda(e);
+    if (rs == LO_OK) {
+      cudaEventRecord(bg.fork, bg.cap);
+      for (int i = 0; i < kPool; ++i) cudaStreamWaitEvent(bg.st[i], bg.fork, 0);
+      if (ni > 0) {
+        rs = from_cuda(lo::launch_batch(ne.d_insts, ni, ne.d_pref, ne.d_counters, smem, bg.st[0]));
+        for (int q = 0; q < ni && rs == LO_OK; ++q) {
+          lo_basis* b = bases[which[q]];
+          rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int) * lo::kFlagCount,
+                                         cudaMemcpyDeviceToHost, bg.st[0]));
+        }
+      }
+      int rr = 0;
+      for (int j = 0; j < count && rs == LO_OK; ++j) {
+        if (ne.persistent[j]) continue;
+        lo_basis* b = bases[j];
+        cudaStream_t st = bg.st[ni > 0 ? 1 + (rr++ % (kPool - 1)) : (rr++ % kPool)];
+        StepArgs a = make_args(b);
+        a.W = Wd[j];
+        a.ldw = ldwd[j];
+        a.U = Ud[j];
+        a.ldu = ldud[j];
+        rs = from_cuda(lo::launch_step(a, st, nullptr));
+        if (rs == LO_OK) rs = copy_small_outputs(b, Hd[j], Rd[j], st);
+        if (rs == LO_OK)
+          rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int) * lo::kFlagCount,
+                                         cudaMemcpyDeviceToHost, st));
+      }
+      for (int i = 0; i < kPool; ++i) {
+        cudaEventRecord(bg.join[i], bg.st[i]);
+        cudaStreamWaitEvent(bg.cap, bg.join[i], 0);
+      }
+      e = cudaStreamEndCapture(bg.cap, &graph);
+      if (rs == LO_OK) rs = from_cuda(e);
     }
-    for (int i = 0; i < kPool; ++i) {
-      cudaEventRecord(bg.join[i], bg.st[i]);
-      cudaStreamWaitEvent(bg.cap, bg.join[i], 0);
+    if (rs == LO_OK) {
+      e = cudaGraphInstantiate(&ne.exec, graph, 0);
+      rs = from_cuda(e);
     }
-    e = cudaStreamEndCapture(bg.cap, &graph);
+    if (graph) cudaGraphDestroy(graph);
     if (rs != LO_OK) {
-      if (graph) cudaGraphDestroy(graph);
+      cudaFree(ne.d_insts);
+      cudaFree(ne.d_pref);
+      cudaFree(ne.d_counters);
       return rs;
     }
-    if (e != cudaSuccess) return from_cuda(e);
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return from_cuda(e);
     if (bg.cache.size() >= kGraphCache) {
       size_t old = 0;
       for (size_t i = 1; i < bg.cache.size(); ++i)
         if (bg.cache[i].stamp < bg.cache[old].stamp) old = i;
-      cudaGraphExecDestroy(bg.cache[old].exec);
+      free_entry(bg.cache[old]);
       bg.cache.erase(bg.cache.begin() + old);
     }
-    bg.cache.push_back(GraphEntry{key, exec, ++bg.clock});
+    ne.stamp = ++bg.clock;
+    bg.cache.push_back(std::move(ne));
+    ent = &bg.cache.back();
   }
-  for (int j = 0; j < count; ++j) bases[j]->h_flags[0] = 0;
-  e = cudaGraphLaunch(exec, cs);
+  const std::vector<char> persistent = ent->persistent;
+  for (int j = 0; j < count; ++j)
+    for (int f = 0; f < lo::kFlagCount; ++f) bases[j]->h_flags[f] = 0;
+  e = cudaGraphLaunch(ent->exec, cs);
   lock.unlock();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  // Instances of the persistent launch that asked for a third local pass or
+  // reduction iteration (or the shifted retry) are redone on the regular
+  // path; the launch left their block count alone.
+  for (int j = 0; j < count; ++j) {
+    if (!persistent[j]) continue;
+    lo_basis* b = bases[j];
+    const int* f = b->h_flags;
+    const bool timeout = (f[0] & (1 << LO_ERR_TIMEOUT)) != 0;
+    if (!timeout && (f[lo::kFlagPass + 2] || f[lo::kFlagTree + 2])) {
+      cudaMemsetAsync(b->flags, 0, sizeof(int), cs);
+      lo_status rs = enqueue_step(b, Wd[j], ldwd[j], Ud[j], ldud[j], cs);
+      if (rs == LO_OK) rs = copy_small_outputs(b, Hd[j], Rd[j], cs);
+      if (rs == LO_OK)
+        rs = from_cuda(cudaMemcpyAsync(b->h_flags, b->flags, sizeof(int), cudaMemcpyDeviceToHost, cs));
+      if (rs != LO_OK) return rs;
+    }
+  }
   // host outputs: after the graph, on the same stream
   for (int j = 0; j < count && e == cudaSuccess; ++j) {
     lo_basis* b = bases[j];
@@ -740,6 +866,24 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const 
     }
   }
   return first;
+}
+
+lo_status lo_set_batched_route(int32_t mode) {
+  if (mode < 0 || mode > 2) return LO_ERR_INVALID_ARG;
+  g_batch_route.store(mode);
+  return LO_OK;
+}
+
+int32_t lo_batched_persistent_count(void) {
+  BatchGraphs& bg = batch_graphs();
+  std::lock_guard<std::mutex> lock(bg.mu);
+  if (bg.cache.empty()) return 0;
+  size_t last = 0;
+  for (size_t i = 1; i < bg.cache.size(); ++i)
+    if (bg.cache[i].stamp > bg.cache[last].stamp) last = i;
+  int32_t c = 0;
+  for (char v : bg.cache[last].persistent) c += v ? 1 : 0;
+  return c;
 }
 
 uint64_t lo_basis_id(const lo_basis* b) { return b ? b->id : 0; }

@@ -136,6 +136,18 @@ struct StepArgs {
   int apply_m, apply_n0;
 };
 
+// One instance of a persistent batched launch (k_batch_step).
+struct BatchInst {
+  StepArgs a;
+  int* tick;        // ticket area of the instance (TickLayout, 4 p + 4 ints)
+  double* H;        // device outputs (or null)
+  double* R;
+  int tile_g;       // tile rows of the generic Gram (pass 2, and pass 1 without gram1)
+  int tile_u;       // tile rows of the assembly
+  int gram1;        // pass 1 by the register-tiled Gram (s in {1, 2, 4, 8, 16, 32})
+  int digitize;     // write the digit planes of the new panel
+};
+
 // TMA descriptors of a basis's digit planes: one box shape per kernel.
 struct UmmaMaps {
   CUtensorMap upd;    // 16 8-row blocks (128 rows) of the 16 columns of one step, all planes
@@ -225,5 +237,17 @@ cudaError_t oz_set_attrs();
 
 cudaError_t launch_laplace5(int nx, int ny, int s, const double* X, int64_t ldx, double* Y,
                             int64_t ldy, cudaStream_t st);
+
+// Persistent batched launch (lo_kernels.cu).  batch_fill: fill the host
+// descriptor of one instance (tile rows, route flags) and return whether the
+// persistent kernel can run it; batch_tick_ints: its ticket area size;
+// launch_batch: init + the persistent kernel over d_insts (device copies),
+// pref the phase-major item prefix (6 x (ninst + 1) ints, device), counters
+// 2 ints (device).  smem: dynamic shared memory of the kernel.
+bool batch_fill(BatchInst* bi);
+int batch_tick_ints(int p);
+size_t batch_smem(const BatchInst* insts, int ninst);
+cudaError_t launch_batch(BatchInst* d_insts, int ninst, const int* d_pref, int* d_counters, size_t smem,
+                         cudaStream_t st);
 
 }  // namespace lo

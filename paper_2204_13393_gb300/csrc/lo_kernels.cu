@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "lo_internal.h"
+#include "lo_oz_common.cuh"
 #include "lo_recombine.h"
 
 namespace lo {
@@ -245,10 +246,8 @@ __device__ __forceinline__ float load_scaled<float>(const double* p, int sh) { r
 // into the new local panel so that the next stage reads it instead of
 // recomputing it.  TileT/Acc = float for the first pass of the mixed form.
 template <typename TileT, typename Acc>
-__global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int tile_rows) {
-  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SlabInfo si = a.slabs[blockIdx.x];
+__device__ void gram_slab(const StepArgs& a, int pass, int tile_rows, int slab, unsigned char* smem_raw) {
+  const SlabInfo si = a.slabs[slab];
   const int s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s;
   TileT* A = reinterpret_cast<TileT*>(smem_raw);  // tile_rows x Kt
   const size_t tm_off = (sizeof(TileT) * (size_t)tile_rows * Kt + 15) & ~(size_t)15;
@@ -325,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
     }
     __syncthreads();
   }
-  double* out = a.part + (int64_t)blockIdx.x * a.Kmax * s;
+  double* out = a.part + (int64_t)slab * a.Kmax * s;
   if (G == 1) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -345,6 +344,12 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
   }
 }
 
+template <typename TileT, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int tile_rows) {
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  gram_slab<TileT, Acc>(a, pass, tile_rows, blockIdx.x, smem_raw);
+}
 
 // Stage 1, first Gram pass, for block widths S in {1, 2, 4, 8, 16, 32}: the
 // partial of C_i = [Q_i W_i]^T W_i over one slab.  Each thread keeps a
@@ -352,10 +357,9 @@ __global__ void __launch_bounds__(kThreads) k_gram(StepArgs a, int pass, int til
 // cover the k + S columns and G = 256 / T row groups split the slab's rows;
 // the groups are summed in a fixed order at the end.
 template <int S, typename Acc>
-__global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
+__device__ void gram1_slab(const StepArgs& a, int slab, double* red) {
   constexpr int TQ = (32 / S) > 0 ? 32 / S : 1;
-  extern __shared__ __align__(16) double red[];
-  const SlabInfo si = a.slabs[blockIdx.x];
+  const SlabInfo si = a.slabs[slab];
   const int k = a.nb * S, Kt = k + S;
   const int T = (Kt + TQ - 1) / TQ;
   const int G = kThreads / T;
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
     // the block's column exponents on this slab: for a tensor-core assembly
     // that follows, and for the scaling of the float32 pass
     slab_col_exponents(hs, S, si.rows, [&](int r, int l) { return a.W[(si.row0 + r) * a.ldw + l]; });
-    if (a.srcexp_slab && tid < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + tid] = hs[tid];
+    if (a.srcexp_slab && tid < S) a.srcexp_slab[(int64_t)slab * 32 + tid] = hs[tid];
   }
   int sh[S];
 #pragma unroll
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
       for (int l = 0; l < S; ++l) red[(g * T + t) * (TQ * S) + i * S + l] = (double)acc[i][l];
   }
   __syncthreads();
-  double* out = a.part + (int64_t)blockIdx.x * a.Kmax * S;
+  double* out = a.part + (int64_t)slab * a.Kmax * S;
   for (int e = tid; e < Kt * S; e += kThreads) {
     const int q = e / S, l = e - q * S, tt = q / TQ, i = q - tt * TQ;
     double v = 0.0;
@@ -415,6 +419,13 @@ __global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
     if (kF32) v = scale2(v, -col_shift(hs[l]) - (q >= k ? col_shift(hs[q - k]) : 0));
     out[e] = v;
   }
+  __syncthreads();
+}
+
+template <int S, typename Acc>
+__global__ void __launch_bounds__(kThreads) k_gram1(StepArgs a) {
+  extern __shared__ __align__(16) double red[];
+  gram1_slab<S, Acc>(a, blockIdx.x, red);
 }
 
 // Stage-1 Gram of a step without prior blocks (k = 0) for narrow blocks
@@ -539,11 +550,9 @@ bool gram1_supported(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s =
 // the unit roundoff of this pass's Gram (float64: DBL_EPSILON; the mixed
 // form's digit Gram: 2^-31): the breakdown test and the shift of the retry
 // scale with it.
-__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel, int allow_shift,
-                                                   double u_gram) {
-  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
-  extern __shared__ __align__(16) double sm[];
-  const int c = blockIdx.x, s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s, ss = s * s;
+__device__ void leaf_chunk(const StepArgs& a, int pass, double shift_rel, int allow_shift, double u_gram, int c,
+                           double* sm) {
+  const int s = a.s, k = a.nb * s, Kt = k + s, E = Kt * s, ss = s * s;
   double* C = sm;             // Kt x s
   double* M = C + E;          // s x s
   double* Ni = M + ss;        // s x s
@@ -633,6 +642,13 @@ __global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double 
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_leaf(StepArgs a, int pass, double shift_rel, int allow_shift,
+                                                   double u_gram) {
+  if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  leaf_chunk(a, pass, shift_rel, allow_shift, u_gram, blockIdx.x, sm);
+}
+
 // ||W||_F^2 of the step from the pass-1 Gram partials (the diagonal of each
 // slab's W^T W block, slabs in order), for the deflation thresholds of the
 // local leaves.  One CTA.
@@ -659,10 +675,8 @@ __global__ void __launch_bounds__(kThreads) k_defl_trace(StepArgs a) {
 // Iteration `it` input: (P_comb, N_comb) for it = 1, else (P_hat, N_hat).
 
 // z_i = [T_i^T X_i ; X_i^T X_i + Nx_i^T Nx_i]  ((k + s) x s)
-__global__ void __launch_bounds__(kThreads) k_tree_contrib(StepArgs a, int it) {
-  if (!a.flags[kFlagTree + it - 1]) return;
-  extern __shared__ __align__(16) double sm[];
-  const int c = blockIdx.x, s = a.s, k = a.nb * s, ss = s * s;
+__device__ void tree_contrib_chunk(const StepArgs& a, int it, int c, double* sm) {
+  const int s = a.s, k = a.nb * s, ss = s * s;
   const SmallLayout SL = SmallLayout::make(a.Kmax, s);
   double* smallc = a.small + (int64_t)c * SL.stride;
   const double* Xg = smallc + (it == 1 ? SL.P_comb : SL.P_hat);
@@ -690,6 +704,12 @@ __global__ void __launch_bounds__(kThreads) k_tree_contrib(StepArgs a, int it) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_tree_contrib(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  tree_contrib_chunk(a, it, blockIdx.x, sm);
+}
+
 // First level of the fixed-order sum over chunks: group g sums chunks
 // [g * kTreeGroup, (g + 1) * kTreeGroup) in index order.
 __global__ void __launch_bounds__(kThreads) k_tree_sum1(StepArgs a, int it) {
@@ -708,10 +728,10 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum1(StepArgs a, int it) {
 // Second level + the small factorization of the reduction PQR:
 // P = sum T_i^T X_i, G = sum (X_i^T X_i + Nx_i^T Nx_i), N = chol(G - P^T P);
 // accumulates P_acc <- P_acc + P N_acc, N_acc <- N N_acc (Alg. 8 combine).
-__global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int ngroups) {
-  if (!a.flags[kFlagTree + it - 1]) return;
-  extern __shared__ __align__(16) double sm[];
-  const int s = a.s, k = a.nb * s, E = (k + s) * s, ss = s * s;
+// The small factorization of iteration `it` once Z (the summed contributions,
+// global Zsum) is complete.  Whole CTA.
+__device__ void tree_sum2_core(const StepArgs& a, int it, double* sm) {
+  const int s = a.s, k = a.nb * s, ss = s * s;
   const GlobLayout GL = GlobLayout::make(a.Kmax, s);
   double* Z = a.glob + GL.Zsum;
   double* M = sm;
@@ -719,12 +739,6 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
   double* Na = Ni + ss;
   double* tmp = Na + ss;
   double* red = tmp + ss;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    double v = 0.0;
-    for (int g = 0; g < ngroups; ++g) v += a.tsum[(int64_t)g * a.Kmax * s + e];
-    Z[e] = v;
-  }
-  __syncthreads();
   for (int e = threadIdx.x; e < ss; e += blockDim.x) {
     const int i = e / s, j = e - i * s;
     double m = Z[(k + i) * s + j];
@@ -788,12 +802,24 @@ __global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int 
   }
 }
 
-// Per chunk: X_hat = (X - T_i P) N^{-1}, Nx_hat = Nx N^{-1}; the result is
-// also written as column block nb of T_i: [Pt_i; Nt_i] (Alg. 9 output).
-__global__ void __launch_bounds__(kThreads) k_tree_update(StepArgs a, int it) {
+__global__ void __launch_bounds__(kThreads) k_tree_sum2(StepArgs a, int it, int ngroups) {
   if (!a.flags[kFlagTree + it - 1]) return;
   extern __shared__ __align__(16) double sm[];
-  const int c = blockIdx.x, s = a.s, k = a.nb * s, ss = s * s;
+  const int s = a.s, k = a.nb * s, E = (k + s) * s;
+  double* Z = a.glob + GlobLayout::make(a.Kmax, s).Zsum;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int g = 0; g < ngroups; ++g) v += a.tsum[(int64_t)g * a.Kmax * s + e];
+    Z[e] = v;
+  }
+  __syncthreads();
+  tree_sum2_core(a, it, sm);
+}
+
+// Per chunk: X_hat = (X - T_i P) N^{-1}, Nx_hat = Nx N^{-1}; the result is
+// also written as column block nb of T_i: [Pt_i; Nt_i] (Alg. 9 output).
+__device__ void tree_update_chunk(const StepArgs& a, int it, int c, double* sm) {
+  const int s = a.s, k = a.nb * s, ss = s * s;
   const SmallLayout SL = SmallLayout::make(a.Kmax, s);
   const GlobLayout GL = GlobLayout::make(a.Kmax, s);
   double* smallc = a.small + (int64_t)c * SL.stride;
@@ -838,14 +864,19 @@ __global__ void __launch_bounds__(kThreads) k_tree_update(StepArgs a, int it) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_tree_update(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  tree_update_chunk(a, it, blockIdx.x, sm);
+}
+
 // ---------------------------------------------------------------------------
 // Stage 2 (assembly, Sec. 4.1): per row of chunk i,
 //   u = (A_last - q P_last) N_last^{-1}   -> new local panel (U_i)
 //   out = q Pt_i + u Nt_i                 -> caller's U
 // where A_last is W (one pass) or the stored previous iterate.
-__global__ void __launch_bounds__(kThreads) k_update(StepArgs a, int tile_rows) {
-  extern __shared__ __align__(16) double sm[];
-  const SlabInfo si = a.slabs[blockIdx.x];
+__device__ void update_slab(const StepArgs& a, int tile_rows, int slab, double* sm) {
+  const SlabInfo si = a.slabs[slab];
   const int s = a.s, k = a.nb * s;
   const int L = passes_run(a);
   double* slot = a.V + (int64_t)a.nb * a.n * s;
@@ -894,6 +925,11 @@ __global__ void __launch_bounds__(kThreads) k_update(StepArgs a, int tile_rows) 
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_update(StepArgs a, int tile_rows) {
+  extern __shared__ __align__(16) double sm[];
+  update_slab(a, tile_rows, blockIdx.x, sm);
 }
 
 // Stage 2 of a step without prior blocks for narrow blocks (S <= 4): per row
@@ -1204,6 +1240,266 @@ __global__ void __launch_bounds__(256) k_hh_assemble(StepArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Many independent PQR steps in one persistent launch.
+//
+// The work of every instance is cut into items -- (instance, slab) for the two
+// Gram passes and the assembly, (instance, chunk) for the reduction's per-chunk
+// products -- and all items form one list in phase order: pass-1 Grams of all
+// instances, pass-2 iterates and Grams, first reduction updates, second
+// reduction updates, assemblies, digit planes.  Each CTA takes the next item
+// from a global counter.  Tickets hand the small factorizations to the CTA
+// that finishes last: the last Gram slab of a chunk runs the chunk's leaf
+// (Alg. 7 / Alg. 8), the last chunk of an instance the reduction's small
+// factorization (the tree's two summation levels in the same fixed order as
+// k_tree_sum1 / k_tree_sum2, so results are bit for bit those of the
+// sequential launches).  An item waits only for work handed out before it
+// (items are taken in list order and every dependency points backwards), so
+// the CTAs that hold it are running and the wait ends; each wait is bounded
+// all the same (about 1 s), after which the batch is aborted with
+// LO_ERR_TIMEOUT.  The instances run BCGS-PIP+ with exactly two local passes
+// and two reduction iterations; one whose estimate asks for more (or whose
+// Cholesky needed the shifted retry) is marked in its flags and redone by the
+// caller on the regular path.
+
+// Per-instance ticket area (ints), p = chunks.
+struct TickLayout {
+  static __host__ __device__ int cntA(int p) { return 0; }      // [p] pass-1 slabs done per chunk
+  static __host__ __device__ int cntB(int p) { return p; }      // [p] pass-2 slabs done per chunk
+  static __host__ __device__ int cntE(int p) { return 2 * p; }  // [p] assembly slabs done per chunk
+  static __host__ __device__ int stage(int p) { return 3 * p; } // [p] chunk stage (1 leaf 1, 2 leaf 2, 4 tree, 5 panel)
+  static __host__ __device__ int inst(int p) { return 4 * p; }  // [4]: chunks done (it 1), (it 2), instance stage
+  static __host__ __device__ int ints(int p) { return 4 * p + 4; }
+};
+
+constexpr int kBatchPhases = 6;
+constexpr long long kBatchWaitCycles = 2000000000ll;  // ~1 s
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Bounded wait of the whole CTA until *p >= v; false if the batch was aborted
+// (here or elsewhere).
+__device__ bool batch_wait(const int* p, int v, int* abort_word, int* flags) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int good = 1;
+    if (ld_acquire(p) < v) {
+      const long long t0 = clock64();
+      while (ld_acquire(p) < v) {
+        if (ld_acquire(abort_word) != 0) {
+          good = 0;
+          break;
+        }
+        if (clock64() - t0 > kBatchWaitCycles) {
+          atomicExch(abort_word, 1);
+          set_status(flags, LO_ERR_TIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  const bool r = ok != 0;
+  __syncthreads();
+  return r;
+}
+
+// Returns true in every thread of the CTA that took the last of `total`
+// tickets on *cnt (after its own work: the release of what it wrote, and the
+// acquire of what the others wrote).
+__device__ bool batch_ticket(int* cnt, int total) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    last = (atomicAdd(cnt, 1) == total - 1) ? 1 : 0;
+    if (last) __threadfence();
+  }
+  __syncthreads();
+  const bool r = last != 0;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void batch_release(int* p, int v) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(p, v);
+}
+
+// The reduction's summed contributions Z = sum_i z_i in the two fixed levels
+// of k_tree_sum1 / k_tree_sum2 (groups of kTreeGroup chunks, then the groups).
+__device__ void batch_tree_sum(const StepArgs& a) {
+  const int s = a.s, E = (a.nb * s + s) * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* Z = a.glob + GlobLayout::make(a.Kmax, s).Zsum;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double tot = 0.0;
+    for (int c0 = 0; c0 < a.p; c0 += kTreeGroup) {
+      double v = 0.0;
+      for (int c = c0; c < min(a.p, c0 + kTreeGroup); ++c) v += a.small[(int64_t)c * SL.stride + SL.Z + e];
+      tot += v;
+    }
+    Z[e] = tot;
+  }
+  __syncthreads();
+}
+
+// Stage 2 of one slab and, for a tensor-core basis, the new panel's column
+// exponents on it (maxima into colexp, zeroed by the chunk's last tree item).
+__device__ void batch_update_slab(const BatchInst& I, int slab, double* sm) {
+  const StepArgs& a = I.a;
+  update_slab(a, I.tile_u, slab, sm);
+  __syncthreads();
+  if (a.colexp) {
+    const SlabInfo si = a.slabs[slab];
+    const int s = a.s, k = a.nb * s;
+    const double* slot = a.V + (int64_t)a.nb * a.n * s;
+    for (int l = 0; l < s; ++l) {
+      int m = 0;
+      for (int r = threadIdx.x; r < si.rows; r += blockDim.x) m = max(m, bexp(slot[(si.row0 + r) * s + l]));
+      m = __reduce_max_sync(0xffffffffu, m);
+      if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&a.colexp[(int64_t)(k + l) * a.p + si.chunk], m);
+    }
+  }
+}
+
+__device__ void batch_gram1(const BatchInst& I, int slab, unsigned char* smem) {
+  const StepArgs& a = I.a;
+  double* red = reinterpret_cast<double*>(smem);
+  if (I.gram1) {
+    switch (a.s) {
+      case 1: gram1_slab<1, double>(a, slab, red); return;
+      case 2: gram1_slab<2, double>(a, slab, red); return;
+      case 4: gram1_slab<4, double>(a, slab, red); return;
+      case 8: gram1_slab<8, double>(a, slab, red); return;
+      case 16: gram1_slab<16, double>(a, slab, red); return;
+      case 32: gram1_slab<32, double>(a, slab, red); return;
+    }
+  }
+  gram_slab<double, double>(a, 1, I.tile_g, slab, smem);
+}
+
+__device__ void batch_digitize(const StepArgs& a, int slab) {
+  switch (a.s) {
+    case 8: digitize_slab<8>(a, slab); break;
+    case 16: digitize_slab<16>(a, slab); break;
+    case 32: digitize_slab<32>(a, slab); break;
+  }
+}
+
+// Flags of every instance as k_step_begin sets them (PIP+: pass 2 and tree
+// iteration 2 forced), zeroed tickets, the item counter and the abort word.
+__global__ void k_batch_init(BatchInst* insts, int ninst, int* counters) {
+  if (blockIdx.x == 0 && threadIdx.x < 2) counters[threadIdx.x] = 0;
+  for (int j = blockIdx.x; j < ninst; j += gridDim.x) {
+    const BatchInst& I = insts[j];
+    if (threadIdx.x == 0) {
+      for (int t = 1; t <= kMaxPass; ++t) I.a.flags[kFlagPass + t - 1] = (t <= 2) ? 1 : 0;
+      for (int t = 1; t <= kMaxTreeIter; ++t) I.a.flags[kFlagTree + t - 1] = (t <= 2) ? 1 : 0;
+    }
+    for (int e = threadIdx.x; e < TickLayout::ints(I.a.p); e += blockDim.x) I.tick[e] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_batch_step(const BatchInst* __restrict__ insts, int ninst,
+                                                         const int* __restrict__ pref, int* counters) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  double* sm = reinterpret_cast<double*>(bsm);
+  __shared__ int item, aborted;
+  int* next = counters;
+  int* abort_word = counters + 1;
+  const int total = pref[kBatchPhases * (ninst + 1) - 1];
+  // every pass takes a new, larger item index, so a CTA makes at most total + 1 passes
+  for (int pass_no = 0; pass_no <= total; ++pass_no) {
+    if (threadIdx.x == 0) {
+      item = atomicAdd(next, 1);
+      aborted = ld_acquire(abort_word);
+    }
+    __syncthreads();
+    const int g = item;
+    const bool skip = aborted != 0;
+    __syncthreads();
+    if (g >= total) break;
+    if (skip) continue;
+    // phase and instance: pref[ph * (ninst + 1) + j] is the first item of instance j in phase ph
+    int ph = 0;
+    while (g >= pref[ph * (ninst + 1) + ninst]) ++ph;  // ph < kBatchPhases: g < total = end of the last phase
+    int j = 0;
+    while (g >= pref[ph * (ninst + 1) + j + 1]) ++j;   // j < ninst: g < the phase's end
+    const int idx = g - pref[ph * (ninst + 1) + j];
+    const BatchInst& I = insts[j];
+    const StepArgs& a = I.a;
+    const int p = a.p;
+    int* tick = I.tick;
+    int* inst = tick + TickLayout::inst(p);
+    if (ph == 0) {  // pass-1 Gram of slab idx
+      batch_gram1(I, idx, bsm);
+      const int c = a.slabs[idx].chunk;
+      if (batch_ticket(tick + TickLayout::cntA(p) + c, a.chunk_slab0[c + 1] - a.chunk_slab0[c])) {
+        leaf_chunk(a, 1, 0.0, a.leaf != LO_LEAF_PIP ? 1 : 0, DBL_EPSILON, c, sm);
+        batch_release(tick + TickLayout::stage(p) + c, 1);
+      }
+    } else if (ph == 1) {  // pass-2 iterate and Gram of slab idx
+      const int c = a.slabs[idx].chunk;
+      if (!batch_wait(tick + TickLayout::stage(p) + c, 1, abort_word, a.flags)) continue;
+      gram_slab<double, double>(a, 2, I.tile_g, idx, bsm);
+      if (batch_ticket(tick + TickLayout::cntB(p) + c, a.chunk_slab0[c + 1] - a.chunk_slab0[c])) {
+        leaf_chunk(a, 2, 0.0, 0, DBL_EPSILON, c, sm);
+        __syncthreads();
+        tree_contrib_chunk(a, 1, c, sm);
+        batch_release(tick + TickLayout::stage(p) + c, 2);
+        if (batch_ticket(inst + 0, p)) {
+          batch_tree_sum(a);
+          tree_sum2_core(a, 1, sm);
+          batch_release(inst + 2, 1);
+        }
+      }
+    } else if (ph == 2) {  // first reduction update and second contribution of chunk idx
+      if (!batch_wait(inst + 2, 1, abort_word, a.flags)) continue;
+      tree_update_chunk(a, 1, idx, sm);
+      __syncthreads();
+      tree_contrib_chunk(a, 2, idx, sm);
+      if (batch_ticket(inst + 1, p)) {
+        batch_tree_sum(a);
+        tree_sum2_core(a, 2, sm);
+        __syncthreads();
+        const GlobLayout GL = GlobLayout::make(a.Kmax, a.s);
+        const int ks = a.nb * a.s * a.s, ss = a.s * a.s;
+        if (I.H)
+          for (int e = threadIdx.x; e < ks; e += blockDim.x) I.H[e] = a.glob[GL.P_acc + e];
+        if (I.R)
+          for (int e = threadIdx.x; e < ss; e += blockDim.x) I.R[e] = a.glob[GL.N_acc + e];
+        batch_release(inst + 2, 2);
+      }
+    } else if (ph == 3) {  // second reduction update of chunk idx: the new column block of T_i
+      if (!batch_wait(inst + 2, 2, abort_word, a.flags)) continue;
+      tree_update_chunk(a, 2, idx, sm);
+      if (a.colexp)
+        for (int l = threadIdx.x; l < a.s; l += blockDim.x) a.colexp[(int64_t)(a.nb * a.s + l) * p + idx] = 0;
+      batch_release(tick + TickLayout::stage(p) + idx, 4);
+    } else if (ph == 4) {  // assembly of slab idx
+      const int c = a.slabs[idx].chunk;
+      if (!batch_wait(tick + TickLayout::stage(p) + c, 4, abort_word, a.flags)) continue;
+      batch_update_slab(I, idx, sm);
+      if (I.digitize && batch_ticket(tick + TickLayout::cntE(p) + c, a.chunk_slab0[c + 1] - a.chunk_slab0[c]))
+        batch_release(tick + TickLayout::stage(p) + c, 5);
+    } else {  // digit planes of the new panel on slab idx (the chunk's exponents are final)
+      const int c = a.slabs[idx].chunk;
+      if (!batch_wait(tick + TickLayout::stage(p) + c, 5, abort_word, a.flags)) continue;
+      batch_digitize(a, idx);
+    }
+  }
+}
+
 // Shared-memory budget of the streaming kernels (bytes).
 constexpr int kTileSmem = 96 * 1024;
 
@@ -1240,6 +1536,7 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_tree_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_apply_y, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
@@ -1451,6 +1748,53 @@ cudaError_t launch_apply_q(const StepArgs& a, const double* C, int m, int64_t ld
   tr = tr < 1 ? 1 : (tr > 32 ? 32 : tr);
   k_apply_y<<<a.nslab, kThreads, (size_t)8 * tr * k, st>>>(a, m, Z, Y, ldy, tr);
   mark(hook, kKindApply, false, st);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+int batch_tick_ints(int p) { return TickLayout::ints(p); }
+
+bool batch_fill(BatchInst* bi) {
+  StepArgs& a = bi->a;
+  const int s = a.s, k = a.nb * s, Kt = k + s;
+  const bool tc = (a.precision == LO_PREC_FP64_TC);
+  if (!(a.precision == LO_PREC_FP64 || tc)) return false;
+  if (!(a.leaf == LO_LEAF_PIP2 || (a.leaf == LO_LEAF_HH && a.nb > 0))) return false;
+  if (a.reduction == 1 || a.deflation_tol > 0.0 || a.test_stall) return false;
+  bi->tile_g = gram_tile_rows(Kt, s, 8);
+  bi->tile_u = update_tile_rows(k, s);
+  bi->gram1 = gram1_supported(s) ? 1 : 0;
+  bi->digitize = (tc && a.dig && a.nb + 1 < a.M && (s == 8 || s == 16 || s == 32)) ? 1 : 0;
+  // float64 arithmetic throughout: no per-pass exponents of the digit forms
+  a.srcexp = nullptr;
+  a.srcexp_slab = nullptr;
+  if (!tc) a.colexp = nullptr;
+  return true;
+}
+
+size_t batch_smem(const BatchInst* insts, int ninst) {
+  size_t m = sizeof(double) * kThreads * 32;  // the register-tiled Gram's reduction buffer
+  for (int j = 0; j < ninst; ++j) {
+    const StepArgs& a = insts[j].a;
+    const size_t s = a.s, k = (size_t)a.nb * a.s, Kt = k + s, ss = s * s, tg = insts[j].tile_g;
+    const size_t need[] = {8 * tg * Kt + 8 * tg * s + 8 * kThreads, 8 * (Kt * s + 4 * ss + 4), 8 * (k * s + 2 * ss),
+                           8 * (4 * ss + 4), 8 * (size_t)insts[j].tile_u * (k + 2 * s)};
+    for (size_t v : need) m = v > m ? v : m;
+  }
+  return m;
+}
+
+cudaError_t launch_batch(BatchInst* d_insts, int ninst, const int* d_pref, int* d_counters, size_t smem,
+                         cudaStream_t st) {
+  cudaError_t e = set_attrs();
+  if (e) return e;
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_step, kThreads, smem) != cudaSuccess || per < 1)
+    per = 1;
+  k_batch_init<<<ninst < 152 ? ninst : 152, 256, 0, st>>>(d_insts, ninst, d_counters);
+  k_batch_step<<<sms * per, kThreads, smem, st>>>(d_insts, ninst, d_pref, d_counters);
   count_launches(2);
   return cudaGetLastError();
 }

@@ -205,5 +205,59 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
 
+// Split 8 float64 values x[0..7] (8 consecutive rows of one column) against
+// exponent e and store their fp16 digits as one 16-byte core-matrix row of
+// each of the first ND planes at dst + t * plane.
+template <int ND = kOzDigits>
+__device__ __forceinline__ void split8_store(const double* x, int e, unsigned char* dst, int plane, int* flags) {
+  unsigned w[ND][4];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned h0, l0, s0, h1, l1, s1;
+    bad |= oz_split(x[2 * i], e, h0, l0, s0);
+    bad |= oz_split(x[2 * i + 1], e, h1, l1, s1);
+    const unsigned sb = (s0 >> 16) | s1;
+#pragma unroll
+    for (int t = 1; t <= ND; ++t) w[t - 1][i] = oz_pack(t, h0, l0, h1, l1, sb);
+  }
+  if (bad) oz_status(flags, LO_ERR_NONFINITE);
+#pragma unroll
+  for (int t = 0; t < ND; ++t)
+    *reinterpret_cast<uint4*>(dst + t * plane) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+}
+
+// Digit planes of the new panel (slot nb) of one slab, once stage 2 has fixed
+// the panel's column exponents.  One thread per (16-row tile, column): 16
+// values, 7 planes of two 16-byte core-matrix rows each.  Whole CTA (256
+// threads); returns after a barrier.
+template <int S>
+__device__ void digitize_slab(const StepArgs& a, int slab) {
+  __shared__ int ex[S];
+  const SlabInfo si = a.slabs[slab];
+  const int k = a.nb * S;
+  if (threadIdx.x < S) ex[threadIdx.x] = a.colexp[(int64_t)(k + threadIdx.x) * a.p + si.chunk];
+  __syncthreads();
+  const double* slot = a.V + (int64_t)a.nb * a.n * S;
+  const int ntile = (si.rows + 15) / 16;
+  const int64_t gtot = (int64_t)a.M * (S / 8);
+  for (int i = threadIdx.x; i < ntile * S; i += 256) {
+    const int tt = i / S, j = i - tt * S;
+    const int64_t G = (int64_t)a.nb * (S / 8) + j / 8;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t eta = 2 * (int64_t)(si.tile0 + tt) + h;
+      double x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = tt * 16 + h * 8 + r;
+        x[r] = row < si.rows ? slot[(si.row0 + row) * S + j] : 0.0;
+      }
+      split8_store(x, ex[j], a.dig + (eta * gtot + G) * (kOzDigits * 128) + (j & 7) * 16, 128, a.flags);
+    }
+  }
+  __syncthreads();
+}
+
 }  // namespace
 }  // namespace lo

@@ -43,6 +43,7 @@ EXPORTED = [
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
     "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_tsqr_noalloc_scratch", "lo_basis_truncate",
     "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries", "lo_basis_last_rank",
+    "lo_set_batched_route", "lo_batched_persistent_count",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
@@ -108,6 +109,10 @@ def _lib():
     L.lo_basis_profile_read.restype = c_int32
     L.lo_basis_last_step_info.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32)]
     L.lo_basis_last_step_info.restype = c_int32
+    L.lo_set_batched_route.argtypes = [c_int32]
+    L.lo_set_batched_route.restype = c_int32
+    L.lo_batched_persistent_count.argtypes = []
+    L.lo_batched_persistent_count.restype = c_int32
     L.lo_basis_last_rank.argtypes = [c_void_p, POINTER(c_int32)]
     L.lo_basis_last_rank.restype = c_int32
     L.lo_tsqr_noalloc.argtypes = [c_int64, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
@@ -329,6 +334,20 @@ def tsqr_noalloc_scratch(n: int, s: int, chunk_rows: int):
     need, cap = ctypes.c_uint64(), ctypes.c_uint64()
     code = _lib().lo_tsqr_noalloc_scratch(int(n), int(s), int(chunk_rows), ctypes.byref(need), ctypes.byref(cap))
     return STATUS.get(code, str(code)), int(need.value), int(cap.value)
+
+
+BATCH_ROUTE = {"auto": 0, "persistent": 1, "graph": 2}
+
+
+def set_batched_route(mode: str = "auto"):
+    """Route of lo_orthogonalize_batched's instances: 'auto', 'persistent'
+    (the persistent launch wherever it can run) or 'graph'."""
+    _check(_lib().lo_set_batched_route(BATCH_ROUTE[mode]), "lo_set_batched_route")
+
+
+def batched_persistent_count() -> int:
+    """Instances the last batched graph runs in the persistent launch."""
+    return int(_lib().lo_batched_persistent_count())
 
 
 def batched_cache_entries(basis_id: int = 0) -> int:

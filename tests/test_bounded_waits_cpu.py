@@ -13,6 +13,11 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 REVIEWED_WHILE = {
     ("lo_umma.cu", "while (!mbar_try(mb, parity))"),   # bounded by clock64() - t0 > kWaitCycles
     ("lo_api.cu", "while (c0 < Kmax) c0 *= 2;"),        # host: chunk-size candidates
+    # the persistent batched launch: its flag wait, bounded by kBatchWaitCycles and the abort word
+    ("lo_kernels.cu", "while (ld_acquire(p) < v) {"),
+    # item decoding: at most kBatchPhases phases and ninst instances (g < the list's end)
+    ("lo_kernels.cu", "while (g >= pref[ph * (ninst + 1) + ninst]) ++ph;"),
+    ("lo_kernels.cu", "while (g >= pref[ph * (ninst + 1) + j + 1]) ++j;"),
 }
 
 
@@ -58,3 +63,17 @@ def test_mbarrier_wait_is_bounded_and_the_only_try_wait():
         want = (["if (mbar_try(mb, parity)) return true;", "while (!mbar_try(mb, parity))"]
                 if fn == "lo_umma.cu" else [])
         assert calls == want, (fn, calls)  # mbar_try only inside the bounded mbar_wait
+
+
+def test_batch_flag_wait_is_bounded():
+    """The persistent batched launch's only spin: it gives up after
+    kBatchWaitCycles clocks (latching LO_ERR_TIMEOUT and the batch's abort
+    word) or as soon as another CTA has aborted; its item loop is bounded by
+    the number of items."""
+    text = dict(sources())["lo_kernels.cu"]
+    body = re.search(r"bool batch_wait\(const int\* p, int v, int\* abort_word, int\* flags\) \{(.*?)\n\}", text,
+                     re.S).group(1)
+    assert "clock64() - t0 > kBatchWaitCycles" in body and "break" in body
+    assert "ld_acquire(abort_word) != 0" in body and "LO_ERR_TIMEOUT" in body
+    assert re.search(r"constexpr long long kBatchWaitCycles = \d+ll;", text)
+    assert "for (int pass_no = 0; pass_no <= total; ++pass_no)" in text

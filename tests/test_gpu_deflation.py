@@ -137,8 +137,8 @@ def test_block_entirely_in_the_span_deflates_to_rank_zero(precision):
 def test_first_block_deficient(leaf):
     """k = 0 with dependent columns (the Householder leaf keeps every local
     column; the reduction drops the dependent ones)."""
-    n, s = 20000, 8
-    cr = 2048
+    s, cr = 8, 2048
+    n = 9 * cr + 1000          # the Householder tile of the last chunk fits
     X = deficient(np.zeros((n, 0)), n, s, I.seed_for(11, 40))
     b = lo().Basis(n, s, 2, cr, leaf=leaf, deflation_tol=DELTA)
     U, _, R = b.orthogonalize(dev(X))

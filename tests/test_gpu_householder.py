@@ -107,8 +107,9 @@ def test_householder_leaf_then_pip2(precision):
     Householder, the next ones by BCGS-PIP+ (with digit planes of the
     Householder panel in the tensor-core form); every output, the explicit
     basis and the representation against the oracle."""
-    n, s, M = 20000, 8, 5
+    s, M = 8, 5
     cr = hh_chunk_rows(s)
+    n = 9 * cr + 1000          # the last chunk (with the remainder) still fits the tile
     L = lo()
     b = L.Basis(n, s, M, cr, precision=precision, leaf="hh")
     ora = O.LocallyOrthogonalBasis(n, s, cr)
@@ -132,8 +133,9 @@ def test_householder_leaf_vanishing_chunks():
     """Columns that are exactly zero on whole chunks: the Householder leaf
     keeps the unit direction there (no reflection, R_jj = 0), as the oracle's
     Householder solver does; U and R are the unique solution."""
-    n, s = 24000, 8
+    s = 8
     cr = hh_chunk_rows(s)
+    n = 11 * cr + 700
     bounds = O.chunk_bounds(n, cr)
     sup = [[bounds[(2 * c) % len(bounds)], bounds[(2 * c + 5) % len(bounds)]] for c in range(s)]
     W = I.localized(n, s, I.seed_for(8, 600), sup)
@@ -153,8 +155,9 @@ def test_householder_leaf_nonfinite_and_tuner():
     tuner only proposes chunks whose tiles fit, and the tuned basis is
     orthonormal."""
     L = lo()
-    n, s = 50000, 8
+    s = 8
     cr = hh_chunk_rows(s)
+    n = 24 * cr + 333
     b = L.Basis(n, s, 2, cr, leaf="hh")
     W = I.gaussian(n, s, I.seed_for(8, 700))
     W[1234, 3] = np.nan
