@@ -238,6 +238,26 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw,
                            double* U, int64_t ldu, double* H, double* R);
 
 /*
+ * One PQR step of block Arnoldi (Alg. 1) with the operator fused into the
+ * step: orthogonalize W = L V, where L is the 2D 5-point Dirichlet Laplacian
+ * on an nx x ny grid (the operator of lo_laplace5_apply, n = nx ny) and V the
+ * previous basis block, against the current basis.  The first Gram pass reads
+ * V and forms each value of W from the stencil as it needs it (no separate
+ * operator pass: the Gram does not read a materialized W), writing W once
+ * into U, where the later passes and the assembly read it; U then receives
+ * the new orthonormal block as in lo_orthogonalize.  The result is bit for
+ * bit that of lo_laplace5_apply followed by lo_orthogonalize.  Forms whose
+ * first pass cannot form the block on the fly (the mixed forms, the
+ * tensor-core form without digit planes, a step without prior blocks, the
+ * Householder leaf) apply the operator into U first.
+ *   V  device, n x s, row stride ldv >= s (read only);
+ *   U  device, n x s, row stride ldu >= s; must not overlap V;
+ *   H, R as in lo_orthogonalize (host or device, may be NULL).
+ */
+lo_status lo_orthogonalize_laplace5(lo_basis* b, int32_t nx, int32_t ny, const double* V, int64_t ldv, double* U,
+                                    int64_t ldu, double* H, double* R);
+
+/*
  * Y = Q C for the current basis (Sec. 5.1: the product QC of the second
  * stage), computed chunk-wise as Y_i = Q_i (T_i C).  C is k x m row-major
  * (k = num_blocks*s, row stride ldc >= m), host or device; Y is n x m

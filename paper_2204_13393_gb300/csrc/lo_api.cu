@@ -608,6 +608,40 @@ lo_status lo_orthogonalize(lo_basis* b, const double* W, int64_t ldw, double* U,
   return LO_OK;
 }
 
+lo_status lo_orthogonalize_laplace5(lo_basis* b, int32_t nx, int32_t ny, const double* V, int64_t ldv, double* U,
+                                    int64_t ldu, double* H, double* R) {
+  if (!b || !V || !U || nx < 1 || ny < 1 || ldv < b->s || ldu < b->s) return LO_ERR_INVALID_ARG;
+  if ((int64_t)nx * ny != b->n) return LO_ERR_INVALID_ARG;
+  if (b->nb >= b->M) return LO_ERR_CAPACITY;
+  cudaSetDevice(b->device);
+  if (!is_device_ptr(V) || !is_device_ptr(U)) return LO_ERR_INVALID_ARG;
+  {  // U is written while the stencil still reads neighbouring rows of V
+    const double* vend = V + (b->n - 1) * ldv + b->s;
+    const double* uend = U + (b->n - 1) * ldu + b->s;
+    if (!(uend <= V || vend <= U)) return LO_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = b->stream;
+  StepArgs a = make_args(b);
+  a.W = U;  // the block is formed into U; the step then reads it there
+  a.ldw = ldu;
+  a.U = U;
+  a.ldu = ldu;
+  a.op_nx = nx;
+  a.op_ny = ny;
+  a.op_V = V;
+  a.op_ldv = ldv;
+  lo_status rs = from_cuda(lo::launch_step(a, st, &b->prof));
+  if (rs != LO_OK) return rs;
+  if ((rs = copy_small_outputs(b, H, R, st)) != LO_OK) return rs;
+  const bool host_small = (H && !is_device_ptr(H)) || (R && !is_device_ptr(R));
+  if (b->opt.sync || host_small) {
+    lo_status d = read_status(b, st);
+    if (d != LO_OK) return d;
+  }
+  b->nb += 1;
+  return LO_OK;
+}
+
 lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count, const double* const* W,
                                    const int64_t* ldw, double* const* U, const int64_t* ldu,
                                    double* const* H, double* const* R) {

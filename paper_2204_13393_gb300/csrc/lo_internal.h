@@ -110,6 +110,13 @@ struct StepArgs {
   int64_t ldw;
   double* U;
   int64_t ldu;
+  // the block as an operator applied to a device block: W = L V for the 2D
+  // 5-point Laplacian on an op_nx x op_ny grid (op_nx = 0: none).  The first
+  // Gram pass forms W from V on the fly and writes it into U (W = U then for
+  // the rest of the step).
+  int op_nx, op_ny;
+  const double* op_V;
+  int64_t op_ldv;
   // float64-accurate tensor-core form (LO_PREC_FP64_TC); null otherwise
   int* colexp;               // [Kmax][p]: largest biased exponent of each local column per chunk
   int* srcexp_slab;          // [nslab][32]: the same for the block of the current pass, per slab
@@ -147,6 +154,24 @@ struct BatchInst {
   int gram1;        // pass 1 by the register-tiled Gram (s in {1, 2, 4, 8, 16, 32})
   int digitize;     // write the digit planes of the new panel
 };
+
+// Entry (row, l) of L V for the 2D 5-point Dirichlet Laplacian of the step's
+// operator (grid points row-major, n = op_nx op_ny): the same expression, in
+// the same order, as k_laplace5, so a fused pass sees bit for bit the block
+// the operator kernel would have written.
+__device__ __forceinline__ double op_value(const StepArgs& a, int64_t row, int l) {
+  const int nx = a.op_nx;
+  const int64_t iy = row / nx;
+  const int ix = (int)(row - iy * nx);
+  const double* V = a.op_V;
+  const int64_t ld = a.op_ldv;
+  double v = 4.0 * V[row * ld + l];
+  if (ix > 0) v -= V[(row - 1) * ld + l];
+  if (ix < nx - 1) v -= V[(row + 1) * ld + l];
+  if (iy > 0) v -= V[(row - nx) * ld + l];
+  if (iy < a.op_ny - 1) v -= V[(row + nx) * ld + l];
+  return v;
+}
 
 // TMA descriptors of a basis's digit planes: one box shape per kernel.
 struct UmmaMaps {
@@ -214,6 +239,8 @@ cudaError_t launch_oz_coef_umma(const StepArgs& a, int nout, int pass, int mode,
 // tcgen05 forms over digit planes (lo_umma.cu): used when a.dig is set and the
 // step has prior blocks (nb >= 1).
 bool umma_enabled(const StepArgs& a);
+// Whether the tensor-core Gram of pass 1 can form the operator's block on the fly.
+bool umma_op_supported(const StepArgs& a);
 cudaError_t launch_umma_gram(const StepArgs& a, int pass, cudaStream_t st);
 // The mixed form's first Gram pass: the leading digits of both factors.
 cudaError_t launch_umma_gram_mixed(const StepArgs& a, cudaStream_t st);

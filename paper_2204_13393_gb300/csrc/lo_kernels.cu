@@ -284,7 +284,13 @@ __device__ void gram_slab(const StepArgs& a, int pass, int tile_rows, int slab, 
     if (pass == 1) {
       for (int idx = tid; idx < rows * s; idx += kThreads) {
         const int r = idx / s, l = idx - r * s;
-        const double w = a.W[(grow0 + r) * a.ldw + l];
+        double w;
+        if (a.op_nx) {  // the operator's block, formed here and kept in U for the later passes
+          w = op_value(a, grow0 + r, l);
+          a.U[(grow0 + r) * a.ldu + l] = w;
+        } else {
+          w = a.W[(grow0 + r) * a.ldw + l];
+        }
         A[r * Kt + k + l] = kF32 ? (TileT)f32_trunc_shift(w, col_shift(hs[l])) : (TileT)w;
       }
     } else {
@@ -387,8 +393,16 @@ __device__ void gram1_slab(const StepArgs& a, int slab, double* red) {
       const int64_t row = si.row0 + r;
       const double* wr = a.W + row * a.ldw;
       Acc b[S];
+      if (a.op_nx) {  // the operator's block (float64 form), kept in U by one thread per row
 #pragma unroll
-      for (int l = 0; l < S; ++l) b[l] = load_scaled<Acc>(wr + l, sh[l]);
+        for (int l = 0; l < S; ++l) b[l] = (Acc)op_value(a, row, l);
+        if (t == 0)
+#pragma unroll
+          for (int l = 0; l < S; ++l) a.U[row * a.ldu + l] = (double)b[l];
+      } else {
+#pragma unroll
+        for (int l = 0; l < S; ++l) b[l] = load_scaled<Acc>(wr + l, sh[l]);
+      }
       Acc av[TQ];
 #pragma unroll
       for (int i = 0; i < TQ; ++i) {
@@ -396,7 +410,7 @@ __device__ void gram1_slab(const StepArgs& a, int slab, double* red) {
         if (q < k)
           av[i] = load_as<Acc>(a.V + (int64_t)(q / S) * a.n * S + row * S + (q % S));
         else if (q < Kt)
-          av[i] = load_scaled<Acc>(wr + (q - k), kF32 ? col_shift(hs[q - k]) : 0);
+          av[i] = a.op_nx ? (Acc)op_value(a, row, q - k) : load_scaled<Acc>(wr + (q - k), kF32 ? col_shift(hs[q - k]) : 0);
         else
           av[i] = Acc(0);
       }
@@ -1641,9 +1655,25 @@ cudaError_t launch_step_hh(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
+cudaError_t launch_step(const StepArgs& a_in, cudaStream_t st, ProfHook* hook) {
   cudaError_t e = set_attrs();
   if (e) return e;
+  StepArgs a = a_in;
+  if (a.op_nx) {
+    // The operator is formed inside the first Gram pass where that pass can
+    // (the float64 Grams; on the tensor cores the digit-plane Gram of the
+    // float64 form); otherwise the operator kernel writes the block into U
+    // first.  Either way the rest of the step reads the block from U.
+    const bool mixed_form = (a.precision == LO_PREC_MIXED_FP32 || a.precision == LO_PREC_MIXED_TC);
+    const bool tc_form = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
+    const bool fused = a.nb > 0 && !mixed_form && a.leaf != LO_LEAF_HH && (!tc_form || umma_op_supported(a));
+    if (!fused) {
+      if ((e = launch_laplace5(a.op_nx, a.op_ny, a.s, a.op_V, a.op_ldv, a.U, a.ldu, st))) return e;
+      a.op_nx = 0;
+      a.W = a.U;
+      a.ldw = a.ldu;
+    }
+  }
   if (a.leaf == LO_LEAF_HH && a.nb == 0) return launch_step_hh(a, st, hook);
   const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
   const bool mixed = (a.precision == LO_PREC_MIXED_FP32 || a.precision == LO_PREC_MIXED_TC);
@@ -1687,6 +1717,11 @@ cudaError_t launch_step(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
       count_launches(1);
     }
     mark(hook, pass == 1 ? kKindGram : kKindRefine, false, st);
+    if (pass == 1 && a.op_nx) {  // the operator's block is in U from here on
+      a.op_nx = 0;
+      a.W = a.U;
+      a.ldw = a.ldu;
+    }
     // the reduced-precision first pass of the mixed form: above a float32
     // Gram a fixed shift of 1e-5 of the trace; above the 32-bit digit Gram on
     // the tensor cores the plain Cholesky, with the shifted retry (and two

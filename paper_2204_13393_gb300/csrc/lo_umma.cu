@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* s
   __syncthreads();
   for (int idx = threadIdx.x; idx < si.rows * S; idx += 256) {
     const int r = idx / S, l = idx - r * S;
-    atomicMax(&hs[l], bexp(src[(si.row0 + r) * lds + l]));
+    const double v = a.op_nx ? op_value(a, si.row0 + r, l) : src[(si.row0 + r) * lds + l];
+    atomicMax(&hs[l], bexp(v));
   }
   __syncthreads();
   if (threadIdx.x < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + threadIdx.x] = hs[threadIdx.x];
@@ -487,7 +488,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           for (int r = 0; r < 8; ++r) {
             const int row = r0 + 8 * ah + r;
             const bool ok = row < c.rows;
-            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + al, ok);
+            if (a.op_nx)  // the operator's block, formed from its input
+              d[r] = ok ? op_value(a, c.row0 + row, al) : 0.0;
+            else
+              cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + al, ok);
           }
         }
         if (b_role) {
@@ -496,7 +500,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           for (int r = 0; r < 4; ++r) {
             const int row = r0 + 4 * bq + r;
             const bool ok = row < c.rows;
-            cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + bn, ok);
+            if (a.op_nx) {  // formed here; the first column group keeps it in U for the later passes
+              const double v = ok ? op_value(a, c.row0 + row, c.z * NB + bn) : 0.0;
+              d[r] = v;
+              if (ok && c.col0 == 0) a.U[(c.row0 + row) * a.ldu + c.z * NB + bn] = v;
+            } else {
+              cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + bn, ok);
+            }
           }
         }
       }
@@ -1611,6 +1621,8 @@ cudaError_t umma_apply_for(const StepArgs& a0, const double* C, int64_t ldc, int
 }
 
 }  // namespace
+
+bool umma_op_supported(const StepArgs& a) { return a.precision == LO_PREC_FP64_TC && umma_enabled(a); }
 
 bool umma_enabled(const StepArgs& a) {
   return a.dig != nullptr && a.nb >= 1 && (a.s == 8 || a.s == 16 || a.s == 32);

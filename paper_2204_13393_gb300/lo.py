@@ -43,7 +43,7 @@ EXPORTED = [
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
     "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_tsqr_noalloc_scratch", "lo_basis_truncate",
     "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries", "lo_basis_last_rank",
-    "lo_set_batched_route", "lo_batched_persistent_count",
+    "lo_set_batched_route", "lo_batched_persistent_count", "lo_orthogonalize_laplace5",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
@@ -109,6 +109,9 @@ def _lib():
     L.lo_basis_profile_read.restype = c_int32
     L.lo_basis_last_step_info.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32)]
     L.lo_basis_last_step_info.restype = c_int32
+    L.lo_orthogonalize_laplace5.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_int64,
+                                            c_void_p, c_void_p]
+    L.lo_orthogonalize_laplace5.restype = c_int32
     L.lo_set_batched_route.argtypes = [c_int32]
     L.lo_set_batched_route.restype = c_int32
     L.lo_batched_persistent_count.argtypes = []
@@ -264,6 +267,21 @@ class Basis:
             R = _empty_like_kind(W, (self.s, self.s))
         _check(_lib().lo_orthogonalize(self._h, _ptr(W), _ld(W, self.s), _ptr(U), _ld(U, self.s),
                                        _ptr(H) if k > 0 else None, _ptr(R)), "lo_orthogonalize")
+        return U, H, R
+
+    def orthogonalize_laplace5(self, nx: int, ny: int, V, U=None, H=None, R=None):
+        """One block-Arnoldi step with the 5-point Laplacian fused in: the PQR
+        step of W = L V (device tensors; U must not overlap V)."""
+        k = self.k
+        if U is None:
+            U = _empty_like_kind(V, (self.n, self.s))
+        if H is None and k > 0:
+            H = _empty_like_kind(V, (k, self.s))
+        if R is None:
+            R = _empty_like_kind(V, (self.s, self.s))
+        _check(_lib().lo_orthogonalize_laplace5(self._h, int(nx), int(ny), _ptr(V), _ld(V, self.s), _ptr(U),
+                                                _ld(U, self.s), _ptr(H) if k > 0 else None, _ptr(R)),
+               "lo_orthogonalize_laplace5")
         return U, H, R
 
     def apply_Q(self, C, Y=None):
