@@ -661,14 +661,18 @@ def run_batched_case(args):
 
     dev = torch.device("cuda", 0)
     lo.library()
-    specs = I.batch_instances(64, I.seed_for(5))
+    if args.batch_recipe == "small":
+        # 64 copies of the small block-Arnoldi step's shape (n = 4096, s = 4, 8 prior blocks, 512-row chunks)
+        specs = [(4096, 4, 8)] * 64
+    else:
+        specs = I.batch_instances(64, I.seed_for(5))
     bases, Ws, Us, Hs, Rs, kbs, nbytes, tuned = [], [], [], [], [], [], 0, {}
     t_tune = time.perf_counter()
     for i, (n, s, kb) in enumerate(specs):
         M = kb + 1
         key = (n, s, M)
         if key not in tuned:
-            tuned[key] = lo.tune_chunk_rows(n, s, M, precision=args.precision)
+            tuned[key] = 512 if args.batch_recipe == "small" else lo.tune_chunk_rows(n, s, M, precision=args.precision)
         cr = tuned[key]
         b = lo.Basis(n, s, M, cr, precision=args.precision, sync=False)
         g = torch.Generator(device=dev)
@@ -723,7 +727,8 @@ def run_batched_case(args):
         if name != "sequential":
             routes[name] = lo.batched_persistent_count()
     lo.set_batched_route("auto")
-    print(json.dumps({"case": "batched", "precision": args.precision, "instances": len(specs),
+    print(json.dumps({"case": "batched", "recipe": args.batch_recipe, "precision": args.precision,
+                      "instances": len(specs),
                       "persistent_instances": routes,
                       "ms_graph_only": round(res["graph"], 3), "ms_persistent_where_possible": round(res["persistent"], 3),
                       "bytes_per_step": nbytes, "ms_batched": round(res["batched"], 3),
@@ -1080,6 +1085,8 @@ def main():
                          "mixed: float64 vs mixed tensor-core forms at n = 2^24, s = 16, k = 480; "
                          "tsqr: k = 0 steps at n = 2^24; step: the small step (n = 4096, s = 4, k = 32), "
                          "graph-replayed")
+    ap.add_argument("--batch-recipe", default="uneven", choices=["uneven", "small"],
+                    help="--case batched: the uneven 64-instance batch, or 64 copies of the small step")
     ap.add_argument("--mixed-n", type=int, default=2 ** 24)
     ap.add_argument("--mixed-cr", type=int, default=0, help="chunk rows for --case mixed (0: lo_tune_chunk_rows)")
     ap.add_argument("--mixed-kappas", default="1e2,1e4,1e6", help="condition numbers for --case mixed")

@@ -299,9 +299,11 @@ lo_status lo_orthogonalize_batched(lo_basis* const* bases, int32_t count,
 /*
  * Route of lo_orthogonalize_batched's instances (process-wide; part of the
  * cached graphs' key):
- *   0 (default) auto: an instance of at most 4e6 n (k + s) whose form the
- *     persistent launch can run goes into it, every other one gets its own
- *     branch of the graph;
+ *   0 (default) auto: an instance of the native float64 form
+ *     (LO_PREC_FP64) of at most 4e6 n (k + s) that the persistent launch can
+ *     run goes into it, every other one gets its own branch of the graph (on
+ *     GB300 the tensor-core forms' own kernels beat the float64 pipe the
+ *     persistent launch computes on);
  *   1: the persistent launch for every instance it can run;
  *   2: graph branches only (each instance's own kernel sequence).
  * The persistent launch is one kernel (after a small init kernel) over a work
