@@ -182,6 +182,7 @@ StepArgs make_args(const lo_basis* b) {
   a.glob = b->glob;
   a.tsum = b->tsum;
   a.flags = b->flags;
+  a.tree_ticket = b->tick + 4 * b->p + 3;  // the ticket area's last int (TickLayout)
   a.slabs = b->d_slabs;
   a.chunk_slab0 = b->d_chunk_slab0;
   a.chunk_row0 = b->d_chunk_row0;
@@ -512,6 +513,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
     e = cudaMemcpy(b->d_chunk_row0, b->chunk_row0.data(), sizeof(int64_t) * b->chunk_row0.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->T, 0, sizeof(double) * (size_t)p * b->tstride);
   if (e == cudaSuccess) e = cudaMemset(b->flags, 0, sizeof(int) * lo::kFlagCount);
+  if (e == cudaSuccess) e = cudaMemset(b->tick, 0, sizeof(int) * lo::batch_tick_ints(p));
   if (e == cudaSuccess) e = cudaMemset(b->glob, 0, sizeof(double) * (size_t)GL.stride);
   if (e != cudaSuccess) {
     lo_status st = from_cuda(e);

@@ -94,6 +94,7 @@ struct StepArgs {
   double* glob;             // global scratch, GlobLayout
   double* tsum;             // tree first-level sums: ngroups x Kmax x s
   int* flags;
+  int* tree_ticket;         // one int, zero between steps: chunks done in a ticketed reduction round
   const SlabInfo* slabs;
   const int32_t* chunk_slab0;   // first slab of chunk c (p + 1 entries)
   const int64_t* chunk_row0;    // first row of chunk c (p + 1 entries)

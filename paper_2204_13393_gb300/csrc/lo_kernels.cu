@@ -1514,6 +1514,50 @@ __global__ void __launch_bounds__(kThreads) k_batch_step(const BatchInst* __rest
   }
 }
 
+// The reduction (Sec. 4.1, BCGS-PIP reiterated as in Alg. 8) in two launches
+// per iteration.  k_tree_round: every chunk's CTA first applies the update of
+// the previous iteration (with_update: X_hat, Nx_hat and the column block of
+// T_i), then forms its contribution z_i of iteration `it`.  k_tree_sum:
+// the first summation level of k_tree_sum1 (groups of kTreeGroup chunks, the
+// entries split over blockIdx.y), and the CTA that finishes last (ticket on
+// a.tree_ticket, reset after use) sums the groups and runs the small
+// factorization of k_tree_sum2.  Nothing waits; the same arithmetic in the
+// same order as the four kernels per iteration, bit for bit.
+__global__ void __launch_bounds__(kThreads) k_tree_round(StepArgs a, int it, int with_update) {
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x;
+  if (with_update && a.flags[kFlagTree + it - 2]) {
+    tree_update_chunk(a, it - 1, c, sm);
+    __syncthreads();
+  }
+  if (!a.flags[kFlagTree + it - 1]) return;
+  tree_contrib_chunk(a, it, c, sm);
+}
+
+__global__ void __launch_bounds__(kThreads) k_tree_sum(StepArgs a, int it, int ngroups) {
+  extern __shared__ __align__(16) double sm[];
+  if (!a.flags[kFlagTree + it - 1]) return;
+  const int s = a.s, E = (a.nb * s + s) * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const int c0 = blockIdx.x * kTreeGroup, c1 = min(a.p, c0 + kTreeGroup);
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < E; e += gridDim.y * blockDim.x) {
+    double v = 0.0;
+    for (int c = c0; c < c1; ++c) v += a.small[(int64_t)c * SL.stride + SL.Z + e];
+    a.tsum[(int64_t)blockIdx.x * a.Kmax * s + e] = v;
+  }
+  if (batch_ticket(a.tree_ticket, (int)(gridDim.x * gridDim.y))) {
+    double* Z = a.glob + GlobLayout::make(a.Kmax, s).Zsum;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+      double v = 0.0;
+      for (int g = 0; g < ngroups; ++g) v += a.tsum[(int64_t)g * a.Kmax * s + e];
+      Z[e] = v;
+    }
+    __syncthreads();
+    tree_sum2_core(a, it, sm);
+    if (threadIdx.x == 0) *a.tree_ticket = 0;
+  }
+}
+
 // Shared-memory budget of the streaming kernels (bytes).
 constexpr int kTileSmem = 96 * 1024;
 
@@ -1551,6 +1595,8 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_apply_y, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_round, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
@@ -1602,13 +1648,27 @@ void count_launches(int k) { g_launches += k; }
 void launch_reduction(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   const int s = a.s, k = a.nb * s, Kt = k + s, ss = s * s;
   const int ngroups = (a.p + kTreeGroup - 1) / kTreeGroup;
+  const int iters = a.reduction == 1 ? 1 : kMaxTreeIter;
   mark(hook, kKindTree, true, st);
-  for (int it = 1; it <= (a.reduction == 1 ? 1 : kMaxTreeIter); ++it) {
-    k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
-    k_tree_sum1<<<dim3(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, it);
-    k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
-    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
-    count_launches(4);
+  if (a.tree_ticket) {
+    // per iteration: (update of it - 1 +) contribution, then the ticketed sums
+    // and factorization; the last update at the end
+    const size_t smr = 8 * ((size_t)k * s + 2 * ss);
+    const dim3 gsum(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads));
+    for (int it = 1; it <= iters; ++it) {
+      k_tree_round<<<a.p, kThreads, smr, st>>>(a, it, it > 1 ? 1 : 0);
+      k_tree_sum<<<gsum, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
+    }
+    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, iters);
+    count_launches(2 * iters + 1);
+  } else {
+    for (int it = 1; it <= iters; ++it) {
+      k_tree_contrib<<<a.p, kThreads, 8 * ((size_t)k * s + ss), st>>>(a, it);
+      k_tree_sum1<<<dim3(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads)), kThreads, 0, st>>>(a, it);
+      k_tree_sum2<<<1, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
+      k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, it);
+      count_launches(4);
+    }
   }
   mark(hook, kKindTree, false, st);
 }

@@ -252,10 +252,16 @@ __global__ void __launch_bounds__(256) k_umma_srcexp(StepArgs a, const double* s
   const SlabInfo si = a.slabs[blockIdx.x];
   if (threadIdx.x < S) hs[threadIdx.x] = 0;
   __syncthreads();
-  for (int idx = threadIdx.x; idx < si.rows * S; idx += 256) {
-    const int r = idx / S, l = idx - r * S;
-    const double v = a.op_nx ? op_value(a, si.row0 + r, l) : src[(si.row0 + r) * lds + l];
-    atomicMax(&hs[l], bexp(v));
+  if (a.op_nx) {
+    for (int idx = threadIdx.x; idx < si.rows * S; idx += 256) {
+      const int r = idx / S, l = idx - r * S;
+      atomicMax(&hs[l], bexp(op_value(a, si.row0 + r, l)));
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < si.rows * S; idx += 256) {
+      const int r = idx / S, l = idx - r * S;
+      atomicMax(&hs[l], bexp(src[(si.row0 + r) * lds + l]));
+    }
   }
   __syncthreads();
   if (threadIdx.x < S) a.srcexp_slab[(int64_t)blockIdx.x * 32 + threadIdx.x] = hs[threadIdx.x];
@@ -332,6 +338,28 @@ struct GramCursor {
 // Whether step st (of nsteps in its item) closes an accumulation interval:
 // exact float32 sums cover 16 steps.
 __device__ __forceinline__ bool interval_end(int st, int nsteps) { return ((st + 1) & 15) == 0 || st + 1 == nsteps; }
+
+// The values a Gram producer thread loads for one step when the pass block is
+// the step's operator applied to its input: rows r0 + 8 ah .. + 7 of column
+// al (A tile) and rows r0 + 4 bq .. + 3 of column n0 + bn (B operand); the
+// first column group also keeps the latter in U for the later passes.
+__device__ __noinline__ void gram_op_values(const StepArgs& a, int64_t row0, int rows, int r0, int col0, int n0,
+                                            bool asrc, int al, int ah, double* da, bool brole, int bq, int bn,
+                                            double* db) {
+  if (asrc)
+    for (int r = 0; r < 8; ++r) {
+      const int row = r0 + 8 * ah + r;
+      da[r] = row < rows ? op_value(a, row0 + row, al) : 0.0;
+    }
+  if (brole)
+    for (int r = 0; r < 4; ++r) {
+      const int row = r0 + 4 * bq + r;
+      const bool ok = row < rows;
+      const double v = ok ? op_value(a, row0 + row, n0 + bn) : 0.0;
+      db[r] = v;
+      if (ok && col0 == 0) a.U[(row0 + row) * a.ldu + n0 + bn] = v;
+    }
+}
 
 template <int S, int ND>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
@@ -482,29 +510,27 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     auto load_src = [&](const GramCursor& c, int j) {
       if (c.valid) {
         const int r0 = c.st * 16;
-        if (is_asrc(c)) {
-          double* d = xa_slot + (j % 3) * 2 * S * 8;
+        if (a.op_nx) {
+          // the operator's block, formed from its input (off the hot loop: the
+          // stencil's index arithmetic stays out of the common path)
+          gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, is_asrc(c), al, ah,
+                         xa_slot + (j % 3) * 2 * S * 8, b_role, bq, bn, xb_slot + (j % 3) * 4 * NB * 4);
+        } else {
+          if (is_asrc(c)) {
+            double* d = xa_slot + (j % 3) * 2 * S * 8;
 #pragma unroll
-          for (int r = 0; r < 8; ++r) {
-            const int row = r0 + 8 * ah + r;
-            const bool ok = row < c.rows;
-            if (a.op_nx)  // the operator's block, formed from its input
-              d[r] = ok ? op_value(a, c.row0 + row, al) : 0.0;
-            else
+            for (int r = 0; r < 8; ++r) {
+              const int row = r0 + 8 * ah + r;
+              const bool ok = row < c.rows;
               cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + al, ok);
+            }
           }
-        }
-        if (b_role) {
-          double* d = xb_slot + (j % 3) * 4 * NB * 4;
+          if (b_role) {
+            double* d = xb_slot + (j % 3) * 4 * NB * 4;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            const int row = r0 + 4 * bq + r;
-            const bool ok = row < c.rows;
-            if (a.op_nx) {  // formed here; the first column group keeps it in U for the later passes
-              const double v = ok ? op_value(a, c.row0 + row, c.z * NB + bn) : 0.0;
-              d[r] = v;
-              if (ok && c.col0 == 0) a.U[(c.row0 + row) * a.ldu + c.z * NB + bn] = v;
-            } else {
+            for (int r = 0; r < 4; ++r) {
+              const int row = r0 + 4 * bq + r;
+              const bool ok = row < c.rows;
               cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + bn, ok);
             }
           }
