@@ -110,17 +110,20 @@ typedef enum lo_leaf {
                            /* shifted CholeskyQR3 and forces two more passes     */
   LO_LEAF_HH = 3           /* Householder QR (Alg. 6, sign rule sigma = -sgn of  */
                            /* the pivot) of each chunk in the step without prior */
-                           /* blocks (k = 0, the tall-skinny QR): one CTA holds  */
-                           /* the chunk tile in shared memory, so the block is   */
-                           /* read once and no Gram matrix is formed (stable at  */
-                           /* any condition number, no shifted retry); the      */
+                           /* blocks (k = 0, the tall-skinny QR): one CTA per    */
+                           /* chunk, the chunk tile in shared memory, so the     */
+                           /* block is read once and no Gram matrix is formed    */
+                           /* (stable at any condition number, no shifted        */
+                           /* retry).  A chunk larger than one tile (rows * s * 8*/
+                           /* above 200 KiB) is walked as sub-tiles in the order */
+                           /* of FlatTSPQR (Alg. 10: each sub-tile factored      */
+                           /* stacked under the previous R, the local factor     */
+                           /* formed backwards), so the recursion has three      */
+                           /* levels: sub-tiles, chunk, reduction tree.  The     */
                            /* reduction stays BCGS-PIP+ (the paper's choice at   */
                            /* the level above the node, Sec. 5.3) and the local  */
                            /* panel is the explicit Householder Q_i.  Steps with */
-                           /* prior blocks run BCGS-PIP+.  Every chunk (the last */
-                           /* one with the remainder rows included) must fit:    */
-                           /* rows * s * 8 <= 200 KiB, else lo_basis_create      */
-                           /* returns LO_ERR_UNSUPPORTED                         */
+                           /* prior blocks run BCGS-PIP+                         */
 } lo_leaf;
 
 /*

@@ -111,6 +111,8 @@ struct lo_basis {
   double* cdev = nullptr;
   size_t cdev_cap = 0;
   // tensor-core form
+  double* hh_scratch = nullptr;  // Householder leaf over chunks larger than one tile
+  int hh_T = 0, hh_stages = 0;
   int* colexp = nullptr;
   int* srcexp_slab = nullptr;
   int* srcexp = nullptr;
@@ -188,6 +190,9 @@ StepArgs make_args(const lo_basis* b) {
   a.chunk_row0 = b->d_chunk_row0;
   a.nslab = b->nslab;
   a.slab_rows = b->slab_rows;
+  a.hh_T = b->hh_T;
+  a.hh_stages = b->hh_stages;
+  a.hh_scratch = b->hh_scratch;
   for (int c = 0; c < b->p; ++c)
     a.max_chunk_rows = std::max<int>(a.max_chunk_rows, (int)(b->chunk_row0[c + 1] - b->chunk_row0[c]));
   a.test_stall = b->opt.test_stall;
@@ -424,11 +429,6 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   const int p = (int)p64;
   const int64_t min_rows = (p == 1) ? n : chunk_rows;
   if (min_rows < Kmax) return LO_ERR_CHUNK_TOO_SMALL;
-  if (o.leaf == LO_LEAF_HH) {  // every chunk tile of the k = 0 step in one CTA's shared memory
-    const int64_t last = n - (int64_t)(p - 1) * chunk_rows;
-    const int64_t maxrows = (p > 1 && chunk_rows > last) ? chunk_rows : last;
-    if (maxrows * s * (int64_t)sizeof(double) > lo::kHHTileBytes) return LO_ERR_UNSUPPORTED;
-  }
 
   lo_basis* b = new (std::nothrow) lo_basis();
   if (!b) return LO_ERR_OOM;
@@ -485,6 +485,16 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   alloc((void**)&b->tsum, sizeof(double) * (size_t)b->ngroups * Kmax * s);
   alloc((void**)&b->flags, sizeof(int) * lo::kFlagCount);
   alloc((void**)&b->tick, sizeof(int) * lo::batch_tick_ints(p));
+  if (o.leaf == LO_LEAF_HH) {
+    // chunks larger than one tile are walked as sub-tiles (FlatTSPQR inside the chunk)
+    int64_t maxrows = 0;
+    for (int c = 0; c < p; ++c) maxrows = std::max<int64_t>(maxrows, b->chunk_row0[c + 1] - b->chunk_row0[c]);
+    if (maxrows * s * (int64_t)sizeof(double) > lo::kHHTileBytes) {
+      b->hh_T = lo::hh_subtile_rows(s);
+      b->hh_stages = (int)((maxrows + b->hh_T - 1) / b->hh_T);
+      alloc((void**)&b->hh_scratch, sizeof(double) * (size_t)p * b->hh_stages * (s * s + s));
+    }
+  }
   alloc((void**)&b->d_slabs, sizeof(SlabInfo) * slabs.size());
   alloc((void**)&b->d_chunk_slab0, sizeof(int32_t) * cs0.size());
   alloc((void**)&b->d_chunk_row0, sizeof(int64_t) * b->chunk_row0.size());
@@ -536,6 +546,7 @@ void lo_basis_destroy(lo_basis* b) {
   cudaFree(b->tsum);
   cudaFree(b->flags);
   cudaFree(b->tick);
+  cudaFree(b->hh_scratch);
   cudaFree(b->d_slabs);
   cudaFree(b->d_chunk_slab0);
   cudaFree(b->d_chunk_row0);

@@ -19,6 +19,13 @@ constexpr int kMaxTreeIter = 3;  // reduction iterations
 constexpr int kTreeGroup = 64;   // chunks summed per CTA in the tree's first level
 constexpr int kHHThreads = 256;  // threads of the Householder leaf (one CTA per chunk)
 constexpr int kHHTileBytes = 200 * 1024;  // shared memory for one chunk tile of the Householder leaf
+// Rows of the Householder leaf's sub-tiles when a chunk exceeds one tile: the
+// largest power of two T with (T + s) s doubles in the tile budget.
+inline int hh_subtile_rows(int s) {
+  int T = 1 << 14;
+  while (T > s && (int64_t)(T + s) * s * 8 > kHHTileBytes) T >>= 1;
+  return T;
+}
 
 // Flag words (int) in device memory.
 enum Flag : int {
@@ -101,6 +108,11 @@ struct StepArgs {
   int nslab;
   int slab_rows;
   int max_chunk_rows;       // rows of the largest chunk (the last one holds the remainder)
+  // Householder leaf over chunks larger than one tile (FlatTSPQR inside the
+  // chunk): sub-tile rows, stages per chunk, and per chunk and stage the
+  // reflectors' parts on the carried rows (s x s) and their tau (s)
+  int hh_T, hh_stages;
+  double* hh_scratch;
   int precision;
   int leaf;
   int reduction;

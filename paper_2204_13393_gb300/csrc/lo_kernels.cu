@@ -1105,11 +1105,11 @@ __device__ __forceinline__ void hh_block_sum(double (&v)[SMAX], int cnt, double*
 // columns j + 1 .. s - 1 of A (rows j ..): w_c = A[j][c] + sum_{r > j} v_r A[r][c],
 // A[., c] -= t v w_c.  Whole CTA; returns after a barrier.
 template <int SMAX>
-__device__ __forceinline__ void hh_apply(double* A, int rows, int s, int j, double t, double* red, double* vsum,
-                                         double* wsh) {
+__device__ __forceinline__ void hh_apply_lda(double* A, int lda, int rows, int s, int j, double t, double* red,
+                                             double* vsum, double* wsh) {
   const int nc = s - j - 1, tid = threadIdx.x;
   if (nc <= 0 || t == 0.0) return;
-  const double* x = A + (int64_t)j * rows;
+  const double* x = A + (int64_t)j * lda;
   double w[SMAX];
 #pragma unroll
   for (int cc = 0; cc < SMAX; ++cc) w[cc] = 0.0;
@@ -1117,19 +1117,25 @@ __device__ __forceinline__ void hh_apply(double* A, int rows, int s, int j, doub
     const double vr = x[r];
 #pragma unroll
     for (int cc = 0; cc < SMAX; ++cc)
-      if (cc < nc) w[cc] = fma(vr, A[(int64_t)(j + 1 + cc) * rows + r], w[cc]);
+      if (cc < nc) w[cc] = fma(vr, A[(int64_t)(j + 1 + cc) * lda + r], w[cc]);
   }
   hh_block_sum<SMAX>(w, nc, red, vsum);
-  if (tid < nc) wsh[tid] = A[(int64_t)(j + 1 + tid) * rows + j] + vsum[tid];
+  if (tid < nc) wsh[tid] = A[(int64_t)(j + 1 + tid) * lda + j] + vsum[tid];
   __syncthreads();
-  if (tid < nc) A[(int64_t)(j + 1 + tid) * rows + j] -= t * wsh[tid];
+  if (tid < nc) A[(int64_t)(j + 1 + tid) * lda + j] -= t * wsh[tid];
   for (int r = j + 1 + tid; r < rows; r += kHHThreads) {
     const double tv = t * x[r];
 #pragma unroll
     for (int cc = 0; cc < SMAX; ++cc)
-      if (cc < nc) A[(int64_t)(j + 1 + cc) * rows + r] -= tv * wsh[cc];
+      if (cc < nc) A[(int64_t)(j + 1 + cc) * lda + r] -= tv * wsh[cc];
   }
   __syncthreads();
+}
+
+template <int SMAX>
+__device__ __forceinline__ void hh_apply(double* A, int rows, int s, int j, double t, double* red, double* vsum,
+                                         double* wsh) {
+  hh_apply_lda<SMAX>(A, rows, rows, s, j, t, red, vsum, wsh);
 }
 
 template <int SMAX>
@@ -1225,6 +1231,191 @@ __global__ void __launch_bounds__(kHHThreads) k_hh_leaf(StepArgs a) {
     smallc[SL.N_last + e] = nv;
     smallc[SL.N_comb + e] = nv;
     smallc[SL.Ninv_last + e] = (i == l) ? 1.0 : 0.0;
+  }
+}
+
+// FlatTSPQR (Alg. 10) inside a chunk too large for one tile, with Householder
+// sub-solvers: one CTA walks the chunk's sub-tiles X_1 .. X_m of up to T rows
+// in order.  Stage 1 is the Householder QR of X_1; stage i > 1 factors the
+// previous R stacked on the next sub-tile, [R_{i-1}; X_i] = Qh_i R_i
+// ((s + rows_i) x s, the carried rows first).  The reflectors stay behind:
+// their parts on the sub-tile's rows in the chunk's rows of the new panel,
+// their parts on the carried rows and the tau in hh_scratch.  The chunk's R
+// is R_m (signs normalized, D = diag(sgn R_jj)).  The explicit local factor
+// then comes from a backward pass: with M_m = D and M_{i-1} = Qh_i^top M_i,
+// the rows of sub-tile i are Qh_i^bot M_i (Qh_1 M_1 for the first), where
+// Qh_i is formed in place from its reflectors as in k_hh_leaf.  Three levels
+// of the method's recursion: sub-tiles (flat) -> chunk -> reduction tree.
+
+// Householder QR of the nrows x s column-major tile A (leading dimension
+// lda): reflectors below the diagonal (v_j[j] = 1 implicit), tau_j in tau[j],
+// R on and above it.  Whole CTA.  Returns false (after latching
+// LO_ERR_NONFINITE) on a non-finite norm.
+template <int SMAX>
+__device__ bool hh_factor_tile(double* A, int lda, int nrows, int s, double* tau, double* red, double* vsum,
+                               double* wsh, int* flags) {
+  const int tid = threadIdx.x;
+  for (int j = 0; j < s; ++j) {
+    double* x = A + (int64_t)j * lda;
+    double v[SMAX];
+#pragma unroll
+    for (int cc = 0; cc < SMAX; ++cc) v[cc] = 0.0;
+    for (int r = j + tid; r < nrows; r += kHHThreads) v[0] = fma(x[r], x[r], v[0]);
+    hh_block_sum<SMAX>(v, 1, red, vsum);
+    const double alpha = sqrt(vsum[0]);
+    const double x0 = x[j];
+    const double beta = (x0 >= 0.0) ? -alpha : alpha;
+    const double t = (alpha == 0.0) ? 0.0 : (beta - x0) / beta;
+    if (!isfinite(alpha)) {
+      if (tid == 0) set_status(flags, LO_ERR_NONFINITE);
+      return false;
+    }
+    __syncthreads();
+    if (alpha != 0.0) {
+      const double scal = 1.0 / (x0 - beta);
+      for (int r = j + 1 + tid; r < nrows; r += kHHThreads) x[r] *= scal;
+    }
+    if (tid == 0) {
+      x[j] = beta;
+      tau[j] = t;
+    }
+    __syncthreads();
+    hh_apply_lda<SMAX>(A, lda, nrows, s, j, t, red, vsum, wsh);
+  }
+  return true;
+}
+
+// Qh = H_0 .. H_{s-1} [I; 0] in place over the reflectors of the tile.
+template <int SMAX>
+__device__ void hh_form_q(double* A, int lda, int nrows, int s, const double* tau, double* red, double* vsum,
+                          double* wsh) {
+  for (int j = s - 1; j >= 0; --j) {
+    const double t = tau[j];
+    hh_apply_lda<SMAX>(A, lda, nrows, s, j, t, red, vsum, wsh);
+    double* x = A + (int64_t)j * lda;
+    for (int r = threadIdx.x; r < nrows; r += kHHThreads) x[r] = (r < j) ? 0.0 : (r == j ? 1.0 - t : -t * x[r]);
+    __syncthreads();
+  }
+}
+
+template <int SMAX>
+__global__ void __launch_bounds__(kHHThreads) k_hh_flat(StepArgs a, int T) {
+  extern __shared__ __align__(16) double A[];  // (s + T) x s, column-major, leading dimension s + T
+  __shared__ double red[(kHHThreads / 32) * 32];
+  __shared__ double vsum[32], wsh[32], tau[32], dsg[32];
+  __shared__ double Rs[32 * 32], Mn[32 * 32];
+  __shared__ int hs[32];
+  const int c = blockIdx.x, s = a.s, tid = threadIdx.x, lda = s + T;
+  const int64_t r0 = a.chunk_row0[c];
+  const int rows = (int)(a.chunk_row0[c + 1] - r0);
+  const int m = (rows + T - 1) / T;
+  const int stage = s * s + s;
+  double* scr = a.hh_scratch + (int64_t)c * a.hh_stages * stage;  // per stage: carried parts s x s, then tau
+  double* slot = a.V;
+  if (tid < 32) hs[tid] = 0;
+  // ---- forward: stage i factors [R_{i-1}; X_i]
+  for (int i = 0; i < m; ++i) {
+    const int off = (i > 0) ? s : 0, ri = min(T, rows - i * T), nr = off + ri;
+    const int64_t g0 = r0 + (int64_t)i * T;
+    if (i > 0)  // the carried rows: R_{i-1}, zeros below its diagonal
+      for (int e = tid; e < s * s; e += kHHThreads) {
+        const int rr = e / s, l = e - rr * s;
+        A[(int64_t)l * lda + rr] = (rr <= l) ? Rs[rr * s + l] : 0.0;
+      }
+    int bad = 0;
+    for (int idx = tid; idx < ri * s; idx += kHHThreads) {
+      const int r = idx / s, l = idx - r * s;
+      const double x = a.W[(g0 + r) * a.ldw + l];
+      bad |= isfinite(x) ? 0 : 1;
+      A[(int64_t)l * lda + off + r] = x;
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) set_status(a.flags, LO_ERR_NONFINITE);
+      return;
+    }
+    if (!hh_factor_tile<SMAX>(A, lda, nr, s, tau, red, vsum, wsh, a.flags)) return;
+    // keep R_i; store the reflectors (carried rows: scratch; sub-tile rows: the panel)
+    for (int e = tid; e < s * s; e += kHHThreads) {
+      const int rr = e / s, l = e - rr * s;
+      Rs[e] = (rr <= l) ? A[(int64_t)l * lda + rr] : 0.0;
+      if (i > 0) scr[(int64_t)i * stage + e] = A[(int64_t)l * lda + rr];
+    }
+    if (tid < s) scr[(int64_t)i * stage + s * s + tid] = tau[tid];
+    for (int idx = tid; idx < ri * s; idx += kHHThreads) {
+      const int r = idx / s, l = idx - r * s;
+      slot[(g0 + r) * s + l] = A[(int64_t)l * lda + off + r];
+    }
+    __syncthreads();
+  }
+  if (tid < s) dsg[tid] = (Rs[tid * s + tid] >= 0.0) ? 1.0 : -1.0;
+  __syncthreads();
+  // ---- the chunk's normalizer D R_m, N_last^{-1} = I
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  for (int e = tid; e < s * s; e += kHHThreads) {
+    const int ii = e / s, l = e - ii * s;
+    const double nv = Rs[e] * dsg[ii];
+    smallc[SL.N_last + e] = nv;
+    smallc[SL.N_comb + e] = nv;
+    smallc[SL.Ninv_last + e] = (ii == l) ? 1.0 : 0.0;
+  }
+  // ---- backward: M_m = D; stage i: Qh_i from its reflectors, rows times M_i
+  for (int e = tid; e < s * s; e += kHHThreads) Rs[e] = ((e / s) == (e % s)) ? dsg[e / s] : 0.0;
+  __syncthreads();
+  int hmax[SMAX];  // this thread's largest biased exponent per panel column
+#pragma unroll
+  for (int l = 0; l < SMAX; ++l) hmax[l] = 0;
+  for (int i = m - 1; i >= 0; --i) {
+    const int off = (i > 0) ? s : 0, ri = min(T, rows - i * T), nr = off + ri;
+    const int64_t g0 = r0 + (int64_t)i * T;
+    if (i > 0)
+      for (int e = tid; e < s * s; e += kHHThreads) {
+        const int rr = e / s, l = e - rr * s;
+        A[(int64_t)l * lda + rr] = scr[(int64_t)i * stage + e];
+      }
+    for (int idx = tid; idx < ri * s; idx += kHHThreads) {
+      const int r = idx / s, l = idx - r * s;
+      A[(int64_t)l * lda + off + r] = slot[(g0 + r) * s + l];
+    }
+    if (tid < s) tau[tid] = scr[(int64_t)i * stage + s * s + tid];
+    __syncthreads();
+    hh_form_q<SMAX>(A, lda, nr, s, tau, red, vsum, wsh);
+    // rows of Qh_i times M_i: the sub-tile's rows into the panel, the carried rows the next M
+    for (int r = tid; r < nr; r += kHHThreads) {
+      double q[SMAX];
+#pragma unroll
+      for (int l = 0; l < SMAX; ++l) q[l] = (l < s) ? A[(int64_t)l * lda + r] : 0.0;
+#pragma unroll
+      for (int l = 0; l < SMAX; ++l) {
+        if (l < s) {
+          double o = 0.0;
+#pragma unroll
+          for (int j = 0; j < SMAX; ++j)
+            if (j < s) o = fma(q[j], Rs[j * s + l], o);
+          if (r >= off) {
+            slot[(g0 + r - off) * s + l] = o;
+            hmax[l] = max(hmax[l], (int)((((unsigned long long)__double_as_longlong(o)) >> 52) & 0x7FF));
+          } else {
+            Mn[r * s + l] = o;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (i > 0) {
+      for (int e = tid; e < s * s; e += kHHThreads) Rs[e] = Mn[e];
+      __syncthreads();
+    }
+  }
+  if (a.colexp) {
+#pragma unroll
+    for (int l = 0; l < SMAX; ++l)
+      if (l < s) {
+        const int mx = __reduce_max_sync(0xffffffffu, hmax[l]);
+        if ((tid & 31) == 0) atomicMax(&hs[l], mx);
+      }
+    __syncthreads();
+    if (tid < s) a.colexp[(int64_t)tid * a.p + c] = hs[tid];
   }
 }
 
@@ -1598,6 +1789,10 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_tree_round, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_tree_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_flat<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_flat<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_flat<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
+  if ((e = cudaFuncSetAttribute(k_hh_flat<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
@@ -1679,21 +1874,33 @@ void launch_reduction(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
 cudaError_t launch_step_hh(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   const int s = a.s;
   const size_t tile = sizeof(double) * (size_t)a.max_chunk_rows * s;
-  if (a.nb != 0 || tile > (size_t)kHHTileBytes) return cudaErrorInvalidValue;
+  const bool flat = tile > (size_t)kHHTileBytes;  // chunks walked as sub-tiles (FlatTSPQR)
+  if (a.nb != 0 || (flat && !a.hh_scratch)) return cudaErrorInvalidValue;
+  const size_t ftile = sizeof(double) * (size_t)(a.hh_T + s) * s;
   const bool tc = (a.precision == LO_PREC_FP64_TC || a.precision == LO_PREC_MIXED_TC);
   cudaError_t e;
   if (tc && (e = umma_set_attrs())) return e;
   k_step_begin<<<1, 32, 0, st>>>(a.flags, 0, a.reduction != 1);
   count_launches(1);
   mark(hook, kKindLeaf, true, st);
-  if (s <= 4)
+  if (flat) {
+    if (s <= 4)
+      k_hh_flat<4><<<a.p, kHHThreads, ftile, st>>>(a, a.hh_T);
+    else if (s <= 8)
+      k_hh_flat<8><<<a.p, kHHThreads, ftile, st>>>(a, a.hh_T);
+    else if (s <= 16)
+      k_hh_flat<16><<<a.p, kHHThreads, ftile, st>>>(a, a.hh_T);
+    else
+      k_hh_flat<32><<<a.p, kHHThreads, ftile, st>>>(a, a.hh_T);
+  } else if (s <= 4) {
     k_hh_leaf<4><<<a.p, kHHThreads, tile, st>>>(a);
-  else if (s <= 8)
+  } else if (s <= 8) {
     k_hh_leaf<8><<<a.p, kHHThreads, tile, st>>>(a);
-  else if (s <= 16)
+  } else if (s <= 16) {
     k_hh_leaf<16><<<a.p, kHHThreads, tile, st>>>(a);
-  else
+  } else {
     k_hh_leaf<32><<<a.p, kHHThreads, tile, st>>>(a);
+  }
   count_launches(1);
   mark(hook, kKindLeaf, false, st);
   launch_reduction(a, st, hook);

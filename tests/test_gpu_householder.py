@@ -170,3 +170,37 @@ def test_householder_leaf_nonfinite_and_tuner():
     bt = L.Basis(n, s, 1, crt, leaf="hh")
     U, _, R = bt.orthogonalize(dev(I.gaussian(n, s, I.seed_for(8, 701))))
     assert O.e_perp(host(U)) <= TOL_PERP
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp64_tc"])
+@pytest.mark.parametrize("kappa", [1e2, 1e10])
+@pytest.mark.parametrize("s,cr", [(1, 65536), (3, 30000), (8, 16384), (16, 6000), (32, 4096)])
+def test_householder_flat_chunks(s, cr, kappa, precision):
+    """Chunks larger than one shared-memory tile: the Householder leaf walks
+    them as sub-tiles in FlatTSPQR order (each factored under the previous R,
+    the local factor formed backwards).  The chunk's QR is unique, so Q_i,
+    T_i, U and R match the oracle's Householder QR of the whole chunk."""
+    if precision == "fp64_tc" and s == 3:
+        pytest.skip("s = 3 has no tensor-core form")
+    n = 3 * cr + cr // 3 + 5
+    A = I.stewart(n, s, kappa, I.seed_for(8, 800 + s + int(np.log10(kappa))))
+    b = lo().Basis(n, s, 2, cr, precision=precision, leaf="hh")
+    U, _, R = b.orthogonalize(dev(A))
+    Ug, Rg = host(U), host(R)
+    assert b.last_step_info()[0] == 1
+    assert O.e_perp(Ug) <= TOL_PERP
+    assert O.residual(A, Ug, Rg) <= TOL_RES
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    Uo, _, No = ora.orthogonalize(A, "hh", "hh")
+    tol = max(TOL_REL, 100 * kappa * EPS)
+    assert close(Ug, Uo, tol) and close(Rg, No, tol), (errs(Ug, Uo), errs(Rg, No))
+    for c in range(b.num_chunks):
+        Qi, Ti = b.export_chunk(c)
+        assert close(Qi, ora.Qloc[c], tol), (c, errs(Qi, ora.Qloc[c]))
+        assert O.e_perp(Qi) <= TOL_PERP
+        assert close(Ti, np.triu(ora.T[c]), tol), c
+    # the basis goes on past the flat leaf (BCGS-PIP+ with the flat panel as prior block)
+    W = I.gaussian(n, s, I.seed_for(8, 900 + s))
+    U2, H2, R2 = b.orthogonalize(dev(W))
+    Uo2, Po2, No2 = ora.orthogonalize(W, "hh", "hh")
+    assert close(host(U2), Uo2, tol) and close(host(H2), Po2, tol) and close(host(R2), No2, tol)

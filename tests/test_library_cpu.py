@@ -160,18 +160,18 @@ def test_batched_cache_hooks_without_device(lib):
     assert lib.lo_batched_cache_entries(12345) == 0
 
 
-def test_householder_leaf_tile_check_without_device(lib):
-    """LO_LEAF_HH needs every chunk tile (the last one with the remainder rows)
-    in one CTA's shared memory: rows * s * 8 <= 200 KiB, checked before any
-    CUDA call (LO_ERR_UNSUPPORTED = 9)."""
+def test_householder_leaf_option_without_device(lib):
+    """LO_LEAF_HH passes validation for any chunk size (chunks larger than one
+    tile are walked as sub-tiles), so on a CPU-only host create gets as far as
+    the device allocation; leaf values past LO_LEAF_HH are rejected."""
     from paper_2204_13393_gb300 import lo
 
     h = ctypes.c_void_p()
     o = lo.Options()
     lib.lo_options_default(ctypes.byref(o))
     o.leaf = lo.LEAF["hh"]
-    for n, s, cr in ((2 ** 20, 8, 4096), (100000, 32, 1024), (30000, 8, 30000), (6000, 8, 4096)):
-        assert lib.lo_basis_create(n, s, 1, cr, ctypes.byref(o), None, ctypes.byref(h)) == 9, (n, s, cr)
+    for n, s, cr in ((2 ** 20, 8, 4096), (100000, 32, 1024), (6000, 8, 512)):
+        assert lib.lo_basis_create(n, s, 1, cr, ctypes.byref(o), None, ctypes.byref(h)) not in (1, 3, 9), (n, s, cr)
         assert h.value is None
     o.leaf = 4
     assert lib.lo_basis_create(4096, 4, 1, 512, ctypes.byref(o), None, ctypes.byref(h)) == 1
