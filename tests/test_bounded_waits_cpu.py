@@ -13,6 +13,8 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 REVIEWED_WHILE = {
     ("lo_umma.cu", "while (!mbar_try(mb, parity))"),   # bounded by clock64() - t0 > kWaitCycles
     ("lo_api.cu", "while (c0 < Kmax) c0 *= 2;"),        # host: chunk-size candidates
+    # host: the Householder sub-tile rows, halving from 2^14 (at most 14 steps)
+    ("lo_internal.h", "while (T > s && (int64_t)(T + s) * s * 8 > kHHTileBytes) T >>= 1;"),
     # the persistent batched launch: its flag wait, bounded by kBatchWaitCycles and the abort word
     ("lo_kernels.cu", "while (ld_acquire(p) < v) {"),
     # item decoding: at most kBatchPhases phases and ninst instances (g < the list's end)
