@@ -193,14 +193,19 @@ def test_householder_flat_chunks(s, cr, kappa, precision):
     ora = O.LocallyOrthogonalBasis(n, s, cr)
     Uo, _, No = ora.orthogonalize(A, "hh", "hh")
     tol = max(TOL_REL, 100 * kappa * EPS)
-    assert close(Ug, Uo, tol) and close(Rg, No, tol), (errs(Ug, Uo), errs(Rg, No))
+    # R is well determined (element by element); U and Q_i element by element
+    # only where their forward-error bound kappa eps is small, else in norm
+    # (their backward errors, e_perp and the residual, are checked above)
+    assert close(Rg, No), errs(Rg, No)
+    cmp = close if kappa * EPS <= 1e-10 else (lambda x, y, t: errs(x, y)[0] <= t)
+    assert cmp(Ug, Uo, tol), errs(Ug, Uo)
     for c in range(b.num_chunks):
         Qi, Ti = b.export_chunk(c)
-        assert close(Qi, ora.Qloc[c], tol), (c, errs(Qi, ora.Qloc[c]))
+        assert cmp(Qi, ora.Qloc[c], tol), (c, errs(Qi, ora.Qloc[c]))
         assert O.e_perp(Qi) <= TOL_PERP
-        assert close(Ti, np.triu(ora.T[c]), tol), c
+        assert cmp(Ti, np.triu(ora.T[c]), tol), c
     # the basis goes on past the flat leaf (BCGS-PIP+ with the flat panel as prior block)
     W = I.gaussian(n, s, I.seed_for(8, 900 + s))
     U2, H2, R2 = b.orthogonalize(dev(W))
     Uo2, Po2, No2 = ora.orthogonalize(W, "hh", "hh")
-    assert close(host(U2), Uo2, tol) and close(host(H2), Po2, tol) and close(host(R2), No2, tol)
+    assert cmp(host(U2), Uo2, tol) and cmp(host(H2), Po2, tol) and cmp(host(R2), No2, tol)
