@@ -166,7 +166,11 @@ typedef struct lo_options {
                          /* no loads and no MMAs, so the kernel's bounded waits  */
                          /* (about 0.25 s each) expire and the step returns      */
                          /* LO_ERR_TIMEOUT with the basis unchanged (the timeout */
-                         /* path; no fault, nothing left in flight)              */
+                         /* path; no fault, nothing left in flight).  2: the     */
+                         /* Gram's drainer warps never release a drained         */
+                         /* accumulator buffer, so the issuer's wait for it      */
+                         /* expires after loads and MMAs were issued; it drains  */
+                         /* them and the step returns LO_ERR_TIMEOUT likewise    */
   double deflation_tol;  /* delta >= 0, default 0 (off).  delta > 0: the        */
                          /* deflated PQR of Sec. 3 (t < s), kept as t = s: a    */
                          /* column of W whose distance to the span of the basis */
@@ -353,6 +357,19 @@ lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_
  */
 uint64_t lo_basis_id(const lo_basis* b);
 int32_t lo_batched_cache_entries(uint64_t basis_id);
+
+/*
+ * Autotuner of the leaf: the chunk size of each leaf from lo_tune_chunk_rows
+ * (BCGS-PIP+; the Householder leaf for a one-block basis), then the step
+ * without prior blocks (k = 0, where the two leaves differ) timed with each on
+ * a synthetic block of this shape; *leaf and *chunk_rows receive the faster
+ * pair (for a basis of several blocks the chunk size is BCGS-PIP+'s, which its
+ * later steps want).  The paper chooses the sub-algorithm per hardware level
+ * (Sec. 5.3); here the choice is measured.  Both leaves are stable, so the
+ * choice is on speed alone.  Allocates temporary device memory.
+ */
+lo_status lo_tune_leaf(int64_t n, int32_t s, int32_t max_blocks, const lo_options* opt, void* cuda_stream,
+                       int32_t* leaf, int32_t* chunk_rows);
 
 /* Wait for the basis stream and return (and clear) any latched device error. */
 lo_status lo_basis_sync(lo_basis* b);

@@ -406,7 +406,7 @@ lo_status lo_basis_create(int64_t n, int32_t s, int32_t max_blocks, int32_t chun
   lo_options_default(&o);
   if (opt) o = *opt;
   if (o.precision < 0 || o.precision > 3 || o.leaf < 0 || o.leaf > 3 || o.reduction < 0 ||
-      o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1 || o.test_stall < 0 || o.test_stall > 1)
+      o.reduction > 2 || o.digit_planes < 0 || o.digit_planes > 1 || o.test_stall < 0 || o.test_stall > 2)
     return LO_ERR_INVALID_ARG;
   // A one-block basis (tall-skinny QR) of at most kNativeMaxS columns runs
   // the native float64 kernels in the tensor-core forms too: with no prior
@@ -1028,6 +1028,66 @@ lo_status lo_tune_chunk_rows(int64_t n, int32_t s, int32_t max_blocks, const lo_
   *chunk_rows = (int32_t)best;
   std::lock_guard<std::mutex> lock(mu);
   memo[mkey] = *chunk_rows;
+  return LO_OK;
+}
+
+lo_status lo_tune_leaf(int64_t n, int32_t s, int32_t max_blocks, const lo_options* opt, void* cuda_stream,
+                       int32_t* leaf, int32_t* chunk_rows) {
+  if (!leaf || !chunk_rows) return LO_ERR_INVALID_ARG;
+  *leaf = LO_LEAF_PIP2;
+  *chunk_rows = 0;
+  lo_options o;
+  lo_options_default(&o);
+  if (opt) o = *opt;
+  o.sync = 1;
+  // chunk rows per leaf (memoized by the chunk-size tuner)
+  lo_options op = o, oh = o;
+  op.leaf = LO_LEAF_PIP2;
+  oh.leaf = LO_LEAF_HH;
+  int32_t crp = 0, crh = 0;
+  lo_status st = lo_tune_chunk_rows(n, s, max_blocks, &op, cuda_stream, &crp);
+  if (st != LO_OK) return st;
+  // a basis of several blocks keeps the chunk size its later steps want; the
+  // leaf only changes its first step
+  if (max_blocks > 1)
+    crh = crp;
+  else if (lo_tune_chunk_rows(n, s, max_blocks, &oh, cuda_stream, &crh) != LO_OK)
+    crh = 0;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  double* Wd = nullptr;
+  double* Ud = nullptr;
+  if (cudaMalloc(&Wd, sizeof(double) * (size_t)n * s) != cudaSuccess ||
+      cudaMalloc(&Ud, sizeof(double) * (size_t)n * s) != cudaSuccess) {
+    cudaFree(Wd);
+    cudaGetLastError();
+    return LO_ERR_OOM;
+  }
+  cudaError_t e = lo::launch_fill_pattern(Wd, n * s, stream);
+  // the first step (k = 0) with each leaf, best of three
+  double best[2] = {1e300, 1e300};
+  const lo_options* ops[2] = {&op, &oh};
+  const int32_t crs[2] = {crp, crh};
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    if (crs[q] <= 0) continue;
+    lo_basis* b = nullptr;
+    if (lo_basis_create(n, s, max_blocks, crs[q], ops[q], cuda_stream, &b) != LO_OK) continue;
+    for (int rep = 0; rep < 4; ++rep) {
+      b->nb = 0;
+      cudaStreamSynchronize(stream);
+      const auto t0 = std::chrono::steady_clock::now();
+      const bool ok = lo_orthogonalize(b, Wd, s, Ud, s, nullptr, nullptr) == LO_OK;
+      const auto t1 = std::chrono::steady_clock::now();
+      if (!ok) break;
+      if (rep > 0) best[q] = std::min(best[q], std::chrono::duration<double>(t1 - t0).count());
+    }
+    lo_basis_destroy(b);
+  }
+  cudaFree(Wd);
+  cudaFree(Ud);
+  if (e != cudaSuccess) return from_cuda(e);
+  const int q = (best[1] < best[0]) ? 1 : 0;
+  *leaf = q ? LO_LEAF_HH : LO_LEAF_PIP2;
+  *chunk_rows = crs[q];
   return LO_OK;
 }
 

@@ -147,7 +147,8 @@ struct StepArgs {
   uint8_t* dig;
   int64_t dtiles;            // 16-row tiles of the slab tiling
   const struct UmmaMaps* maps;  // host-side TMA descriptors of dig (lo_umma.cu)
-  int32_t test_stall;           // test hook: the k > 0 tensor-core Gram issues nothing (lo_options)
+  int32_t test_stall;           // test hook (lo_options): 1 the k > 0 tensor-core Gram issues nothing,
+                                // 2 its drainers never release a drained accumulator buffer
   // apply_Q on the tensor cores: k_umma_update<S, 1> writes columns
   // apply_n0 .. apply_n0 + S - 1 (those below apply_m) of Y = apply_y (device,
   // row stride apply_ldy) instead of the new panel; null in the steps

@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   if (warp == 8) {
     // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
     // (the test hook withholds all of it: every bounded wait then expires)
-    if (lane == 0 && !a.test_stall) {
+    if (lane == 0 && a.test_stall != 1) {
       uint32_t idesc[ND];
 #pragma unroll
       for (int t = 1; t <= ND; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB, ND), 0, 0);
@@ -611,7 +611,9 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(empty0 + 8 * buf);
+      // (test hook 2: the drained buffer is never released, so the issuer's
+      // wait for it expires with loads and MMAs already issued)
+      if (lane == 0 && a.test_stall != 2) mbar_arrive(empty0 + 8 * buf);
       if (cur.st + 1 == cur.nsteps) {
         // partial of this slab: column col0 + m, block columns z NB .. z NB + NB - 1
         const int m = (warp & 3) * 32 + lane, colm = cur.col0 + m;

@@ -43,7 +43,7 @@ EXPORTED = [
     "lo_laplace5_apply", "lo_launch_count", "lo_basis_set_profiling", "lo_basis_profile_read",
     "lo_basis_last_step_info", "lo_tsqr_noalloc", "lo_tsqr_noalloc_scratch", "lo_basis_truncate",
     "lo_tune_chunk_rows", "lo_basis_id", "lo_batched_cache_entries", "lo_basis_last_rank",
-    "lo_set_batched_route", "lo_batched_persistent_count", "lo_orthogonalize_laplace5",
+    "lo_set_batched_route", "lo_batched_persistent_count", "lo_orthogonalize_laplace5", "lo_tune_leaf",
 ]
 KERNEL_GROUPS = ["gram", "leaf", "tree", "update", "apply_q", "refine"]
 
@@ -112,6 +112,9 @@ def _lib():
     L.lo_orthogonalize_laplace5.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_int64, c_void_p, c_int64,
                                             c_void_p, c_void_p]
     L.lo_orthogonalize_laplace5.restype = c_int32
+    L.lo_tune_leaf.argtypes = [c_int64, c_int32, c_int32, POINTER(Options), c_void_p, POINTER(c_int32),
+                               POINTER(c_int32)]
+    L.lo_tune_leaf.restype = c_int32
     L.lo_set_batched_route.argtypes = [c_int32]
     L.lo_set_batched_route.restype = c_int32
     L.lo_batched_persistent_count.argtypes = []
@@ -209,7 +212,7 @@ class Basis:
         if refine_tol > 0:
             o.refine_tol = refine_tol
         o.digit_planes = 0 if digit_planes else 1
-        o.test_stall = 1 if test_stall else 0
+        o.test_stall = int(test_stall)
         o.deflation_tol = float(deflation_tol)
         h = c_void_p()
         self._h = None
@@ -394,6 +397,18 @@ def tune_chunk_rows(n: int, s: int, max_blocks: int, precision: str = "fp64", le
     _check(L.lo_tune_chunk_rows(int(n), int(s), int(max_blocks), ctypes.byref(o),
                                 c_void_p(_stream_handle(stream)), ctypes.byref(out)), "lo_tune_chunk_rows")
     return out.value
+
+
+def tune_leaf(n: int, s: int, max_blocks: int, precision: str = "fp64", stream=None):
+    """lo_tune_leaf: (leaf name, chunk rows) of the faster leaf for this shape (measured)."""
+    L = _lib()
+    o = Options()
+    L.lo_options_default(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    leaf, cr = c_int32(), c_int32()
+    _check(L.lo_tune_leaf(int(n), int(s), int(max_blocks), ctypes.byref(o), c_void_p(_stream_handle(stream)),
+                          ctypes.byref(leaf), ctypes.byref(cr)), "lo_tune_leaf")
+    return {v: k for k, v in LEAF.items()}[leaf.value], cr.value
 
 
 def launch_count() -> int:

@@ -209,3 +209,16 @@ def test_householder_flat_chunks(s, cr, kappa, precision):
     U2, H2, R2 = b.orthogonalize(dev(W))
     Uo2, Po2, No2 = ora.orthogonalize(W, "hh", "hh")
     assert cmp(host(U2), Uo2, tol) and cmp(host(H2), Po2, tol) and cmp(host(R2), No2, tol)
+
+
+@pytest.mark.parametrize("M", [1, 4])
+def test_leaf_tuner(M):
+    """lo_tune_leaf returns one of the two leaves with a chunk size the basis
+    accepts; the tuned basis orthogonalizes to float64 accuracy."""
+    L = lo()
+    n, s = 300000, 8
+    leaf, cr = L.tune_leaf(n, s, M, precision="fp64_tc")
+    assert leaf in ("pip2", "hh") and cr >= 256
+    b = L.Basis(n, s, M, cr, precision="fp64_tc", leaf=leaf)
+    U, _, R = b.orthogonalize(dev(I.gaussian(n, s, I.seed_for(8, 950))))
+    assert O.e_perp(host(U)) <= TOL_PERP

@@ -705,6 +705,35 @@ def test_bounded_wait_expires_cleanly():
     assert O.e_perp(Q) <= TOL_PERP
 
 
+def test_bounded_wait_expires_with_work_in_flight():
+    """The timeout path with loads and MMAs in flight, without a fault: with
+    test hook 2 the Gram's drainers never release a drained accumulator
+    buffer, so the issuer's bounded wait for it expires after it has issued
+    the loads and MMAs of the first intervals; it waits for those to finish,
+    and the step returns LO_ERR_TIMEOUT with the basis unchanged.  The
+    context stays usable: the same basis runs a k = 0 step, and a fresh basis
+    the same two steps, matching the oracle."""
+    n, s, cr = 65536, 8, 4096
+    L = lo()
+    W0h, W1h = (I.gaussian(n, s, 7300 + j) for j in range(2))
+    W0, W1 = dev(W0h), dev(W1h)
+    b = L.Basis(n, s, 3, cr, precision="fp64_tc", test_stall=2)
+    b.orthogonalize(W0)
+    with pytest.raises(L.LoError) as e:
+        b.orthogonalize(W1)
+    assert e.value.name == "LO_ERR_TIMEOUT"
+    assert b.num_blocks == 1
+    b.truncate(0)
+    U, _, R = b.orthogonalize(W0)
+    assert O.e_perp(host(U)) <= TOL_PERP
+    ok = L.Basis(n, s, 3, cr, precision="fp64_tc")
+    ora = O.LocallyOrthogonalBasis(n, s, cr)
+    for Wd, Wh in ((W0, W0h), (W1, W1h)):
+        U, H, R = ok.orthogonalize(Wd)
+        Uo, Po, No = ora.orthogonalize(Wh, "hh", "hh")
+        assert close(host(U), Uo) and close(host(R), No)
+
+
 def vanishing_blocks(n, s, cr, count, seed0):
     """Blocks that are exactly zero on whole chunks: column c lives on two
     chunks, chunk 1 is empty for every column, and odd blocks add the first

@@ -79,7 +79,7 @@ def test_create_rejects_bad_arguments_without_device(lib):
     bad.digit_planes = 2
     assert lib.lo_basis_create(4096, 4, 8, 512, ctypes.byref(bad), None, ctypes.byref(h)) == 1
     lib.lo_options_default(ctypes.byref(bad))
-    bad.test_stall = 2
+    bad.test_stall = 3
     assert lib.lo_basis_create(4096, 4, 8, 512, ctypes.byref(bad), None, ctypes.byref(h)) == 1
 
 
@@ -191,3 +191,10 @@ def test_deflation_option_checks_without_device(lib):
         o.deflation_tol = tol
         assert lib.lo_basis_create(4096, 8, 4, 512, ctypes.byref(o), None, ctypes.byref(h)) == want, (prec, tol)
         assert h.value is None
+
+
+def test_tune_leaf_rejects_bad_arguments_without_device(lib):
+    out1, out2 = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    assert lib.lo_tune_leaf(4096, 4, 8, None, None, None, ctypes.byref(out2)) == 1
+    assert lib.lo_tune_leaf(4096, 4, 8, None, None, ctypes.byref(out1), None) == 1
+    assert lib.lo_tune_leaf(0, 4, 8, None, None, ctypes.byref(out1), ctypes.byref(out2)) == 1
