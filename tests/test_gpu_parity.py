@@ -712,8 +712,10 @@ def test_bounded_wait_expires_with_work_in_flight():
     the loads and MMAs of the first intervals; it waits for those to finish,
     and the step returns LO_ERR_TIMEOUT with the basis unchanged.  The
     context stays usable: the same basis runs a k = 0 step, and a fresh basis
-    the same two steps, matching the oracle."""
-    n, s, cr = 65536, 8, 4096
+    the same two steps, matching the oracle.  2^18 rows: 1024 slab items over
+    the persistent CTAs, so each CTA reaches a third accumulation interval and
+    waits for a released buffer."""
+    n, s, cr = 2 ** 18, 8, 4096
     L = lo()
     W0h, W1h = (I.gaussian(n, s, 7300 + j) for j in range(2))
     W0, W1 = dev(W0h), dev(W1h)
