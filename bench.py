@@ -47,22 +47,30 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flo
 # The translation unit (with the headers it includes) of each kernel whose DRAM
 # traffic was captured: a change to any of these files invalidates the capture.
 KERNEL_TU = {
-    "k_umma_update": ["paper_2204_13393_gb300/csrc/lo_umma.cu", "paper_2204_13393_gb300/csrc/lo_oz_common.cuh",
-                      "paper_2204_13393_gb300/csrc/lo_recombine.h", "paper_2204_13393_gb300/csrc/lo_internal.h",
-                      "include/lo.h"],
+    "tc_step": ["paper_2204_13393_gb300/csrc/lo_umma.cu", "paper_2204_13393_gb300/csrc/lo_ozaki.cu",
+                "paper_2204_13393_gb300/csrc/lo_oz_common.cuh", "paper_2204_13393_gb300/csrc/lo_recombine.h",
+                "paper_2204_13393_gb300/csrc/lo_internal.h", "include/lo.h"],
 }
-# DRAM bytes of one launch of the dominant kernel from one ncu capture (bench.py
-# --case profile: n = 2^20, s = 8, k = 120), with that launch's algorithmic bytes,
-# keyed by (kernel group, precision); "src" is the sha256 prefix of the kernel's
-# translation unit (comments stripped) when the counters were taken.  The
-# reported traffic scales the measured ratio to the average launch of the cycle;
-# a code change in that unit invalidates the entry (traffic: null).
+# DRAM bytes of one step's launches of each kernel group from one ncu capture
+# (bench.py --case profile: n = 2^20, s = 8, k = 120, 8192-row chunks, two local
+# passes), with that group's algorithmic bytes in the same step, keyed by
+# (kernel group, precision); "src" is the sha256 prefix of the translation
+# units (comments stripped) when the counters were taken.  The reported
+# traffic scales the measured ratio to the average launch group of the cycle;
+# a code change in those units invalidates the entry (traffic: null).
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none --profile-from-start off python bench.py --case profile
 TRAFFIC = {
-    # ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-    #     --clock-control none --profile-from-start off -k regex:k_umma_update -s 2 -c 1
-    #     python bench.py --case profile   (the stage-2 k_umma_update<8, 2>, k = 120: 659.4 us)
-    ("update", "fp64_tc"): {"kernel": "k_umma_update", "src": "0d97e169f48f294b",
-                            "dram_bytes": 1955405824 + 129437696, "algorithmic_bytes": 1210056704},
+    # k_oz_coef<8,1,1> + k_umma_update<8,1> (the iterate) + k_umma_gram<8,7> (its Gram), and the
+    # pass-3 launches that exit at once; algorithmic 16nK + 8ns
+    ("refine", "fp64_tc"): {"kernel": "tc_step", "src": "f6537e0efdfb2f5a",
+                            "dram_bytes": 3898086400 + 93840896, "algorithmic_bytes": 2214592512},
+    # k_oz_coef<8,2,1> + k_umma_update<8,2>; algorithmic 8nK + 16ns + 8pKs
+    ("update", "fp64_tc"): {"kernel": "tc_step", "src": "f6537e0efdfb2f5a",
+                            "dram_bytes": 1953551616 + 126891264, "algorithmic_bytes": 1209008128},
+    # k_umma_srcexp<8> + k_umma_gram<8,7> (pass 1); algorithmic 8nK
+    ("gram", "fp64_tc"): {"kernel": "tc_step", "src": "f6537e0efdfb2f5a",
+                          "dram_bytes": 2014402048 + 31204352, "algorithmic_bytes": 1073741824},
 }
 
 
