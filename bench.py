@@ -423,7 +423,7 @@ def run_gpu(args):
                                                   args.warmup, t_local / args.steps, bytes_cycle)}
             basis.close()
             torch.cuda.empty_cache()
-            targets = target_points(lo, torch, dev, args)
+            targets.update(target_points(lo, torch, dev, args))
         out = {
             "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_local / args.steps, 4), "higher_is_better": True,
