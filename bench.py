@@ -1086,10 +1086,10 @@ def run_tsqr_case(args):
 
 
 def target_points(lo, torch, dev, args):
-    """The two measurements the benchmark spec states beside the cycle, on this
-    GPU in this run: the tall-skinny QR at n = 2^24, s = 8 (FP64 target: >= 70 %
-    of the HBM roofline, e_perp <= 1e-12) and the mixed form's speedup over
-    the float64 form at n = 2^24, s = 16, k = 480, kappa <= 1e6."""
+    """The two measurements reported beside the cycle, on the current GPU: the
+    tall-skinny QR at n = 2^24, s = 8 (FP64 target: >= 70 % of the HBM
+    roofline, e_perp <= 1e-12) and the mixed form's speedup over the float64
+    form at n = 2^24, s = 16, k = 480, kappa <= 1e6."""
     hbm, _ = peaks()
     out = {}
     t0 = time.perf_counter()
