@@ -420,12 +420,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
       // loads of global step j (cursor c): the digit planes of the group's prior
-      // panels (all 7: two contiguous runs; the leading ND: one 3D TMA box
-      // that skips the other planes of every group), or a bare arrival when
-      // it has none
+      // panels (all 7: two contiguous runs of the k / 8 - g0 prior column
+      // groups only; the leading ND: one 3D TMA box that skips the other
+      // planes of every group), or a bare arrival when it has none.  Stage
+      // rows of the block's own columns are split in by the producers; rows
+      // past them keep what the stage held and only reach accumulator rows
+      // (columns >= k + S) that the drainers never read.
       auto issue = [&](const GramCursor& c, int j) {
-        const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, gtot - g0);
-        if (k > c.col0 && ng > 0) {
+        const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, k / 8 - g0);
+        if (ng > 0) {
           const int64_t eta = 2 * (int64_t)(c.tile0 + c.st);
           if constexpr (ND == kOzDigits) {
             const uint32_t run = (uint32_t)ng * kOzDigits * 128;
