@@ -47,11 +47,12 @@
 namespace lo {
 namespace {
 
-constexpr int kUmmaThreads = 288;     // 8 worker warps + 1 issuer warp
+constexpr int kUmmaThreads = 288;     // k = 0 kernels: 8 worker warps + 1 issuer warp
 constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (warps 0..7)
-constexpr int kStages = 5;            // TMA ring depth
-constexpr int kDist = 3;              // steps loaded ahead (a stage is refilled once its MMAs are done)
-constexpr int kBBuf = 4;              // steps the producer warps may run ahead of the MMAs
+constexpr int kUmmaKThreads = 320;    // k > 0 kernels: 8 worker warps, a load warp and an MMA warp
+constexpr int kStages = 5;            // ring depth: stages, B buffers and step commits (one index)
+constexpr int kSrcSlots = 4;          // private cp.async slots of a producer thread
+constexpr int kSrcAhead = kSrcSlots - 1;   // steps a producer thread loads ahead
 constexpr int kMixedDigits = 4;       // leading digits of the mixed form's first Gram (8 bits each)
 constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
 constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
@@ -109,6 +110,16 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return false;
   return true;
 }
+// The same, also giving up as soon as another role of the CTA set *abort.
+__device__ __forceinline__ bool mbar_wait_live(uint32_t mb, uint32_t parity, const int* abort) {
+  if (mbar_try(mb, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(mb, parity)) {
+    if (*reinterpret_cast<const volatile int*>(abort)) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t mb) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -162,9 +173,9 @@ __device__ __forceinline__ void tmem_ld(uint32_t ta, uint32_t (&r)[N]) {
 
 // Per-CTA control block at the end of dynamic shared memory.
 struct UmmaCtl {
-  uint64_t full[kStages];   // loads of a stage landed (the issuer arms them every step)
+  uint64_t full[kStages];   // loads of a stage landed (the load warp arms them every step)
   uint64_t ready[kStages];  // the producer warps wrote their part of a step's operands
-  uint64_t mmad[kBBuf];     // MMAs of a step done (commit), by step modulo kBBuf
+  uint64_t mmad[kStages];   // MMAs of a step done (commit): its stage and B buffer are free
   uint64_t empty[2];        // a TMEM accumulator buffer was drained (drainer warp arrivals)
   uint64_t accf[2];         // the last MMAs of an accumulation interval in a buffer are done
   uint32_t tslot;           // TMEM base written by tcgen05.alloc
@@ -285,13 +296,16 @@ struct GramLayout {
   static constexpr int RB = umma_round16(ND * NB);
   static constexpr int STAGE = ND * 4096;                       // [2][16][ND][128 B]
   static constexpr int STG = 0;                                 // kStages stages
-  static constexpr int BBUF = STG + kStages * STAGE;            // kBBuf x RB x 32 B
-  // private cp.async slots (3 steps) of the float64 values a thread splits:
-  // the block's own columns of the A tile (2 S units of 8 rows) and the B
-  // operand (4 NB units of 4 rows)
-  static constexpr int SRCA = BBUF + kBBuf * RB * 32;
-  static constexpr int SRCB = SRCA + 3 * 2 * S * 8 * 8;
-  static constexpr int CTL = SRCB + 3 * 4 * NB * 4 * 8;
+  static constexpr int BBUF = STG + kStages * STAGE;            // kStages x RB x 32 B
+  // private cp.async slots (kSrcSlots steps) of the float64 values a thread
+  // splits, and of the exponent it splits them against: the block's own
+  // columns of the A tile (2 S units of 8 rows) and the B operand (4 NB
+  // units of 4 rows)
+  static constexpr int SRCA = BBUF + kStages * RB * 32;
+  static constexpr int SRCB = SRCA + kSrcSlots * 2 * S * 8 * 8;
+  static constexpr int EXA = SRCB + kSrcSlots * 4 * NB * 4 * 8;
+  static constexpr int EXB = EXA + kSrcSlots * 2 * S * 4;
+  static constexpr int CTL = EXB + kSrcSlots * 4 * NB * 4;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
 };
 
@@ -331,9 +345,14 @@ struct GramCursor {
 // The role of a thread of the persistent k > 0 kernels: warps 0..3 split the
 // pass block into the operands of each step (producers), warps 4..7 read the
 // accumulators of each finished interval back from TMEM (drainers), lane 0
-// of warp 8 issues the loads and MMAs.  Producers run up to kBBuf steps ahead
-// of the MMAs and never wait for a drain; drainers wait on accf, a commit of
-// the interval's last MMAs into that TMEM buffer.
+// of warp 8 issues the loads of each step as soon as its stage is free (load
+// warp) and lane 0 of warp 9 issues its MMAs (MMA warp).  One thread issuing
+// both spent about 2000 cycles per step on the serial chain of barrier waits,
+// copy and MMA instructions; split, the two chains overlap.  mmad[s], the
+// commit of a step's MMAs, frees its stage (for the load warp) and its B
+// buffer (for the producers); no role runs more than kStages steps ahead of
+// the MMAs, so no barrier is waited on more than one phase late.  Drainers
+// wait on accf, a commit of the interval's last MMAs into that TMEM buffer.
 
 // Whether step st (of nsteps in its item) closes an accumulation interval:
 // exact float32 sums cover 16 steps.
@@ -362,7 +381,7 @@ __device__ __noinline__ void gram_op_values(const StepArgs& a, int64_t row0, int
 }
 
 template <int S, int ND>
-__global__ void __launch_bounds__(kUmmaThreads, 1)
+__global__ void __launch_bounds__(kUmmaKThreads, 1)
     k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass, const __grid_constant__ CUtensorMap tm) {
   using L = GramLayout<S, ND>;
   constexpr int NB = L::NB, RB = L::RB, NSPL = L::NSPL, NACC = umma_nacc(NB, ND), STAGE = L::STAGE;
@@ -383,7 +402,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       mbar_init(full0 + 8 * i, 1);
       mbar_init(ready0 + 8 * i, 4);
     }
-    for (int i = 0; i < kBBuf; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(empty0 + 8 * i, 4);
       mbar_init(accf0 + 8 * i, 1);
@@ -397,7 +416,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if constexpr (RB > ND * NB) {  // B pad rows stay zero
-    for (int i = tid; i < kBBuf * (RB - ND * NB) * 2; i += kUmmaThreads) {
+    for (int i = tid; i < kStages * (RB - ND * NB) * 2; i += kUmmaKThreads) {
       const int h = i & 1, rest = i >> 1, r = ND * NB + rest % (RB - ND * NB), bb = rest / (RB - ND * NB);
       *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
           make_uint4(0u, 0u, 0u, 0u);
@@ -410,15 +429,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   const uint32_t tbase = ctl.tslot;
 
   if (warp == 8) {
-    // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
-    // (the test hook withholds all of it: every bounded wait then expires)
+    // ---- load warp: the digit planes of each step once its stage is free ----
+    // (the test hook withholds the loads and the MMAs: every bounded wait
+    // then expires)
     if (lane == 0 && a.test_stall != 1) {
-      uint32_t idesc[ND];
-#pragma unroll
-      for (int t = 1; t <= ND; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB, ND), 0, 0);
-      // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
-      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
-      const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
       // loads of global step j (cursor c): the digit planes of the group's prior
       // panels (all 7: two contiguous runs of the k / 8 - g0 prior column
       // groups only; the leading ND: one 3D TMA box that skips the other
@@ -445,52 +459,70 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           mbar_arrive(full0 + 8 * sj);
         }
       };
-      GramCursor ld, cur;
+      GramCursor ld;
       ld.start(a, nitems, ngroups);
+      int issued = 0;
+      for (; ld.valid; ++issued, ld.next(a, nitems, ngroups)) {
+        const int sj = issued % kStages;
+        // the stage last served step issued - kStages
+        if (issued >= kStages &&
+            !mbar_wait_live(mmad0 + 8 * sj, (uint32_t)(((issued - kStages) / kStages) & 1), &ctl.abort)) {
+          umma_timeout(ctl, a.flags);
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&ctl.abort)) break;
+        issue(ld, issued);
+      }
+      // the copies in flight land before the CTA's memory is released (the
+      // last load into each stage: no later phase exists)
+      for (int j = issued > kStages ? issued - kStages : 0; j < issued; ++j)
+        mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 9) {
+    // ---- MMA warp: one MMA group per step -------------------------------------
+    if (lane == 0 && a.test_stall != 1) {
+      uint32_t idesc[ND];
+#pragma unroll
+      for (int t = 1; t <= ND; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB, ND), 0, 0);
+      // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
+      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
+      const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
+      GramCursor cur;
       cur.start(a, nitems, ngroups);
-      int issued = 0, landed = 0, intervals = 0;
+      int intervals = 0;
       int64_t committed = -1;
-      for (; issued < kDist && ld.valid; ++issued, ld.next(a, nitems, ngroups)) issue(ld, issued);
       for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-        const int s = g % kStages, bb = g % kBBuf;
-        bool ok = true;
-        // the stage of global step g + kDist last served step g - 2
-        if (g >= 2) ok = mbar_wait(mmad0 + 8 * ((g - 2) % kBBuf), (uint32_t)(((g - 2) / kBBuf) & 1));
-        if (ok && ld.valid) {
-          issue(ld, issued++);
-          ld.next(a, nitems, ngroups);
-        }
-        if (ok) {
-          ok = mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1));
-          if (ok) landed = g + 1;
-        }
-        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((g / kStages) & 1));
+        const int s = g % kStages;
+        const uint32_t par = (uint32_t)((g / kStages) & 1);
+        bool ok = mbar_wait_live(full0 + 8 * s, par, &ctl.abort);
+        if (ok) ok = mbar_wait_live(ready0 + 8 * s, par, &ctl.abort);
         if ((cur.st & 15) == 0) {  // a new accumulation interval: its buffer must be drained
           const int b = intervals % NACC;
-          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1));
+          if (ok && intervals >= NACC)
+            ok = mbar_wait_live(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1), &ctl.abort);
           ++intervals;
         }
         const int buf = (intervals - 1) % NACC;
-        if (!ok || ctl.abort) {
+        if (!ok || *reinterpret_cast<volatile int*>(&ctl.abort)) {
           umma_timeout(ctl, a.flags);
           break;
         }
         tc_fence_after();
-        const uint64_t db = dB0 + (uint64_t)((bb * (RB * 32)) >> 4);
+        const uint64_t db = dB0 + (uint64_t)((s * (RB * 32)) >> 4);
         const uint32_t accum = (cur.st & 15) ? 1u : 0u;
 #pragma unroll
         for (int t = 1; t <= ND; ++t) {
           const uint64_t da = dA0 + (uint64_t)((s * STAGE + (t - 1) * 128) >> 4);
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB, ND)), da, db, idesc[t - 1], accum);
         }
-        umma_commit(mmad0 + 8 * bb);
+        umma_commit(mmad0 + 8 * s);
         if (interval_end(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
-      // what is still in flight completes before the CTA's memory is released
-      for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+      // the MMAs in flight complete before the CTA's memory is released
       if (committed >= 0)
-        mbar_wait(mmad0 + 8 * (int)(committed % kBBuf), (uint32_t)((committed / kBBuf) & 1));
+        mbar_wait(mmad0 + 8 * (int)(committed % kStages), (uint32_t)((committed / kStages) & 1));
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -498,29 +530,37 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     // threads 0 .. 2S - 1 split the block's own columns into the A tile
     // (column l = tid / 2, rows 8 (tid % 2) .. + 7; only in the group that
     // holds them); threads 64 .. 64 + 4 NB - 1 split the B operand (column
-    // n, rows 4 q .. 4 q + 3) into B buffer g % kBBuf
+    // n, rows 4 q .. 4 q + 3) into B buffer g % kStages.  Each thread's
+    // values and the slab exponent it splits them against arrive by cp.async
+    // kSrcAhead steps ahead.
     const int al = tid >> 1, ah = tid & 1;
     const int bi = tid - 64;
     const bool b_role = bi >= 0 && bi < 4 * NB;
     const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
     double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (tid < 2 * S ? tid : 0) * 8;
     double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + (b_role ? bi : 0) * 4;
+    int* ea_slot = reinterpret_cast<int*>(sm + L::EXA) + (tid < 2 * S ? tid : 0);
+    int* eb_slot = reinterpret_cast<int*>(sm + L::EXB) + (b_role ? bi : 0);
     auto is_asrc = [&](const GramCursor& c) {
       const int am = k - c.col0 + al;
       return tid < 2 * S && am >= 0 && am < 128;
     };
-    // the float64 values this thread splits in global step j (cursor c), into slot j % 3
+    // the float64 values this thread splits in global step j (cursor c), and
+    // their exponent, into slot j % kSrcSlots
     auto load_src = [&](const GramCursor& c, int j) {
       if (c.valid) {
-        const int r0 = c.st * 16;
+        const int r0 = c.st * 16, sl = j % kSrcSlots;
+        const int* hs = a.srcexp_slab + (int64_t)c.slab * 32;
+        if (is_asrc(c)) cp_async4(ea_slot + sl * 2 * S, hs + al);
+        if (b_role) cp_async4(eb_slot + sl * 4 * NB, hs + c.z * NB + bn);
         if (a.op_nx) {
           // the operator's block, formed from its input (off the hot loop: the
           // stencil's index arithmetic stays out of the common path)
           gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, is_asrc(c), al, ah,
-                         xa_slot + (j % 3) * 2 * S * 8, b_role, bq, bn, xb_slot + (j % 3) * 4 * NB * 4);
+                         xa_slot + sl * 2 * S * 8, b_role, bq, bn, xb_slot + sl * 4 * NB * 4);
         } else {
           if (is_asrc(c)) {
-            double* d = xa_slot + (j % 3) * 2 * S * 8;
+            double* d = xa_slot + sl * 2 * S * 8;
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
               const int row = r0 + 8 * ah + r;
@@ -529,7 +569,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
             }
           }
           if (b_role) {
-            double* d = xb_slot + (j % 3) * 4 * NB * 4;
+            double* d = xb_slot + sl * 4 * NB * 4;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int row = r0 + 4 * bq + r;
@@ -544,34 +584,41 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
     GramCursor ahead, cur;
     ahead.start(a, nitems, ngroups);
     cur.start(a, nitems, ngroups);
-    load_src(ahead, 0);
-    ahead.next(a, nitems, ngroups);
-    load_src(ahead, 1);
-    ahead.next(a, nitems, ngroups);
-    for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-      const int s = g % kStages, bb = g % kBBuf;
-      load_src(ahead, g + 2);
+#pragma unroll
+    for (int j = 0; j < kSrcAhead; ++j) {
+      load_src(ahead, j);
       ahead.next(a, nitems, ngroups);
-      asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
-      // MMAs of step g - kBBuf done: B buffer bb is free (and no warp runs further ahead)
-      if (g >= kBBuf && !ctl.abort && !mbar_wait(mmad0 + 8 * bb, (uint32_t)(((g - kBBuf) / kBBuf) & 1)))
+    }
+    for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
+      const int s = g % kStages, sl = g % kSrcSlots;
+      load_src(ahead, g + kSrcAhead);
+      ahead.next(a, nitems, ngroups);
+      static_assert(kSrcAhead == 3, "cp.async.wait_group count");
+      asm volatile("cp.async.wait_group 3;" ::: "memory");   // this thread's values of step g
+      // MMAs of step g - kStages done: B buffer and stage s are free (and no
+      // warp runs further ahead)
+      if (g >= kStages && !ctl.abort &&
+          !mbar_wait_live(mmad0 + 8 * s, (uint32_t)(((g - kStages) / kStages) & 1), &ctl.abort))
         umma_timeout(ctl, a.flags);
       unsigned char* stage = sm + L::STG + s * STAGE;
       if (is_asrc(cur)) {
         const int am = k - cur.col0 + al;
-        if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
-        split8_store<ND>(xa_slot + (g % 3) * 2 * S * 8, a.srcexp_slab[(int64_t)cur.slab * 32 + al],
+        // the 7-plane loads never cover the block's own columns; the leading-
+        // digit box does, so its producers write only after it landed
+        if (ND != kOzDigits && !ctl.abort && !mbar_wait_live(full0 + 8 * s, (uint32_t)((g / kStages) & 1), &ctl.abort))
+          umma_timeout(ctl, a.flags);
+        split8_store<ND>(xa_slot + sl * 2 * S * 8, ea_slot[sl * 2 * S],
                          stage + ah * (STAGE / 2) + (am >> 3) * (ND * 128) + (am & 7) * 16, 128, a.flags);
       }
       if (b_role) {
         unsigned h[4], l[4], gg[4];
         bool bad = false;
-        const int e = a.srcexp_slab[(int64_t)cur.slab * 32 + cur.z * NB + bn];
-        const double* x = xb_slot + (g % 3) * 4 * NB * 4;
+        const int e = eb_slot[sl * 4 * NB];
+        const double* x = xb_slot + sl * 4 * NB * 4;
 #pragma unroll
         for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], gg[r]);
         if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-        unsigned char* bbuf = sm + L::BBUF + bb * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
+        unsigned char* bbuf = sm + L::BBUF + s * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
 #pragma unroll
         for (int u = 1; u <= ND; ++u) {
           const int row = (u - 1) * NB + bn;
@@ -702,7 +749,7 @@ struct UpdCursor {
 };
 
 template <int S, int NOUT, bool APPLY = false>
-__global__ void __launch_bounds__(kUmmaThreads, 1)
+__global__ void __launch_bounds__(kUmmaKThreads, 1)
     k_umma_update(StepArgs a, const double* src_fixed, int64_t lds_fixed, int pass,
                   const __grid_constant__ CUtensorMap tm) {
   using L = UpdLayout<S, NOUT>;
@@ -734,7 +781,7 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       mbar_init(full0 + 8 * i, 1);
       mbar_init(ready0 + 8 * i, 4);
     }
-    for (int i = 0; i < kBBuf; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(empty0 + 8 * i, 4);
       mbar_init(accf0 + 8 * i, 1);
@@ -758,13 +805,8 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   };
 
   if (warp == 8) {
-    // ---- issuer: loads kDist steps ahead, one MMA group per step -----------
+    // ---- load warp: each step's planes and coefficient image once its stage is free
     if (lane == 0) {
-      uint32_t idesc[kOzDigits];
-#pragma unroll
-      for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 1, 0);
-      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kOzDigits * 128, 2 * kOzDigits * 128);
-      const uint64_t dB0 = umma_sdesc(su32(sm + L::BST), 128, 256);
       // loads of global step j (cursor c): the digit planes of its prior
       // columns (TMA) and its coefficient image (bulk copy), on full[j % kStages]
       auto issue = [&](const UpdCursor& c, int j) {
@@ -780,33 +822,50 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         bulk_load(su32(sm + L::BST + sj * umma_round16(BIMG / 16) * 16), img + (int64_t)(zj * KSMAX + ks) * BIMG,
                   BIMG, full0 + 8 * sj);
       };
-      UpdCursor ld, cur;
+      UpdCursor ld;
       ld.start(a, per_tile);
+      int issued = 0;
+      for (; ld.valid; ++issued, ld.next(a, per_tile)) {
+        const int sj = issued % kStages;
+        // the stage last served step issued - kStages
+        if (issued >= kStages &&
+            !mbar_wait_live(mmad0 + 8 * sj, (uint32_t)(((issued - kStages) / kStages) & 1), &ctl.abort)) {
+          umma_timeout(ctl, a.flags);
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&ctl.abort)) break;
+        issue(ld, issued);
+      }
+      // the copies in flight land before the CTA's memory is released
+      for (int j = issued > kStages ? issued - kStages : 0; j < issued; ++j)
+        mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+    }
+    __syncwarp();
+  } else if (warp == 9) {
+    // ---- MMA warp: one MMA group per step -------------------------------------
+    if (lane == 0) {
+      uint32_t idesc[kOzDigits];
+#pragma unroll
+      for (int t = 1; t <= kOzDigits; ++t) idesc[t - 1] = umma_idesc(128, umma_nt(t, NB), 1, 0);
+      const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), kOzDigits * 128, 2 * kOzDigits * 128);
+      const uint64_t dB0 = umma_sdesc(su32(sm + L::BST), 128, 256);
+      UpdCursor cur;
       cur.start(a, per_tile);
-      int issued = 0, landed = 0, intervals = 0;
+      int intervals = 0;
       int64_t committed = -1;
-      for (; issued < kDist && ld.valid; ++issued, ld.next(a, per_tile)) issue(ld, issued);
       for (int g = 0; cur.valid; ++g, cur.next(a, per_tile)) {
         const int s = g % kStages, ks = cur.st % KS;
-        bool ok = true;
-        // the stage of global step g + kDist last served step g - 2
-        if (g >= 2) ok = mbar_wait(mmad0 + 8 * ((g - 2) % kBBuf), (uint32_t)(((g - 2) / kBBuf) & 1));
-        if (ok && ld.valid) {
-          issue(ld, issued++);
-          ld.next(a, per_tile);
-        }
-        if (ok) {
-          ok = mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1));
-          if (ok) landed = g + 1;
-        }
-        if (ok) ok = mbar_wait(ready0 + 8 * s, (uint32_t)((g / kStages) & 1));
+        const uint32_t par = (uint32_t)((g / kStages) & 1);
+        bool ok = mbar_wait_live(full0 + 8 * s, par, &ctl.abort);
+        if (ok) ok = mbar_wait_live(ready0 + 8 * s, par, &ctl.abort);
         if ((ks & 15) == 0) {  // a new accumulation interval: its buffer must be drained
           const int b = intervals % NACC;
-          if (ok && intervals >= NACC) ok = mbar_wait(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1));
+          if (ok && intervals >= NACC)
+            ok = mbar_wait_live(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1), &ctl.abort);
           ++intervals;
         }
         const int buf = (intervals - 1) % NACC;
-        if (!ok || ctl.abort) {
+        if (!ok || *reinterpret_cast<volatile int*>(&ctl.abort)) {
           umma_timeout(ctl, a.flags);
           break;
         }
@@ -818,13 +877,12 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
           const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
-        umma_commit(mmad0 + 8 * (g % kBBuf));
+        umma_commit(mmad0 + 8 * s);
         if (closes(cur)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
-      for (int j = landed; j < issued; ++j) mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
       if (committed >= 0)
-        mbar_wait(mmad0 + 8 * (int)(committed % kBBuf), (uint32_t)((committed / kBBuf) & 1));
+        mbar_wait(mmad0 + 8 * (int)(committed % kStages), (uint32_t)((committed / kStages) & 1));
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -865,12 +923,13 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       load_src(ahead, g + 2);
       ahead.next(a, per_tile);
       asm volatile("cp.async.wait_group 2;" ::: "memory");   // this thread's values of step g
-      // no warp runs more than kBBuf steps ahead of the MMAs
-      if (g >= kBBuf && !ctl.abort &&
-          !mbar_wait(mmad0 + 8 * (g % kBBuf), (uint32_t)(((g - kBBuf) / kBBuf) & 1)))
+      // no warp runs more than kStages steps ahead of the MMAs
+      if (g >= kStages && !ctl.abort &&
+          !mbar_wait_live(mmad0 + 8 * s, (uint32_t)(((g - kStages) / kStages) & 1), &ctl.abort))
         umma_timeout(ctl, a.flags);
       if (q >= k) {  // the block's own columns, or zeros past Kt, once the stage's loads landed
-        if (!ctl.abort && !mbar_wait(full0 + 8 * s, (uint32_t)((g / kStages) & 1))) umma_timeout(ctl, a.flags);
+        if (!ctl.abort && !mbar_wait_live(full0 + 8 * s, (uint32_t)((g / kStages) & 1), &ctl.abort))
+          umma_timeout(ctl, a.flags);
         unsigned char* stage = sm + L::STG + s * kStageBytes;
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -1567,7 +1626,7 @@ cudaError_t umma_gram_for(const StepArgs& a, int pass, cudaStream_t st) {
   // the pass block's exponents per slab: from a small pass over W for pass 1,
   // from the reiteration's assembly (k_umma_update<S, 1>) afterwards
   if (pass == 1) k_umma_srcexp<S><<<a.nslab, 256, 0, st>>>(a, src, lds);
-  k_umma_gram<S, ND><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram_lead);
+  k_umma_gram<S, ND><<<grid, kUmmaKThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->gram_lead);
   return cudaGetLastError();
 }
 
@@ -1581,7 +1640,7 @@ cudaError_t umma_update_for(const StepArgs& a, int pass, cudaStream_t st) {
     src = (pass == 2) ? a.W : a.V + (int64_t)a.nb * a.n * S;
     lds = (pass == 2) ? a.ldw : S;
   }
-  k_umma_update<S, NOUT><<<grid, kUmmaThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->upd);
+  k_umma_update<S, NOUT><<<grid, kUmmaKThreads, L::BYTES, st>>>(a, src, lds, pass, a.maps->upd);
   return cudaGetLastError();
 }
 
@@ -1646,7 +1705,7 @@ cudaError_t umma_apply_for(const StepArgs& a0, const double* C, int64_t ldc, int
   for (int n0 = 0; n0 < m; n0 += S) {
     a.apply_n0 = n0;
     k_apply_coef<S><<<a.p, 256, apply_coef_smem<S>(a0.nb * S), st>>>(a, C, ldc);
-    k_umma_update<S, 1, true><<<grid, kUmmaThreads, L::BYTES, st>>>(a, last, S, 0, a.maps->upd);
+    k_umma_update<S, 1, true><<<grid, kUmmaKThreads, L::BYTES, st>>>(a, last, S, 0, a.maps->upd);
   }
   return cudaGetLastError();
 }

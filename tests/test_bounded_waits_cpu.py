@@ -12,6 +12,8 @@ CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
 # the while loops of the sources, reviewed: (file, loop text)
 REVIEWED_WHILE = {
     ("lo_umma.cu", "while (!mbar_try(mb, parity))"),   # bounded by clock64() - t0 > kWaitCycles
+    # the same wait, which also returns when another role of the CTA set its abort word
+    ("lo_umma.cu", "while (!mbar_try(mb, parity)) {"),
     ("lo_api.cu", "while (c0 < Kmax) c0 *= 2;"),        # host: chunk-size candidates
     # host: the Householder sub-tile rows, halving from 2^14 (at most 14 steps)
     ("lo_internal.h", "while (T > s && (int64_t)(T + s) * s * 8 > kHHTileBytes) T >>= 1;"),
@@ -57,14 +59,18 @@ def test_mbarrier_wait_is_bounded_and_the_only_try_wait():
     text = dict(sources())["lo_umma.cu"]
     body = re.search(r"bool mbar_wait\(uint32_t mb, uint32_t parity\) \{(.*?)\n\}", text, re.S).group(1)
     assert "clock64() - t0 > kWaitCycles" in body and "return false" in body
+    live = re.search(r"bool mbar_wait_live\(uint32_t mb, uint32_t parity, const int\* abort\) \{(.*?)\n\}", text,
+                     re.S).group(1)
+    assert "clock64() - t0 > kWaitCycles) return false;" in live and "abort)) return false;" in live
     assert re.search(r"constexpr long long kWaitCycles = \d+ll;", text)
     for fn, t in sources():
         hits = [l for l in code_lines(t) if "try_wait" in l]
         assert len(hits) == (1 if fn == "lo_umma.cu" else 0), (fn, hits)
         calls = [l for l in code_lines(t) if "mbar_try(" in l and "bool mbar_try(" not in l]
-        want = (["if (mbar_try(mb, parity)) return true;", "while (!mbar_try(mb, parity))"]
+        want = (["if (mbar_try(mb, parity)) return true;", "while (!mbar_try(mb, parity))",
+                 "if (mbar_try(mb, parity)) return true;", "while (!mbar_try(mb, parity)) {"]
                 if fn == "lo_umma.cu" else [])
-        assert calls == want, (fn, calls)  # mbar_try only inside the bounded mbar_wait
+        assert calls == want, (fn, calls)  # mbar_try only inside the two bounded waits
 
 
 def test_batch_flag_wait_is_bounded():
