@@ -232,6 +232,33 @@ __device__ __forceinline__ void split8_store(const double* x, int e, unsigned ch
     *reinterpret_cast<uint4*>(dst + t * plane) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
 }
 
+// Split V (1, 2 or 4) consecutive values of one column against exponent e and
+// store the fp16 digits of the first ND planes: per plane the V values as
+// consecutive 2-byte entries at dst + (t - 1) * stride.
+template <int V, int ND>
+__device__ __forceinline__ void split_rows_store(const double* x, int e, unsigned char* dst, int stride, int* flags) {
+  static_assert(V == 1 || V == 2 || V == 4, "split_rows_store: 1, 2 or 4 values");
+  unsigned h[V], l[V], g[V];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < V; ++i) bad |= oz_split(x[i], e, h[i], l[i], g[i]);
+  if (bad) oz_status(flags, LO_ERR_NONFINITE);
+#pragma unroll
+  for (int t = 1; t <= ND; ++t) {
+    unsigned char* d = dst + (t - 1) * stride;
+    if constexpr (V == 1) {
+      const unsigned w = t <= 3 ? h[0] : l[0];
+      const unsigned digit = (w >> (8 * (t <= 3 ? 3 - t : 7 - t))) & 0xFFu;
+      *reinterpret_cast<unsigned short*>(d) = (unsigned short)((g[0] >> 16) | digit);
+    } else if constexpr (V == 2) {
+      *reinterpret_cast<unsigned*>(d) = oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
+    } else {
+      *reinterpret_cast<uint2*>(d) = make_uint2(oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]),
+                                                oz_pack(t, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]));
+    }
+  }
+}
+
 // Digit planes of the new panel (slot nb) of one slab, once stage 2 has fixed
 // the panel's column exponents.  One thread per (16-row tile, column): 16
 // values, 7 planes of two 16-byte core-matrix rows each.  Whole CTA (256

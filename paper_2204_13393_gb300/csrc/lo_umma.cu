@@ -51,7 +51,7 @@ constexpr int kUmmaThreads = 288;     // k = 0 kernels: 8 worker warps + 1 issue
 constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (warps 0..7)
 constexpr int kUmmaKThreads = 320;    // k > 0 kernels: 8 worker warps, a load warp and an MMA warp
 constexpr int kStages = 5;            // ring depth: stages, B buffers and step commits (one index)
-constexpr int kSrcSlots = 4;          // private cp.async slots of a producer thread
+constexpr int kSrcSlots = 6;          // private cp.async slots of a producer thread
 constexpr int kSrcAhead = kSrcSlots - 1;   // steps a producer thread loads ahead
 constexpr int kMixedDigits = 4;       // leading digits of the mixed form's first Gram (8 bits each)
 constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
@@ -297,15 +297,16 @@ struct GramLayout {
   static constexpr int STAGE = ND * 4096;                       // [2][16][ND][128 B]
   static constexpr int STG = 0;                                 // kStages stages
   static constexpr int BBUF = STG + kStages * STAGE;            // kStages x RB x 32 B
-  // private cp.async slots (kSrcSlots steps) of the float64 values a thread
-  // splits, and of the exponent it splits them against: the block's own
-  // columns of the A tile (2 S units of 8 rows) and the B operand (4 NB
-  // units of 4 rows)
+  // private cp.async slots (kSrcSlots steps) of the float64 values each of
+  // the 128 producer threads splits, and of the exponents it splits them
+  // against: VA values of the block's own columns (the A tile: S x 16 per
+  // step) and VB values of the B operand (NB x 16 per step)
+  static constexpr int VA = S / 8, VB = NB / 8;
   static constexpr int SRCA = BBUF + kStages * RB * 32;
-  static constexpr int SRCB = SRCA + kSrcSlots * 2 * S * 8 * 8;
-  static constexpr int EXA = SRCB + kSrcSlots * 4 * NB * 4 * 8;
-  static constexpr int EXB = EXA + kSrcSlots * 2 * S * 4;
-  static constexpr int CTL = EXB + kSrcSlots * 4 * NB * 4;
+  static constexpr int SRCB = SRCA + kSrcSlots * 128 * VA * 8;
+  static constexpr int EXA = SRCB + kSrcSlots * 128 * VB * 8;
+  static constexpr int EXB = EXA + kSrcSlots * 128 * 4;
+  static constexpr int CTL = EXB + kSrcSlots * 128 * 4;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
 };
 
@@ -359,25 +360,25 @@ struct GramCursor {
 __device__ __forceinline__ bool interval_end(int st, int nsteps) { return ((st + 1) & 15) == 0 || st + 1 == nsteps; }
 
 // The values a Gram producer thread loads for one step when the pass block is
-// the step's operator applied to its input: rows r0 + 8 ah .. + 7 of column
-// al (A tile) and rows r0 + 4 bq .. + 3 of column n0 + bn (B operand); the
-// first column group also keeps the latter in U for the later passes.
+// the step's operator applied to its input: rows r0 + ar0 .. + va - 1 of
+// column al (A tile) and rows r0 + br0 .. + vb - 1 of column n0 + bn (B
+// operand); the first column group also keeps the latter in U for the later
+// passes.
 __device__ __noinline__ void gram_op_values(const StepArgs& a, int64_t row0, int rows, int r0, int col0, int n0,
-                                            bool asrc, int al, int ah, double* da, bool brole, int bq, int bn,
+                                            bool asrc, int al, int ar0, int va, double* da, int bn, int br0, int vb,
                                             double* db) {
   if (asrc)
-    for (int r = 0; r < 8; ++r) {
-      const int row = r0 + 8 * ah + r;
-      da[r] = row < rows ? op_value(a, row0 + row, al) : 0.0;
+    for (int i = 0; i < va; ++i) {
+      const int row = r0 + ar0 + i;
+      da[i] = row < rows ? op_value(a, row0 + row, al) : 0.0;
     }
-  if (brole)
-    for (int r = 0; r < 4; ++r) {
-      const int row = r0 + 4 * bq + r;
-      const bool ok = row < rows;
-      const double v = ok ? op_value(a, row0 + row, n0 + bn) : 0.0;
-      db[r] = v;
-      if (ok && col0 == 0) a.U[(row0 + row) * a.ldu + n0 + bn] = v;
-    }
+  for (int i = 0; i < vb; ++i) {
+    const int row = r0 + br0 + i;
+    const bool ok = row < rows;
+    const double v = ok ? op_value(a, row0 + row, n0 + bn) : 0.0;
+    db[i] = v;
+    if (ok && col0 == 0) a.U[(row0 + row) * a.ldu + n0 + bn] = v;
+  }
 }
 
 template <int S, int ND>
@@ -527,55 +528,52 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     __syncwarp();
   } else if (warp < 4) {
     // ---- producers (warps 0..3) -----------------------------------------------
-    // threads 0 .. 2S - 1 split the block's own columns into the A tile
-    // (column l = tid / 2, rows 8 (tid % 2) .. + 7; only in the group that
-    // holds them); threads 64 .. 64 + 4 NB - 1 split the B operand (column
-    // n, rows 4 q .. 4 q + 3) into B buffer g % kStages.  Each thread's
-    // values and the slab exponent it splits them against arrive by cp.async
-    // kSrcAhead steps ahead.
-    const int al = tid >> 1, ah = tid & 1;
-    const int bi = tid - 64;
-    const bool b_role = bi >= 0 && bi < 4 * NB;
-    const int bn = b_role ? bi % NB : 0, bq = b_role ? bi / NB : 0;
-    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + (tid < 2 * S ? tid : 0) * 8;
-    double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + (b_role ? bi : 0) * 4;
-    int* ea_slot = reinterpret_cast<int*>(sm + L::EXA) + (tid < 2 * S ? tid : 0);
-    int* eb_slot = reinterpret_cast<int*>(sm + L::EXB) + (b_role ? bi : 0);
+    // every thread splits VA rows a_r0 .. of the block's own column a_l into
+    // the A tile (only in the column group that holds them) and VB rows b_r0
+    // .. of column z NB + b_n into B buffer g % kStages.  Its values and the
+    // slab exponents it splits them against arrive by cp.async kSrcAhead steps
+    // ahead.
+    constexpr int VA = L::VA, VB = L::VB;
+    const int a_l = tid / (16 / VA), a_r0 = (tid % (16 / VA)) * VA;
+    const int b_n = tid / (16 / VB), b_r0 = (tid % (16 / VB)) * VB;
+    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + tid * VA;
+    double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + tid * VB;
+    int* ea_slot = reinterpret_cast<int*>(sm + L::EXA) + tid;
+    int* eb_slot = reinterpret_cast<int*>(sm + L::EXB) + tid;
     auto is_asrc = [&](const GramCursor& c) {
-      const int am = k - c.col0 + al;
-      return tid < 2 * S && am >= 0 && am < 128;
+      const int am = k - c.col0 + a_l;
+      return am >= 0 && am < 128;
     };
     // the float64 values this thread splits in global step j (cursor c), and
-    // their exponent, into slot j % kSrcSlots
+    // their exponents, into slot j % kSrcSlots
     auto load_src = [&](const GramCursor& c, int j) {
       if (c.valid) {
         const int r0 = c.st * 16, sl = j % kSrcSlots;
         const int* hs = a.srcexp_slab + (int64_t)c.slab * 32;
-        if (is_asrc(c)) cp_async4(ea_slot + sl * 2 * S, hs + al);
-        if (b_role) cp_async4(eb_slot + sl * 4 * NB, hs + c.z * NB + bn);
+        const bool asrc = is_asrc(c);
+        if (asrc) cp_async4(ea_slot + sl * 128, hs + a_l);
+        cp_async4(eb_slot + sl * 128, hs + c.z * NB + b_n);
         if (a.op_nx) {
           // the operator's block, formed from its input (off the hot loop: the
           // stencil's index arithmetic stays out of the common path)
-          gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, is_asrc(c), al, ah,
-                         xa_slot + sl * 2 * S * 8, b_role, bq, bn, xb_slot + sl * 4 * NB * 4);
+          gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, asrc, a_l, a_r0, VA, xa_slot + sl * 128 * VA,
+                         b_n, b_r0, VB, xb_slot + sl * 128 * VB);
         } else {
-          if (is_asrc(c)) {
-            double* d = xa_slot + sl * 2 * S * 8;
+          if (asrc) {
+            double* d = xa_slot + sl * 128 * VA;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-              const int row = r0 + 8 * ah + r;
+            for (int i = 0; i < VA; ++i) {
+              const int row = r0 + a_r0 + i;
               const bool ok = row < c.rows;
-              cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + al, ok);
+              cp_async8(d + i, src + (c.row0 + (ok ? row : 0)) * lds + a_l, ok);
             }
           }
-          if (b_role) {
-            double* d = xb_slot + sl * 4 * NB * 4;
+          double* d = xb_slot + sl * 128 * VB;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int row = r0 + 4 * bq + r;
-              const bool ok = row < c.rows;
-              cp_async8(d + r, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + bn, ok);
-            }
+          for (int i = 0; i < VB; ++i) {
+            const int row = r0 + b_r0 + i;
+            const bool ok = row < c.rows;
+            cp_async8(d + i, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + b_n, ok);
           }
         }
       }
@@ -589,12 +587,13 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       load_src(ahead, j);
       ahead.next(a, nitems, ngroups);
     }
+    // B buffer position of rows b_r0 .. of column b_n (digit 1; the planes are NB * 32 bytes apart)
+    const int b_off = (b_n & 7) * 16 + (b_n >> 3) * 256 + (b_r0 & 7) * 2 + (b_r0 >> 3) * 128;
     for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
       const int s = g % kStages, sl = g % kSrcSlots;
       load_src(ahead, g + kSrcAhead);
       ahead.next(a, nitems, ngroups);
-      static_assert(kSrcAhead == 3, "cp.async.wait_group count");
-      asm volatile("cp.async.wait_group 3;" ::: "memory");   // this thread's values of step g
+      asm volatile("cp.async.wait_group %0;" ::"n"(kSrcAhead) : "memory");   // this thread's values of step g
       // MMAs of step g - kStages done: B buffer and stage s are free (and no
       // warp runs further ahead)
       if (g >= kStages && !ctl.abort &&
@@ -602,31 +601,18 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         umma_timeout(ctl, a.flags);
       unsigned char* stage = sm + L::STG + s * STAGE;
       if (is_asrc(cur)) {
-        const int am = k - cur.col0 + al;
+        const int am = k - cur.col0 + a_l;
         // the 7-plane loads never cover the block's own columns; the leading-
         // digit box does, so its producers write only after it landed
         if (ND != kOzDigits && !ctl.abort && !mbar_wait_live(full0 + 8 * s, (uint32_t)((g / kStages) & 1), &ctl.abort))
           umma_timeout(ctl, a.flags);
-        split8_store<ND>(xa_slot + sl * 2 * S * 8, ea_slot[sl * 2 * S],
-                         stage + ah * (STAGE / 2) + (am >> 3) * (ND * 128) + (am & 7) * 16, 128, a.flags);
+        split_rows_store<VA, ND>(xa_slot + sl * 128 * VA, ea_slot[sl * 128],
+                                 stage + (a_r0 >> 3) * (STAGE / 2) + (am >> 3) * (ND * 128) + (am & 7) * 16 +
+                                     (a_r0 & 7) * 2,
+                                 128, a.flags);
       }
-      if (b_role) {
-        unsigned h[4], l[4], gg[4];
-        bool bad = false;
-        const int e = eb_slot[sl * 4 * NB];
-        const double* x = xb_slot + sl * 4 * NB * 4;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) bad |= oz_split(x[r], e, h[r], l[r], gg[r]);
-        if (bad) oz_status(a.flags, LO_ERR_NONFINITE);
-        unsigned char* bbuf = sm + L::BBUF + s * (RB * 32) + (bq & 1) * 8 + (bq >> 1) * 128;
-#pragma unroll
-        for (int u = 1; u <= ND; ++u) {
-          const int row = (u - 1) * NB + bn;
-          const unsigned w0 = oz_pack(u, h[0], l[0], h[1], l[1], (gg[0] >> 16) | gg[1]);
-          const unsigned w1 = oz_pack(u, h[2], l[2], h[3], l[3], (gg[2] >> 16) | gg[3]);
-          *reinterpret_cast<uint2*>(bbuf + (row & 7) * 16 + (row >> 3) * 256) = make_uint2(w0, w1);
-        }
-      }
+      split_rows_store<VB, ND>(xb_slot + sl * 128 * VB, eb_slot[sl * 128], sm + L::BBUF + s * (RB * 32) + b_off,
+                               NB * 32, a.flags);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
