@@ -49,7 +49,9 @@ namespace {
 
 constexpr int kUmmaThreads = 288;     // k = 0 kernels: 8 worker warps + 1 issuer warp
 constexpr int kUmma0Threads = 256;    // worker threads of the k = 0 kernels (warps 0..7)
-constexpr int kUmmaKThreads = 320;    // k > 0 kernels: 8 worker warps, a load warp and an MMA warp
+constexpr int kUmmaKThreads = 352;    // k > 0 kernels: 8 worker warps, a load warp and two MMA warps
+constexpr int kMmaWarps = 2;          // MMA-issuing warps of the k > 0 kernels (warps 9 and 10)
+constexpr int kMmaSplit = 3;          // warp 9 issues digits t <= kMmaSplit (the wider MMAs), warp 10 the rest
 constexpr int kStages = 5;            // ring depth: stages, B buffers and step commits (one index)
 constexpr int kSrcSlots = 6;          // private cp.async slots of a producer thread
 constexpr int kSrcAhead = kSrcSlots - 1;   // steps a producer thread loads ahead
@@ -178,6 +180,7 @@ struct UmmaCtl {
   uint64_t mmad[kStages];   // MMAs of a step done (commit): its stage and B buffer are free
   uint64_t empty[2];        // a TMEM accumulator buffer was drained (drainer warp arrivals)
   uint64_t accf[2];         // the last MMAs of an accumulation interval in a buffer are done
+  uint64_t fin[kMmaWarps];  // an MMA warp's own MMAs are all done (its teardown)
   uint32_t tslot;           // TMEM base written by tcgen05.alloc
   int abort;                // a bounded wait gave up: no further TMA or MMA is issued
 };
@@ -347,13 +350,15 @@ struct GramCursor {
 // pass block into the operands of each step (producers), warps 4..7 read the
 // accumulators of each finished interval back from TMEM (drainers), lane 0
 // of warp 8 issues the loads of each step as soon as its stage is free (load
-// warp) and lane 0 of warp 9 issues its MMAs (MMA warp).  One thread issuing
-// both spent about 2000 cycles per step on the serial chain of barrier waits,
-// copy and MMA instructions; split, the two chains overlap.  mmad[s], the
-// commit of a step's MMAs, frees its stage (for the load warp) and its B
-// buffer (for the producers); no role runs more than kStages steps ahead of
-// the MMAs, so no barrier is waited on more than one phase late.  Drainers
-// wait on accf, a commit of the interval's last MMAs into that TMEM buffer.
+// warp) and lanes 0 of warps 9 and 10 issue its MMAs (MMA warps: digits t <=
+// 3 and t > 3 of the streamed operand).  One thread issuing loads and MMAs
+// spent about 2000 cycles per step on the serial chain of barrier waits,
+// copy and MMA instructions (about 100 cycles per tcgen05.mma); split, the
+// chains overlap.  mmad[s], the commits of a step's MMAs by both MMA warps,
+// frees its stage (for the load warp) and its B buffer (for the producers);
+// no role runs more than kStages steps ahead of the MMAs, so no barrier is
+// waited on more than one phase late.  Drainers wait on accf, the commits of
+// the interval's last MMAs into that TMEM buffer.
 
 // Whether step st (of nsteps in its item) closes an accumulation interval:
 // exact float32 sums cover 16 steps.
@@ -403,11 +408,12 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       mbar_init(full0 + 8 * i, 1);
       mbar_init(ready0 + 8 * i, 4);
     }
-    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, kMmaWarps);
     for (int i = 0; i < 2; ++i) {
       mbar_init(empty0 + 8 * i, 4);
-      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(accf0 + 8 * i, kMmaWarps);
     }
+    for (int i = 0; i < kMmaWarps; ++i) mbar_init(su32(&ctl.fin[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -480,8 +486,9 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
     }
     __syncwarp();
-  } else if (warp == 9) {
-    // ---- MMA warp: one MMA group per step -------------------------------------
+  } else if (warp == 9 || warp == 10) {
+    // ---- MMA warps: digits t0 .. t1 of each step ---------------------------------
+    const int mw = warp - 9, t0 = mw ? kMmaSplit + 1 : 1, t1 = mw ? ND : kMmaSplit;
     if (lane == 0 && a.test_stall != 1) {
       uint32_t idesc[ND];
 #pragma unroll
@@ -514,6 +521,7 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         const uint32_t accum = (cur.st & 15) ? 1u : 0u;
 #pragma unroll
         for (int t = 1; t <= ND; ++t) {
+          if (t < t0 || t > t1) continue;
           const uint64_t da = dA0 + (uint64_t)((s * STAGE + (t - 1) * 128) >> 4);
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB, ND)), da, db, idesc[t - 1], accum);
         }
@@ -521,9 +529,11 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         if (interval_end(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
-      // the MMAs in flight complete before the CTA's memory is released
-      if (committed >= 0)
-        mbar_wait(mmad0 + 8 * (int)(committed % kStages), (uint32_t)((committed / kStages) & 1));
+      // this warp's MMAs in flight complete before the CTA's memory is released
+      if (committed >= 0) {
+        umma_commit(su32(&ctl.fin[mw]));
+        mbar_wait(su32(&ctl.fin[mw]), 0);
+      }
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -767,11 +777,12 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       mbar_init(full0 + 8 * i, 1);
       mbar_init(ready0 + 8 * i, 4);
     }
-    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, 1);
+    for (int i = 0; i < kStages; ++i) mbar_init(mmad0 + 8 * i, kMmaWarps);
     for (int i = 0; i < 2; ++i) {
       mbar_init(empty0 + 8 * i, 4);
-      mbar_init(accf0 + 8 * i, 1);
+      mbar_init(accf0 + 8 * i, kMmaWarps);
     }
+    for (int i = 0; i < kMmaWarps; ++i) mbar_init(su32(&ctl.fin[i]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     ctl.abort = 0;
   }
@@ -827,8 +838,9 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
     }
     __syncwarp();
-  } else if (warp == 9) {
-    // ---- MMA warp: one MMA group per step -------------------------------------
+  } else if (warp == 9 || warp == 10) {
+    // ---- MMA warps: digits t0 .. t1 of each step ---------------------------------
+    const int mw = warp - 9, t0 = mw ? kMmaSplit + 1 : 1, t1 = mw ? kOzDigits : kMmaSplit;
     if (lane == 0) {
       uint32_t idesc[kOzDigits];
 #pragma unroll
@@ -860,6 +872,7 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         const uint32_t accum = (ks & 15) ? 1u : 0u;
 #pragma unroll
         for (int t = 1; t <= kOzDigits; ++t) {
+          if (t < t0 || t > t1) continue;
           const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
           umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
         }
@@ -867,8 +880,10 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         if (closes(cur)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
-      if (committed >= 0)
-        mbar_wait(mmad0 + 8 * (int)(committed % kStages), (uint32_t)((committed / kStages) & 1));
+      if (committed >= 0) {
+        umma_commit(su32(&ctl.fin[mw]));
+        mbar_wait(su32(&ctl.fin[mw]), 0);
+      }
     }
     __syncwarp();
   } else if (warp < 4) {
