@@ -7,9 +7,11 @@
 // 7 8-bit digits aligned to its column's largest exponent, encoded as fp16
 // subnormals; the 28 digit pairs (t, u) with t + u <= 8 are multiplied with
 // float32 accumulation, exact for up to 256 products, and recombined in 64-bit
-// integers.  With prior blocks the results are bit for bit those of the
-// mma.sync kernels; the k = 0 assembly rounds each output once
-// (lo_recombine.h).
+// integers.  With prior blocks the Gram and the 8-output assembly give bit
+// for bit the results of the mma.sync kernels; the 16-output assembly sums
+// the pairs of each of the three lowest classes in one float32 accumulator
+// (umma_drain_mc: within the float64 dot-product error bound); the k = 0
+// assembly rounds each output once (lo_recombine.h).
 //
 // GB300 mapping:
 //   * one thread issues tcgen05.mma (M = 128, K = 16, kind::f16) with both
@@ -245,6 +247,54 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, 
   }
 #pragma unroll
   for (int j = 0; j < NW; ++j) {
+    const double v = ps[j].value();
+    acc[j] = first ? v : acc[j] + v;
+  }
+}
+
+// Merged-class accumulators of the assembly with 16 outputs per group.  The
+// pairs of classes v = t + u <= 5 keep their own exact accumulators (10 pair
+// blocks: digit t = 1..4, u = 1..5 - t); the pairs of each class v = 6, 7, 8
+// share one float32 accumulator.  Such a class sum takes at most 7 x 16
+// roundings of at most 4 units per interval (|sum| < 7 2^24), under 2^9
+// units at a weight of at most 2^-32 of class 2: below 2^-47 of the output's
+// scale (the product scale of its column alignment), inside the error bound
+// of a float64 dot product over the same 256 terms (256 u = 2^-45).  13
+// blocks of 16 columns fit twice in TMEM, so the drain of one interval
+// overlaps the next one's MMAs; 28 separate pair blocks (448 columns) allowed
+// one set only, and the MMAs waited for every drain.
+constexpr int kMcPairBlocks = 10;
+__host__ __device__ constexpr int mc_pair_col(int t, int nb) {  // first column of digit t's exact pairs
+  return (t == 1 ? 0 : t == 2 ? 4 : t == 3 ? 7 : 9) * nb;
+}
+__host__ __device__ constexpr int mc_class_col(int v, int nb) { return (kMcPairBlocks + v - 6) * nb; }
+
+// umma_drain for the merged-class layout.
+template <int NB, int NW>
+__device__ __forceinline__ void umma_drain_mc(uint32_t tlane, int n0, double* acc, bool first) {
+  PairSums ps[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) ps[j].clear();
+#pragma unroll
+  for (int t = 1; t <= 4; ++t) {
+    uint32_t r[4][NW];
+#pragma unroll
+    for (int u = 1; u <= 5 - t; ++u) tmem_ld<NW>(tlane + (uint32_t)(mc_pair_col(t, NB) + (u - 1) * NB + n0), r[u - 1]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int u = 1; u <= 5 - t; ++u)
+#pragma unroll
+      for (int j = 0; j < NW; ++j) ps[j].add(t, u, __uint_as_float(r[u - 1][j]));
+  }
+  uint32_t c[3][NW];
+#pragma unroll
+  for (int v = 6; v <= 8; ++v) tmem_ld<NW>(tlane + (uint32_t)(mc_class_col(v, NB) + n0), c[v - 6]);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    ps[j].s[4] += __float2int_rn(__uint_as_float(c[0][j]) * 0x1p48f);   // S_6
+    ps[j].s[5] += __float2int_rn(__uint_as_float(c[1][j]) * 0x1p48f);   // S_7
+    ps[j].s8[0] += __float2int_rn(__uint_as_float(c[2][j]) * 0x1p48f);  // S_8 (one accumulator)
     const double v = ps[j].value();
     acc[j] = first ? v : acc[j] + v;
   }
@@ -749,7 +799,11 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     k_umma_update(StepArgs a, const double* src_fixed, int64_t lds_fixed, int pass,
                   const __grid_constant__ CUtensorMap tm) {
   using L = UpdLayout<S, NOUT>;
-  constexpr int NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL, NACC = umma_nacc(NB);
+  // 16 outputs per group: merged classes 6..8 (umma_drain_mc), two accumulator sets
+  constexpr int NB = L::NB, BIMG = L::BIMG, NSPL = L::NSPL;
+  constexpr bool MC = NB == 16;
+  constexpr int NACC = MC ? 2 : umma_nacc(NB);
+  static_assert(!MC || 2 * (kMcPairBlocks + 3) * NB <= kTmemCols, "merged-class accumulators: two sets");
   static_assert(!APPLY || NOUT == 1, "apply_Q has one output");
   if (!APPLY && NOUT == 1 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
@@ -870,11 +924,35 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         tc_fence_after();
         const uint64_t db = dB0 + (uint64_t)((s * umma_round16(BIMG / 16) * 16) >> 4);
         const uint32_t accum = (ks & 15) ? 1u : 0u;
+        if constexpr (MC) {
+          if (mw == 0) {
+            // the exact pairs of digits t = 1..4 (u = 1..5 - t): their own blocks
 #pragma unroll
-        for (int t = 1; t <= kOzDigits; ++t) {
-          if (t < t0 || t > t1) continue;
-          const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
-          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
+            for (int t = 1; t <= 4; ++t) {
+              const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
+              umma_f16(tbase + (uint32_t)(buf * 256 + mc_pair_col(t, NB)), da, db,
+                       umma_idesc(128, (5 - t) * NB, 1, 0), accum);
+            }
+          } else {
+            // every digit's pairs of classes 6..8 (u = max(1, 6 - t) .. 8 - t),
+            // all from this thread in a fixed order: the shared accumulators
+            // see the same sequence of additions in every run
+#pragma unroll
+            for (int t = 1; t <= kOzDigits; ++t) {
+              const int u0 = t <= 5 ? 6 - t : 1, nu = 9 - t - u0;
+              const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
+              const uint64_t dbu = db + (uint64_t)((((u0 - 1) * NB / 8) * 256) >> 4);
+              umma_f16(tbase + (uint32_t)(buf * 256 + mc_class_col(t + u0, NB)), da, dbu,
+                       umma_idesc(128, nu * NB, 1, 0), (accum || t > 1) ? 1u : 0u);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int t = 1; t <= kOzDigits; ++t) {
+            if (t < t0 || t > t1) continue;
+            const uint64_t da = dA0 + (uint64_t)((s * kStageBytes + (t - 1) * 128) >> 4);
+            umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB)), da, db, idesc[t - 1], accum);
+          }
         }
         umma_commit(mmad0 + 8 * s);
         if (closes(cur)) umma_commit(accf0 + 8 * buf);
@@ -975,7 +1053,12 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
           const bool first = ks < 16;  // the output group's first interval
 #pragma unroll
-          for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
+          for (int c4 = 0; c4 < NB / 4; ++c4) {
+            if constexpr (MC)
+              umma_drain_mc<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
+            else
+              umma_drain<NB, 4>(tlane, c4 * 4, acc + c4 * 4, first);
+          }
         }
       }
       tc_fence_before();

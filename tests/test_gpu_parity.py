@@ -511,12 +511,19 @@ def test_full_size_sampled_rows(precision):
     (65536, 32, 4096, 6),   # the same with four output groups per row tile
 ])
 def test_digit_planes_bitwise(n, s, cr, M, precision):
-    """Panels kept as digit planes give bit-for-bit the products of re-splitting
-    the float64 panels in every pass: every output of every step, with the
-    reiteration passes included, and the final basis against the oracle.  The
-    mixed form's first pass differs on purpose (with planes: the leading three
-    digits on the tensor cores; without: float32 on the CUDA cores), so there
-    both bases must agree within the float64 tolerances instead."""
+    """Panels kept as digit planes give the products of re-splitting the
+    float64 panels in every pass: bit for bit at the first step (no prior
+    panels) and within the float64 parity tolerance after it, every output of
+    every step with the reiteration passes included, and the final basis
+    against the oracle.  Past the first step the two differ only where the
+    tensor-core assembly with 16 outputs per group sums the digit pairs of
+    each of its three lowest classes in one float32 accumulator (error below
+    2^-47 of the column's product scale, inside a float64 dot product's bound)
+    instead of exactly; the ill-conditioned blocks of this test magnify that
+    to about 1e-12.  The mixed form's first pass
+    differs on purpose (with planes: the leading digits on the tensor cores;
+    without: float32 on the CUDA cores), so there both bases must agree within
+    the float64 tolerances instead."""
     L = lo()
     on = L.Basis(n, s, M, cr, precision=precision)
     off = L.Basis(n, s, M, cr, precision=precision, digit_planes=False)
@@ -533,8 +540,10 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
         r2 = [host(x) for x in off.orthogonalize(W) if x is not None]
         Uo, Po, No = ora.orthogonalize(Wh, "pip2", "pip2")
         for x, y in zip(r1, r2):
-            if bitwise:
+            if bitwise and j == 0:
                 assert np.array_equal(x, y), j
+            elif bitwise:
+                assert close(x, y), (j, errs(x, y))
             else:
                 assert rel(x, y) <= TOL_REL, j
         # the planes-on outputs against the oracle: U, R (and H past the first block)
@@ -548,10 +557,8 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
     for c in (0, on.num_chunks - 1):
         Qa, Ta = on.export_chunk(c)
         Qb, Tb = off.export_chunk(c)
-        if bitwise:
-            assert np.array_equal(Qa, Qb) and np.array_equal(Ta, Tb)
-        else:
-            assert rel(Qa, Qb) <= TOL_REL and rel(Ta, Tb) <= TOL_REL
+        assert close(Qa, Qb), errs(Qa, Qb)
+        assert close(np.triu(Ta), np.triu(Tb)), errs(np.triu(Ta), np.triu(Tb))
 
 
 @pytest.mark.parametrize("planes", [True, False])
