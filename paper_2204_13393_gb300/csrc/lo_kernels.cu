@@ -878,6 +878,129 @@ __device__ void tree_update_chunk(const StepArgs& a, int it, int c, double* sm) 
   }
 }
 
+// The same two products with T_i read through shared memory, kTreeRows rows
+// at a time across all its column blocks: every thread's sums read T_i from
+// global memory one dependent term after another, which left both latency-
+// bound (80 us per round at k = 120).  Each output keeps the order of its
+// terms, so the results are those of the functions above, bit for bit.
+constexpr int kTreeRows = 32;
+
+// Bytes of shared memory of the staged reduction kernels (0: does not fit).
+size_t tree_staged_smem(int k, int s) {
+  const int nb = k / s;
+  const size_t b = 8 * (3 * (size_t)k * s + 2 * (size_t)s * s + (size_t)nb * kTreeRows * s);
+  return b <= 200 * 1024 ? b : 0;
+}
+
+// Rows r0 .. r1 - 1 of every column block cb of T_i that has them (block cb
+// holds rows 0 .. (cb + 1) s - 1) into Tst[(cb kTreeRows + r - r0) s + qq].
+__device__ __forceinline__ void tree_stage_rows(const double* Tc, int nb, int s, int r0, int r1, double* Tst) {
+  const int cb0 = r0 / s, per = kTreeRows * s;
+  for (int e = threadIdx.x; e < (nb - cb0) * per; e += blockDim.x) {
+    const int cb = cb0 + e / per, w = e - (cb - cb0) * per, rr = w / s, qq = w - rr * s, r = r0 + rr;
+    if (r < r1 && r < (cb + 1) * s) Tst[(cb * kTreeRows + rr) * s + qq] = Tc[tblock_offset(cb, s) + (int64_t)r * s + qq];
+  }
+}
+
+// tree_update_chunk with T_i and P staged; smem: t, P (k x s), Nx, Nin (s x s), the row window.
+__device__ void tree_update_chunk_st(const StepArgs& a, int it, int c, double* sm) {
+  const int s = a.s, nb = a.nb, k = nb * s, ss = s * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  const GlobLayout GL = GlobLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  const double* Xg = smallc + (it == 1 ? SL.P_comb : SL.P_hat);
+  const double* Nxg = smallc + (it == 1 ? SL.N_comb : SL.N_hat);
+  const double* Pg = a.glob + GL.P_it;
+  const double* Ninv = a.glob + GL.Ninv_it;
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* t = sm;            // k x s
+  double* P = t + k * s;     // k x s
+  double* Nx = P + k * s;    // s x s
+  double* Nin = Nx + ss;     // s x s
+  double* Tst = Nin + ss;    // nb x kTreeRows x s
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    Nx[e] = Nxg[e];
+    Nin[e] = Ninv[e];
+  }
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) P[e] = Pg[e];
+  for (int r0 = 0; r0 < k; r0 += kTreeRows) {
+    const int r1 = min(k, r0 + kTreeRows);
+    __syncthreads();
+    tree_stage_rows(Tc, nb, s, r0, r1, Tst);
+    __syncthreads();
+    for (int e = r0 * s + threadIdx.x; e < r1 * s; e += blockDim.x) {
+      const int r = e / s, l = e - r * s;
+      double v = Xg[e];
+      for (int cb = r / s; cb < nb; ++cb) {
+        const double* Tb = Tst + (cb * kTreeRows + (r - r0)) * s;
+        for (int qq = 0; qq < s; ++qq) v -= Tb[qq] * P[(cb * s + qq) * s + l];
+      }
+      t[e] = v;
+    }
+  }
+  __syncthreads();
+  double* Ph = smallc + SL.P_hat;
+  double* Tnew = a.T + (int64_t)c * a.tstride + tblock_offset(nb, s);  // (k + s) x s
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+    const int r = e / s, l = e - r * s;
+    double v = 0.0;
+    for (int j = 0; j <= l; ++j) v += t[r * s + j] * Nin[j * s + l];
+    Ph[e] = v;
+    Tnew[e] = v;
+  }
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, l = e - i * s;
+    double v = 0.0;
+    if (i <= l)
+      for (int j = i; j <= l; ++j) v += Nx[i * s + j] * Nin[j * s + l];
+    smallc[SL.N_hat + e] = v;
+    Tnew[k * s + e] = v;
+  }
+}
+
+// tree_contrib_chunk with T_i staged; smem: X, the partial sums (k x s), Nx (s x s), the row window.
+__device__ void tree_contrib_chunk_st(const StepArgs& a, int it, int c, double* sm) {
+  const int s = a.s, nb = a.nb, k = nb * s, ss = s * s;
+  const SmallLayout SL = SmallLayout::make(a.Kmax, s);
+  double* smallc = a.small + (int64_t)c * SL.stride;
+  const double* Xg = smallc + (it == 1 ? SL.P_comb : SL.P_hat);
+  const double* Nxg = smallc + (it == 1 ? SL.N_comb : SL.N_hat);
+  const double* Tc = a.T + (int64_t)c * a.tstride;
+  double* X = sm;             // k x s
+  double* Zp = X + k * s;     // k x s
+  double* Nx = Zp + k * s;    // s x s
+  double* Tst = Nx + 2 * ss;  // nb x kTreeRows x s (after the update's layout size)
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+    X[e] = Xg[e];
+    Zp[e] = 0.0;
+  }
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) Nx[e] = Nxg[e];
+  for (int r0 = 0; r0 < k; r0 += kTreeRows) {
+    const int r1 = min(k, r0 + kTreeRows);
+    __syncthreads();
+    tree_stage_rows(Tc, nb, s, r0, r1, Tst);
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * s; e += blockDim.x) {
+      const int q = e / s, l = e - q * s, cb = q / s, qq = q - cb * s;
+      const int rend = min(r1, (cb + 1) * s);
+      if (r0 >= rend) continue;
+      double v = Zp[e];
+      for (int r = r0; r < rend; ++r) v += Tst[(cb * kTreeRows + (r - r0)) * s + qq] * X[r * s + l];
+      Zp[e] = v;
+    }
+  }
+  __syncthreads();
+  double* Z = smallc + SL.Z;
+  for (int e = threadIdx.x; e < k * s; e += blockDim.x) Z[e] = Zp[e];
+  for (int e = threadIdx.x; e < ss; e += blockDim.x) {
+    const int i = e / s, j = e - i * s;
+    double v = 0.0;
+    for (int r = 0; r < k; ++r) v += X[r * s + i] * X[r * s + j];
+    for (int r = 0; r < s; ++r) v += Nx[r * s + i] * Nx[r * s + j];
+    Z[k * s + e] = v;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_tree_update(StepArgs a, int it) {
   if (!a.flags[kFlagTree + it - 1]) return;
   extern __shared__ __align__(16) double sm[];
@@ -1725,6 +1848,25 @@ __global__ void __launch_bounds__(kThreads) k_tree_round(StepArgs a, int it, int
   tree_contrib_chunk(a, it, c, sm);
 }
 
+// k_tree_round and k_tree_update with T_i staged in shared memory (when
+// tree_staged_smem fits).
+__global__ void __launch_bounds__(kThreads) k_tree_round_st(StepArgs a, int it, int with_update) {
+  extern __shared__ __align__(16) double sm[];
+  const int c = blockIdx.x;
+  if (with_update && a.flags[kFlagTree + it - 2]) {
+    tree_update_chunk_st(a, it - 1, c, sm);
+    __syncthreads();
+  }
+  if (!a.flags[kFlagTree + it - 1]) return;
+  tree_contrib_chunk_st(a, it, c, sm);
+}
+
+__global__ void __launch_bounds__(kThreads) k_tree_update_st(StepArgs a, int it) {
+  if (!a.flags[kFlagTree + it - 1]) return;
+  extern __shared__ __align__(16) double sm[];
+  tree_update_chunk_st(a, it, blockIdx.x, sm);
+}
+
 __global__ void __launch_bounds__(kThreads) k_tree_sum(StepArgs a, int it, int ngroups) {
   extern __shared__ __align__(16) double sm[];
   if (!a.flags[kFlagTree + it - 1]) return;
@@ -1788,6 +1930,8 @@ cudaError_t set_attrs() {
   if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_tree_round, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_tree_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_round_st, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
+  if ((e = cudaFuncSetAttribute(k_tree_update_st, cudaFuncAttributeMaxDynamicSharedMemorySize, big))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_leaf<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_flat<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
   if ((e = cudaFuncSetAttribute(k_hh_flat<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kHHTileBytes))) return e;
@@ -1848,13 +1992,19 @@ void launch_reduction(const StepArgs& a, cudaStream_t st, ProfHook* hook) {
   if (a.tree_ticket) {
     // per iteration: (update of it - 1 +) contribution, then the ticketed sums
     // and factorization; the last update at the end
-    const size_t smr = 8 * ((size_t)k * s + 2 * ss);
+    const size_t smr = 8 * ((size_t)k * s + 2 * ss), sst = tree_staged_smem(k, s);
     const dim3 gsum(ngroups, (unsigned)((Kt * s + kThreads - 1) / kThreads));
     for (int it = 1; it <= iters; ++it) {
-      k_tree_round<<<a.p, kThreads, smr, st>>>(a, it, it > 1 ? 1 : 0);
+      if (sst)
+        k_tree_round_st<<<a.p, kThreads, sst, st>>>(a, it, it > 1 ? 1 : 0);
+      else
+        k_tree_round<<<a.p, kThreads, smr, st>>>(a, it, it > 1 ? 1 : 0);
       k_tree_sum<<<gsum, kThreads, 8 * (4 * (size_t)ss + 4), st>>>(a, it, ngroups);
     }
-    k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, iters);
+    if (sst)
+      k_tree_update_st<<<a.p, kThreads, sst, st>>>(a, iters);
+    else
+      k_tree_update<<<a.p, kThreads, 8 * ((size_t)k * s + 2 * ss), st>>>(a, iters);
     count_launches(2 * iters + 1);
   } else {
     for (int it = 1; it <= iters; ++it) {
