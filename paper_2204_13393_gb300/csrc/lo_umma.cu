@@ -55,8 +55,7 @@ constexpr int kUmmaKThreads = 352;    // k > 0 kernels: 8 worker warps, a load w
 constexpr int kMmaWarps = 2;          // MMA-issuing warps of the k > 0 kernels (warps 9 and 10)
 constexpr int kMmaSplit = 3;          // warp 9 issues digits t <= kMmaSplit (the wider MMAs), warp 10 the rest
 constexpr int kStages = 5;            // ring depth: stages, B buffers and step commits (one index)
-constexpr int kSrcSlots = 6;          // private cp.async slots of a producer thread
-constexpr int kSrcAhead = kSrcSlots - 1;   // steps a producer thread loads ahead
+constexpr int kSrcSlots = 6;          // private cp.async slots of a producer thread (one-slice Gram steps)
 constexpr int kMixedDigits = 4;       // leading digits of the mixed form's first Gram (8 bits each)
 constexpr int kStageBytes = 28672;    // one step's A operand: 7 digit planes of 128 x 16 fp16
 constexpr long long kWaitCycles = 500000000ll;   // ~0.25 s at 2 GHz
@@ -347,24 +346,31 @@ template <int S, int ND = kOzDigits>
 struct GramLayout {
   static constexpr int NB = S < 16 ? S : 16, NSPL = S / NB;
   static constexpr int RB = umma_round16(ND * NB);
-  static constexpr int STAGE = ND * 4096;                       // [2][16][ND][128 B]
-  static constexpr int STG = 0;                                 // kStages stages
-  static constexpr int BBUF = STG + kStages * STAGE;            // kStages x RB x 32 B
-  // private cp.async slots (kSrcSlots steps) of the float64 values each of
-  // the 128 producer threads splits, and of the exponents it splits them
-  // against: VA values of the block's own columns (the A tile: S x 16 per
-  // step) and VB values of the B operand (NB x 16 per step)
+  static constexpr int STAGE = ND * 4096;                       // one K-slice: [2][16][ND][128 B]
+  // K-slices of 16 rows per step: two for S <= 16 (the per-step barrier and
+  // loop work of the MMA warps then covers 32 rows), in a ring of NST steps
+  static constexpr int SL = S <= 16 ? 2 : 1;
+  static constexpr int NST = SL == 2 ? 3 : kStages;
+  static constexpr int IS = 16 / SL;                            // steps per exact float32 interval
+  // private cp.async slots (SLOTS steps) of the float64 values each of the 128
+  // producer threads splits, and of the exponents it splits them against: VA
+  // values of the block's own columns (the A tile: S x 16 per slice) and VB
+  // values of the B operand (NB x 16 per slice), per slice
+  static constexpr int SLOTS = S <= 8 ? 4 : (S == 16 ? 3 : kSrcSlots);
   static constexpr int VA = S / 8, VB = NB / 8;
-  static constexpr int SRCA = BBUF + kStages * RB * 32;
-  static constexpr int SRCB = SRCA + kSrcSlots * 128 * VA * 8;
-  static constexpr int EXA = SRCB + kSrcSlots * 128 * VB * 8;
-  static constexpr int EXB = EXA + kSrcSlots * 128 * 4;
-  static constexpr int CTL = EXB + kSrcSlots * 128 * 4;
+  static constexpr int STG = 0;                                 // NST x SL slices
+  static constexpr int BBUF = STG + NST * SL * STAGE;           // NST x SL x RB x 32 B
+  static constexpr int SRCA = BBUF + NST * SL * RB * 32;
+  static constexpr int SRCB = SRCA + SLOTS * 128 * SL * VA * 8;
+  static constexpr int EXA = SRCB + SLOTS * 128 * SL * VB * 8;
+  static constexpr int EXB = EXA + SLOTS * 128 * 4;
+  static constexpr int CTL = EXB + SLOTS * 128 * 4;
   static constexpr int BYTES = CTL + (int)sizeof(UmmaCtl) + 1024;  // + alignment slack
 };
 
 // One Gram work item and the walk over a CTA's items (w = blockIdx.x,
-// blockIdx.x + gridDim.x, ...), step by step.
+// blockIdx.x + gridDim.x, ...), step by step (SL slices of 16 rows each).
+template <int SL>
 struct GramCursor {
   int w, st, nsteps, slab, rows, tile0, chunk, col0, z;
   int64_t row0;
@@ -381,7 +387,12 @@ struct GramCursor {
     rows = si.rows;
     tile0 = si.tile0;
     chunk = si.chunk;
-    nsteps = (rows + 15) / 16;
+    nsteps = (rows + 16 * SL - 1) / (16 * SL);
+  }
+  // slices of the current step inside the slab (a prefix of 1 .. SL)
+  __device__ __forceinline__ int slices() const {
+    const int left = rows - st * 16 * SL;
+    return left >= 16 * SL ? SL : (left + 15) / 16;
   }
   __device__ __forceinline__ void start(const StepArgs& a, int nitems, int ngroups) {
     w = blockIdx.x;
@@ -411,8 +422,9 @@ struct GramCursor {
 // the interval's last MMAs into that TMEM buffer.
 
 // Whether step st (of nsteps in its item) closes an accumulation interval:
-// exact float32 sums cover 16 steps.
-__device__ __forceinline__ bool interval_end(int st, int nsteps) { return ((st + 1) & 15) == 0 || st + 1 == nsteps; }
+// exact float32 sums cover 256 rows, IS steps.
+template <int IS>
+__device__ __forceinline__ bool interval_end(int st, int nsteps) { return (st + 1) % IS == 0 || st + 1 == nsteps; }
 
 // The values a Gram producer thread loads for one step when the pass block is
 // the step's operator applied to its input: rows r0 + ar0 .. + va - 1 of
@@ -441,6 +453,8 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     k_umma_gram(StepArgs a, const double* src, int64_t lds, int pass, const __grid_constant__ CUtensorMap tm) {
   using L = GramLayout<S, ND>;
   constexpr int NB = L::NB, RB = L::RB, NSPL = L::NSPL, NACC = umma_nacc(NB, ND), STAGE = L::STAGE;
+  constexpr int SL = L::SL, NST = L::NST, IS = L::IS;
+  using Cursor = GramCursor<SL>;
   if (pass >= 2 && !a.flags[kFlagPass + pass - 1]) return;
   if (umma_timed_out(a.flags)) return;
   extern __shared__ unsigned char smem_raw[];
@@ -473,7 +487,7 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if constexpr (RB > ND * NB) {  // B pad rows stay zero
-    for (int i = tid; i < kStages * (RB - ND * NB) * 2; i += kUmmaKThreads) {
+    for (int i = tid; i < NST * SL * (RB - ND * NB) * 2; i += kUmmaKThreads) {
       const int h = i & 1, rest = i >> 1, r = ND * NB + rest % (RB - ND * NB), bb = rest / (RB - ND * NB);
       *reinterpret_cast<uint4*>(sm + L::BBUF + bb * (RB * 32) + (r & 7) * 16 + (r >> 3) * 256 + h * 128) =
           make_uint4(0u, 0u, 0u, 0u);
@@ -497,33 +511,40 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       // rows of the block's own columns are split in by the producers; rows
       // past them keep what the stage held and only reach accumulator rows
       // (columns >= k + S) that the drainers never read.
-      auto issue = [&](const GramCursor& c, int j) {
-        const int sj = j % kStages, g0 = c.col0 / 8, ng = min(16, k / 8 - g0);
+      // (per slice of the step inside the slab: slices past the slab's rows
+      // are neither loaded nor multiplied)
+      auto issue = [&](const Cursor& c, int j) {
+        const int sj = j % NST, g0 = c.col0 / 8, ng = min(16, k / 8 - g0), nsl = c.slices();
         if (ng > 0) {
-          const int64_t eta = 2 * (int64_t)(c.tile0 + c.st);
           if constexpr (ND == kOzDigits) {
             const uint32_t run = (uint32_t)ng * kOzDigits * 128;
-            const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
-            mbar_expect_tx(full0 + 8 * sj, 2 * run);
-            bulk_load(su32(sm + L::STG + sj * STAGE), gsrc, run, full0 + 8 * sj);
-            bulk_load(su32(sm + L::STG + sj * STAGE + STAGE / 2), gsrc + (int64_t)gtot * kOzDigits * 128, run,
-                      full0 + 8 * sj);
+            mbar_expect_tx(full0 + 8 * sj, (uint32_t)nsl * 2 * run);
+            for (int h = 0; h < nsl; ++h) {
+              const int64_t eta = 2 * (int64_t)(c.tile0 + c.st * SL + h);
+              const unsigned char* gsrc = a.dig + (eta * gtot + g0) * (kOzDigits * 128);
+              unsigned char* dst = sm + L::STG + (sj * SL + h) * STAGE;
+              bulk_load(su32(dst), gsrc, run, full0 + 8 * sj);
+              bulk_load(su32(dst + STAGE / 2), gsrc + (int64_t)gtot * kOzDigits * 128, run, full0 + 8 * sj);
+            }
           } else {
-            mbar_expect_tx(full0 + 8 * sj, STAGE);  // the whole box (groups past gtot arrive as zeros)
-            tma_load_3d(su32(sm + L::STG + sj * STAGE), &tm, 0, g0, (int)eta, full0 + 8 * sj);
+            // whole boxes (groups past gtot arrive as zeros)
+            mbar_expect_tx(full0 + 8 * sj, (uint32_t)(nsl * STAGE));
+            for (int h = 0; h < nsl; ++h)
+              tma_load_3d(su32(sm + L::STG + (sj * SL + h) * STAGE), &tm, 0, g0, (int)(2 * (c.tile0 + c.st * SL + h)),
+                          full0 + 8 * sj);
           }
         } else {
           mbar_arrive(full0 + 8 * sj);
         }
       };
-      GramCursor ld;
+      Cursor ld;
       ld.start(a, nitems, ngroups);
       int issued = 0;
       for (; ld.valid; ++issued, ld.next(a, nitems, ngroups)) {
-        const int sj = issued % kStages;
-        // the stage last served step issued - kStages
-        if (issued >= kStages &&
-            !mbar_wait_live(mmad0 + 8 * sj, (uint32_t)(((issued - kStages) / kStages) & 1), &ctl.abort)) {
+        const int sj = issued % NST;
+        // the stage last served step issued - NST
+        if (issued >= NST &&
+            !mbar_wait_live(mmad0 + 8 * sj, (uint32_t)(((issued - NST) / NST) & 1), &ctl.abort)) {
           umma_timeout(ctl, a.flags);
           break;
         }
@@ -532,8 +553,8 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       }
       // the copies in flight land before the CTA's memory is released (the
       // last load into each stage: no later phase exists)
-      for (int j = issued > kStages ? issued - kStages : 0; j < issued; ++j)
-        mbar_wait(full0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1));
+      for (int j = issued > NST ? issued - NST : 0; j < issued; ++j)
+        mbar_wait(full0 + 8 * (j % NST), (uint32_t)((j / NST) & 1));
     }
     __syncwarp();
   } else if (warp == 9 || warp == 10) {
@@ -546,16 +567,16 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       // descriptors of stage 0 / buffer 0; a stage or buffer only moves the start address
       const uint64_t dA0 = umma_sdesc(su32(sm + L::STG), STAGE / 2, ND * 128);
       const uint64_t dB0 = umma_sdesc(su32(sm + L::BBUF), 128, 256);
-      GramCursor cur;
+      Cursor cur;
       cur.start(a, nitems, ngroups);
       int intervals = 0;
       int64_t committed = -1;
       for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-        const int s = g % kStages;
-        const uint32_t par = (uint32_t)((g / kStages) & 1);
+        const int s = g % NST;
+        const uint32_t par = (uint32_t)((g / NST) & 1);
         bool ok = mbar_wait_live(full0 + 8 * s, par, &ctl.abort);
         if (ok) ok = mbar_wait_live(ready0 + 8 * s, par, &ctl.abort);
-        if ((cur.st & 15) == 0) {  // a new accumulation interval: its buffer must be drained
+        if (cur.st % IS == 0) {  // a new accumulation interval: its buffer must be drained
           const int b = intervals % NACC;
           if (ok && intervals >= NACC)
             ok = mbar_wait_live(empty0 + 8 * b, (uint32_t)(((intervals / NACC) - 1) & 1), &ctl.abort);
@@ -567,16 +588,21 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint64_t db = dB0 + (uint64_t)((s * (RB * 32)) >> 4);
-        const uint32_t accum = (cur.st & 15) ? 1u : 0u;
+        const int nsl = cur.slices();
 #pragma unroll
-        for (int t = 1; t <= ND; ++t) {
-          if (t < t0 || t > t1) continue;
-          const uint64_t da = dA0 + (uint64_t)((s * STAGE + (t - 1) * 128) >> 4);
-          umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB, ND)), da, db, idesc[t - 1], accum);
+        for (int h = 0; h < SL; ++h) {
+          if (h >= nsl) break;
+          const uint64_t db = dB0 + (uint64_t)((((s * SL + h) * RB) * 32) >> 4);
+          const uint32_t accum = (cur.st % IS != 0 || h > 0) ? 1u : 0u;
+#pragma unroll
+          for (int t = 1; t <= ND; ++t) {
+            if (t < t0 || t > t1) continue;
+            const uint64_t da = dA0 + (uint64_t)(((s * SL + h) * STAGE + (t - 1) * 128) >> 4);
+            umma_f16(tbase + (uint32_t)(buf * 256 + umma_col(t, NB, ND)), da, db, idesc[t - 1], accum);
+          }
         }
         umma_commit(mmad0 + 8 * s);
-        if (interval_end(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
+        if (interval_end<IS>(cur.st, cur.nsteps)) umma_commit(accf0 + 8 * buf);
         committed = g;
       }
       // this warp's MMAs in flight complete before the CTA's memory is released
@@ -588,91 +614,98 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     __syncwarp();
   } else if (warp < 4) {
     // ---- producers (warps 0..3) -----------------------------------------------
-    // every thread splits VA rows a_r0 .. of the block's own column a_l into
-    // the A tile (only in the column group that holds them) and VB rows b_r0
-    // .. of column z NB + b_n into B buffer g % kStages.  Its values and the
-    // slab exponents it splits them against arrive by cp.async kSrcAhead steps
-    // ahead.
-    constexpr int VA = L::VA, VB = L::VB;
+    // in every slice of a step each thread splits VA rows a_r0 .. of the
+    // block's own column a_l into the A tile (only in the column group that
+    // holds them) and VB rows b_r0 .. of column z NB + b_n into the slice's B
+    // buffer.  Its values and the slab exponents it splits them against
+    // arrive by cp.async AH steps ahead.
+    constexpr int VA = L::VA, VB = L::VB, SLOTS = L::SLOTS, AH = SLOTS - 1;
     const int a_l = tid / (16 / VA), a_r0 = (tid % (16 / VA)) * VA;
     const int b_n = tid / (16 / VB), b_r0 = (tid % (16 / VB)) * VB;
-    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + tid * VA;
-    double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + tid * VB;
+    double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + tid * SL * VA;
+    double* xb_slot = reinterpret_cast<double*>(sm + L::SRCB) + tid * SL * VB;
     int* ea_slot = reinterpret_cast<int*>(sm + L::EXA) + tid;
     int* eb_slot = reinterpret_cast<int*>(sm + L::EXB) + tid;
-    auto is_asrc = [&](const GramCursor& c) {
+    auto is_asrc = [&](const Cursor& c) {
       const int am = k - c.col0 + a_l;
       return am >= 0 && am < 128;
     };
     // the float64 values this thread splits in global step j (cursor c), and
-    // their exponents, into slot j % kSrcSlots
-    auto load_src = [&](const GramCursor& c, int j) {
+    // their exponents, into slot j % SLOTS (rows past the slab read as zeros)
+    auto load_src = [&](const Cursor& c, int j) {
       if (c.valid) {
-        const int r0 = c.st * 16, sl = j % kSrcSlots;
+        const int sl = j % SLOTS;
         const int* hs = a.srcexp_slab + (int64_t)c.slab * 32;
         const bool asrc = is_asrc(c);
         if (asrc) cp_async4(ea_slot + sl * 128, hs + a_l);
         cp_async4(eb_slot + sl * 128, hs + c.z * NB + b_n);
-        if (a.op_nx) {
-          // the operator's block, formed from its input (off the hot loop: the
-          // stencil's index arithmetic stays out of the common path)
-          gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, asrc, a_l, a_r0, VA, xa_slot + sl * 128 * VA,
-                         b_n, b_r0, VB, xb_slot + sl * 128 * VB);
-        } else {
-          if (asrc) {
-            double* d = xa_slot + sl * 128 * VA;
 #pragma unroll
-            for (int i = 0; i < VA; ++i) {
-              const int row = r0 + a_r0 + i;
-              const bool ok = row < c.rows;
-              cp_async8(d + i, src + (c.row0 + (ok ? row : 0)) * lds + a_l, ok);
+        for (int h = 0; h < SL; ++h) {
+          const int r0 = (c.st * SL + h) * 16;
+          double* da = xa_slot + (sl * 128 * SL + h) * VA;
+          double* db = xb_slot + (sl * 128 * SL + h) * VB;
+          if (a.op_nx) {
+            // the operator's block, formed from its input (off the hot loop: the
+            // stencil's index arithmetic stays out of the common path)
+            gram_op_values(a, c.row0, c.rows, r0, c.col0, c.z * NB, asrc, a_l, a_r0, VA, da, b_n, b_r0, VB, db);
+          } else {
+            if (asrc) {
+#pragma unroll
+              for (int i = 0; i < VA; ++i) {
+                const int row = r0 + a_r0 + i;
+                const bool ok = row < c.rows;
+                cp_async8(da + i, src + (c.row0 + (ok ? row : 0)) * lds + a_l, ok);
+              }
             }
-          }
-          double* d = xb_slot + sl * 128 * VB;
 #pragma unroll
-          for (int i = 0; i < VB; ++i) {
-            const int row = r0 + b_r0 + i;
-            const bool ok = row < c.rows;
-            cp_async8(d + i, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + b_n, ok);
+            for (int i = 0; i < VB; ++i) {
+              const int row = r0 + b_r0 + i;
+              const bool ok = row < c.rows;
+              cp_async8(db + i, src + (c.row0 + (ok ? row : 0)) * lds + c.z * NB + b_n, ok);
+            }
           }
         }
       }
       cp_async_commit();
     };
-    GramCursor ahead, cur;
+    Cursor ahead, cur;
     ahead.start(a, nitems, ngroups);
     cur.start(a, nitems, ngroups);
 #pragma unroll
-    for (int j = 0; j < kSrcAhead; ++j) {
+    for (int j = 0; j < AH; ++j) {
       load_src(ahead, j);
       ahead.next(a, nitems, ngroups);
     }
     // B buffer position of rows b_r0 .. of column b_n (digit 1; the planes are NB * 32 bytes apart)
     const int b_off = (b_n & 7) * 16 + (b_n >> 3) * 256 + (b_r0 & 7) * 2 + (b_r0 >> 3) * 128;
     for (int g = 0; cur.valid; ++g, cur.next(a, nitems, ngroups)) {
-      const int s = g % kStages, sl = g % kSrcSlots;
-      load_src(ahead, g + kSrcAhead);
+      const int s = g % NST, sl = g % SLOTS;
+      load_src(ahead, g + AH);
       ahead.next(a, nitems, ngroups);
-      asm volatile("cp.async.wait_group %0;" ::"n"(kSrcAhead) : "memory");   // this thread's values of step g
-      // MMAs of step g - kStages done: B buffer and stage s are free (and no
+      asm volatile("cp.async.wait_group %0;" ::"n"(AH) : "memory");   // this thread's values of step g
+      // MMAs of step g - NST done: the B buffers and stage s are free (and no
       // warp runs further ahead)
-      if (g >= kStages && !ctl.abort &&
-          !mbar_wait_live(mmad0 + 8 * s, (uint32_t)(((g - kStages) / kStages) & 1), &ctl.abort))
+      if (g >= NST && !ctl.abort &&
+          !mbar_wait_live(mmad0 + 8 * s, (uint32_t)(((g - NST) / NST) & 1), &ctl.abort))
         umma_timeout(ctl, a.flags);
-      unsigned char* stage = sm + L::STG + s * STAGE;
-      if (is_asrc(cur)) {
-        const int am = k - cur.col0 + a_l;
-        // the 7-plane loads never cover the block's own columns; the leading-
-        // digit box does, so its producers write only after it landed
-        if (ND != kOzDigits && !ctl.abort && !mbar_wait_live(full0 + 8 * s, (uint32_t)((g / kStages) & 1), &ctl.abort))
-          umma_timeout(ctl, a.flags);
-        split_rows_store<VA, ND>(xa_slot + sl * 128 * VA, ea_slot[sl * 128],
-                                 stage + (a_r0 >> 3) * (STAGE / 2) + (am >> 3) * (ND * 128) + (am & 7) * 16 +
-                                     (a_r0 & 7) * 2,
-                                 128, a.flags);
+      const bool asrc = is_asrc(cur);
+      // the 7-plane loads never cover the block's own columns; the leading-
+      // digit box does, so its producers write only after it landed
+      if (asrc && ND != kOzDigits && !ctl.abort &&
+          !mbar_wait_live(full0 + 8 * s, (uint32_t)((g / NST) & 1), &ctl.abort))
+        umma_timeout(ctl, a.flags);
+#pragma unroll
+      for (int h = 0; h < SL; ++h) {
+        if (asrc) {
+          const int am = k - cur.col0 + a_l;
+          split_rows_store<VA, ND>(xa_slot + (sl * 128 * SL + h) * VA, ea_slot[sl * 128],
+                                   sm + L::STG + (s * SL + h) * STAGE + (a_r0 >> 3) * (STAGE / 2) +
+                                       (am >> 3) * (ND * 128) + (am & 7) * 16 + (a_r0 & 7) * 2,
+                                   128, a.flags);
+        }
+        split_rows_store<VB, ND>(xb_slot + (sl * 128 * SL + h) * VB, eb_slot[sl * 128],
+                                 sm + L::BBUF + (s * SL + h) * (RB * 32) + b_off, NB * 32, a.flags);
       }
-      split_rows_store<VB, ND>(xb_slot + sl * 128 * VB, eb_slot[sl * 128], sm + L::BBUF + s * (RB * 32) + b_off,
-                               NB * 32, a.flags);
       fence_async_smem();
       __syncwarp();
       if (lane == 0) mbar_arrive(ready0 + 8 * s);
@@ -680,14 +713,14 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
   } else {
     // ---- drainers (warps 4..7): TMEM lanes 32 (w % 4) .. + 31 = columns
     // col0 + m of the item, all NB block columns, once per interval ----------
-    GramCursor cur;
+    Cursor cur;
     cur.start(a, nitems, ngroups);
     double acc[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) acc[j] = 0.0;
     int intervals = 0;
     for (; cur.valid; cur.next(a, nitems, ngroups)) {
-      if (!interval_end(cur.st, cur.nsteps)) continue;
+      if (!interval_end<IS>(cur.st, cur.nsteps)) continue;
       const int buf = intervals % NACC;
       const uint32_t use = (uint32_t)(intervals / NACC);
       ++intervals;
@@ -700,7 +733,7 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         } else {
           tc_fence_after();
           const uint32_t tlane = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(buf * 256);
-          const bool first = cur.st < 16;  // the item's first interval
+          const bool first = cur.st < IS;  // the item's first interval
 #pragma unroll
           for (int c4 = 0; c4 < NB / 4; ++c4) umma_drain<NB, 4, ND>(tlane, c4 * 4, acc + c4 * 4, first);
         }
