@@ -660,15 +660,16 @@ def run_reference(args):
 
 def run_profile_case(args):
     """A single mid-cycle orthogonalization (n = 2^20, s = 8, k = 120 prior
-    columns from Gaussian blocks, 4096-row chunks) for ncu captures: the basis
-    (1 GB) is larger than L2.  The last step runs between cudaProfilerStart and
-    cudaProfilerStop (ncu --profile-from-start off captures only it)."""
+    columns from Gaussian blocks by default, --profile-blocks sets k / 8;
+    8192-row chunks) for ncu captures: the basis is larger than L2.  The last
+    step runs between cudaProfilerStart and cudaProfilerStop (ncu
+    --profile-from-start off captures only it)."""
     import torch
 
     from paper_2204_13393_gb300 import inputs as I
     from paper_2204_13393_gb300 import lo
 
-    n, s, kb = 2 ** 20, 8, 15
+    n, s, kb = 2 ** 20, 8, args.profile_blocks
     dev = torch.device("cuda", 0)
     lo.library()
     b = lo.Basis(n, s, kb + 1, CHUNK, sync=True, precision=args.precision)
@@ -1130,6 +1131,8 @@ def main():
     ap.add_argument("--mixed-cr", type=int, default=0, help="chunk rows for --case mixed (0: lo_tune_chunk_rows)")
     ap.add_argument("--mixed-kappas", default="1e2,1e4,1e6", help="condition numbers for --case mixed")
     ap.add_argument("--step-precisions", default="fp64,fp64_tc", help="forms for --case step")
+    ap.add_argument("--profile-blocks", type=int, default=15,
+                    help="--case profile: prior blocks of the profiled step (k = 8 x this)")
     ap.add_argument("--chunk-rows", type=int, default=CHUNK,
                     help="chunk rows of the cycle's basis (0: lo_tune_chunk_rows, measured on this GPU)")
     ap.add_argument("--tsqr-n", default=str(2 ** 24), help="comma-separated row counts for --case tsqr")
