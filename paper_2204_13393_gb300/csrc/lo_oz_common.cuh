@@ -259,6 +259,39 @@ __device__ __forceinline__ void split_rows_store(const double* x, int e, unsigne
   }
 }
 
+// split_rows_store into two destinations (planes stride1 and stride2 bytes
+// apart): one split, the same digits stored twice.
+template <int V, int ND>
+__device__ __forceinline__ void split_rows_store2(const double* x, int e, unsigned char* dst1, int stride1,
+                                                  unsigned char* dst2, int stride2, int* flags) {
+  static_assert(V == 1 || V == 2 || V == 4, "split_rows_store2: 1, 2 or 4 values");
+  unsigned h[V], l[V], g[V];
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < V; ++i) bad |= oz_split(x[i], e, h[i], l[i], g[i]);
+  if (bad) oz_status(flags, LO_ERR_NONFINITE);
+#pragma unroll
+  for (int t = 1; t <= ND; ++t) {
+    unsigned char* d1 = dst1 + (t - 1) * stride1;
+    unsigned char* d2 = dst2 + (t - 1) * stride2;
+    if constexpr (V == 1) {
+      const unsigned w = t <= 3 ? h[0] : l[0];
+      const unsigned short v = (unsigned short)((g[0] >> 16) | ((w >> (8 * (t <= 3 ? 3 - t : 7 - t))) & 0xFFu));
+      *reinterpret_cast<unsigned short*>(d1) = v;
+      *reinterpret_cast<unsigned short*>(d2) = v;
+    } else if constexpr (V == 2) {
+      const unsigned v = oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]);
+      *reinterpret_cast<unsigned*>(d1) = v;
+      *reinterpret_cast<unsigned*>(d2) = v;
+    } else {
+      const uint2 v = make_uint2(oz_pack(t, h[0], l[0], h[1], l[1], (g[0] >> 16) | g[1]),
+                                 oz_pack(t, h[2], l[2], h[3], l[3], (g[2] >> 16) | g[3]));
+      *reinterpret_cast<uint2*>(d1) = v;
+      *reinterpret_cast<uint2*>(d2) = v;
+    }
+  }
+}
+
 // Digit planes of the new panel (slot nb) of one slab, once stage 2 has fixed
 // the panel's column exponents.  One thread per (16-row tile, column): 16
 // values, 7 planes of two 16-byte core-matrix rows each.  Whole CTA (256

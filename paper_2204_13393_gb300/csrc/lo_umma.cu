@@ -620,6 +620,10 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
     // buffer.  Its values and the slab exponents it splits them against
     // arrive by cp.async AH steps ahead.
     constexpr int VA = L::VA, VB = L::VB, SLOTS = L::SLOTS, AH = SLOTS - 1;
+    // S <= 16 (one group of block columns): the block's own columns of the A
+    // tile are the B operand's columns, thread for thread (same values, same
+    // exponents), so their split is done once and stored twice
+    constexpr bool SAMEAB = NSPL == 1;
     const int a_l = tid / (16 / VA), a_r0 = (tid % (16 / VA)) * VA;
     const int b_n = tid / (16 / VB), b_r0 = (tid % (16 / VB)) * VB;
     double* xa_slot = reinterpret_cast<double*>(sm + L::SRCA) + tid * SL * VA;
@@ -636,7 +640,7 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
       if (c.valid) {
         const int sl = j % SLOTS;
         const int* hs = a.srcexp_slab + (int64_t)c.slab * 32;
-        const bool asrc = is_asrc(c);
+        const bool asrc = is_asrc(c) && !SAMEAB;
         if (asrc) cp_async4(ea_slot + sl * 128, hs + a_l);
         cp_async4(eb_slot + sl * 128, hs + c.z * NB + b_n);
 #pragma unroll
@@ -696,15 +700,18 @@ __global__ void __launch_bounds__(kUmmaKThreads, 1)
         umma_timeout(ctl, a.flags);
 #pragma unroll
       for (int h = 0; h < SL; ++h) {
-        if (asrc) {
-          const int am = k - cur.col0 + a_l;
-          split_rows_store<VA, ND>(xa_slot + (sl * 128 * SL + h) * VA, ea_slot[sl * 128],
-                                   sm + L::STG + (s * SL + h) * STAGE + (a_r0 >> 3) * (STAGE / 2) +
-                                       (am >> 3) * (ND * 128) + (am & 7) * 16 + (a_r0 & 7) * 2,
-                                   128, a.flags);
+        unsigned char* bdst = sm + L::BBUF + (s * SL + h) * (RB * 32) + b_off;
+        const int am = k - cur.col0 + a_l;
+        unsigned char* adst = sm + L::STG + (s * SL + h) * STAGE + (a_r0 >> 3) * (STAGE / 2) +
+                              (am >> 3) * (ND * 128) + (am & 7) * 16 + (a_r0 & 7) * 2;
+        if (SAMEAB && asrc) {
+          split_rows_store2<VB, ND>(xb_slot + (sl * 128 * SL + h) * VB, eb_slot[sl * 128], bdst, NB * 32, adst, 128,
+                                    a.flags);
+        } else {
+          if (asrc)
+            split_rows_store<VA, ND>(xa_slot + (sl * 128 * SL + h) * VA, ea_slot[sl * 128], adst, 128, a.flags);
+          split_rows_store<VB, ND>(xb_slot + (sl * 128 * SL + h) * VB, eb_slot[sl * 128], bdst, NB * 32, a.flags);
         }
-        split_rows_store<VB, ND>(xb_slot + (sl * 128 * SL + h) * VB, eb_slot[sl * 128],
-                                 sm + L::BBUF + (s * SL + h) * (RB * 32) + b_off, NB * 32, a.flags);
       }
       fence_async_smem();
       __syncwarp();
