@@ -16,7 +16,7 @@ constexpr int kMaxKS = 8192;     // (k + s) * s entries of one Gram tile
 constexpr int kThreads = 256;    // threads of the streaming kernels
 constexpr int kMaxPass = 3;      // local Gram passes (PIP, PIP+, one more)
 constexpr int kMaxTreeIter = 3;  // reduction iterations
-constexpr int kTreeGroup = 64;   // chunks summed per CTA in the tree's first level
+constexpr int kTreeGroup = 16;   // chunks summed per CTA in the tree's first level (more CTAs: float64 adds)
 constexpr int kHHThreads = 256;  // threads of the Householder leaf (one CTA per chunk)
 constexpr int kHHTileBytes = 200 * 1024;  // shared memory for one chunk tile of the Householder leaf
 // Rows of the Householder leaf's sub-tiles when a chunk exceeds one tile: the
