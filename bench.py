@@ -63,14 +63,14 @@ KERNEL_TU = {
 TRAFFIC = {
     # k_oz_coef<8,1,1> + k_umma_update<8,1> (the iterate) + k_umma_gram<8,7> (its Gram), and the
     # pass-3 launches that exit at once; algorithmic 16nK + 8ns
-    ("refine", "fp64_tc"): {"kernel": "tc_step", "src": "9deeef1a4a05d13f",
-                            "dram_bytes": 3781076992 + 92735232, "algorithmic_bytes": 2214592512},
+    ("refine", "fp64_tc"): {"kernel": "tc_step", "src": "16fbce56b5ce6596",
+                            "dram_bytes": 3781129728 + 92645376, "algorithmic_bytes": 2214592512},
     # k_oz_coef<8,2,1> + k_umma_update<8,2>; algorithmic 8nK + 16ns + 8pKs
-    ("update", "fp64_tc"): {"kernel": "tc_step", "src": "9deeef1a4a05d13f",
-                            "dram_bytes": 1952301824 + 122368512, "algorithmic_bytes": 1209008128},
+    ("update", "fp64_tc"): {"kernel": "tc_step", "src": "16fbce56b5ce6596",
+                            "dram_bytes": 1952426752 + 122739456, "algorithmic_bytes": 1209008128},
     # k_umma_srcexp<8> + k_umma_gram<8,7> (pass 1); algorithmic 8nK
-    ("gram", "fp64_tc"): {"kernel": "tc_step", "src": "9deeef1a4a05d13f",
-                          "dram_bytes": 1897120768 + 30483456, "algorithmic_bytes": 1073741824},
+    ("gram", "fp64_tc"): {"kernel": "tc_step", "src": "16fbce56b5ce6596",
+                          "dram_bytes": 1897126912 + 30527488, "algorithmic_bytes": 1073741824},
 }
 
 
