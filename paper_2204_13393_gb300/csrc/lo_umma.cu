@@ -255,10 +255,12 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, 
 // pairs of classes v = t + u <= 5 keep their own exact accumulators (10 pair
 // blocks: digit t = 1..4, u = 1..5 - t); the pairs of each class v = 6, 7, 8
 // share one float32 accumulator.  Such a class sum takes at most 7 x 16
-// roundings of at most 4 units per interval (|sum| < 7 2^24), under 2^9
-// units at a weight of at most 2^-32 of class 2: below 2^-47 of the output's
-// scale (the product scale of its column alignment), inside the error bound
-// of a float64 dot product over the same 256 terms (256 u = 2^-45).  13
+// roundings per interval, each off by less than one unit in the last place
+// (at most 8 units: |sum| < 7 2^24; rounding or truncating accumulation
+// alike), under 2^10 units at a weight of at most 2^-32 of class 2: below
+// 2^-46 of the output's scale (the product scale of its column alignment),
+// inside the error bound of a float64 dot product over the same 256 terms
+// (256 u = 2^-45).  13
 // blocks of 16 columns fit twice in TMEM, so the drain of one interval
 // overlaps the next one's MMAs; 28 separate pair blocks (448 columns) allowed
 // one set only, and the MMAs waited for every drain.
