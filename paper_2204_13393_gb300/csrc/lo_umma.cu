@@ -10,7 +10,7 @@
 // integers.  With prior blocks the Gram and the 8-output assembly give bit
 // for bit the results of the mma.sync kernels; the 16-output assembly sums
 // the pairs of each of the three lowest classes in one float32 accumulator
-// (umma_drain_mc: within the float64 dot-product error bound); the k = 0
+// (umma_drain_mc: an error of the size of a float64 dot product's); the k = 0
 // assembly rounds each output once (lo_recombine.h).
 //
 // GB300 mapping:
@@ -257,10 +257,11 @@ __device__ __forceinline__ void umma_drain(uint32_t tlane, int n0, double* acc, 
 // share one float32 accumulator.  Such a class sum takes at most 7 x 16
 // roundings per interval, each off by less than one unit in the last place
 // (at most 8 units: |sum| < 7 2^24; rounding or truncating accumulation
-// alike), under 2^10 units at a weight of at most 2^-32 of class 2: below
-// 2^-46 of the output's scale (the product scale of its column alignment),
-// inside the error bound of a float64 dot product over the same 256 terms
-// (256 u = 2^-45).  13
+// alike), under 2^10 units at a weight of at most 2^-32 of class 2: an
+// absolute error below 2^-46 of 256 max|q| max|c| (the largest sum an
+// interval can hold, in its column alignment), the size of a float64 dot
+// product's rounding error over 256 terms near the columns' maxima (256 u =
+// 2^-45); tests/test_merged_classes_cpu.py checks it in an exact model.  13
 // blocks of 16 columns fit twice in TMEM, so the drain of one interval
 // overlaps the next one's MMAs; 28 separate pair blocks (448 columns) allowed
 // one set only, and the MMAs waited for every drain.

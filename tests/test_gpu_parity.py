@@ -517,9 +517,9 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
     every step with the reiteration passes included, and the final basis
     against the oracle.  Past the first step the two differ only where the
     tensor-core assembly with 16 outputs per group sums the digit pairs of
-    each of its three lowest classes in one float32 accumulator (error below
-    2^-46 of the column's product scale, inside a float64 dot product's bound)
-    instead of exactly; the ill-conditioned blocks of this test magnify that
+    each of its three lowest classes in one float32 accumulator (an error of
+    the size of a float64 dot product's, test_merged_classes_cpu.py) instead
+    of exactly; the ill-conditioned blocks of this test magnify that
     to about 1e-12.  The mixed form's first pass
     differs on purpose (with planes: the leading digits on the tensor cores;
     without: float32 on the CUDA cores), so there both bases must agree within
