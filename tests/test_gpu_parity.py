@@ -513,7 +513,9 @@ def test_full_size_sampled_rows(precision):
 def test_digit_planes_bitwise(n, s, cr, M, precision):
     """Panels kept as digit planes give the products of re-splitting the
     float64 panels in every pass: bit for bit at the first step (no prior
-    panels) and within the float64 parity tolerance after it, every output of
+    panels) and, at s = 8, for H and R of the second (the Gram and the
+    8-output iterate are exact), within the float64 parity tolerance
+    elsewhere, every output of
     every step with the reiteration passes included, and the final basis
     against the oracle.  Past the first step the two differ only where the
     tensor-core assembly with 16 outputs per group sums the digit pairs of
@@ -539,9 +541,12 @@ def test_digit_planes_bitwise(n, s, cr, M, precision):
         r1 = [host(x) for x in on.orthogonalize(W) if x is not None]
         r2 = [host(x) for x in off.orthogonalize(W) if x is not None]
         Uo, Po, No = ora.orthogonalize(Wh, "pip2", "pip2")
-        for x, y in zip(r1, r2):
-            if bitwise and j == 0:
-                assert np.array_equal(x, y), j
+        for i, (x, y) in enumerate(zip(r1, r2)):
+            # at s = 8 the second step's H and R come from exact digit products
+            # only (the k = 0 panel, the 8-output iterate, the Gram): bit for bit
+            exact_hr = s == 8 and j == 1 and i >= 1
+            if bitwise and (j == 0 or exact_hr):
+                assert np.array_equal(x, y), (j, i)
             elif bitwise:
                 assert close(x, y), (j, errs(x, y))
             else:
